@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark of the fused lattice-Boltzmann step with the wall-link boundary
+schemes (one JSON line on rank 0).
+
+Default workload: 64 batched 2D Hartmann channels (widths U{64..512}, Ha
+U[1,30], wall-to-node fraction q U[0,1), Shercliff c_w log-U[1e-3,1], seed
+2506), FP16 offset storage with FP32 arithmetic, all cases advanced by one
+kernel launch per time step, replayed as CUDA graphs; the FP64 invariant /
+residual reduction runs every 100 steps inside the timed region.
+``--workload pipe`` and ``--workload cd`` time the 3D MHD pipe and the
+flow + concentration channel instead.
+
+``--impl reference`` times the FP64 CPU oracle (the baseline this build is
+checked against) on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline; time-to-steady-state at fixed error"
+CHECK_EVERY = 100
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["hartmann_batch", "pipe", "pipe_fp32", "cd"], default="hartmann_batch")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-iters", type=int, default=5)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- workloads
+def build_workload(name):
+    """Returns dict(cases, geo=[(solid, links)], lattice, prec, physics, infos, desc)."""
+    from paper_2506_00907_gb300 import cases as CS
+    from paper_2506_00907_gb300 import inputs as IN
+    from paper_2506_00907_gb300 import lbm
+    if name == "hartmann_batch":
+        cases, geo, infos = [], [], []
+        for dr in IN.hartmann_batch(64):
+            c, s, l, info = CS.hartmann_channel(dr["W"], dr["Ha"], dr["q"], dr["cw"])
+            cases.append(c)
+            geo.append((s, l))
+            infos.append(info)
+        return dict(cases=cases, geo=geo, infos=infos, lattice=lbm.LBM_D2Q9, prec=lbm.LBM_FP16S,
+                    physics=lbm.LBM_FLOW | lbm.LBM_MHD, planes=19, storage="fp16-offset", dim=2,
+                    desc="64 batched 2D Hartmann channels, W~U{64..512} (W x (W+2) nodes), Ha~U[1,30], "
+                         "q~U[0,1), c_w~logU[1e-3,1], seed 2506; D2Q9 + D2Q5 x 2 (B1, B2)")
+    if name in ("pipe", "pipe_fp32"):
+        dr = IN.pipe_draws(1, Ha=(5.0, 20.0), cw=(0.01, 1.0))[0]
+        c, s, l, info = CS.pipe((32, 128, 128), 62.0, dr["Ha"], ("shercliff", dr["cw"]))
+        prec = lbm.LBM_FP16S if name == "pipe" else lbm.LBM_FP32
+        return dict(cases=[c], geo=[(s, l)], infos=[info], lattice=lbm.LBM_D3Q19, prec=prec,
+                    physics=lbm.LBM_FLOW | lbm.LBM_MHD, planes=40, dim=3,
+                    storage="fp16-offset" if name == "pipe" else "fp32",
+                    desc="3D MHD pipe 32x128x128 (periodic axial), R = 62, Ha=%.2f, Shercliff c_w=%.3g; "
+                         "D3Q19 + D3Q7 x 3" % (dr["Ha"], dr["cw"]))
+    c, s, l, info = CS.reactive_channel(512, 256, 0.25, 0.05, 1e-2)
+    return dict(cases=[c], geo=[(s, l)], infos=[info], lattice=lbm.LBM_D2Q9, prec=lbm.LBM_FP32,
+                physics=lbm.LBM_FLOW | lbm.LBM_CD, planes=14, storage="fp32", dim=2,
+                desc="D2Q9 flow + D2Q5 concentration 512x256, moving top wall U=0.05 with given C, "
+                     "Robin reactive bottom wall k=1e-2, q=0.25")
+
+
+# ----------------------------------------------------------------------------- helpers
+def kernel_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2506_00907_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload):
+    """DRAM bytes per step launch from the committed ncu summary, if it was
+    taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "step_traffic.json")
+    try:
+        rec = json.load(open(p)).get(workload)
+    except Exception:
+        return None
+    if not rec or rec.get("kernel_hash") != kernel_hash():
+        return None
+    return rec.get("bytes_per_launch")
+
+
+def peak_hbm():
+    try:
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device, self.lines, self.proc = device, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=lambda: self.lines.extend(iter(self.proc.stdout.readline, "")),
+                                      daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def oracle_sample(wl, target_nodes):
+    """OracleSim objects for the first cases of the workload up to target_nodes
+    fluid nodes, with links from the oracle's own builder."""
+    import oracle as O
+    from oracle import links as LK
+    sims, nodes = [], 0
+    threads = os.cpu_count() or 1
+    for (c, info) in zip(wl["cases"], wl["infos"]):
+        shape = (c.nx, c.ny, c.nz)
+        dim = wl["dim"]
+        if "W" in info:
+            d = 1.0 - info["q"]
+            walls = LK.channel_y(2, c.nx, c.ny, 1, d, d)
+            p = {(1, s, O.F): dict(kind=O.VELOCITY) for s in (0, 1)}
+            p.update({(1, s, O.G0): dict(kind=O.FLUX, kappa1=info["kappa1"]) for s in (0, 1)})
+            p.update({(1, s, O.G0 + 1): dict(kind=O.GIVEN, phi_wall=info["B0"]) for s in (0, 1)})
+            solid = LK.box_solid(shape, walls)
+            links = LK.box_links(2, shape, walls, p, has_g=True)
+            has_h, has_g = False, True
+        elif "R" in info:
+            wall = info["wall"]
+            g0 = dict(kind=O.GIVEN, phi_wall=0.0) if wall == "insulating" else \
+                dict(kind=O.FLUX) if wall == "conducting" else dict(kind=O.FLUX, kappa1=-info["eta"] / (wall[1] * info["R"]))
+            params = {O.F: dict(kind=O.VELOCITY), O.G0: g0, O.G0 + 1: dict(kind=O.GIVEN, phi_wall=info["B0"]),
+                      O.G0 + 2: dict(kind=O.GIVEN, phi_wall=0.0)}
+            solid = LK.pipe_solid(shape, info["R"])
+            links, _ = LK.pipe_links(shape, info["R"], params)
+            has_h, has_g = False, True
+        else:
+            d = 1.0 - info["q"]
+            walls = LK.channel_y(2, c.nx, c.ny, 1, d, d)
+            p = {(1, 0, O.F): dict(kind=O.VELOCITY), (1, 1, O.F): dict(kind=O.VELOCITY, u_wall=(info["U"], 0, 0)),
+                 (1, 0, O.H): dict(kind=O.FLUX, kappa0=info["k"], kappa1=-info["k"]),
+                 (1, 1, O.H): dict(kind=O.GIVEN, phi_wall=2.0, u_wall=(info["U"], 0, 0))}
+            solid = LK.box_solid(shape, walls)
+            links = LK.box_links(2, shape, walls, p, has_h=True)
+            has_h, has_g = True, False
+        s = O.OracleSim(dim, shape, solid, c.tau_nu, c.tau_D, c.tau_eta, tuple(c.accel), has_h, has_g, threads)
+        s.set_links(links)
+        s.init(rho0=c.rho0, C0=c.C0, B0=tuple(c.B0))
+        sims.append((s, int(np.sum(np.asarray(solid) == 0))))
+        nodes += sims[-1][1]
+        if nodes >= target_nodes:
+            break
+    return sims, nodes, threads
+
+
+def time_oracle(sims, budget_s=12.0, max_steps=None):
+    """Steps the sample until the budget is used; returns (MLUPS, steps)."""
+    for s, _ in sims:
+        s.step(1)                       # warm
+    nodes = sum(n for _, n in sims)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        for s, _ in sims:
+            s.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or (max_steps and steps >= max_steps):
+            break
+    return nodes * steps / el / 1e6, steps, el
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    wl = build_workload(args.workload)
+    sims, nodes, threads = oracle_sample(wl, 2.0e5)
+    for _ in range(args.warmup):
+        for s, _ in sims:
+            s.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for s, _ in sims:
+            s.step(1)
+    el = time.perf_counter() - t0
+    mlups = nodes * args.steps / el / 1e6
+    sample = "first %d cases of the workload (%d fluid nodes), FP64 oracle, one time step per bench step" % (
+        len(sims), nodes)
+    line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl["desc"], "sample": sample},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2506_00907_gb300 import build as B
+    from paper_2506_00907_gb300 import lbm
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    wl = build_workload(args.workload)
+    stream = torch.cuda.current_stream()
+    sol = lbm.Solver(wl["lattice"], wl["prec"], wl["physics"], wl["cases"], stream=stream.cuda_stream, device=local)
+    for i, (s, l) in enumerate(wl["geo"]):
+        sol.set_walls(i, s, l)
+    fluid = sum(int(np.sum(np.asarray(s) == 0)) for s, _ in wl["geo"])
+    tune = None
+    if not args.no_autotune:
+        cache = os.path.join(ROOT, "paper_2506_00907_gb300", "_build", "autotune.txt")
+        tune = sol.autotune(cache, iters=20)
+    sol.set_graph(CHECK_EVERY)
+    K = max(CHECK_EVERY, (args.steps // CHECK_EVERY) * CHECK_EVERY)
+    W = max(3, args.warmup)
+
+    def run(nsteps):
+        done = 0
+        while done < nsteps:
+            k = min(CHECK_EVERY, nsteps - done)
+            sol.step(k)
+            done += k
+            if done % CHECK_EVERY == 0:
+                sol.check(raise_unstable=False)
+    run(W)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    run(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    ms_step = ms / K
+    value = world * fluid * K / (ms * 1e-3) / 1e6
+    launches = K * lbm.lbm_launches_per_step(sol.ctx) + 2 * (K // CHECK_EVERY)
+    elem = {lbm.LBM_FP64: 8, lbm.LBM_FP32: 4}.get(wl["prec"], 2)
+    alg_bytes = 2.0 * wl["planes"] * elem * fluid                # one read + one write per population
+    peak, peak_kind = peak_hbm()
+    achieved = alg_bytes / (ms_step * 1e-3) / 1e9
+    out = sol.check(raise_unstable=False)
+    stable = bool(np.all(out[:, 5] == 0))
+
+    # end to end through the C ABI: pinned host state in, 100 steps, reductions out
+    blob_np = sol.get_state()
+    pinned = torch.empty(blob_np.size, dtype=torch.uint8, pin_memory=True)
+    pinned.numpy()[:] = blob_np
+    red = np.zeros(8 * len(wl["cases"]))
+    L = lbm.lib()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_iters):
+        L.lbm_set_state(sol.ctx, pinned.data_ptr(), blob_np.size)
+        sol.step(CHECK_EVERY)
+        L.lbm_check(sol.ctx, red.ctypes.data_as(lbm.ctypes.POINTER(lbm.ctypes.c_double)))
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * fluid * CHECK_EVERY * args.e2e_iters / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": int(blob_np.size) / CHECK_EVERY, "d2h_bytes_per_step": red.nbytes / CHECK_EVERY,
+           "step": "host->device state copy from pinned memory, %d time steps, FP64 reductions read back; "
+                   "bytes are per time step" % CHECK_EVERY}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sims, nodes, threads = oracle_sample(wl, 1.5e6)
+        mlups, steps, el = time_oracle(sims, budget_s=12.0)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+               "sample": "FP64 oracle on the first %d cases (%d fluid nodes), %d steps in %.1f s" % (
+                   len(sims), nodes, steps, el)}
+    if rank == 0:
+        traffic = measured_traffic(args.workload)
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl["desc"], "storage": wl["storage"], "cases": len(wl["cases"]),
+                           "fluid_nodes": fluid, "launch": {"block": tune[0], "blocks_per_sm": tune[1]} if tune else None,
+                           "graph_steps": CHECK_EVERY, "reduction_every": CHECK_EVERY,
+                           "l2": "state %.0f MB > 129 MB L2, no flush" % (2 * wl["planes"] * elem * fluid / 1e6),
+                           "stable": stable},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": traffic,
+                             "peak_kind": peak_kind,
+                             "bytes_per_launch": alg_bytes,
+                             "kernel": "k_step (fused step + wall links), one launch per time step"},
+                "e2e": e2e, "gpu_launches": launches, "clocks": clk}
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    sol.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,261 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) lattice-Boltzmann solver with the
+ * moment-conserving wall-link boundary schemes of Li, Chan, Feng & Wang,
+ * "Lattice Boltzmann Boundary Conditions for Flow, Convection-Diffusion and
+ * MHD Simulations" (arXiv 2506.00907).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Lattice units: dx = dt = 1, c = 1, mu = 1.  Flow on D2Q9 / D3Q19 with
+ *   c_s^2 = 1/3; concentration C and the vector magnetic field B on D2Q5 /
+ *   D3Q7 with c_h^2 = c_g^2 = 1/4 (weights 1/2, 1/8 in 2D and 1/4, 1/8 in 3D).
+ * - Direction numbering (used by lbm_link.dir):
+ *     D2Q9 : 0 rest, 1 +x, 2 +y, 3 -x, 4 -y, 5 (+x+y), 6 (-x+y), 7 (-x-y), 8 (+x-y)
+ *     D2Q5 : 0 rest, 1 +x, 2 +y, 3 -x, 4 -y
+ *     D3Q19: 0 rest, 1 +x, 2 -x, 3 +y, 4 -y, 5 +z, 6 -z, 7 (+x+y), 8 (-x-y),
+ *            9 (+x-y), 10 (-x+y), 11 (+x+z), 12 (-x-z), 13 (+x-z), 14 (-x+z),
+ *            15 (+y+z), 16 (-y-z), 17 (+y-z), 18 (-y+z)
+ *     D3Q7 : 0 rest, 1 +x, 2 -x, 3 +y, 4 -y, 5 +z, 6 -z
+ * - Node index n = x + nx*(y + ny*z).  Every axis wraps periodically; a wall is
+ *   a layer of solid nodes plus one wall link for every population that would
+ *   stream from a solid node into a fluid node.
+ * - Body force: Guo forcing with F = rho * accel (the paper, Sec. 2.4, only
+ *   says the right-hand side of Eq. 1 "can be modified").  Lorentz force:
+ *   magnetic stress 1/2|B|^2 I - BB in the second moment of f^eq (Sec. 2.3).
+ * - Host arrays passed in are copied; the caller keeps ownership of every
+ *   pointer it passes.  No call throws or aborts; every call returns an
+ *   lbm_status and lbm_last_error() gives a message for the last failure.
+ * - Device work is issued on the context's stream and is asynchronous unless
+ *   the entry point says it synchronises.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,     /* bad argument: sizes, tau <= 1/2, bad or incomplete link list */
+    LBM_ENOMEM = 2,     /* device or pinned host allocation failed */
+    LBM_ECUDA = 3,      /* a CUDA runtime call failed (message in lbm_last_error) */
+    LBM_EUNSTABLE = 4,  /* a non-finite population was found by a check */
+    LBM_ETIMEOUT = 5,   /* a bounded device wait gave up */
+    LBM_ESTATE = 6      /* call out of order (e.g. stepping a case without walls) */
+} lbm_status;
+
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
+
+/* Storage precision of the populations.  FP64 and FP32 store p; FP16S and
+ * BF16S store the offset p - w_a * phi_ref in 16 bits and compute in FP32. */
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16S = 2, LBM_BF16S = 3 } lbm_prec;
+
+/* physics mask: LBM_FLOW is required */
+enum { LBM_FLOW = 1, LBM_CD = 2, LBM_MHD = 4 };
+
+/* One case (one domain).  tau_* > 1/2 (nu = (tau_nu - 1/2)/3, D = (tau_D - 1/2)/4,
+ * eta = (tau_eta - 1/2)/4: Eq. 1, 3, 5).  rho0, C0, B0 are the default initial
+ * state (rest at equilibrium; the paper initialises with u = 0, Sec. 5.2) and
+ * the references of the 16-bit offset storage. */
+typedef struct {
+    int32_t nx, ny, nz;            /* nz = 1 for D2Q9; each >= 1 */
+    double tau_nu, tau_D, tau_eta;
+    double accel[3];               /* body force per unit mass */
+    double rho0, C0, B0[3];
+} lbm_case;
+
+typedef struct {
+    lbm_lattice lattice;
+    lbm_prec prec;
+    uint32_t physics;              /* LBM_FLOW | optional LBM_CD | optional LBM_MHD */
+    int32_t ncases;                /* >= 1; all cases are advanced by one launch per step */
+    const lbm_case *cases;         /* ncases entries, copied */
+    void *stream;                  /* cudaStream_t; NULL = legacy default stream */
+    int32_t device;                /* CUDA device ordinal */
+} lbm_config;
+
+/* Wall-link kinds (Sec. 3-4).  Fields: 0 = f (flow), 1 = h (C), 2 + k = g_k (B_k). */
+typedef enum {
+    LBM_W_VELOCITY = 0,    /* field f.  Given wall velocity u_wall: Eq. 15 with Eq. 16 for d < 1/2,
+                              Eq. 43 for d >= 1/2 (static walls: Bouzidi, Eq. 11/12) */
+    LBM_W_GIVEN = 1,       /* h or g_k.  Given C or B_k = phi_wall: Eq. 19/20 (C), Eq. 34/35 (B_k) */
+    LBM_W_FLUX = 2,        /* h or g_k.  Flux -lambda dphi/dn = F(phi) = k0 + k1 phi (per link and
+                              step, Eq. 23, 48) with the moving-wall correction Eq. 24,
+                              imposed by the M scheme, Eq. 25-27 (Robin, Shercliff Eq. 30,
+                              zero gradient with k0 = k1 = 0) */
+    LBM_W_NEUMANN_BFL = 3  /* h or g_k.  Zero gradient by interpolated bounce-back, Eq. 21/22 */
+} lbm_wall_kind;
+
+/* One wall link: the unknown population of direction dir (pointing from the
+ * wall into the fluid) at fluid node A = node, whose neighbour A - e_dir is
+ * solid.  d = |AX| / |EA| in (0, 1] is the fraction of the link between A and
+ * the wall point X (Eq. 13).  64 bytes. */
+typedef struct {
+    uint32_t node;
+    uint8_t field;                 /* 0 f, 1 h, 2 + k g_k */
+    uint8_t dir;
+    uint8_t kind;                  /* lbm_wall_kind */
+    uint8_t reserved;
+    double d;
+    double u_wall[3];              /* wall velocity (never extrapolated) */
+    double phi_wall;               /* LBM_W_GIVEN: C or B_k on the wall */
+    double k0, k1;                 /* LBM_W_FLUX: increment k0 + k1 * phi_X per step */
+} lbm_link;
+
+/* Create a context: validates the configuration, allocates all device memory
+ * for every case (two population buffers, node flags, tile list, reduction
+ * scratch) and initialises every case at rest (equilibrium of rho0, C0, B0).
+ * Errors: LBM_EINVAL (bad config), LBM_ENOMEM, LBM_ECUDA.  *out is NULL on error. */
+lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out);
+
+/* Free all device and host memory of the context.  NULL is a no-op. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Message of the last failing call on this context ("" if none). */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Geometry and wall links of one case (Sec. 4, 6).
+ * solid: host, nx*ny*nz bytes, nonzero = solid.  links: host, nlinks records.
+ * The list must hold exactly one link per (fluid node, field, direction) whose
+ * upstream neighbour is solid, for every field the physics mask enables.
+ * Links whose second fluid node E = A + e_dir is solid are evaluated at
+ * d = 1/2 with phi(E) = phi(A) (the paper is silent; this needs no E).
+ * Re-initialises the case at rest.  Synchronises.
+ * Errors: LBM_EINVAL (range, kind/field mismatch, d outside (0,1], A solid,
+ * A - e_dir fluid, duplicate, missing link), LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_set_walls(lbm_ctx *ctx, int32_t case_id, const uint8_t *solid,
+                         const lbm_link *links, size_t nlinks);
+
+/* Initial state of one case: populations at equilibrium (Eq. 2, 4, 6) of the
+ * given host fields, N = nx*ny*nz entries each, u and B as [N][3]; any
+ * pointer may be NULL (then rho0, 0, C0, B0).  Resets the step counter of the
+ * context's residual history.  Synchronises.  Errors: LBM_EINVAL, LBM_ECUDA. */
+lbm_status lbm_init_equilibrium(lbm_ctx *ctx, int32_t case_id, const double *rho,
+                                const double *u, const double *C, const double *B);
+
+/* Same, from DEVICE fields in FP32 (u and B as [N][3], rho/C may be NULL):
+ * the warm-start path.  Asynchronous on the context stream. */
+lbm_status lbm_init_equilibrium_device(lbm_ctx *ctx, int32_t case_id, const float *rho,
+                                       const float *u, const float *C, const float *B);
+
+/* Advance every case by nsteps time steps (Eq. 1, 3, 5 with all wall links).
+ * One fused kernel launch per step covers all cases; with graphs enabled
+ * (lbm_set_graph) whole blocks of steps replay as one CUDA graph.
+ * Asynchronous.  Errors: LBM_EINVAL (nsteps < 0), LBM_ESTATE (walls missing),
+ * LBM_ECUDA. */
+lbm_status lbm_step(lbm_ctx *ctx, int32_t nsteps);
+
+/* Capture blocks of `steps_per_graph` steps (even, >= 2; 0 disables) as a CUDA
+ * graph that lbm_step replays.  Errors: LBM_EINVAL, LBM_ECUDA. */
+lbm_status lbm_set_graph(lbm_ctx *ctx, int32_t steps_per_graph);
+
+/* Macroscopic fields of one case at the current time, FP64, host arrays of N
+ * (rho, C) or 3N (u, B) entries; NULL skips.  Solid nodes report 0.
+ * Synchronises.  Errors: LBM_EINVAL, LBM_ECUDA. */
+lbm_status lbm_moments(lbm_ctx *ctx, int32_t case_id, double *rho, double *u,
+                       double *C, double *B);
+
+/* FP64 reductions over the fluid nodes of every case (invariants and the
+ * steady-state test; the paper states no convergence criterion):
+ * out[8*c + 0..7] = { sum rho, sum C, sum B_x, sum B_y, sum B_z,
+ *                     number of non-finite populations,
+ *                     sum |phi - phi_prev|^2, sum |phi|^2 }
+ * with phi = (u, C, B - B0) (the parts the physics mask enables) and phi_prev
+ * the value at the previous call (the first call compares with zero).  The
+ * reduction is deterministic (fixed order).  out: host, 8*ncases doubles.
+ * Synchronises.  Returns LBM_EUNSTABLE (after filling out) if any population
+ * is not finite.  Errors: LBM_ECUDA. */
+lbm_status lbm_check(lbm_ctx *ctx, double *out);
+
+/* Step until every case's relative residual sqrt(sum|phi-phi_prev|^2 / sum|phi|^2)
+ * over `interval` steps is below tol, or max_steps are done.  *steps_done and
+ * *residual (largest over cases) may be NULL.  Errors: LBM_EUNSTABLE, LBM_ECUDA. */
+lbm_status lbm_run_to_steady(lbm_ctx *ctx, int64_t max_steps, int32_t interval, double tol,
+                             int64_t *steps_done, double *residual);
+
+/* Checkpoint: size in bytes of the state blob, and copy it out / in (host
+ * memory, synchronises).  The blob holds every population of every case and
+ * the step count; restoring it and stepping is bitwise identical to not
+ * having stopped.  Errors: LBM_EINVAL (size mismatch), LBM_ECUDA. */
+size_t lbm_state_bytes(const lbm_ctx *ctx);
+lbm_status lbm_get_state(lbm_ctx *ctx, void *host, size_t bytes);
+lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes);
+
+/* Number of steps taken since creation (or the restored state). */
+int64_t lbm_steps_done(const lbm_ctx *ctx);
+
+/* Launch shape of the fused step: threads per block (64..1024, multiple of 32)
+ * and blocks per SM for the persistent tile loop (0 = one block per tile).
+ * Errors: LBM_EINVAL. */
+lbm_status lbm_set_launch(lbm_ctx *ctx, int32_t block, int32_t blocks_per_sm);
+
+/* Autotuner: times the fused step for every candidate launch shape on this
+ * context (each candidate `iters` steps after one warm-up, CUDA events),
+ * keeps the fastest, and records it in the text cache file `cache_path`
+ * (NULL = no cache) keyed by GPU name, lattice, precision, physics and case
+ * sizes; a later call with the same key reads the cache instead of timing.
+ * The context's populations are saved and restored around the timing.
+ * best_ms (may be NULL) receives the time per step of the choice.
+ * Errors: LBM_ECUDA. */
+lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters,
+                        int32_t *block, int32_t *blocks_per_sm, double *best_ms);
+
+/* Kernel launches issued per lbm_step step (for launch accounting). */
+int32_t lbm_launches_per_step(const lbm_ctx *ctx);
+
+/* Device storage of the current populations (for zero-copy inspection):
+ * base pointer, bytes per population, plane stride in elements and element
+ * offset of case_id's first plane.  Errors: LBM_EINVAL. */
+lbm_status lbm_device_state(lbm_ctx *ctx, int32_t case_id, void **base, int32_t *elem_bytes,
+                            int64_t *plane_stride, int64_t *case_offset, int32_t *planes);
+
+/* ------------------------------------------------------------------------
+ * Wall-link builders (host only; no context and no GPU needed).
+ * ------------------------------------------------------------------------ */
+
+/* Boundary condition of one field on one wall.  Field f takes LBM_W_VELOCITY;
+ * h and g_k take the other kinds.  The flux of LBM_W_FLUX is the physical
+ * F(phi) = kappa0 + kappa1 * phi per unit wall area and time (Eq. 17, 30), in
+ * lattice units; the builder converts it to the per-link increment
+ * k0 + k1 * phi_X (Eq. 23 for flat walls; Eq. 48 with the surface segments for
+ * the pipe). */
+typedef struct {
+    int32_t kind;
+    double u_wall[3];
+    double phi_wall;
+    double kappa0, kappa1;
+} lbm_wall_bc;
+
+/* Channel with two flat walls normal to `axis` (0 = x, 1 = y, 2 = z): solid
+ * layers at index 0 and n_axis - 1, walls at 1 - d_lo and n_axis - 2 + d_hi
+ * (d = |AX| / dx of Eq. 13, the same for axis and diagonal links, Sec. 4.1);
+ * the other axes are periodic.  bc[side * 5 + field] for side 0 (low) / 1
+ * (high) and field 0 f, 1 h, 2 + k g_k; only fields enabled by `physics` are
+ * read.  solid: host output, nx*ny*nz bytes.  links: host output of capacity
+ * `cap` records (NULL with cap = 0 to query the count).  *nlinks receives the
+ * number of links.  Errors: LBM_EINVAL (sizes, d outside (0, 1], capacity). */
+lbm_status lbm_build_channel(int32_t dim, int32_t nx, int32_t ny, int32_t nz, int32_t axis, double d_lo,
+                             double d_hi, uint32_t physics, const lbm_wall_bc *bc, uint8_t *solid,
+                             lbm_link *links, size_t cap, size_t *nlinks);
+
+/* Circular pipe along x (Sec. 6): fluid where (y - cy)^2 + (z - cz)^2 < R^2
+ * with cy = (ny - 1)/2, cz = (nz - 1)/2.  d per node and direction from the
+ * intersection of the link with the circle (Fig. 9a).  Flux coefficients are
+ * spread over the outer-layer solid points with S_i = (theta_{i+1} -
+ * theta_{i-1}) R dx / 2 (azimuth-sorted per axial slice) and split over each
+ * point's D3Q7 links by e_a.n / sum e_g.n for e.n > 0 (Eq. 48).  bc[field]
+ * for the 5 fields.  Other arguments as lbm_build_channel. */
+lbm_status lbm_build_pipe(int32_t nx, int32_t ny, int32_t nz, double R, uint32_t physics, const lbm_wall_bc *bc,
+                          uint8_t *solid, lbm_link *links, size_t cap, size_t *nlinks);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

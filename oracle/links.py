@@ -51,12 +51,17 @@ def box_solid(shape, walls):
     return (~fluid).astype(np.uint8)
 
 
-def _link_record(node, field, a, kind, d, u_wall=(0, 0, 0), phi_wall=0.0, k0=0.0, k1=0.0):
-    r = np.zeros(1, LINK_DTYPE)
-    r["node"], r["field"], r["dir"], r["kind"], r["d"] = node, field, a, kind, d
-    r["u_wall"] = u_wall
+def _records(nodes, field, a, kind, d, u_wall, phi_wall, k0, k1):
+    r = np.zeros(len(nodes), LINK_DTYPE)
+    r["node"], r["field"], r["dir"], r["kind"], r["d"] = nodes, field, a, kind, d
+    r["u_wall"] = np.broadcast_to(np.asarray(u_wall, dtype=np.float64), (len(nodes), 3)) if len(nodes) else 0
     r["phi_wall"], r["k0"], r["k1"] = phi_wall, k0, k1
     return r
+
+
+def _upstream_solid(solid3, e):
+    """mask over nodes A of solid[A - e] (periodic)."""
+    return np.roll(solid3, shift=(e[2], e[1], e[0]), axis=(0, 1, 2))
 
 
 def box_links(dim, shape, walls, params, has_h=False, has_g=False):
@@ -65,42 +70,47 @@ def box_links(dim, shape, walls, params, has_h=False, has_g=False):
     walls:  axis -> (lo, hi) wall coordinates (see ``box_solid``).
     params: (axis, side, field) -> dict(kind, u_wall, phi_wall, kappa0, kappa1)
             with side 0 = lo wall, 1 = hi wall.
-    Ties at corners (two walls crossed at the same distance) go to the wall
+    d is the distance along the link to the first wall plane it crosses
+    (s in (0, 1] with A - s e_a on the plane); ties at corners go to the wall
     listed first in ``walls`` (lo before hi).
     """
     nx, ny, nz = shape
-    solid = box_solid(shape, walls).reshape(-1)
-    recs = []
+    solid3 = box_solid(shape, walls)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    coords = (x.ravel(), y.ravel(), z.ravel())
+    out = []
     for field in _fields(dim, has_h, has_g):
         e, _ = lattice(dim, scalar=(field != F))
-        for n in np.flatnonzero(solid == 0):
-            x, y, z = n % nx, (n // nx) % ny, n // (nx * ny)
-            A = (x, y, z)
-            for a in range(1, len(e)):
-                bx, by, bz = _wrap(x - e[a][0], nx), _wrap(y - e[a][1], ny), _wrap(z - e[a][2], nz)
-                if not solid[bx + nx * (by + ny * bz)]:
+        for a in range(1, len(e)):
+            mask = (solid3 == 0) & (_upstream_solid(solid3, e[a]) == 1)
+            nodes = np.flatnonzero(mask.ravel())
+            if nodes.size == 0:
+                continue
+            best = np.full(nodes.size, np.inf)
+            which = np.full(nodes.size, -1)
+            cands = []
+            for ax, (lo, hi) in walls.items():
+                if e[a][ax] == 0:
                     continue
-                # first wall crossed by the ray A - s e_a, s in (0, 1]
-                best = None
-                for ax, (lo, hi) in walls.items():
-                    if e[a][ax] == 0:
-                        continue
-                    for side, pos in ((0, lo), (1, hi)):
-                        s = (A[ax] - pos) / e[a][ax]
-                        if 0.0 < s <= 1.0 + 1e-12 and (best is None or s < best[0] - 1e-12):
-                            best = (min(s, 1.0), ax, side)
-                if best is None:
-                    raise ValueError("no wall between fluid node %s and solid node" % (A,))
-                d, ax, side = best
+                for side, pos in ((0, lo), (1, hi)):
+                    cands.append((ax, side, pos))
+            for ci, (ax, side, pos) in enumerate(cands):
+                s = (coords[ax][nodes] - pos) / e[a][ax]
+                ok = (s > 0.0) & (s <= 1.0 + 1e-12) & (s < best - 1e-12)
+                best = np.where(ok, np.minimum(s, 1.0), best)
+                which = np.where(ok, ci, which)
+            if np.any(which < 0):
+                raise ValueError("a fluid node next to a solid node has no wall between them")
+            for ci, (ax, side, pos) in enumerate(cands):
+                sel = which == ci
+                if not np.any(sel):
+                    continue
                 p = params[(ax, side, field)]
-                kind = p["kind"]
-                k0 = p.get("kappa0", 0.0)
-                k1 = p.get("kappa1", 0.0)
-                recs.append(_link_record(n, field, a, kind, d, p.get("u_wall", (0, 0, 0)),
-                                         p.get("phi_wall", 0.0), k0, k1))
-    if not recs:
+                out.append(_records(nodes[sel], field, a, p["kind"], best[sel], p.get("u_wall", (0, 0, 0)),
+                                    p.get("phi_wall", 0.0), p.get("kappa0", 0.0), p.get("kappa1", 0.0)))
+    if not out:
         return np.zeros(0, LINK_DTYPE)
-    return np.concatenate(recs)
+    return np.concatenate(out)
 
 
 def channel_y(dim, nx, ny, nz, d_lo, d_hi):
@@ -126,7 +136,7 @@ def ray_circle_d(ay, az, ey, ez, R):
     ee = ey * ey + ez * ez
     ae = ay * ey + az * ez
     disc = ae * ae + ee * (R * R - (ay * ay + az * az))
-    return (ae + math.sqrt(disc)) / ee
+    return (ae + np.sqrt(disc)) / ee
 
 
 def pipe_segments(shape, R, center=None):
@@ -136,31 +146,28 @@ def pipe_segments(shape, R, center=None):
     Returns dict node -> (S_i, n_i[3])."""
     nx, ny, nz = shape
     cy, cz = center if center is not None else ((ny - 1) / 2.0, (nz - 1) / 2.0)
-    solid = pipe_solid(shape, R, center).reshape(-1)
+    solid3 = pipe_solid(shape, R, center)
     e7, _ = lattice(3, scalar=True)
+    touches = np.zeros_like(solid3, dtype=bool)
+    for g in range(1, 7):
+        # neighbour B + e_g is fluid
+        touches |= np.roll(solid3, shift=(-e7[g][2], -e7[g][1], -e7[g][0]), axis=(0, 1, 2)) == 0
+    outer = (solid3 == 1) & touches
     out = {}
     for x in range(nx):
-        pts = []
-        for z in range(nz):
-            for y in range(ny):
-                n = x + nx * (y + ny * z)
-                if not solid[n]:
-                    continue
-                touches = False
-                for g in range(1, 7):
-                    A = _wrap(x + e7[g][0], nx) + nx * (_wrap(y + e7[g][1], ny) + ny * _wrap(z + e7[g][2], nz))
-                    if not solid[A]:
-                        touches = True
-                if touches:
-                    pts.append((math.atan2(z - cz, y - cy), n, y - cy, z - cz))
-        pts.sort()
-        m = len(pts)
-        for i, (th, n, by, bz) in enumerate(pts):
-            th_next = pts[(i + 1) % m][0] + (2 * math.pi if i + 1 == m else 0.0)
-            th_prev = pts[(i - 1) % m][0] - (2 * math.pi if i == 0 else 0.0)
-            S = (th_next - th_prev) * R / 2.0
-            r = math.hypot(by, bz)
-            out[n] = (S, np.array([0.0, -by / r, -bz / r]))
+        zz, yy = np.nonzero(outer[:, :, x])
+        nodes = x + nx * (yy + ny * zz)
+        th = np.arctan2(zz - cz, yy - cy)
+        order = np.lexsort((nodes, th))
+        th, nodes, yy, zz = th[order], nodes[order], yy[order], zz[order]
+        th_next = np.roll(th, -1)
+        th_next[-1] += 2 * np.pi
+        th_prev = np.roll(th, 1)
+        th_prev[0] -= 2 * np.pi
+        S = (th_next - th_prev) * R / 2.0
+        r = np.hypot(yy - cy, zz - cz)
+        for i in range(len(nodes)):
+            out[int(nodes[i])] = (float(S[i]), np.array([0.0, -(yy[i] - cy) / r[i], -(zz[i] - cz) / r[i]]))
     return out
 
 
@@ -173,41 +180,46 @@ def pipe_links(shape, R, params, has_g=True, center=None):
     """
     nx, ny, nz = shape
     cy, cz = center if center is not None else ((ny - 1) / 2.0, (nz - 1) / 2.0)
-    solid = pipe_solid(shape, R, center).reshape(-1)
+    solid3 = pipe_solid(shape, R, center)
+    solid = solid3.reshape(-1)
     segs = pipe_segments(shape, R, center)
-    recs = []
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    x, y, z = x.ravel(), y.ravel(), z.ravel()
+    out = []
     e_solid = 0
+    e7, _ = lattice(3, scalar=True)
     for field in _fields(3, False, has_g):
         e, _ = lattice(3, scalar=(field != F))
         p = params[field]
-        for n in np.flatnonzero(solid == 0):
-            x, y, z = n % nx, (n // nx) % ny, n // (nx * ny)
-            for a in range(1, len(e)):
-                bx, by, bz = _wrap(x - e[a][0], nx), _wrap(y - e[a][1], ny), _wrap(z - e[a][2], nz)
+        for a in range(1, len(e)):
+            mask = ((solid3 == 0) & (_upstream_solid(solid3, e[a]) == 1)).ravel()
+            nodes = np.flatnonzero(mask)
+            if nodes.size == 0:
+                continue
+            d = ray_circle_d(y[nodes] - cy, z[nodes] - cz, e[a][1], e[a][2], R)
+            d = np.minimum(np.maximum(d, 1e-12), 1.0)
+            En = (x[nodes] + e[a][0]) % nx + nx * (((y[nodes] + e[a][1]) % ny) + ny * ((z[nodes] + e[a][2]) % nz))
+            e_solid += int(np.sum(solid[En]))
+            k0 = np.zeros(nodes.size)
+            k1 = np.zeros(nodes.size)
+            if p["kind"] == FLUX:
+                bx, by, bz = (x[nodes] - e[a][0]) % nx, (y[nodes] - e[a][1]) % ny, (z[nodes] - e[a][2]) % nz
                 Bn = bx + nx * (by + ny * bz)
-                if not solid[Bn]:
-                    continue
-                d = ray_circle_d(y - cy, z - cz, e[a][1], e[a][2], R)
-                d = min(max(d, 1e-12), 1.0)
-                En = _wrap(x + e[a][0], nx) + nx * (_wrap(y + e[a][1], ny) + ny * _wrap(z + e[a][2], nz))
-                if solid[En]:
-                    e_solid += 1
-                k0 = k1 = 0.0
-                if p["kind"] == FLUX:
-                    S, nB = segs[Bn]
-                    proj = [float(np.dot(e[g], nB)) for g in range(1, len(e))]
+                for i in range(nodes.size):
+                    S, nB = segs[int(Bn[i])]
                     tot = 0.0
-                    for g in range(1, len(e)):
-                        Ag = _wrap(bx + e[g][0], nx) + nx * (_wrap(by + e[g][1], ny) + ny * _wrap(bz + e[g][2], nz))
-                        if not solid[Ag] and proj[g - 1] > 0:
-                            tot += proj[g - 1]
+                    for g in range(1, 7):
+                        pg = float(np.dot(e7[g], nB))
+                        Ag = (bx[i] + e7[g][0]) % nx + nx * (((by[i] + e7[g][1]) % ny) + ny * ((bz[i] + e7[g][2]) % nz))
+                        if pg > 0 and not solid[Ag]:
+                            tot += pg
                     ea_n = float(np.dot(e[a], nB))
                     w = ea_n / tot if ea_n > 0 else 0.0
-                    k0 = p.get("kappa0", 0.0) * S * w
-                    k1 = p.get("kappa1", 0.0) * S * w
-                recs.append(_link_record(n, field, a, p["kind"], d, p.get("u_wall", (0, 0, 0)),
-                                         p.get("phi_wall", 0.0), k0, k1))
-    return np.concatenate(recs), {"segments": segs, "e_solid_links": e_solid}
+                    k0[i] = p.get("kappa0", 0.0) * S * w
+                    k1[i] = p.get("kappa1", 0.0) * S * w
+            out.append(_records(nodes, field, a, p["kind"], d, p.get("u_wall", (0, 0, 0)),
+                                p.get("phi_wall", 0.0), k0, k1))
+    return np.concatenate(out), {"segments": segs, "e_solid_links": e_solid}
 
 
 # ---------------------------------------------------------------------------
@@ -218,24 +230,28 @@ def random_links(dim, shape, solid, rng, has_h=False, has_g=False, kinds=None):
     drawn from ``rng`` (numpy Generator).  d in (0, 1]; both branches of every
     scheme occur."""
     nx, ny, nz = shape
-    solid = np.asarray(solid, dtype=np.uint8).reshape(-1)
-    recs = []
+    solid3 = np.asarray(solid, dtype=np.uint8).reshape(nz, ny, nx)
+    out = []
     for field in _fields(dim, has_h, has_g):
         e, _ = lattice(dim, scalar=(field != F))
-        allowed = [VELOCITY] if field == F else (kinds or [GIVEN, FLUX, NEUMANN_BFL])
-        for n in np.flatnonzero(solid == 0):
-            x, y, z = n % nx, (n // nx) % ny, n // (nx * ny)
-            for a in range(1, len(e)):
-                bx, by, bz = _wrap(x - e[a][0], nx), _wrap(y - e[a][1], ny), _wrap(z - e[a][2], nz)
-                if not solid[bx + nx * (by + ny * bz)]:
-                    continue
-                kind = allowed[rng.integers(len(allowed))]
-                d = 1.0 - rng.random()            # (0, 1]
-                uw = rng.uniform(-0.02, 0.02, 3)
-                if dim == 2:
-                    uw[2] = 0.0
-                recs.append(_link_record(n, field, a, kind, d, uw, rng.uniform(-0.5, 1.5),
-                                         rng.uniform(-0.01, 0.01), rng.uniform(-0.05, 0.0)))
-    if not recs:
+        allowed = np.array([VELOCITY] if field == F else (kinds or [GIVEN, FLUX, NEUMANN_BFL]))
+        for a in range(1, len(e)):
+            nodes = np.flatnonzero(((solid3 == 0) & (_upstream_solid(solid3, e[a]) == 1)).ravel())
+            m = nodes.size
+            if m == 0:
+                continue
+            r = np.zeros(m, LINK_DTYPE)
+            r["node"], r["field"], r["dir"] = nodes, field, a
+            r["kind"] = allowed[rng.integers(len(allowed), size=m)]
+            r["d"] = 1.0 - rng.random(m)
+            uw = rng.uniform(-0.02, 0.02, (m, 3))
+            if dim == 2:
+                uw[:, 2] = 0.0
+            r["u_wall"] = uw
+            r["phi_wall"] = rng.uniform(-0.5, 1.5, m)
+            r["k0"] = rng.uniform(-0.01, 0.01, m)
+            r["k1"] = rng.uniform(-0.05, 0.0, m)
+            out.append(r)
+    if not out:
         return np.zeros(0, LINK_DTYPE)
-    return np.concatenate(recs)
+    return np.concatenate(out)

@@ -1,0 +1,894 @@
+// api.cu -- the C ABI of include/lbm.h: context, validation of the wall-link
+// lists, folding of each link's boundary formula into coefficients, memory
+// layout, launches, CUDA graphs, reductions, checkpoints and the autotuner.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "dispatch.cuh"
+#include "lbm.h"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_err;
+
+struct CaseHost {
+    lbm_case cfg;
+    int32_t N = 0;
+    int64_t stride = 0, pop_off = 0, node_off = 0;
+    int32_t brow_off = 0;
+    std::vector<uint8_t> solid;      // empty = all fluid
+    std::vector<lbm_link> links;
+};
+
+// runtime view of the compile-time lattices
+struct Lat {
+    int q;
+    int e[19][3];
+    double w[19];
+    int opp[19];
+};
+
+template <class L>
+Lat make_lat() {
+    Lat l{};
+    l.q = L::Q;
+    for (int a = 0; a < L::Q; ++a) {
+        l.e[a][0] = L::ex(a);
+        l.e[a][1] = L::ey(a);
+        l.e[a][2] = L::ez(a);
+        l.w[a] = L::w(a);
+        l.opp[a] = L::opp(a);
+    }
+    return l;
+}
+
+}  // namespace
+
+struct lbm_ctx {
+    lbm_config cfg{};
+    int dim = 2;
+    bool hh = false, hg = false, dbl = false, offset = false;
+    int QF = 9, QM = 5, NB = 2, H0 = 9, G0 = 9, P = 9;
+    size_t elem = 4;
+    Lat latf{}, latm{};
+    std::vector<CaseHost> cases;
+    int64_t pool_elems = 0, total_nodes = 0;
+    void *pool[2] = {nullptr, nullptr};
+    int cur = 0;
+    uint8_t *d_flags = nullptr;
+    void *d_cases = nullptr;
+    int block = 256, bpsm = 0;
+    int2 *d_tiles = nullptr;
+    int32_t ntiles = 0;
+    int32_t *d_case_tile_lo = nullptr;
+    BRec *d_brec = nullptr;
+    int32_t *d_brow = nullptr;
+    void *d_links = nullptr;
+    size_t cap_brec = 0, cap_brow = 0, cap_links = 0;
+    double *d_snap = nullptr, *d_part = nullptr, *d_red = nullptr, *h_red = nullptr;
+    double *d_mom = nullptr;
+    int64_t max_case_nodes = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int graph_steps = 0;
+    int64_t steps = 0;
+    int sm_count = 1;
+    KernelSet ks{};
+    std::string err;
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx *c, lbm_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    g_err = buf;
+    return st;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", \
+                        #call, cudaGetErrorString(e_));                                       \
+    } while (0)
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+bool finite3(const double *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+// base plane of a field: 0 f, 1 h, 2 + k g_k
+int field_base(const lbm_ctx *c, int field) {
+    return field == 0 ? 0 : (field == 1 ? c->H0 : c->G0 + (field - 2) * c->QM);
+}
+
+int64_t wrap_node(const CaseHost &cs, int64_t n, const int e[3], int sign) {
+    const int nx = cs.cfg.nx, ny = cs.cfg.ny, nz = cs.cfg.nz;
+    int x = (int)(n % nx), y = (int)((n / nx) % ny), z = (int)(n / ((int64_t)nx * ny));
+    x = ((x + sign * e[0]) % nx + nx) % nx;
+    y = ((y + sign * e[1]) % ny + ny) % ny;
+    z = ((z + sign * e[2]) % nz + nz) % nz;
+    return x + (int64_t)nx * (y + (int64_t)ny * z);
+}
+
+template <class T>
+CaseDev<T> case_dev(const lbm_ctx *c, const CaseHost &cs) {
+    CaseDev<T> d{};
+    d.nx = cs.cfg.nx;
+    d.ny = cs.cfg.ny;
+    d.nz = cs.cfg.nz;
+    d.N = cs.N;
+    d.pop_off = cs.pop_off;
+    d.stride = cs.stride;
+    d.node_off = cs.node_off;
+    d.brow_off = cs.brow_off;
+    d.om_f = T(1.0 / cs.cfg.tau_nu);
+    d.om_h = c->hh ? T(1.0 / cs.cfg.tau_D) : T(0);
+    d.om_g = c->hg ? T(1.0 / cs.cfg.tau_eta) : T(0);
+    d.guo = T(1.0 - 0.5 / cs.cfg.tau_nu);
+    d.ax = T(cs.cfg.accel[0]);
+    d.ay = T(cs.cfg.accel[1]);
+    d.az = c->dim == 3 ? T(cs.cfg.accel[2]) : T(0);
+    d.ref_rho = c->offset ? T(cs.cfg.rho0) : T(0);
+    d.ref_C = c->offset ? T(cs.cfg.C0) : T(0);
+    for (int k = 0; k < 3; ++k) {
+        d.ref_B[k] = c->offset ? T(cs.cfg.B0[k]) : T(0);
+        d.B0[k] = T(cs.cfg.B0[k]);
+    }
+    if (c->dim == 2) { d.ref_B[2] = T(0); d.B0[2] = T(0); }
+    return d;
+}
+
+// The boundary formula of one link folded into the coefficients of LinkDev
+// (see types.cuh).  All branch decisions are taken here in FP64.
+template <class T>
+LinkDev<T> link_dev(const lbm_ctx *c, const CaseHost &cs, const lbm_link &lk) {
+    const bool scalar = lk.field != 0;
+    const Lat &L = scalar ? c->latm : c->latf;
+    const int a = lk.dir, ap = L.opp[a];
+    const double w = L.w[a];
+    const int *e = L.e[a];
+    const double eu = e[0] * lk.u_wall[0] + e[1] * lk.u_wall[1] + e[2] * lk.u_wall[2];
+    const int64_t A = lk.node;
+    int64_t E = wrap_node(cs, A, e, +1);
+    double d = lk.d;
+    if (!cs.solid.empty() && cs.solid[E]) {   // no second fluid node: evaluate at d = 1/2
+        E = A;
+        d = 0.5;
+    }
+    double c0 = 0, ca = 0, cap = 0, cape = 0, cphi = 0, cB[3] = {0, 0, 0};
+    switch (lk.kind) {
+    case LBM_W_VELOCITY: {
+        // increment f^eq_a(X) - f^eq_a'(X) = 2 rho_X w (e.u_w)/c_s^2 (Sec. 4.1)
+        const double inc = 6.0 * w * eu;
+        if (d < 0.5) { cap = 2 * d; cape = 1 - 2 * d; cphi = inc; }          // Eq. 15, 16
+        else { ca = (2 * d - 1) / (2 * d); cap = 1 / (2 * d); cphi = inc / (2 * d); }  // Eq. 43
+        break;
+    }
+    case LBM_W_GIVEN:
+        // Eq. 19/34 with Eq. 20/35: p^eq_a(X) + p^eq_a'(X) = 2 w phi_w
+        c0 = 2 * w * lk.phi_wall;
+        cap = -2 * d;
+        cape = -(1 - 2 * d);
+        break;
+    case LBM_W_NEUMANN_BFL:
+        if (d < 0.5) { cap = 2 * d; cape = 1 - 2 * d; }                       // Eq. 21
+        else { ca = (2 * d - 1) / (2 * d); cap = 1 / (2 * d); }               // Eq. 22
+        break;
+    case LBM_W_FLUX: {
+        // M scheme, Eq. 25-27: [ (d - 1/2) p_a(A) + (1/2 - d) p_a'(E) + (1/2 + d) p_a'(A)
+        //                        + dflux + dmove ] / (d + 1/2)
+        const double s = 1.0 / (d + 0.5);
+        ca = (d - 0.5) * s;
+        cap = (0.5 + d) * s;
+        cape = (0.5 - d) * s;
+        c0 = lk.k0 * s;
+        if (lk.field == 1) {
+            // dmove = h^eq_a'(-u) - h^eq_a(-u) = 2 w C_X (e.u)/c_h^2 (Eq. 24)
+            cphi = (lk.k1 + 8.0 * w * eu) * s;
+        } else {
+            // dmove = 2 w [(e.u) B_k - (e.B) u_k]/c_g^2 at B_X (Eq. 24)
+            const int k = lk.field - 2;
+            cphi = lk.k1 * s;
+            for (int j = 0; j < 3; ++j) cB[j] = 8.0 * w * ((j == k ? eu : 0.0) - e[j] * lk.u_wall[k]) * s;
+        }
+        break;
+    }
+    default:
+        break;
+    }
+    LinkDev<T> r{};
+    r.nodeA = (int32_t)A;
+    r.nodeE = (int32_t)E;
+    const int base = field_base(c, lk.field);
+    r.plane_a = (uint8_t)(base + a);
+    r.plane_ap = (uint8_t)(base + ap);
+    r.phi_plane0 = (uint8_t)base;
+    r.flags = (uint8_t)((cphi != 0.0 ? LINK_NEED_PHI : 0) |
+                        ((cB[0] != 0.0 || cB[1] != 0.0 || cB[2] != 0.0) ? LINK_NEED_B : 0));
+    r.d = T(d);
+    r.c0 = T(c0);
+    r.ca = T(ca);
+    r.cap = T(cap);
+    r.cape = T(cape);
+    r.cphi = T(cphi);
+    for (int j = 0; j < 3; ++j) r.cB[j] = T(cB[j]);
+    double ref = 0.0;
+    if (c->offset) ref = lk.field == 0 ? cs.cfg.rho0 : (lk.field == 1 ? cs.cfg.C0 : cs.cfg.B0[lk.field - 2]);
+    r.off_a = T(w * ref);
+    r.off_ap = T(w * ref);
+    r.ref_phi = T(ref);
+    return r;
+}
+
+lbm_status upload_cases(lbm_ctx *ctx) {
+    if (ctx->dbl) {
+        std::vector<CaseDev<double>> v;
+        for (auto &cs : ctx->cases) v.push_back(case_dev<double>(ctx, cs));
+        CK(cudaMemcpyAsync(ctx->d_cases, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    } else {
+        std::vector<CaseDev<float>> v;
+        for (auto &cs : ctx->cases) v.push_back(case_dev<float>(ctx, cs));
+        CK(cudaMemcpyAsync(ctx->d_cases, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return LBM_OK;
+}
+
+void drop_graphs(lbm_ctx *ctx) {
+    for (auto &g : ctx->gexec)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
+lbm_status build_tiles(lbm_ctx *ctx) {
+    std::vector<int2> tiles;
+    std::vector<int32_t> lo;
+    for (size_t c = 0; c < ctx->cases.size(); ++c) {
+        lo.push_back((int32_t)tiles.size());
+        for (int32_t s = 0; s < ctx->cases[c].N; s += ctx->block) tiles.push_back(make_int2((int)c, s));
+    }
+    lo.push_back((int32_t)tiles.size());
+    if (ctx->d_tiles) cudaFree(ctx->d_tiles);
+    if (ctx->d_case_tile_lo) cudaFree(ctx->d_case_tile_lo);
+    if (ctx->d_part) cudaFree(ctx->d_part);
+    ctx->d_tiles = nullptr;
+    ctx->d_case_tile_lo = nullptr;
+    ctx->d_part = nullptr;
+    ctx->ntiles = (int32_t)tiles.size();
+    CK(cudaMalloc(&ctx->d_tiles, tiles.size() * sizeof(int2)));
+    CK(cudaMalloc(&ctx->d_case_tile_lo, lo.size() * sizeof(int32_t)));
+    CK(cudaMalloc(&ctx->d_part, (size_t)ctx->ntiles * RED_Q * sizeof(double)));
+    CK(cudaMemcpy(ctx->d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_case_tile_lo, lo.data(), lo.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    drop_graphs(ctx);
+    return LBM_OK;
+}
+
+template <class T>
+lbm_status upload_walls_t(lbm_ctx *ctx) {
+    std::vector<BRec> brec;
+    std::vector<int32_t> brow;
+    std::vector<LinkDev<T>> links;
+    std::vector<uint8_t> flags((size_t)ctx->total_nodes, 0);
+    for (auto &cs : ctx->cases) {
+        const int64_t rows = (int64_t)cs.cfg.ny * cs.cfg.nz;
+        cs.brow_off = (int32_t)brow.size();
+        std::vector<int32_t> order(cs.links.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = (int32_t)i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int32_t a, int32_t b) { return cs.links[a].node < cs.links[b].node; });
+        for (int32_t n = 0; n < cs.N; ++n)
+            flags[cs.node_off + n] = (cs.solid.empty() || !cs.solid[n]) ? NODE_FLUID : 0;
+        size_t i = 0;
+        int64_t row = 0;
+        for (; i < order.size();) {
+            const uint32_t node = cs.links[order[i]].node;
+            const int64_t r = node / cs.cfg.nx;
+            while (row <= r) { brow.push_back((int32_t)brec.size()); ++row; }
+            BRec b{};
+            b.node = (int32_t)node;
+            b.lo = (int32_t)links.size();
+            while (i < order.size() && cs.links[order[i]].node == node) {
+                links.push_back(link_dev<T>(ctx, cs, cs.links[order[i]]));
+                ++i;
+            }
+            b.hi = (int32_t)links.size();
+            brec.push_back(b);
+            flags[cs.node_off + node] |= NODE_BOUNDARY;
+        }
+        while (row <= rows) { brow.push_back((int32_t)brec.size()); ++row; }
+    }
+    if (brec.empty()) brec.push_back(BRec{-1, 0, 0, 0});
+    if (links.empty()) links.push_back(LinkDev<T>{});
+    auto grow = [&](void **ptr, size_t &cap, size_t bytes) -> lbm_status {
+        if (bytes > cap) {
+            if (*ptr) cudaFree(*ptr);
+            *ptr = nullptr;
+            CK(cudaMalloc(ptr, bytes));
+            cap = bytes;
+        }
+        return LBM_OK;
+    };
+    lbm_status st;
+    if ((st = grow((void **)&ctx->d_brec, ctx->cap_brec, brec.size() * sizeof(BRec))) != LBM_OK) return st;
+    if ((st = grow((void **)&ctx->d_brow, ctx->cap_brow, brow.size() * sizeof(int32_t))) != LBM_OK) return st;
+    if ((st = grow(&ctx->d_links, ctx->cap_links, links.size() * sizeof(LinkDev<T>))) != LBM_OK) return st;
+    CK(cudaMemcpy(ctx->d_brec, brec.data(), brec.size() * sizeof(BRec), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_brow, brow.data(), brow.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_links, links.data(), links.size() * sizeof(LinkDev<T>), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_flags, flags.data(), flags.size(), cudaMemcpyHostToDevice));
+    drop_graphs(ctx);
+    return upload_cases(ctx);
+}
+
+lbm_status upload_walls(lbm_ctx *ctx) {
+    return ctx->dbl ? upload_walls_t<double>(ctx) : upload_walls_t<float>(ctx);
+}
+
+template <class T>
+StepParams<T> step_params(const lbm_ctx *c) {
+    StepParams<T> p{};
+    p.src = c->pool[c->cur];
+    p.dst = c->pool[1 - c->cur];
+    p.flags = c->d_flags;
+    p.cases = static_cast<const CaseDev<T> *>(c->d_cases);
+    p.tiles = c->d_tiles;
+    p.ntiles = c->ntiles;
+    p.brec = c->d_brec;
+    p.brow = c->d_brow;
+    p.links = static_cast<const LinkDev<T> *>(c->d_links);
+    return p;
+}
+
+int step_grid(const lbm_ctx *c) {
+    if (c->bpsm <= 0) return c->ntiles;
+    return std::max(1, std::min(c->ntiles, c->bpsm * c->sm_count));
+}
+
+lbm_status launch_step(lbm_ctx *ctx) {
+    cudaError_t e;
+    if (ctx->dbl) {
+        const StepParams<double> p = step_params<double>(ctx);
+        e = ctx->ks.step(&p, step_grid(ctx), ctx->block, ctx->stream);
+    } else {
+        const StepParams<float> p = step_params<float>(ctx);
+        e = ctx->ks.step(&p, step_grid(ctx), ctx->block, ctx->stream);
+    }
+    if (e != cudaSuccess) return fail(ctx, LBM_ECUDA, "step launch: %s", cudaGetErrorString(e));
+    ctx->cur ^= 1;
+    return LBM_OK;
+}
+
+template <class T, class FT>
+lbm_status launch_init(lbm_ctx *ctx, int case_id, const FT *rho, const FT *u, const FT *C, const FT *B,
+                       cudaError_t (*fn)(const void *, int, int, cudaStream_t)) {
+    const CaseHost &cs = ctx->cases[case_id];
+    InitParams<T, FT> ip{};
+    ip.dst = ctx->pool[ctx->cur];
+    ip.flags = ctx->d_flags;
+    ip.cases = static_cast<const CaseDev<T> *>(ctx->d_cases);
+    ip.case_id = case_id;
+    ip.rho = rho;
+    ip.u = u;
+    ip.C = C;
+    ip.B = B;
+    ip.rho0 = T(cs.cfg.rho0);
+    ip.C0 = T(cs.cfg.C0);
+    for (int k = 0; k < 3; ++k) ip.B0[k] = T(cs.cfg.B0[k]);
+    const int grid = (int)((cs.N + 255) / 256);
+    CK(fn(&ip, grid, 256, ctx->stream));
+    // residual history of the case starts again from zero
+    for (int k = 0; k < SNAP_Q; ++k)
+        CK(cudaMemsetAsync(ctx->d_snap + (int64_t)k * ctx->total_nodes + cs.node_off, 0,
+                           (size_t)cs.N * sizeof(double), ctx->stream));
+    return LBM_OK;
+}
+
+lbm_status init_case_host(lbm_ctx *ctx, int case_id, const double *rho, const double *u, const double *C,
+                          const double *B) {
+    const CaseHost &cs = ctx->cases[case_id];
+    double *dr = nullptr, *du = nullptr, *dC = nullptr, *dB = nullptr;
+    auto up = [&](const double *h, double **d, size_t cnt) -> lbm_status {
+        if (!h) return LBM_OK;
+        CK(cudaMalloc(d, cnt * sizeof(double)));
+        CK(cudaMemcpy(*d, h, cnt * sizeof(double), cudaMemcpyHostToDevice));
+        return LBM_OK;
+    };
+    lbm_status st = LBM_OK;
+    if (st == LBM_OK) st = up(rho, &dr, cs.N);
+    if (st == LBM_OK) st = up(u, &du, 3 * (size_t)cs.N);
+    if (st == LBM_OK) st = up(C, &dC, cs.N);
+    if (st == LBM_OK) st = up(B, &dB, 3 * (size_t)cs.N);
+    if (st == LBM_OK) {
+        if (ctx->dbl) st = launch_init<double, double>(ctx, case_id, dr, du, dC, dB, ctx->ks.init_d);
+        else st = launch_init<float, double>(ctx, case_id, dr, du, dC, dB, ctx->ks.init_d);
+    }
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(dr);
+    cudaFree(du);
+    cudaFree(dC);
+    cudaFree(dB);
+    if (st != LBM_OK) return st;
+    if (e != cudaSuccess) return fail(ctx, LBM_ECUDA, "init: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+void free_ctx(lbm_ctx *c) {
+    if (!c) return;
+    drop_graphs(c);
+    void *ptrs[] = {c->pool[0], c->pool[1], c->d_flags, c->d_cases, c->d_tiles, c->d_case_tile_lo,
+                    c->d_brec, c->d_brow, c->d_links, c->d_snap, c->d_part, c->d_red, c->d_mom};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->h_red) cudaFreeHost(c->h_red);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // namespace
+
+// =============================================================================
+extern "C" {
+
+const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
+    lbm_ctx *ctx = nullptr;
+    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!cfg || !cfg->cases || cfg->ncases < 1) return fail(nullptr, LBM_EINVAL, "config needs >= 1 case");
+    if (cfg->lattice != LBM_D2Q9 && cfg->lattice != LBM_D3Q19) return fail(nullptr, LBM_EINVAL, "bad lattice");
+    if (cfg->prec < LBM_FP64 || cfg->prec > LBM_BF16S) return fail(nullptr, LBM_EINVAL, "bad precision");
+    if (!(cfg->physics & LBM_FLOW) || (cfg->physics & ~7u)) return fail(nullptr, LBM_EINVAL, "bad physics mask");
+    ctx = new lbm_ctx();
+    ctx->cfg = *cfg;
+    ctx->cfg.cases = nullptr;
+    ctx->dim = cfg->lattice == LBM_D2Q9 ? 2 : 3;
+    ctx->hh = (cfg->physics & LBM_CD) != 0;
+    ctx->hg = (cfg->physics & LBM_MHD) != 0;
+    ctx->dbl = cfg->prec == LBM_FP64;
+    ctx->offset = cfg->prec == LBM_FP16S || cfg->prec == LBM_BF16S;
+    ctx->elem = cfg->prec == LBM_FP64 ? 8 : (cfg->prec == LBM_FP32 ? 4 : 2);
+    ctx->latf = ctx->dim == 2 ? make_lat<D2Q9>() : make_lat<D3Q19>();
+    ctx->latm = ctx->dim == 2 ? make_lat<D2Q5>() : make_lat<D3Q7>();
+    ctx->QF = ctx->latf.q;
+    ctx->QM = ctx->latm.q;
+    ctx->NB = ctx->dim;
+    ctx->H0 = ctx->QF;
+    ctx->G0 = ctx->QF + (ctx->hh ? ctx->QM : 0);
+    ctx->P = ctx->G0 + (ctx->hg ? ctx->NB * ctx->QM : 0);
+    int64_t pool = 0, nodes = 0;
+    for (int c = 0; c < cfg->ncases; ++c) {
+        const lbm_case &k = cfg->cases[c];
+        CaseHost cs;
+        cs.cfg = k;
+        if (k.nx < 1 || k.ny < 1 || k.nz < 1 || (ctx->dim == 2 && k.nz != 1)) {
+            lbm_status s = fail(ctx, LBM_EINVAL, "case %d: bad sizes", c);
+            free_ctx(ctx);
+            return s;
+        }
+        const int64_t N = (int64_t)k.nx * k.ny * k.nz;
+        bool bad_tau = !(k.tau_nu > 0.5) || (ctx->hh && !(k.tau_D > 0.5)) || (ctx->hg && !(k.tau_eta > 0.5));
+        if (N > (int64_t)1 << 30 || bad_tau || !finite3(k.accel) || !finite3(k.B0) || !std::isfinite(k.rho0) ||
+            !(k.rho0 > 0) || !std::isfinite(k.C0)) {
+            lbm_status s = fail(ctx, LBM_EINVAL, "case %d: bad parameters (tau must exceed 1/2)", c);
+            free_ctx(ctx);
+            return s;
+        }
+        cs.N = (int32_t)N;
+        cs.stride = round_up(N, 64);
+        cs.pop_off = pool;
+        cs.node_off = nodes;
+        pool += cs.stride * ctx->P;
+        nodes += round_up(N, 64);
+        ctx->max_case_nodes = std::max<int64_t>(ctx->max_case_nodes, N);
+        ctx->cases.push_back(cs);
+    }
+    ctx->pool_elems = pool;
+    ctx->total_nodes = nodes;
+    switch ((ctx->dim == 3 ? 4 : 0) + (int)cfg->prec) {
+    case 0: ctx->ks = kernels_2d_f64(ctx->hh, ctx->hg); break;
+    case 1: ctx->ks = kernels_2d_f32(ctx->hh, ctx->hg); break;
+    case 2: ctx->ks = kernels_2d_f16(ctx->hh, ctx->hg); break;
+    case 3: ctx->ks = kernels_2d_bf16(ctx->hh, ctx->hg); break;
+    case 4: ctx->ks = kernels_3d_f64(ctx->hh, ctx->hg); break;
+    case 5: ctx->ks = kernels_3d_f32(ctx->hh, ctx->hg); break;
+    case 6: ctx->ks = kernels_3d_f16(ctx->hh, ctx->hg); break;
+    default: ctx->ks = kernels_3d_bf16(ctx->hh, ctx->hg); break;
+    }
+    lbm_status st = LBM_OK;
+    auto ck = [&](cudaError_t e, const char *what) {
+        if (st == LBM_OK && e != cudaSuccess)
+            st = fail(ctx, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", what,
+                      cudaGetErrorString(e));
+    };
+    ck(cudaSetDevice(cfg->device), "cudaSetDevice");
+    if (st == LBM_OK) {
+        if (cfg->stream) {
+            ctx->stream = static_cast<cudaStream_t>(cfg->stream);
+        } else {
+            ck(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+            ctx->own_stream = st == LBM_OK;
+        }
+    }
+    ck(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, cfg->device), "sm count");
+    const size_t pool_bytes = (size_t)pool * ctx->elem;
+    ck(cudaMalloc(&ctx->pool[0], pool_bytes), "population buffer 0");
+    ck(cudaMalloc(&ctx->pool[1], pool_bytes), "population buffer 1");
+    if (st == LBM_OK) {
+        ck(cudaMemset(ctx->pool[0], 0, pool_bytes), "memset");
+        ck(cudaMemset(ctx->pool[1], 0, pool_bytes), "memset");
+    }
+    ck(cudaMalloc(&ctx->d_flags, (size_t)nodes), "flags");
+    ck(cudaMalloc(&ctx->d_cases, ctx->cases.size() * (ctx->dbl ? sizeof(CaseDev<double>) : sizeof(CaseDev<float>))),
+       "case table");
+    ck(cudaMalloc(&ctx->d_snap, (size_t)nodes * SNAP_Q * sizeof(double)), "snapshot");
+    if (st == LBM_OK) ck(cudaMemset(ctx->d_snap, 0, (size_t)nodes * SNAP_Q * sizeof(double)), "memset");
+    ck(cudaMalloc(&ctx->d_red, ctx->cases.size() * RED_Q * sizeof(double)), "reduction output");
+    ck(cudaMallocHost(&ctx->h_red, ctx->cases.size() * RED_Q * sizeof(double)), "pinned reduction output");
+    ck(cudaMalloc(&ctx->d_mom, (size_t)ctx->max_case_nodes * 8 * sizeof(double)), "moment scratch");
+    if (st == LBM_OK) st = build_tiles(ctx);
+    if (st == LBM_OK) st = upload_walls(ctx);
+    for (int c = 0; st == LBM_OK && c < (int)ctx->cases.size(); ++c)
+        st = init_case_host(ctx, c, nullptr, nullptr, nullptr, nullptr);
+    if (st != LBM_OK) {
+        g_err = ctx->err;
+        free_ctx(ctx);
+        return st;
+    }
+    *out = ctx;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *ctx) { free_ctx(ctx); }
+
+lbm_status lbm_set_walls(lbm_ctx *ctx, int32_t case_id, const uint8_t *solid, const lbm_link *links,
+                         size_t nlinks) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (case_id < 0 || case_id >= (int)ctx->cases.size()) return fail(ctx, LBM_EINVAL, "bad case id %d", case_id);
+    if (!solid || (nlinks && !links)) return fail(ctx, LBM_EINVAL, "solid/links pointer is NULL");
+    CaseHost &cs = ctx->cases[case_id];
+    const int64_t N = cs.N;
+    std::vector<uint8_t> sol(solid, solid + N);
+    for (auto &v : sol) v = v ? 1 : 0;
+    const int nfields = 1 + (ctx->hh ? 1 : 0) + (ctx->hg ? ctx->NB : 0);
+    (void)nfields;
+    // coverage bitmap over (node, plane)
+    std::vector<uint8_t> seen((size_t)N * ctx->P, 0);
+    for (size_t i = 0; i < nlinks; ++i) {
+        const lbm_link &lk = links[i];
+        const int f = lk.field;
+        const bool ok_field = f == 0 || (f == 1 && ctx->hh) || (f >= 2 && f < 2 + ctx->NB && ctx->hg);
+        if (!ok_field) return fail(ctx, LBM_EINVAL, "link %zu: field %d not enabled", i, f);
+        const Lat &L = f == 0 ? ctx->latf : ctx->latm;
+        if (lk.dir < 1 || lk.dir >= L.q) return fail(ctx, LBM_EINVAL, "link %zu: bad direction %d", i, lk.dir);
+        const bool ok_kind = f == 0 ? lk.kind == LBM_W_VELOCITY
+                                    : (lk.kind == LBM_W_GIVEN || lk.kind == LBM_W_FLUX || lk.kind == LBM_W_NEUMANN_BFL);
+        if (!ok_kind) return fail(ctx, LBM_EINVAL, "link %zu: kind %d not valid for field %d", i, lk.kind, f);
+        if (lk.node >= (uint64_t)N || sol[lk.node]) return fail(ctx, LBM_EINVAL, "link %zu: node %u not fluid", i, lk.node);
+        if (!(lk.d > 0.0 && lk.d <= 1.0)) return fail(ctx, LBM_EINVAL, "link %zu: d = %g outside (0, 1]", i, lk.d);
+        if (!finite3(lk.u_wall) || !std::isfinite(lk.phi_wall) || !std::isfinite(lk.k0) || !std::isfinite(lk.k1))
+            return fail(ctx, LBM_EINVAL, "link %zu: non-finite wall data", i);
+        CaseHost tmp;
+        tmp.cfg = cs.cfg;
+        const int64_t Bn = wrap_node(tmp, lk.node, L.e[lk.dir], -1);
+        if (!sol[Bn]) return fail(ctx, LBM_EINVAL, "link %zu: node %u - e_%d is fluid", i, lk.node, lk.dir);
+        uint8_t &slot = seen[(size_t)lk.node * ctx->P + field_base(ctx, f) + lk.dir];
+        if (slot) return fail(ctx, LBM_EINVAL, "link %zu: duplicate (node %u, field %d, dir %d)", i, lk.node, f, lk.dir);
+        slot = 1;
+    }
+    CaseHost tmp;
+    tmp.cfg = cs.cfg;
+    for (int64_t n = 0; n < N; ++n) {
+        if (sol[n]) continue;
+        for (int f = 0; f < 2 + ctx->NB; ++f) {
+            if ((f == 1 && !ctx->hh) || (f >= 2 && !ctx->hg)) continue;
+            const Lat &L = f == 0 ? ctx->latf : ctx->latm;
+            for (int a = 1; a < L.q; ++a) {
+                if (sol[wrap_node(tmp, n, L.e[a], -1)] && !seen[(size_t)n * ctx->P + field_base(ctx, f) + a])
+                    return fail(ctx, LBM_EINVAL, "missing link: node %lld field %d dir %d", (long long)n, f, a);
+            }
+        }
+    }
+    cs.solid = std::move(sol);
+    cs.links.assign(links, links + nlinks);
+    lbm_status st = upload_walls(ctx);
+    if (st != LBM_OK) return st;
+    return init_case_host(ctx, case_id, nullptr, nullptr, nullptr, nullptr);
+}
+
+lbm_status lbm_init_equilibrium(lbm_ctx *ctx, int32_t case_id, const double *rho, const double *u,
+                                const double *C, const double *B) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (case_id < 0 || case_id >= (int)ctx->cases.size()) return fail(ctx, LBM_EINVAL, "bad case id %d", case_id);
+    return init_case_host(ctx, case_id, rho, u, C, B);
+}
+
+lbm_status lbm_init_equilibrium_device(lbm_ctx *ctx, int32_t case_id, const float *rho, const float *u,
+                                       const float *C, const float *B) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (case_id < 0 || case_id >= (int)ctx->cases.size()) return fail(ctx, LBM_EINVAL, "bad case id %d", case_id);
+    if (ctx->dbl) return launch_init<double, float>(ctx, case_id, rho, u, C, B, ctx->ks.init_f);
+    return launch_init<float, float>(ctx, case_id, rho, u, C, B, ctx->ks.init_f);
+}
+
+lbm_status lbm_set_graph(lbm_ctx *ctx, int32_t steps_per_graph) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (steps_per_graph < 0 || steps_per_graph % 2) return fail(ctx, LBM_EINVAL, "steps per graph must be even");
+    drop_graphs(ctx);
+    ctx->graph_steps = steps_per_graph;
+    return LBM_OK;
+}
+
+static lbm_status capture_graph(lbm_ctx *ctx) {
+    const int parity = ctx->cur;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    lbm_status st = LBM_OK;
+    for (int i = 0; i < ctx->graph_steps && st == LBM_OK; ++i) st = launch_step(ctx);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    ctx->cur = parity;
+    if (st != LBM_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return fail(ctx, LBM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ctx->gexec[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(ctx, LBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx *ctx, int32_t nsteps) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (nsteps < 0) return fail(ctx, LBM_EINVAL, "nsteps < 0");
+    int32_t left = nsteps;
+    while (left > 0) {
+        if (ctx->graph_steps > 0 && left >= ctx->graph_steps) {
+            if (!ctx->gexec[ctx->cur]) {
+                lbm_status st = capture_graph(ctx);
+                if (st != LBM_OK) return st;
+            }
+            CK(cudaGraphLaunch(ctx->gexec[ctx->cur], ctx->stream));
+            left -= ctx->graph_steps;
+            ctx->steps += ctx->graph_steps;
+        } else {
+            lbm_status st = launch_step(ctx);
+            if (st != LBM_OK) return st;
+            --left;
+            ++ctx->steps;
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_ctx *ctx, int32_t case_id, double *rho, double *u, double *C, double *B) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (case_id < 0 || case_id >= (int)ctx->cases.size()) return fail(ctx, LBM_EINVAL, "bad case id %d", case_id);
+    const CaseHost &cs = ctx->cases[case_id];
+    const int64_t N = cs.N;
+    double *d = ctx->d_mom;
+    const int grid = (int)((N + 255) / 256);
+    if (ctx->dbl) {
+        MomParams<double> mp{ctx->pool[ctx->cur], ctx->d_flags, static_cast<const CaseDev<double> *>(ctx->d_cases),
+                             case_id, d, d + N, d + 4 * N, d + 5 * N};
+        CK(ctx->ks.moments(&mp, grid, 256, ctx->stream));
+    } else {
+        MomParams<float> mp{ctx->pool[ctx->cur], ctx->d_flags, static_cast<const CaseDev<float> *>(ctx->d_cases),
+                            case_id, d, d + N, d + 4 * N, d + 5 * N};
+        CK(ctx->ks.moments(&mp, grid, 256, ctx->stream));
+    }
+    if (rho) CK(cudaMemcpyAsync(rho, d, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (u) CK(cudaMemcpyAsync(u, d + N, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (C) CK(cudaMemcpyAsync(C, d + 4 * N, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (B) CK(cudaMemcpyAsync(B, d + 5 * N, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_check(lbm_ctx *ctx, double *out) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (ctx->dbl) {
+        RedParams<double> rp{ctx->pool[ctx->cur], ctx->d_flags, static_cast<const CaseDev<double> *>(ctx->d_cases),
+                             ctx->d_tiles, ctx->ntiles, ctx->d_snap, ctx->total_nodes, ctx->d_part};
+        CK(ctx->ks.reduce(&rp, ctx->ntiles, ctx->block, ctx->stream));
+    } else {
+        RedParams<float> rp{ctx->pool[ctx->cur], ctx->d_flags, static_cast<const CaseDev<float> *>(ctx->d_cases),
+                            ctx->d_tiles, ctx->ntiles, ctx->d_snap, ctx->total_nodes, ctx->d_part};
+        CK(ctx->ks.reduce(&rp, ctx->ntiles, ctx->block, ctx->stream));
+    }
+    k_reduce_final<<<(int)ctx->cases.size(), 256, 0, ctx->stream>>>(ctx->d_part, ctx->d_case_tile_lo, ctx->d_red);
+    CK(cudaGetLastError());
+    const size_t bytes = ctx->cases.size() * RED_Q * sizeof(double);
+    CK(cudaMemcpyAsync(ctx->h_red, ctx->d_red, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (out) std::memcpy(out, ctx->h_red, bytes);
+    for (size_t c = 0; c < ctx->cases.size(); ++c)
+        if (ctx->h_red[c * RED_Q + 5] != 0.0)
+            return fail(ctx, LBM_EUNSTABLE, "case %zu: %g non-finite populations", c, ctx->h_red[c * RED_Q + 5]);
+    return LBM_OK;
+}
+
+lbm_status lbm_run_to_steady(lbm_ctx *ctx, int64_t max_steps, int32_t interval, double tol, int64_t *steps_done,
+                             double *residual) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (interval < 1 || max_steps < 0) return fail(ctx, LBM_EINVAL, "bad interval / max_steps");
+    std::vector<double> out(ctx->cases.size() * RED_Q);
+    lbm_status st = lbm_check(ctx, out.data());   // baseline snapshot
+    if (st != LBM_OK) return st;
+    int64_t done = 0;
+    double worst = INFINITY;
+    while (done < max_steps) {
+        const int32_t k = (int32_t)std::min<int64_t>(interval, max_steps - done);
+        if ((st = lbm_step(ctx, k)) != LBM_OK) break;
+        done += k;
+        if ((st = lbm_check(ctx, out.data())) != LBM_OK) break;
+        worst = 0.0;
+        for (size_t c = 0; c < ctx->cases.size(); ++c) {
+            const double den = out[c * RED_Q + 7];
+            const double r = den > 0 ? std::sqrt(out[c * RED_Q + 6] / den) : 0.0;
+            worst = std::max(worst, r);
+        }
+        if (worst < tol) break;
+    }
+    if (steps_done) *steps_done = done;
+    if (residual) *residual = worst;
+    return st;
+}
+
+size_t lbm_state_bytes(const lbm_ctx *ctx) {
+    return ctx ? 16 + (size_t)ctx->pool_elems * ctx->elem : 0;
+}
+
+lbm_status lbm_get_state(lbm_ctx *ctx, void *host, size_t bytes) {
+    if (!ctx || !host) return fail(ctx, LBM_EINVAL, "NULL argument");
+    if (bytes != lbm_state_bytes(ctx)) return fail(ctx, LBM_EINVAL, "state size mismatch");
+    uint64_t hdr[2] = {0x4c424d5354415445ull, (uint64_t)ctx->steps};
+    std::memcpy(host, hdr, 16);
+    CK(cudaMemcpyAsync(static_cast<char *>(host) + 16, ctx->pool[ctx->cur], bytes - 16, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes) {
+    if (!ctx || !host) return fail(ctx, LBM_EINVAL, "NULL argument");
+    if (bytes != lbm_state_bytes(ctx)) return fail(ctx, LBM_EINVAL, "state size mismatch");
+    uint64_t hdr[2];
+    std::memcpy(hdr, host, 16);
+    if (hdr[0] != 0x4c424d5354415445ull) return fail(ctx, LBM_EINVAL, "not a state blob");
+    CK(cudaMemcpyAsync(ctx->pool[ctx->cur], static_cast<const char *>(host) + 16, bytes - 16,
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->steps = (int64_t)hdr[1];
+    return LBM_OK;
+}
+
+int64_t lbm_steps_done(const lbm_ctx *ctx) { return ctx ? ctx->steps : 0; }
+
+lbm_status lbm_set_launch(lbm_ctx *ctx, int32_t block, int32_t blocks_per_sm) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (block < 64 || block > 256 || block % 32 || blocks_per_sm < 0 || blocks_per_sm > 64)
+        return fail(ctx, LBM_EINVAL, "block must be 64..256 in steps of 32, blocks_per_sm 0..64");
+    ctx->bpsm = blocks_per_sm;
+    if (block != ctx->block) {
+        ctx->block = block;
+        return build_tiles(ctx);
+    }
+    drop_graphs(ctx);
+    return LBM_OK;
+}
+
+int32_t lbm_launches_per_step(const lbm_ctx *ctx) { return ctx ? 1 : 0; }
+
+lbm_status lbm_device_state(lbm_ctx *ctx, int32_t case_id, void **base, int32_t *elem_bytes, int64_t *plane_stride,
+                            int64_t *case_offset, int32_t *planes) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (case_id < 0 || case_id >= (int)ctx->cases.size()) return fail(ctx, LBM_EINVAL, "bad case id %d", case_id);
+    if (base) *base = ctx->pool[ctx->cur];
+    if (elem_bytes) *elem_bytes = (int32_t)ctx->elem;
+    if (plane_stride) *plane_stride = ctx->cases[case_id].stride;
+    if (case_offset) *case_offset = ctx->cases[case_id].pop_off;
+    if (planes) *planes = ctx->P;
+    return LBM_OK;
+}
+
+// ----------------------------------------------------------------------------- autotuner
+lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, int32_t *block_out, int32_t *bpsm_out,
+                        double *best_ms) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (iters < 1) iters = 20;
+    cudaDeviceProp prop{};
+    CK(cudaGetDeviceProperties(&prop, ctx->cfg.device));
+    std::ostringstream key;
+    key << prop.name << "|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
+        << ctx->cases.size();
+    int64_t tot = 0;
+    for (auto &c : ctx->cases) tot += c.N;
+    key << "|nodes" << tot;
+    std::string k = key.str();
+    for (auto &ch : k)
+        if (ch == ' ') ch = '_';
+    if (cache_path) {
+        std::ifstream in(cache_path);
+        std::string line;
+        while (std::getline(in, line)) {
+            std::istringstream ls(line);
+            std::string kk;
+            int b, p;
+            double ms;
+            if (ls >> kk >> b >> p >> ms && kk == k) {
+                lbm_status st = lbm_set_launch(ctx, b, p);
+                if (st != LBM_OK) return st;
+                if (block_out) *block_out = b;
+                if (bpsm_out) *bpsm_out = p;
+                if (best_ms) *best_ms = ms;
+                return LBM_OK;
+            }
+        }
+    }
+    // save the state; timing steps must not change the caller's solution
+    const size_t bytes = (size_t)ctx->pool_elems * ctx->elem;
+    void *save = nullptr;
+    CK(cudaMalloc(&save, bytes));
+    CK(cudaMemcpyAsync(save, ctx->pool[ctx->cur], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    const int64_t steps0 = ctx->steps;
+    const int saved_graph = ctx->graph_steps;
+    ctx->graph_steps = 0;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int blocks[] = {64, 128, 192, 256};
+    const int bps[] = {0, 2, 4, 8, 16};
+    int bb = ctx->block, bp = ctx->bpsm;
+    double best = INFINITY;
+    lbm_status st = LBM_OK;
+    for (int b : blocks) {
+        for (int p : bps) {
+            if ((st = lbm_set_launch(ctx, b, p)) != LBM_OK) break;
+            if ((st = lbm_step(ctx, 2)) != LBM_OK) break;
+            cudaEventRecord(e0, ctx->stream);
+            if ((st = lbm_step(ctx, iters)) != LBM_OK) break;
+            cudaEventRecord(e1, ctx->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double per = ms / iters;
+            if (per < best) { best = per; bb = b; bp = p; }
+        }
+        if (st != LBM_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->graph_steps = saved_graph;
+    if (st == LBM_OK) st = lbm_set_launch(ctx, bb, bp);
+    cudaMemcpyAsync(ctx->pool[ctx->cur], save, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(save);
+    ctx->steps = steps0;
+    if (st != LBM_OK) return st;
+    if (cache_path) {
+        std::ofstream o(cache_path, std::ios::app);
+        o << k << " " << bb << " " << bp << " " << best << "\n";
+    }
+    if (block_out) *block_out = bb;
+    if (bpsm_out) *bpsm_out = bp;
+    if (best_ms) *best_ms = best;
+    return LBM_OK;
+}
+
+}  // extern "C"

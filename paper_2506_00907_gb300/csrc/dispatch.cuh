@@ -1,0 +1,68 @@
+// dispatch.cuh -- type-erased launchers of one (lattice, physics, precision)
+// variant of the kernels, so that the C ABI picks a variant at run time.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace lbm {
+
+struct KernelSet {
+    cudaError_t (*step)(const void *params, int grid, int block, cudaStream_t s);
+    cudaError_t (*init_d)(const void *params, int grid, int block, cudaStream_t s);   // FP64 host-side fields
+    cudaError_t (*init_f)(const void *params, int grid, int block, cudaStream_t s);   // FP32 device fields
+    cudaError_t (*moments)(const void *params, int grid, int block, cudaStream_t s);
+    cudaError_t (*reduce)(const void *params, int grid, int block, cudaStream_t s);
+    const void *step_fn;          // kernel symbol (occupancy queries)
+};
+
+template <int DIM, bool HH, bool HG, class S>
+struct Launch {
+    using T = typename Codec<S>::T;
+    static cudaError_t step(const void *p, int g, int b, cudaStream_t s) {
+        k_step<DIM, HH, HG, S><<<g, b, 0, s>>>(*static_cast<const StepParams<T> *>(p));
+        return cudaGetLastError();
+    }
+    static cudaError_t init_d(const void *p, int g, int b, cudaStream_t s) {
+        k_init<DIM, HH, HG, S, double><<<g, b, 0, s>>>(*static_cast<const InitParams<T, double> *>(p));
+        return cudaGetLastError();
+    }
+    static cudaError_t init_f(const void *p, int g, int b, cudaStream_t s) {
+        k_init<DIM, HH, HG, S, float><<<g, b, 0, s>>>(*static_cast<const InitParams<T, float> *>(p));
+        return cudaGetLastError();
+    }
+    static cudaError_t moments(const void *p, int g, int b, cudaStream_t s) {
+        k_moments<DIM, HH, HG, S><<<g, b, 0, s>>>(*static_cast<const MomParams<T> *>(p));
+        return cudaGetLastError();
+    }
+    static cudaError_t reduce(const void *p, int g, int b, cudaStream_t s) {
+        k_reduce<DIM, HH, HG, S><<<g, b, 0, s>>>(*static_cast<const RedParams<T> *>(p));
+        return cudaGetLastError();
+    }
+    static KernelSet make() {
+        return KernelSet{&step, &init_d, &init_f, &moments, &reduce,
+                         reinterpret_cast<const void *>(&k_step<DIM, HH, HG, S>)};
+    }
+};
+
+// prec: 0 FP64, 1 FP32, 2 FP16S, 3 BF16S
+KernelSet kernels_2d_f64(bool hh, bool hg);
+KernelSet kernels_2d_f32(bool hh, bool hg);
+KernelSet kernels_2d_f16(bool hh, bool hg);
+KernelSet kernels_2d_bf16(bool hh, bool hg);
+KernelSet kernels_3d_f64(bool hh, bool hg);
+KernelSet kernels_3d_f32(bool hh, bool hg);
+KernelSet kernels_3d_f16(bool hh, bool hg);
+KernelSet kernels_3d_bf16(bool hh, bool hg);
+
+}  // namespace lbm
+
+#define LBM_DEFINE_KERNEL_SET(NAME, DIM, S)                               \
+    namespace lbm {                                                       \
+    KernelSet NAME(bool hh, bool hg) {                                    \
+        if (hh && hg) return Launch<DIM, true, true, S>::make();          \
+        if (hh) return Launch<DIM, true, false, S>::make();               \
+        if (hg) return Launch<DIM, false, true, S>::make();               \
+        return Launch<DIM, false, false, S>::make();                      \
+    }                                                                     \
+    }

@@ -1,0 +1,505 @@
+// kernels.cuh -- the fused coupled lattice-Boltzmann step and its helpers.
+//
+// Storage: one structure-of-arrays plane per population, x fastest; the two
+// buffers hold the RELAXED populations p_rel(x, t).  One thread per node:
+//   1. pull p(x, t+1) = p_rel(x - e_a, t) for every plane (Eq. 1, 3, 5);
+//   2. boundary nodes replace the populations that come from solid nodes by
+//      their wall-link formulas (Sec. 3-4), evaluated from p_rel at A and E and
+//      the moments at t recovered from p_rel (mass, C and B are conserved by
+//      the relaxation, so sum_a p_rel = sum_a p);
+//   3. moments, equilibria (Eq. 2, 4, 6 with the magnetic stress), BGK
+//      relaxation with the Guo source, store p_rel(x, t+1) to the other buffer.
+// Every step is one launch over a flat list of node tiles of all cases.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "lattice.cuh"
+#include "types.cuh"
+
+#define LBM_DEV __device__ __forceinline__
+
+namespace lbm {
+
+// ------------------------------------------------------------------ storage
+template <class S> struct Codec;
+template <> struct Codec<double> {
+    using T = double;
+    static constexpr bool OFFSET = false;
+    LBM_DEV static double ld(const double *p) { return __ldg(p); }
+    LBM_DEV static void st(double *p, double v) { *p = v; }
+};
+template <> struct Codec<float> {
+    using T = float;
+    static constexpr bool OFFSET = false;
+    LBM_DEV static float ld(const float *p) { return __ldg(p); }
+    LBM_DEV static void st(float *p, float v) { *p = v; }
+};
+// 16-bit storage holds p - w_a * phi_ref, decoded to FP32 for all arithmetic.
+template <> struct Codec<__half> {
+    using T = float;
+    static constexpr bool OFFSET = true;
+    LBM_DEV static float ld(const __half *p) { return __half2float(__ldg(p)); }
+    LBM_DEV static void st(__half *p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Codec<__nv_bfloat16> {
+    using T = float;
+    static constexpr bool OFFSET = true;
+    LBM_DEV static float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    LBM_DEV static void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+template <class T>
+struct StepParams {
+    const void *src;
+    void *dst;
+    const uint8_t *flags;
+    const CaseDev<T> *cases;
+    const int2 *tiles;        // (case, first node) per tile of blockDim.x nodes
+    int32_t ntiles;
+    const BRec *brec;
+    const int32_t *brow;
+    const LinkDev<T> *links;
+};
+
+// storage offset w_q * ref(field of q) of plane q
+template <class PL, class S, class T>
+LBM_DEV T plane_off(int q, const CaseDev<T> &c) {
+    if constexpr (!Codec<S>::OFFSET) {
+        return T(0);
+    } else {
+        const int f = PL::field(q);
+        const T ref = f == 0 ? c.ref_rho : (f == 1 ? c.ref_C : c.ref_B[f - 2]);
+        return T(PL::w(q)) * ref;
+    }
+}
+
+// ------------------------------------------------------------------ equilibria
+// Eq. 2 plus the magnetic stress w/(2 cs^4) [1/2|B|^2 (|e|^2 - D cs^2) - ((e.B)^2 - cs^2 |B|^2)]
+template <class F, bool HG, class T>
+LBM_DEV T feq_dir(int a, T rho, const T (&u)[3], T usq, const T (&B)[3], T Bsq) {
+    const T ex = T(F::ex(a)), ey = T(F::ey(a)), ez = T(F::ez(a));
+    const T w = T(F::w(a));
+    const T eu = ex * u[0] + ey * u[1] + ez * u[2];
+    T feq = w * rho * (T(1) + T(3) * eu + T(4.5) * eu * eu - T(1.5) * usq);
+    if constexpr (HG) {
+        const T eB = ex * B[0] + ey * B[1] + ez * B[2];
+        const T ee = T(F::ex(a) * F::ex(a) + F::ey(a) * F::ey(a) + F::ez(a) * F::ez(a));
+        feq += w * T(4.5) * (T(0.5) * Bsq * (ee - T(F::DIM) / T(3)) - eB * eB + Bsq / T(3));
+    }
+    return feq;
+}
+// Eq. 4 with c_h^2 = 1/4
+template <class M, class T>
+LBM_DEV T heq_dir(int a, T C, const T (&u)[3]) {
+    const T eu = T(M::ex(a)) * u[0] + T(M::ey(a)) * u[1] + T(M::ez(a)) * u[2];
+    return T(M::w(a)) * C * (T(1) + T(4) * eu);
+}
+// Eq. 6, component k, with c_g^2 = 1/4
+template <class M, class T>
+LBM_DEV T geq_dir(int a, int k, const T (&B)[3], const T (&u)[3]) {
+    const T ex = T(M::ex(a)), ey = T(M::ey(a)), ez = T(M::ez(a));
+    const T eu = ex * u[0] + ey * u[1] + ez * u[2];
+    const T eB = ex * B[0] + ey * B[1] + ez * B[2];
+    return T(M::w(a)) * (B[k] + T(4) * (eu * B[k] - eB * u[k]));
+}
+
+// ------------------------------------------------------------------ collision
+// In place: p (populations at x, t) -> p_rel (Eq. 1, 3, 5).
+template <class PL, bool HH, bool HG, class T>
+LBM_DEV void collide(T (&p)[PL::P], const CaseDev<T> &c) {
+    using F = typename PL::F;
+    using M = typename PL::M;
+    constexpr int QF = PL::QF, QM = PL::QM, NB = PL::NB, DIM = F::DIM;
+    T rho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int a = 0; a < QF; ++a) {
+        rho += p[a];
+        if (F::ex(a)) jx += T(F::ex(a)) * p[a];
+        if (F::ey(a)) jy += T(F::ey(a)) * p[a];
+        if (F::ez(a)) jz += T(F::ez(a)) * p[a];
+    }
+    const T inv = T(1) / rho;
+    // Guo forcing: u = (sum e f + F/2) / rho with F = rho * accel
+    const T ux = jx * inv + T(0.5) * c.ax;
+    const T uy = jy * inv + T(0.5) * c.ay;
+    const T uz = DIM == 3 ? jz * inv + T(0.5) * c.az : T(0);
+    const T Fx = rho * c.ax, Fy = rho * c.ay, Fz = DIM == 3 ? rho * c.az : T(0);
+    const T usq = ux * ux + uy * uy + uz * uz;
+    T B[3] = {T(0), T(0), T(0)};
+    if constexpr (HG) {
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            T s = 0;
+#pragma unroll
+            for (int a = 0; a < QM; ++a) s += p[PL::G0 + k * QM + a];
+            B[k] = s;
+        }
+    }
+    const T Bsq = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const T u[3] = {ux, uy, uz};
+#pragma unroll
+    for (int a = 0; a < QF; ++a) {
+        const T ex = T(F::ex(a)), ey = T(F::ey(a)), ez = T(F::ez(a));
+        const T w = T(F::w(a));
+        const T feq = feq_dir<F, HG, T>(a, rho, u, usq, B, Bsq);
+        const T eu = ex * ux + ey * uy + ez * uz;
+        const T eF = ex * Fx + ey * Fy + ez * Fz;
+        // Guo source (1 - 1/(2 tau)) w [3 (e - u).F + 9 (e.u)(e.F)]
+        const T S = c.guo * w * (T(3) * ((ex - ux) * Fx + (ey - uy) * Fy + (ez - uz) * Fz) + T(9) * eu * eF);
+        p[a] = p[a] + c.om_f * (feq - p[a]) + S;
+    }
+    if constexpr (HH) {
+        T C = 0;
+#pragma unroll
+        for (int a = 0; a < QM; ++a) C += p[PL::H0 + a];
+#pragma unroll
+        for (int a = 0; a < QM; ++a)
+            p[PL::H0 + a] = p[PL::H0 + a] + c.om_h * (heq_dir<M, T>(a, C, u) - p[PL::H0 + a]);
+    }
+    if constexpr (HG) {
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+#pragma unroll
+            for (int a = 0; a < QM; ++a) {
+                const int q = PL::G0 + k * QM + a;
+                p[q] = p[q] + c.om_g * (geq_dir<M, T>(a, k, B, u) - p[q]);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ wall links
+template <class PL, class S, class T>
+LBM_DEV T field_sum(const S *src, int64_t stride, int q0, int nq, int node) {
+    T s = 0;
+    for (int j = 0; j < nq; ++j) s += Codec<S>::ld(src + (int64_t)(q0 + j) * stride + node);
+    return s;
+}
+
+template <class PL, class S, class T>
+LBM_DEV T eval_link(const LinkDev<T> &L, const S *src, const CaseDev<T> &c) {
+    const int64_t st = c.stride;
+    const T paA = Codec<S>::ld(src + (int64_t)L.plane_a * st + L.nodeA) + L.off_a;
+    const T papA = Codec<S>::ld(src + (int64_t)L.plane_ap * st + L.nodeA) + L.off_ap;
+    const T papE = Codec<S>::ld(src + (int64_t)L.plane_ap * st + L.nodeE) + L.off_ap;
+    T v = L.c0 + L.ca * paA + L.cap * papA + L.cape * papE;
+    if (L.flags & LINK_NEED_PHI) {
+        const int nq = L.phi_plane0 < PL::QF ? PL::QF : PL::QM;
+        const T phA = field_sum<PL, S, T>(src, st, L.phi_plane0, nq, L.nodeA) + L.ref_phi;
+        const T phE = field_sum<PL, S, T>(src, st, L.phi_plane0, nq, L.nodeE) + L.ref_phi;
+        v += L.cphi * ((T(1) + L.d) * phA - L.d * phE);
+    }
+    if constexpr (PL::G0 < PL::P) {
+        if (L.flags & LINK_NEED_B) {
+#pragma unroll
+            for (int k = 0; k < PL::NB; ++k) {
+                const int q0 = PL::G0 + k * PL::QM;
+                const T bA = field_sum<PL, S, T>(src, st, q0, PL::QM, L.nodeA) + c.ref_B[k];
+                const T bE = field_sum<PL, S, T>(src, st, q0, PL::QM, L.nodeE) + c.ref_B[k];
+                v += L.cB[k] * ((T(1) + L.d) * bA - L.d * bE);
+            }
+        }
+    }
+    return v;
+}
+
+// ------------------------------------------------------------------ fused step
+template <int DIM, bool HH, bool HG, class S>
+__global__ void __launch_bounds__(256) k_step(const StepParams<typename Codec<S>::T> prm) {
+    using PL = Planes<DIM, HH, HG>;
+    using T = typename Codec<S>::T;
+    constexpr int P = PL::P;
+    for (int t = blockIdx.x; t < prm.ntiles; t += gridDim.x) {
+        const int2 tile = prm.tiles[t];
+        const CaseDev<T> &c = prm.cases[tile.x];
+        const int n = tile.y + (int)threadIdx.x;
+        if (n >= c.N) continue;
+        const uint8_t fl = prm.flags[c.node_off + n];
+        if (!(fl & NODE_FLUID)) continue;
+        const S *src = static_cast<const S *>(prm.src) + c.pop_off;
+        S *dst = static_cast<S *>(prm.dst) + c.pop_off;
+        const int nx = c.nx, ny = c.ny;
+        const int x = n % nx;
+        const int r = n / nx;
+        const int y = r % ny;
+        const int z = r / ny;
+        // source node x - e_a with periodic wrap: index of x-1 is xi[0] (e_x = +1)
+        const int xi[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
+        const int yi[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};
+        int zi[3] = {0, 0, 0};
+        if constexpr (DIM == 3) {
+            const int nz = c.nz, nxy = nx * ny;
+            zi[0] = (z == 0 ? nz - 1 : z - 1) * nxy;
+            zi[1] = z * nxy;
+            zi[2] = (z == nz - 1 ? 0 : z + 1) * nxy;
+        }
+        T p[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int src_node = xi[1 - PL::ex(q)] + yi[1 - PL::ey(q)] + zi[1 - PL::ez(q)];
+            p[q] = Codec<S>::ld(src + (int64_t)q * c.stride + src_node) + plane_off<PL, S, T>(q, c);
+        }
+        if (fl & NODE_BOUNDARY) {
+            const int row = r;
+            int lo = prm.brow[c.brow_off + row];
+            const int hi0 = prm.brow[c.brow_off + row + 1];
+            int hi = hi0;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (prm.brec[mid].node < n) lo = mid + 1; else hi = mid;
+            }
+            if (lo < hi0 && prm.brec[lo].node == n) {
+                const BRec br = prm.brec[lo];
+                for (int li = br.lo; li < br.hi; ++li) {
+                    const LinkDev<T> L = prm.links[li];
+                    const T v = eval_link<PL, S, T>(L, src, c);
+                    // select per plane (an indexed store would move p to local memory)
+                    const int pa = L.plane_a;
+#pragma unroll
+                    for (int q = 0; q < P; ++q) p[q] = (q == pa) ? v : p[q];
+                }
+            }
+        }
+        collide<PL, HH, HG, T>(p, c);
+#pragma unroll
+        for (int q = 0; q < P; ++q)
+            Codec<S>::st(dst + (int64_t)q * c.stride + n, p[q] - plane_off<PL, S, T>(q, c));
+    }
+}
+
+// ------------------------------------------------------------------ initial state
+// Equilibrium (Eq. 2, 4, 6) of the given fields, relaxed once, stored as
+// p_rel(x, 0).  Fields are case-relative arrays (u, B as [N][3]); null means
+// the case defaults.  Solid nodes store zero.
+template <class T, class FT>
+struct InitParams {
+    void *dst;
+    const uint8_t *flags;
+    const CaseDev<T> *cases;
+    int32_t case_id;
+    const FT *rho, *u, *C, *B;
+    T rho0, C0, B0[3];
+};
+
+template <int DIM, bool HH, bool HG, class S, class FT>
+__global__ void __launch_bounds__(256) k_init(const InitParams<typename Codec<S>::T, FT> ip) {
+    using PL = Planes<DIM, HH, HG>;
+    using F = typename PL::F;
+    using M = typename PL::M;
+    using T = typename Codec<S>::T;
+    constexpr int P = PL::P;
+    const CaseDev<T> &c = ip.cases[ip.case_id];
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= c.N) return;
+    S *dst = static_cast<S *>(ip.dst) + c.pop_off;
+    if (!(ip.flags[c.node_off + n] & NODE_FLUID)) {
+#pragma unroll
+        for (int q = 0; q < P; ++q) Codec<S>::st(dst + (int64_t)q * c.stride + n, T(0));
+        return;
+    }
+    const T rho = ip.rho ? T(ip.rho[n]) : ip.rho0;
+    T u[3] = {T(0), T(0), T(0)}, B[3] = {ip.B0[0], ip.B0[1], ip.B0[2]};
+    if (ip.u) for (int k = 0; k < 3; ++k) u[k] = T(ip.u[3 * n + k]);
+    if (ip.B) for (int k = 0; k < 3; ++k) B[k] = T(ip.B[3 * n + k]);
+    if (DIM == 2) { u[2] = T(0); B[2] = T(0); }
+    const T C = ip.C ? T(ip.C[n]) : ip.C0;
+    T p[P];
+    const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const T Bsq = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+#pragma unroll
+    for (int a = 0; a < PL::QF; ++a) p[a] = feq_dir<F, HG, T>(a, rho, u, usq, B, Bsq);
+    if constexpr (HH) {
+#pragma unroll
+        for (int a = 0; a < PL::QM; ++a) p[PL::H0 + a] = heq_dir<M, T>(a, C, u);
+    }
+    if constexpr (HG) {
+#pragma unroll
+        for (int k = 0; k < PL::NB; ++k)
+#pragma unroll
+            for (int a = 0; a < PL::QM; ++a) p[PL::G0 + k * PL::QM + a] = geq_dir<M, T>(a, k, B, u);
+    }
+    collide<PL, HH, HG, T>(p, c);
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+        Codec<S>::st(dst + (int64_t)q * c.stride + n, p[q] - plane_off<PL, S, T>(q, c));
+}
+
+// ------------------------------------------------------------------ moments
+// Moments at the current time from the stored p_rel: rho = sum f_rel,
+// u = (sum e f_rel - F/2)/rho (the relaxation adds F/2 to the momentum),
+// C = sum h_rel, B = sum g_rel.
+template <class PL, class S, class T>
+LBM_DEV void node_moments(const S *src, int64_t stride, int n, const CaseDev<T> &c,
+                          T &rho, T (&u)[3], T &C, T (&B)[3], int &nonfinite) {
+    using F = typename PL::F;
+    rho = 0;
+    T j[3] = {T(0), T(0), T(0)};
+    nonfinite = 0;
+#pragma unroll
+    for (int a = 0; a < PL::QF; ++a) {
+        const T v = Codec<S>::ld(src + (int64_t)a * stride + n) + plane_off<PL, S, T>(a, c);
+        nonfinite += !isfinite(v);
+        rho += v;
+        j[0] += T(F::ex(a)) * v;
+        j[1] += T(F::ey(a)) * v;
+        j[2] += T(F::ez(a)) * v;
+    }
+    u[0] = j[0] / rho - T(0.5) * c.ax;
+    u[1] = j[1] / rho - T(0.5) * c.ay;
+    u[2] = F::DIM == 3 ? j[2] / rho - T(0.5) * c.az : T(0);
+    C = 0;
+    B[0] = B[1] = B[2] = T(0);
+    if constexpr (PL::G0 > PL::H0) {
+#pragma unroll
+        for (int a = 0; a < PL::QM; ++a) {
+            const T v = Codec<S>::ld(src + (int64_t)(PL::H0 + a) * stride + n) + plane_off<PL, S, T>(PL::H0 + a, c);
+            nonfinite += !isfinite(v);
+            C += v;
+        }
+    }
+    if constexpr (PL::P > PL::G0) {
+#pragma unroll
+        for (int k = 0; k < PL::NB; ++k)
+#pragma unroll
+            for (int a = 0; a < PL::QM; ++a) {
+                const int q = PL::G0 + k * PL::QM + a;
+                const T v = Codec<S>::ld(src + (int64_t)q * stride + n) + plane_off<PL, S, T>(q, c);
+                nonfinite += !isfinite(v);
+                B[k] += v;
+            }
+    }
+}
+
+template <class T>
+struct MomParams {
+    const void *src;
+    const uint8_t *flags;
+    const CaseDev<T> *cases;
+    int32_t case_id;
+    double *rho, *u, *C, *B;  // case-relative device outputs (u, B as [N][3])
+};
+
+template <int DIM, bool HH, bool HG, class S>
+__global__ void __launch_bounds__(256) k_moments(const MomParams<typename Codec<S>::T> mp) {
+    using PL = Planes<DIM, HH, HG>;
+    using T = typename Codec<S>::T;
+    const CaseDev<T> &c = mp.cases[mp.case_id];
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= c.N) return;
+    if (!(mp.flags[c.node_off + n] & NODE_FLUID)) {
+        mp.rho[n] = 0;
+        mp.C[n] = 0;
+        for (int k = 0; k < 3; ++k) { mp.u[3 * n + k] = 0; mp.B[3 * n + k] = 0; }
+        return;
+    }
+    T rho, u[3], C, B[3];
+    int nf;
+    node_moments<PL, S, T>(static_cast<const S *>(mp.src) + c.pop_off, c.stride, n, c, rho, u, C, B, nf);
+    mp.rho[n] = (double)rho;
+    mp.C[n] = (double)C;
+    for (int k = 0; k < 3; ++k) { mp.u[3 * n + k] = (double)u[k]; mp.B[3 * n + k] = (double)B[k]; }
+}
+
+// ------------------------------------------------------------------ FP64 reductions
+// One block per tile: partial sums (rho, C, Bx, By, Bz, non-finite count,
+// |phi - phi_prev|^2, |phi|^2) in FP64, written to part[tile][8]; the previous
+// phi = (u, C, B - B0) lives in snap[7][total nodes] (FP64) and is replaced.
+constexpr int RED_Q = 8;
+constexpr int SNAP_Q = 7;
+
+template <class T>
+struct RedParams {
+    const void *src;
+    const uint8_t *flags;
+    const CaseDev<T> *cases;
+    const int2 *tiles;
+    int32_t ntiles;
+    double *snap;
+    int64_t snap_stride;
+    double *part;             // [ntiles][RED_Q]
+};
+
+LBM_DEV double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int DIM, bool HH, bool HG, class S>
+__global__ void __launch_bounds__(256) k_reduce(const RedParams<typename Codec<S>::T> rp) {
+    using PL = Planes<DIM, HH, HG>;
+    using T = typename Codec<S>::T;
+    __shared__ double sh[RED_Q][32];
+    const int t = blockIdx.x;
+    const int2 tile = rp.tiles[t];
+    const CaseDev<T> &c = rp.cases[tile.x];
+    const int n = tile.y + (int)threadIdx.x;
+    double acc[RED_Q];
+#pragma unroll
+    for (int i = 0; i < RED_Q; ++i) acc[i] = 0.0;
+    if (n < c.N && (rp.flags[c.node_off + n] & NODE_FLUID)) {
+        T rho, u[3], C, B[3];
+        int nf;
+        node_moments<PL, S, T>(static_cast<const S *>(rp.src) + c.pop_off, c.stride, n, c, rho, u, C, B, nf);
+        acc[0] = rho;
+        acc[1] = C;
+        acc[2] = B[0];
+        acc[3] = B[1];
+        acc[4] = B[2];
+        acc[5] = nf;
+        const double phi[SNAP_Q] = {(double)u[0], (double)u[1], (double)u[2],
+                                    HH ? (double)C : 0.0,
+                                    HG ? (double)B[0] - (double)c.B0[0] : 0.0,
+                                    HG ? (double)B[1] - (double)c.B0[1] : 0.0,
+                                    HG ? (double)B[2] - (double)c.B0[2] : 0.0};
+        double *sp = rp.snap + c.node_off + n;
+#pragma unroll
+        for (int k = 0; k < SNAP_Q; ++k) {
+            const double old = sp[k * rp.snap_stride];
+            const double dd = phi[k] - old;
+            acc[6] += dd * dd;
+            acc[7] += phi[k] * phi[k];
+            sp[k * rp.snap_stride] = phi[k];
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < RED_Q; ++i) {
+        const double v = warp_sum(acc[i]);
+        if (lane == 0) sh[i][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < RED_Q) {
+        const int nw = (blockDim.x + 31) >> 5;
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += sh[threadIdx.x][w];
+        rp.part[(int64_t)t * RED_Q + threadIdx.x] = s;
+    }
+}
+
+// One block (256 threads) per case: sums the case's tile partials in a fixed
+// order (deterministic for a given tile list).
+inline __global__ void __launch_bounds__(256) k_reduce_final(const double *part, const int32_t *case_tile_lo,
+                                                             double *out) {
+    __shared__ double sh[256];
+    const int c = blockIdx.x;
+    const int lo = case_tile_lo[c], hi = case_tile_lo[c + 1];
+    for (int i = 0; i < RED_Q; ++i) {
+        double s = 0.0;
+        for (int t = lo + (int)threadIdx.x; t < hi; t += blockDim.x) s += part[(int64_t)t * RED_Q + i];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[c * RED_Q + i] = sh[0];
+        __syncthreads();
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,56 @@
+// types.cuh -- device-side records shared by the host driver and the kernels.
+#pragma once
+#include <cstdint>
+
+namespace lbm {
+
+// Per-case descriptor, one per domain, read warp-uniformly by every tile.
+template <class T>
+struct CaseDev {
+    int32_t nx, ny, nz, N;
+    int64_t pop_off;      // element offset of the case's first plane in a population buffer
+    int64_t stride;       // elements between consecutive planes of the case
+    int64_t node_off;     // offset of the case's nodes in the flag / snapshot arrays
+    int32_t brow_off;     // offset of the case's row table (ny*nz + 1 entries) in brow
+    int32_t pad0;
+    T om_f, om_h, om_g;   // 1/tau_nu, 1/tau_D, 1/tau_eta
+    T guo;                // 1 - 1/(2 tau_nu): weight of the Guo source
+    T ax, ay, az;         // body force per unit mass
+    T ref_rho, ref_C;     // 16-bit offset-storage references (0 for FP32/FP64 storage)
+    T ref_B[3];
+    T B0[3];              // B_ext for the residual (phi uses B - B0)
+};
+
+// Per-link record with the wall formula of the link folded into coefficients
+// (the host derives them from the link kind, d and the wall data):
+//   p_a(A, t+1) = c0 + ca p_a(A) + cap p_a'(A) + cape p_a'(E)
+//               + cphi phi_X + sum_j cB[j] B_X,j
+// with the relaxed populations at t, phi_X = -d phi(E) + (1 + d) phi(A)
+// (Eq. 13) of the link's own field (rho for f, C for h, B_k for g_k), and
+// B_X the extrapolated magnetic field vector (moving flux walls of g, Eq. 24).
+enum : uint8_t { LINK_NEED_PHI = 1, LINK_NEED_B = 2 };
+
+template <class T>
+struct alignas(16) LinkDev {
+    int32_t nodeA;        // case-relative node indices
+    int32_t nodeE;        // = nodeA when E is solid (then d = 1/2)
+    uint8_t plane_a;      // plane of the unknown direction a
+    uint8_t plane_ap;     // plane of the opposite direction a'
+    uint8_t phi_plane0;   // first plane of the link's field
+    uint8_t flags;        // LINK_NEED_PHI | LINK_NEED_B
+    T d, c0, ca, cap, cape, cphi;
+    T cB[3];
+    T off_a, off_ap;      // storage offsets w * ref of planes a and a' (16-bit storage)
+    T ref_phi;            // reference of the link's field (16-bit storage)
+};
+
+// Boundary record of a fluid node that owns links.
+struct BRec {
+    int32_t node;         // case-relative node index
+    int32_t lo, hi;       // link range [lo, hi) in the global link array
+    int32_t pad;
+};
+
+enum : uint8_t { NODE_FLUID = 1, NODE_BOUNDARY = 2 };
+
+}  // namespace lbm

@@ -54,3 +54,17 @@ def norm_rel(a, b):
     b = np.asarray(b, dtype=np.float64)
     den = np.abs(b).max()
     return np.abs(a - b).max() / (den if den > 0 else 1.0)
+
+
+def to_abi_links(orc_links):
+    """Copy oracle link records field by field into the C-ABI record layout."""
+    from paper_2506_00907_gb300 import lbm
+    out = np.zeros(len(orc_links), dtype=lbm.LINK_DTYPE)
+    for k in ("node", "field", "dir", "kind", "d", "u_wall", "phi_wall", "k0", "k1"):
+        out[k] = orc_links[k]
+    return out
+
+
+def sort_links(links):
+    order = np.lexsort((links["dir"], links["field"], links["node"]))
+    return links[order]

@@ -1,0 +1,280 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+FP64 storage must match the oracle within 1e-12 norm-relative per field
+(max|gpu - oracle| / max|oracle|).  FP32 and the 16-bit offset storages are
+held to the tolerances stated in each test (their rounding, not the scheme,
+sets them).  All inputs are seeded; links come from the oracle's builders."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import links as LK
+from paper_2506_00907_gb300 import inputs as IN
+from paper_2506_00907_gb300 import lbm
+from tests.helpers import norm_rel, to_abi_links
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+def _phys(has_h, has_g):
+    return lbm.LBM_FLOW | (lbm.LBM_CD if has_h else 0) | (lbm.LBM_MHD if has_g else 0)
+
+
+class Pair:
+    """The same case on the oracle and on the GPU."""
+
+    def __init__(self, dim, shape, solid, links, prec=lbm.LBM_FP64, taus=(0.8, 0.9, 0.7),
+                 accel=(0.0, 0.0, 0.0), has_h=False, has_g=False, fields=None, C0=1.0, B0=(0, 0, 0), threads=8):
+        self.dim, self.shape = dim, shape
+        self.N = shape[0] * shape[1] * shape[2]
+        self.fluid = np.asarray(solid).reshape(-1) == 0
+        self.orc = O.OracleSim(dim, shape, solid, taus[0], taus[1], taus[2], accel, has_h, has_g, threads)
+        self.orc.set_links(links)
+        f = fields or {}
+        self.orc.init(rho=f.get("rho"), u=f.get("u"), C=f.get("C"), B=f.get("B"), rho0=1.0, C0=C0, B0=B0)
+        case = lbm.make_case(shape, taus[0], taus[1], taus[2], accel, 1.0, C0, B0)
+        self.gpu = lbm.Solver(lbm.LBM_D2Q9 if dim == 2 else lbm.LBM_D3Q19, prec, _phys(has_h, has_g), [case])
+        self.gpu.set_walls(0, solid, to_abi_links(links))
+        if fields:
+            self.gpu.init_equilibrium(0, rho=f.get("rho"), u=f.get("u"), C=f.get("C"), B=f.get("B"))
+        self.has_h, self.has_g = has_h, has_g
+
+    def step(self, n):
+        self.orc.step(n)
+        self.gpu.step(n)
+
+    def errors(self):
+        a, b = self.gpu.moments(0), self.orc.moments()
+        fl = self.fluid
+        out = {"rho": norm_rel(a["rho"][fl], b["rho"][fl]), "u": norm_rel(a["u"][fl], b["u"][fl])}
+        if self.has_h:
+            out["C"] = norm_rel(a["C"][fl], b["C"][fl])
+        if self.has_g:
+            out["B"] = norm_rel(a["B"][fl], b["B"][fl])
+        return out
+
+
+def _random_pair(dim, has_h, has_g, seed, prec=lbm.LBM_FP64, shape=None):
+    r = IN.rng(seed)
+    shape = shape or ((37, 29, 1) if dim == 2 else (13, 11, 9))
+    solid = IN.random_solid(r, shape, fill=0.12)
+    links = LK.random_links(dim, shape, solid, r, has_h, has_g)
+    N = shape[0] * shape[1] * shape[2]
+    fields = IN.random_fields(r, N, dim, B0=(0.0, 0.3, 0.0))
+    accel = (1e-5, -2e-5, 5e-6 if dim == 3 else 0.0)
+    return Pair(dim, shape, solid, links, prec=prec, accel=accel, has_h=has_h, has_g=has_g, fields=fields,
+                C0=1.0, B0=(0.0, 0.3, 0.0))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("has_h,has_g", [(False, False), (True, False), (False, True), (True, True)])
+def test_fp64_random_geometry_all_link_kinds(dim, has_h, has_g):
+    """Random solids (ragged against the tile size, with E-solid links), every
+    wall-link kind with random d in (0, 1], moving walls, fluxes, body force."""
+    p = _random_pair(dim, has_h, has_g, seed=100 + 10 * dim + 2 * has_h + has_g)
+    p.step(1)
+    for k, v in p.errors().items():
+        assert v < FP64_TOL, (k, v)
+    p.step(39)
+    for k, v in p.errors().items():
+        assert v < FP64_TOL, (k, v)
+
+
+def test_fp64_poiseuille_64x32_5000_steps():
+    """Body-force channel, 64 x 32 nodes, tau = 0.8, half-grid walls, 5000
+    steps: the GPU matches the oracle and both match the analytic parabola to
+    the scheme's O(dx^2) slip."""
+    from oracle import analytic as AN
+    nx, ny, a = 64, 32, 1e-6
+    walls = LK.channel_y(2, nx, ny, 1, 0.5, 0.5)
+    solid = LK.box_solid((nx, ny, 1), walls)
+    links = LK.box_links(2, (nx, ny, 1), walls, {(1, 0, O.F): dict(kind=O.VELOCITY),
+                                                  (1, 1, O.F): dict(kind=O.VELOCITY)})
+    p = Pair(2, (nx, ny, 1), solid, links, accel=(a, 0, 0))
+    p.step(5000)
+    e = p.errors()
+    assert e["u"] < FP64_TOL and e["rho"] < FP64_TOL
+    u = p.gpu.moments(0)["u"][:, 0].reshape(ny, nx)[1:-1, 0]
+    ua = AN.poiseuille(np.arange(ny)[1:-1], walls[1][0], walls[1][1], a, 0.1)
+    # 5000 steps is about 0.5 H^2/nu: the profile is still developing; its shape is parabolic
+    c = np.polyfit(np.arange(ny)[1:-1], u, 2)
+    assert np.abs(u - np.polyval(c, np.arange(ny)[1:-1])).max() < 0.05 * u.max()
+    assert 0.1 < u.max() / ua.max() < 1.0
+
+
+def _hartmann_links(W, q, cw, Ha, tau=0.8, taue=0.9):
+    nu, eta = (tau - 0.5) / 3, (taue - 0.5) / 4
+    d = 1.0 - q
+    ny = W + 2
+    walls = LK.channel_y(2, W, ny, 1, d, d)
+    H = (walls[1][1] - walls[1][0]) / 2
+    B0 = Ha * math.sqrt(nu * eta) / H
+    b1 = dict(kind=O.FLUX, kappa1=-eta / (cw * H))
+    p = {(1, s, O.F): dict(kind=O.VELOCITY) for s in (0, 1)}
+    p.update({(1, s, O.G0): b1 for s in (0, 1)})
+    p.update({(1, s, O.G0 + 1): dict(kind=O.GIVEN, phi_wall=B0) for s in (0, 1)})
+    shape = (W, ny, 1)
+    return shape, LK.box_solid(shape, walls), LK.box_links(2, shape, walls, p, has_g=True), B0
+
+
+def test_fp64_batched_uneven_cases():
+    """Several uneven Hartmann channels (different width, Ha, q, c_w) advanced
+    by one launch per step; each matches its own oracle run."""
+    draws = [dict(W=20, q=0.3, cw=0.05, Ha=4.0), dict(W=33, q=0.0, cw=1.0, Ha=12.0),
+             dict(W=9, q=0.75, cw=0.5, Ha=1.5), dict(W=64, q=0.5, cw=0.2, Ha=25.0)]
+    cases, orcs, geo = [], [], []
+    for i, dr in enumerate(draws):
+        shape, solid, links, B0 = _hartmann_links(dr["W"], dr["q"], dr["cw"], dr["Ha"])
+        acc = (1e-6 * (i + 1), 0.0, 0.0)
+        o = O.OracleSim(2, shape, solid, 0.8, 1.0, 0.9, acc, False, True, 4)
+        o.set_links(links)
+        o.init(B0=(0, B0, 0))
+        orcs.append(o)
+        cases.append(lbm.make_case(shape, 0.8, 1.0, 0.9, acc, 1.0, 0.0, (0, B0, 0)))
+        geo.append((solid, links))
+    g = lbm.Solver(lbm.LBM_D2Q9, lbm.LBM_FP64, lbm.LBM_FLOW | lbm.LBM_MHD, cases)
+    for i, (solid, links) in enumerate(geo):
+        g.set_walls(i, solid, to_abi_links(links))
+    g.set_graph(4)
+    g.step(60)
+    for o in orcs:
+        o.step(60)
+    for i, o in enumerate(orcs):
+        a, b = g.moments(i), o.moments()
+        fl = geo[i][0].reshape(-1) == 0
+        assert norm_rel(a["u"][fl], b["u"][fl]) < FP64_TOL
+        assert norm_rel(a["B"][fl], b["B"][fl]) < FP64_TOL
+
+
+@pytest.mark.parametrize("prec,tol_u,tol_B", [(lbm.LBM_FP32, 2e-5, 2e-6), (lbm.LBM_FP16S, 3e-2, 5e-3),
+                                              (lbm.LBM_BF16S, 2e-1, 4e-2)])
+def test_reduced_precision_against_fp64_oracle(prec, tol_u, tol_B):
+    """Hartmann channel, 300 steps from rest: FP32 arithmetic and storage,
+    and FP32 arithmetic with 16-bit offset storage, against the FP64 oracle.
+    The tolerances are the rounding of each storage format (FP32 ~ 6e-8,
+    FP16 ~ 5e-4, BF16 ~ 4e-3 per stored value relative to the offsets)
+    carried through the steps, relative to max|u| and max|B|."""
+    shape, solid, links, B0 = _hartmann_links(48, 0.3, 0.1, 8.0)
+    p = Pair(2, shape, solid, links, prec=prec, taus=(0.8, 1.0, 0.9), accel=(2e-6, 0, 0), has_g=True,
+             B0=(0, B0, 0))
+    p.step(300)
+    e = p.errors()
+    assert e["u"] < tol_u, e
+    assert e["B"] < tol_B, e
+
+
+def test_checkpoint_restore_and_graph_are_bitwise():
+    """2N steps equal N + save + restore (fresh context) + N, and graph replay
+    equals plain launches, bit for bit (FP32)."""
+    def make():
+        p = _random_pair(2, True, True, seed=7, prec=lbm.LBM_FP32)
+        return p.gpu
+    a = make()
+    a.step(24)
+    ref = a.get_state()
+    b = make()
+    b.step(12)
+    blob = b.get_state()
+    c = make()
+    c.set_state(blob)
+    c.step(12)
+    assert np.array_equal(c.get_state()[16:], ref[16:])
+    d = make()
+    d.set_graph(4)
+    d.step(24)
+    assert np.array_equal(d.get_state()[16:], ref[16:])
+    assert d.steps == 24
+
+
+def test_fp64_reductions_match_oracle():
+    """lbm_check: FP64 sums of rho, C and B over fluid nodes match the oracle;
+    the residual numerator is the squared change of (u, C, B - B0)."""
+    p = _random_pair(3, True, True, seed=31)
+    p.gpu.check()
+    p.step(5)
+    out = p.gpu.check()[0]
+    s = p.orc.sums()
+    assert abs(out[0] - s[0]) < 1e-12 * abs(s[0])
+    assert abs(out[1] - s[1]) < 1e-12 * abs(s[1])
+    assert np.abs(out[2:5] - s[2:5]).max() < 1e-11 * max(1.0, np.abs(s[2:5]).max())
+    assert out[5] == 0
+    m0 = p.orc.moments()
+    p.step(3)
+    out = p.gpu.check()[0]
+    m1 = p.orc.moments()
+    fl = p.fluid
+    phi0 = np.concatenate([m0["u"][fl], m0["C"][fl, None], m0["B"][fl] - [0, 0.3, 0]], axis=1)
+    phi1 = np.concatenate([m1["u"][fl], m1["C"][fl, None], m1["B"][fl] - [0, 0.3, 0]], axis=1)
+    assert abs(out[6] - np.sum((phi1 - phi0) ** 2)) < 1e-9 * np.sum((phi1 - phi0) ** 2)
+    assert abs(out[7] - np.sum(phi1 ** 2)) < 1e-12 * np.sum(phi1 ** 2)
+
+
+def test_nonfinite_population_is_reported():
+    """A NaN planted in the initial field is found by the FP64 check
+    (LBM_EUNSTABLE) without any device fault."""
+    shape, solid, links, B0 = _hartmann_links(16, 0.5, 0.5, 3.0)
+    case = lbm.make_case(shape, 0.8, 1.0, 0.9, (0, 0, 0), 1.0, 0.0, (0, B0, 0))
+    g = lbm.Solver(lbm.LBM_D2Q9, lbm.LBM_FP32, lbm.LBM_FLOW | lbm.LBM_MHD, [case])
+    g.set_walls(0, solid, to_abi_links(links))
+    N = shape[0] * shape[1]
+    rho = np.ones(N)
+    rho[N // 2] = np.nan
+    g.init_equilibrium(0, rho=rho)
+    g.step(3)
+    with pytest.raises(lbm.LbmError) as ei:
+        g.check()
+    assert ei.value.status == lbm.LBM_EUNSTABLE
+    out = g.check(raise_unstable=False)
+    assert out[0, 5] > 0
+
+
+def test_invalid_link_lists_are_rejected():
+    shape, solid, links, B0 = _hartmann_links(10, 0.5, 0.5, 3.0)
+    case = lbm.make_case(shape, 0.8, 1.0, 0.9, (0, 0, 0), 1.0, 0.0, (0, B0, 0))
+    g = lbm.Solver(lbm.LBM_D2Q9, lbm.LBM_FP32, lbm.LBM_FLOW | lbm.LBM_MHD, [case])
+    good = to_abi_links(links)
+    bad = []
+    x = good.copy(); x["d"][3] = 0.0; bad.append(x)                    # d outside (0, 1]
+    x = good.copy(); x["d"][3] = 1.5; bad.append(x)
+    bad.append(good[1:])                                                # missing link
+    bad.append(np.concatenate([good, good[:1]]))                        # duplicate
+    x = good.copy(); x["kind"][np.flatnonzero(good["field"] == 0)[0]] = lbm.LBM_W_GIVEN; bad.append(x)
+    x = good.copy(); x["node"][0] = 0; bad.append(x)                    # node 0 is solid
+    x = good.copy(); x["field"][0] = 1; bad.append(x)                   # CD not enabled
+    for b in bad:
+        with pytest.raises(lbm.LbmError) as ei:
+            g.set_walls(0, solid, b)
+        assert ei.value.status == lbm.LBM_EINVAL
+    g.set_walls(0, solid, good)
+    with pytest.raises(lbm.LbmError):
+        lbm.Solver(lbm.LBM_D2Q9, lbm.LBM_FP32, lbm.LBM_FLOW, [lbm.make_case((8, 8, 1), 0.5)])
+
+
+def test_fully_periodic_domain_and_single_node_axes():
+    """No walls at all (empty link list) and nx = 1 axes: the step reduces to
+    the bulk update; FP64 parity with the oracle."""
+    for shape in ((1, 17, 1), (5, 1, 1)):
+        N = shape[0] * shape[1]
+        r = IN.rng(5)
+        solid = np.zeros(N, dtype=np.uint8)
+        fields = IN.random_fields(r, N, 2)
+        p = Pair(2, shape, solid, np.zeros(0, O.LINK_DTYPE), accel=(1e-5, 0, 0), has_h=True, fields=fields)
+        p.step(25)
+        for k, v in p.errors().items():
+            assert v < FP64_TOL, (shape, k, v)
+
+
+def test_autotune_keeps_solution():
+    p = _random_pair(3, False, True, seed=9, prec=lbm.LBM_FP32, shape=(24, 20, 18))
+    p.gpu.step(3)
+    before = p.gpu.get_state()
+    block, bpsm, ms = p.gpu.autotune(None, iters=3)
+    assert block in (64, 128, 192, 256) and ms > 0
+    after = p.gpu.get_state()
+    assert np.array_equal(before, after)
+    p.gpu.step(2)   # still runs with the chosen launch shape
