@@ -351,7 +351,8 @@ def run_ours(args):
                 "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": wl["desc"], "storage": wl["storage"], "cases": len(wl["cases"]),
-                           "fluid_nodes": fluid, "launch": {"block": tune[0], "blocks_per_sm": tune[1]} if tune else None,
+                           "fluid_nodes": fluid, "launch": {"variant": ["one thread per node", "bulk-copy pipeline"][tune[0]], "block": tune[1],
+                                      "param": tune[2]} if tune else None,
                            "graph_steps": CHECK_EVERY, "reduction_every": CHECK_EVERY,
                            "l2": "state %.0f MB > 129 MB L2, no flush" % (2 * wl["planes"] * elem * fluid / 1e6),
                            "stable": stable},

@@ -52,8 +52,10 @@ typedef enum {
 
 typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
 
-/* Storage precision of the populations.  FP64 and FP32 store p; FP16S and
- * BF16S store the offset p - w_a * phi_ref in 16 bits and compute in FP32. */
+/* Storage precision of the populations.  Every precision stores the shifted
+ * value p - w_a * phi_ref (phi_ref = rho0, C0 or B0_k of the case), which keeps
+ * the small deviations that carry the solution resolvable; FP16S and BF16S
+ * store it in 16 bits and compute in FP32, FP32 in FP32, FP64 in FP64. */
 typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16S = 2, LBM_BF16S = 3 } lbm_prec;
 
 /* physics mask: LBM_FLOW is required */
@@ -170,7 +172,8 @@ lbm_status lbm_moments(lbm_ctx *ctx, int32_t case_id, double *rho, double *u,
  * the value at the previous call (the first call compares with zero).  The
  * reduction is deterministic (fixed order).  out: host, 8*ncases doubles.
  * Synchronises.  Returns LBM_EUNSTABLE (after filling out) if any population
- * is not finite.  Errors: LBM_ECUDA. */
+ * is not finite, LBM_ETIMEOUT if a bounded device wait of an earlier step
+ * gave up.  Errors: LBM_ECUDA. */
 lbm_status lbm_check(lbm_ctx *ctx, double *out);
 
 /* Step until every case's relative residual sqrt(sum|phi-phi_prev|^2 / sum|phi|^2)
@@ -190,28 +193,35 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes);
 /* Number of steps taken since creation (or the restored state). */
 int64_t lbm_steps_done(const lbm_ctx *ctx);
 
-/* Launch shape of the fused step: threads per block (64..1024, multiple of 32)
- * and blocks per SM for the persistent tile loop (0 = one block per tile).
- * Errors: LBM_EINVAL. */
-lbm_status lbm_set_launch(lbm_ctx *ctx, int32_t block, int32_t blocks_per_sm);
+/* Launch shape of the fused step.
+ *   variant 0: one thread per node, blocks of `block` threads over tiles of
+ *              `block` nodes; param = resident blocks per SM of a persistent
+ *              tile loop (0 = one block per tile, 1..64).
+ *   variant 1: bulk-copy pipeline (FP32 and 16-bit storage): persistent
+ *              blocks stage the next tile's source windows in shared memory
+ *              with cp.async.bulk while computing the current tile; param =
+ *              nodes per thread (1..8), tile = block * param nodes.
+ * block: 64..256, multiple of 32.  Errors: LBM_EINVAL (out of range, or the
+ * pipeline's shared memory does not fit), LBM_ECUDA. */
+lbm_status lbm_set_launch(lbm_ctx *ctx, int32_t variant, int32_t block, int32_t param);
 
 /* Autotuner: times the fused step for every candidate launch shape on this
- * context (each candidate `iters` steps after one warm-up, CUDA events),
- * keeps the fastest, and records it in the text cache file `cache_path`
- * (NULL = no cache) keyed by GPU name, lattice, precision, physics and case
- * sizes; a later call with the same key reads the cache instead of timing.
- * The context's populations are saved and restored around the timing.
- * best_ms (may be NULL) receives the time per step of the choice.
- * Errors: LBM_ECUDA. */
-lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters,
-                        int32_t *block, int32_t *blocks_per_sm, double *best_ms);
+ * context (each candidate `iters` steps after two warm-up steps, CUDA
+ * events), keeps the fastest, and records it in the text cache file
+ * `cache_path` (NULL = no cache) keyed by GPU name, lattice, precision,
+ * physics and case sizes; a later call with the same key reads the cache
+ * instead of timing.  The context's populations and step count are saved and
+ * restored around the timing.  Outputs may be NULL.  Errors: LBM_ECUDA. */
+lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, int32_t *variant,
+                        int32_t *block, int32_t *param, double *best_ms);
 
 /* Kernel launches issued per lbm_step step (for launch accounting). */
 int32_t lbm_launches_per_step(const lbm_ctx *ctx);
 
 /* Device storage of the current populations (for zero-copy inspection):
  * base pointer, bytes per population, plane stride in elements and element
- * offset of case_id's first plane.  Errors: LBM_EINVAL. */
+ * offset of case_id's first plane.  Planes hold the relaxed populations
+ * shifted by w_a * phi_ref.  Errors: LBM_EINVAL. */
 lbm_status lbm_device_state(lbm_ctx *ctx, int32_t case_id, void **base, int32_t *elem_bytes,
                             int64_t *plane_stride, int64_t *case_offset, int32_t *planes);
 

@@ -225,10 +225,11 @@ def pipe_links(shape, R, params, has_g=True, center=None):
 # ---------------------------------------------------------------------------
 # Random links for parity fuzzing
 # ---------------------------------------------------------------------------
-def random_links(dim, shape, solid, rng, has_h=False, has_g=False, kinds=None):
+def random_links(dim, shape, solid, rng, has_h=False, has_g=False, kinds=None, phi_range=None):
     """Every required link of a given solid mask, with kind, d and wall data
     drawn from ``rng`` (numpy Generator).  d in (0, 1]; both branches of every
-    scheme occur."""
+    scheme occur.  phi_range maps a field to the (lo, hi) range of its given
+    wall values (default (-0.5, 1.5))."""
     nx, ny, nz = shape
     solid3 = np.asarray(solid, dtype=np.uint8).reshape(nz, ny, nx)
     out = []
@@ -248,7 +249,8 @@ def random_links(dim, shape, solid, rng, has_h=False, has_g=False, kinds=None):
             if dim == 2:
                 uw[:, 2] = 0.0
             r["u_wall"] = uw
-            r["phi_wall"] = rng.uniform(-0.5, 1.5, m)
+            lo, hi = (phi_range or {}).get(field, (-0.5, 1.5))
+            r["phi_wall"] = rng.uniform(lo, hi, m)
             r["k0"] = rng.uniform(-0.01, 0.01, m)
             r["k1"] = rng.uniform(-0.05, 0.0, m)
             out.append(r)

@@ -39,7 +39,9 @@ def build(force=False, verbose=False):
         o = os.path.join(OUT, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or _stale(o, [s] + heads):
-            jobs.append([nvcc] + ARCH + FLAGS + ["-c", s, "-o", o])
+            # the FP64 variants serve parity with the FP64 oracle: no FMA contraction
+            extra = ["-fmad=false"] if s.endswith("_f64.cu") else []
+            jobs.append([nvcc] + ARCH + FLAGS + extra + ["-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -67,7 +67,10 @@ struct lbm_ctx {
     int cur = 0;
     uint8_t *d_flags = nullptr;
     void *d_cases = nullptr;
-    int block = 256, bpsm = 0;
+    int variant = 0, block = 256, param = 0;   // see lbm_set_launch
+    int tile_nodes = 256, tma_grid = 0;
+    size_t tma_smem = 0;
+    int32_t *d_err = nullptr;
     int2 *d_tiles = nullptr;
     int32_t ntiles = 0;
     int32_t *d_case_tile_lo = nullptr;
@@ -127,9 +130,22 @@ int64_t wrap_node(const CaseHost &cs, int64_t n, const int e[3], int sign) {
     return x + (int64_t)nx * (y + (int64_t)ny * z);
 }
 
+// magic numbers of q = (umulhi(n, m) + n) >> s = floor(n / d) for n < 2^31
+FastDiv fast_div_of(uint32_t d) {
+    uint32_t s = 0;
+    while ((1ull << s) < d) ++s;
+    const unsigned __int128 num = ((unsigned __int128)1 << 32) * (((uint64_t)1 << s) - d);
+    FastDiv f;
+    f.m = (uint32_t)(num / d + 1);
+    f.s = s;
+    return f;
+}
+
 template <class T>
 CaseDev<T> case_dev(const lbm_ctx *c, const CaseHost &cs) {
     CaseDev<T> d{};
+    d.div_nx = fast_div_of((uint32_t)cs.cfg.nx);
+    d.div_ny = fast_div_of((uint32_t)cs.cfg.ny);
     d.nx = cs.cfg.nx;
     d.ny = cs.cfg.ny;
     d.nz = cs.cfg.nz;
@@ -145,10 +161,11 @@ CaseDev<T> case_dev(const lbm_ctx *c, const CaseHost &cs) {
     d.ax = T(cs.cfg.accel[0]);
     d.ay = T(cs.cfg.accel[1]);
     d.az = c->dim == 3 ? T(cs.cfg.accel[2]) : T(0);
-    d.ref_rho = c->offset ? T(cs.cfg.rho0) : T(0);
-    d.ref_C = c->offset ? T(cs.cfg.C0) : T(0);
+    // every precision stores p - w_a phi_ref
+    d.ref_rho = T(cs.cfg.rho0);
+    d.ref_C = c->hh ? T(cs.cfg.C0) : T(0);
     for (int k = 0; k < 3; ++k) {
-        d.ref_B[k] = c->offset ? T(cs.cfg.B0[k]) : T(0);
+        d.ref_B[k] = c->hg ? T(cs.cfg.B0[k]) : T(0);
         d.B0[k] = T(cs.cfg.B0[k]);
     }
     if (c->dim == 2) { d.ref_B[2] = T(0); d.B0[2] = T(0); }
@@ -223,16 +240,15 @@ LinkDev<T> link_dev(const lbm_ctx *c, const CaseHost &cs, const lbm_link &lk) {
     r.flags = (uint8_t)((cphi != 0.0 ? LINK_NEED_PHI : 0) |
                         ((cB[0] != 0.0 || cB[1] != 0.0 || cB[2] != 0.0) ? LINK_NEED_B : 0));
     r.d = T(d);
-    r.c0 = T(c0);
     r.ca = T(ca);
     r.cap = T(cap);
     r.cape = T(cape);
     r.cphi = T(cphi);
     for (int j = 0; j < 3; ++j) r.cB[j] = T(cB[j]);
-    double ref = 0.0;
-    if (c->offset) ref = lk.field == 0 ? cs.cfg.rho0 : (lk.field == 1 ? cs.cfg.C0 : cs.cfg.B0[lk.field - 2]);
-    r.off_a = T(w * ref);
-    r.off_ap = T(w * ref);
+    // the planes store s = p - w phi_ref (w_a = w_a'): the formula on s gains
+    // the constant (ca + cap + cape - 1) w phi_ref
+    const double ref = lk.field == 0 ? cs.cfg.rho0 : (lk.field == 1 ? cs.cfg.C0 : cs.cfg.B0[lk.field - 2]);
+    r.c0 = T(c0 + (ca + cap + cape - 1.0) * w * ref);
     r.ref_phi = T(ref);
     return r;
 }
@@ -262,7 +278,7 @@ lbm_status build_tiles(lbm_ctx *ctx) {
     std::vector<int32_t> lo;
     for (size_t c = 0; c < ctx->cases.size(); ++c) {
         lo.push_back((int32_t)tiles.size());
-        for (int32_t s = 0; s < ctx->cases[c].N; s += ctx->block) tiles.push_back(make_int2((int)c, s));
+        for (int32_t s = 0; s < ctx->cases[c].N; s += ctx->tile_nodes) tiles.push_back(make_int2((int)c, s));
     }
     lo.push_back((int32_t)tiles.size());
     if (ctx->d_tiles) cudaFree(ctx->d_tiles);
@@ -358,19 +374,27 @@ StepParams<T> step_params(const lbm_ctx *c) {
 }
 
 int step_grid(const lbm_ctx *c) {
-    if (c->bpsm <= 0) return c->ntiles;
-    return std::max(1, std::min(c->ntiles, c->bpsm * c->sm_count));
+    if (c->variant == 1) return std::max(1, std::min(c->ntiles, c->tma_grid));
+    if (c->param <= 0) return c->ntiles;
+    return std::max(1, std::min(c->ntiles, c->param * c->sm_count));
+}
+
+template <class T>
+cudaError_t launch_step_t(lbm_ctx *ctx) {
+    const StepParams<T> p = step_params<T>(ctx);
+    if (ctx->variant == 1) {
+        TmaParams tp;
+        tp.tile_nodes = ctx->tile_nodes;
+        const int A = 16 / (int)ctx->elem;
+        tp.cap = ctx->tile_nodes + 2 * A;
+        tp.err = ctx->d_err;
+        return ctx->ks.step_tma(&p, tp, step_grid(ctx), ctx->block, ctx->tma_smem, ctx->stream);
+    }
+    return ctx->ks.step(&p, step_grid(ctx), ctx->block, ctx->stream);
 }
 
 lbm_status launch_step(lbm_ctx *ctx) {
-    cudaError_t e;
-    if (ctx->dbl) {
-        const StepParams<double> p = step_params<double>(ctx);
-        e = ctx->ks.step(&p, step_grid(ctx), ctx->block, ctx->stream);
-    } else {
-        const StepParams<float> p = step_params<float>(ctx);
-        e = ctx->ks.step(&p, step_grid(ctx), ctx->block, ctx->stream);
-    }
+    const cudaError_t e = ctx->dbl ? launch_step_t<double>(ctx) : launch_step_t<float>(ctx);
     if (e != cudaSuccess) return fail(ctx, LBM_ECUDA, "step launch: %s", cudaGetErrorString(e));
     ctx->cur ^= 1;
     return LBM_OK;
@@ -434,7 +458,7 @@ void free_ctx(lbm_ctx *c) {
     if (!c) return;
     drop_graphs(c);
     void *ptrs[] = {c->pool[0], c->pool[1], c->d_flags, c->d_cases, c->d_tiles, c->d_case_tile_lo,
-                    c->d_brec, c->d_brow, c->d_links, c->d_snap, c->d_part, c->d_red, c->d_mom};
+                    c->d_brec, c->d_brow, c->d_links, c->d_snap, c->d_part, c->d_red, c->d_mom, c->d_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_red) cudaFreeHost(c->h_red);
@@ -544,6 +568,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
     ck(cudaMalloc(&ctx->d_red, ctx->cases.size() * RED_Q * sizeof(double)), "reduction output");
     ck(cudaMallocHost(&ctx->h_red, ctx->cases.size() * RED_Q * sizeof(double)), "pinned reduction output");
     ck(cudaMalloc(&ctx->d_mom, (size_t)ctx->max_case_nodes * 8 * sizeof(double)), "moment scratch");
+    ck(cudaMalloc(&ctx->d_err, sizeof(int32_t)), "error word");
+    if (st == LBM_OK) ck(cudaMemset(ctx->d_err, 0, sizeof(int32_t)), "memset");
     if (st == LBM_OK) st = build_tiles(ctx);
     if (st == LBM_OK) st = upload_walls(ctx);
     for (int c = 0; st == LBM_OK && c < (int)ctx->cases.size(); ++c)
@@ -704,19 +730,22 @@ lbm_status lbm_check(lbm_ctx *ctx, double *out) {
     if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (ctx->dbl) {
         RedParams<double> rp{ctx->pool[ctx->cur], ctx->d_flags, static_cast<const CaseDev<double> *>(ctx->d_cases),
-                             ctx->d_tiles, ctx->ntiles, ctx->d_snap, ctx->total_nodes, ctx->d_part};
-        CK(ctx->ks.reduce(&rp, ctx->ntiles, ctx->block, ctx->stream));
+                             ctx->d_tiles, ctx->ntiles, ctx->tile_nodes, ctx->d_snap, ctx->total_nodes, ctx->d_part};
+        CK(ctx->ks.reduce(&rp, ctx->ntiles, 256, ctx->stream));
     } else {
         RedParams<float> rp{ctx->pool[ctx->cur], ctx->d_flags, static_cast<const CaseDev<float> *>(ctx->d_cases),
-                            ctx->d_tiles, ctx->ntiles, ctx->d_snap, ctx->total_nodes, ctx->d_part};
-        CK(ctx->ks.reduce(&rp, ctx->ntiles, ctx->block, ctx->stream));
+                            ctx->d_tiles, ctx->ntiles, ctx->tile_nodes, ctx->d_snap, ctx->total_nodes, ctx->d_part};
+        CK(ctx->ks.reduce(&rp, ctx->ntiles, 256, ctx->stream));
     }
     k_reduce_final<<<(int)ctx->cases.size(), 256, 0, ctx->stream>>>(ctx->d_part, ctx->d_case_tile_lo, ctx->d_red);
     CK(cudaGetLastError());
     const size_t bytes = ctx->cases.size() * RED_Q * sizeof(double);
     CK(cudaMemcpyAsync(ctx->h_red, ctx->d_red, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    int32_t err = 0;
+    CK(cudaMemcpyAsync(&err, ctx->d_err, sizeof(err), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     if (out) std::memcpy(out, ctx->h_red, bytes);
+    if (err) return fail(ctx, LBM_ETIMEOUT, "a bounded device wait gave up (code %d)", err);
     for (size_t c = 0; c < ctx->cases.size(); ++c)
         if (ctx->h_red[c * RED_Q + 5] != 0.0)
             return fail(ctx, LBM_EUNSTABLE, "case %zu: %g non-finite populations", c, ctx->h_red[c * RED_Q + 5]);
@@ -780,13 +809,34 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes) {
 
 int64_t lbm_steps_done(const lbm_ctx *ctx) { return ctx ? ctx->steps : 0; }
 
-lbm_status lbm_set_launch(lbm_ctx *ctx, int32_t block, int32_t blocks_per_sm) {
+lbm_status lbm_set_launch(lbm_ctx *ctx, int32_t variant, int32_t block, int32_t param) {
     if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
-    if (block < 64 || block > 256 || block % 32 || blocks_per_sm < 0 || blocks_per_sm > 64)
-        return fail(ctx, LBM_EINVAL, "block must be 64..256 in steps of 32, blocks_per_sm 0..64");
-    ctx->bpsm = blocks_per_sm;
-    if (block != ctx->block) {
-        ctx->block = block;
+    if (variant < 0 || variant > 1 || block < 64 || block > 256 || block % 32)
+        return fail(ctx, LBM_EINVAL, "variant must be 0 or 1 and block 64..256 in steps of 32");
+    int tile = block;
+    if (variant == 0) {
+        if (param < 0 || param > 64) return fail(ctx, LBM_EINVAL, "blocks per SM must be 0..64");
+    } else {
+        if (param < 1 || param > 8) return fail(ctx, LBM_EINVAL, "nodes per thread must be 1..8");
+        if (ctx->dbl) return fail(ctx, LBM_EINVAL, "the bulk-copy pipeline serves FP32 and 16-bit storage");
+        tile = block * param;
+        const int A = 16 / (int)ctx->elem;
+        const size_t smem = (size_t)tma_header_bytes(ctx->P) + 2 * (size_t)ctx->P * (tile + 2 * A) * ctx->elem;
+        int maxsm = 0;
+        CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->cfg.device));
+        if (smem > (size_t)maxsm) return fail(ctx, LBM_EINVAL, "tile of %d nodes needs %zu B of shared memory", tile, smem);
+        CK(cudaFuncSetAttribute(ctx->ks.step_tma_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ctx->ks.step_tma_fn, block, smem));
+        if (per_sm < 1) return fail(ctx, LBM_EINVAL, "the pipeline does not fit on an SM");
+        ctx->tma_smem = smem;
+        ctx->tma_grid = per_sm * ctx->sm_count;
+    }
+    ctx->variant = variant;
+    ctx->param = param;
+    ctx->block = block;
+    if (tile != ctx->tile_nodes) {
+        ctx->tile_nodes = tile;
         return build_tiles(ctx);
     }
     drop_graphs(ctx);
@@ -808,14 +858,14 @@ lbm_status lbm_device_state(lbm_ctx *ctx, int32_t case_id, void **base, int32_t 
 }
 
 // ----------------------------------------------------------------------------- autotuner
-lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, int32_t *block_out, int32_t *bpsm_out,
-                        double *best_ms) {
+lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, int32_t *variant_out,
+                        int32_t *block_out, int32_t *param_out, double *best_ms) {
     if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (iters < 1) iters = 20;
     cudaDeviceProp prop{};
     CK(cudaGetDeviceProperties(&prop, ctx->cfg.device));
     std::ostringstream key;
-    key << prop.name << "|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
+    key << prop.name << "|v2|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
         << ctx->cases.size();
     int64_t tot = 0;
     for (auto &c : ctx->cases) tot += c.N;
@@ -829,13 +879,14 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, int
         while (std::getline(in, line)) {
             std::istringstream ls(line);
             std::string kk;
-            int b, p;
+            int v, b, p;
             double ms;
-            if (ls >> kk >> b >> p >> ms && kk == k) {
-                lbm_status st = lbm_set_launch(ctx, b, p);
+            if (ls >> kk >> v >> b >> p >> ms && kk == k) {
+                lbm_status st = lbm_set_launch(ctx, v, b, p);
                 if (st != LBM_OK) return st;
+                if (variant_out) *variant_out = v;
                 if (block_out) *block_out = b;
-                if (bpsm_out) *bpsm_out = p;
+                if (param_out) *param_out = p;
                 if (best_ms) *best_ms = ms;
                 return LBM_OK;
             }
@@ -852,30 +903,32 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, int
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    const int blocks[] = {64, 128, 192, 256};
-    const int bps[] = {0, 2, 4, 8, 16};
-    int bb = ctx->block, bp = ctx->bpsm;
+    struct Cand { int v, b, p; };
+    std::vector<Cand> cands;
+    for (int b : {128, 256})
+        for (int p : {0, 4, 8}) cands.push_back({0, b, p});
+    if (!ctx->dbl)
+        for (int b : {128, 256})
+            for (int p : {1, 2, 4}) cands.push_back({1, b, p});
+    int bv = ctx->variant, bb = ctx->block, bp = ctx->param;
     double best = INFINITY;
     lbm_status st = LBM_OK;
-    for (int b : blocks) {
-        for (int p : bps) {
-            if ((st = lbm_set_launch(ctx, b, p)) != LBM_OK) break;
-            if ((st = lbm_step(ctx, 2)) != LBM_OK) break;
-            cudaEventRecord(e0, ctx->stream);
-            if ((st = lbm_step(ctx, iters)) != LBM_OK) break;
-            cudaEventRecord(e1, ctx->stream);
-            cudaEventSynchronize(e1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            const double per = ms / iters;
-            if (per < best) { best = per; bb = b; bp = p; }
-        }
-        if (st != LBM_OK) break;
+    for (const Cand &cd : cands) {
+        if (lbm_set_launch(ctx, cd.v, cd.b, cd.p) != LBM_OK) continue;   // does not fit: skip
+        if ((st = lbm_step(ctx, 2)) != LBM_OK) break;
+        cudaEventRecord(e0, ctx->stream);
+        if ((st = lbm_step(ctx, iters)) != LBM_OK) break;
+        cudaEventRecord(e1, ctx->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / iters;
+        if (per < best) { best = per; bv = cd.v; bb = cd.b; bp = cd.p; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->graph_steps = saved_graph;
-    if (st == LBM_OK) st = lbm_set_launch(ctx, bb, bp);
+    if (st == LBM_OK) st = lbm_set_launch(ctx, bv, bb, bp);
     cudaMemcpyAsync(ctx->pool[ctx->cur], save, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
     cudaFree(save);
@@ -883,10 +936,11 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, int
     if (st != LBM_OK) return st;
     if (cache_path) {
         std::ofstream o(cache_path, std::ios::app);
-        o << k << " " << bb << " " << bp << " " << best << "\n";
+        o << k << " " << bv << " " << bb << " " << bp << " " << best << "\n";
     }
+    if (variant_out) *variant_out = bv;
     if (block_out) *block_out = bb;
-    if (bpsm_out) *bpsm_out = bp;
+    if (param_out) *param_out = bp;
     if (best_ms) *best_ms = best;
     return LBM_OK;
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
+#include "kernels_tma.cuh"
 
 namespace lbm {
 
@@ -13,7 +14,10 @@ struct KernelSet {
     cudaError_t (*init_f)(const void *params, int grid, int block, cudaStream_t s);   // FP32 device fields
     cudaError_t (*moments)(const void *params, int grid, int block, cudaStream_t s);
     cudaError_t (*reduce)(const void *params, int grid, int block, cudaStream_t s);
-    const void *step_fn;          // kernel symbol (occupancy queries)
+    cudaError_t (*step_tma)(const void *params, const TmaParams &tp, int grid, int block, size_t smem,
+                            cudaStream_t s);
+    const void *step_fn;          // kernel symbols (occupancy queries, attributes)
+    const void *step_tma_fn;
 };
 
 template <int DIM, bool HH, bool HG, class S>
@@ -39,9 +43,14 @@ struct Launch {
         k_reduce<DIM, HH, HG, S><<<g, b, 0, s>>>(*static_cast<const RedParams<T> *>(p));
         return cudaGetLastError();
     }
+    static cudaError_t step_tma(const void *p, const TmaParams &tp, int g, int b, size_t smem, cudaStream_t s) {
+        k_step_tma<DIM, HH, HG, S><<<g, b, smem, s>>>(*static_cast<const StepParams<T> *>(p), tp);
+        return cudaGetLastError();
+    }
     static KernelSet make() {
-        return KernelSet{&step, &init_d, &init_f, &moments, &reduce,
-                         reinterpret_cast<const void *>(&k_step<DIM, HH, HG, S>)};
+        return KernelSet{&step, &init_d, &init_f, &moments, &reduce, &step_tma,
+                         reinterpret_cast<const void *>(&k_step<DIM, HH, HG, S>),
+                         reinterpret_cast<const void *>(&k_step_tma<DIM, HH, HG, S>)};
     }
 };
 

@@ -1,14 +1,19 @@
 // kernels.cuh -- the fused coupled lattice-Boltzmann step and its helpers.
 //
-// Storage: one structure-of-arrays plane per population, x fastest; the two
-// buffers hold the RELAXED populations p_rel(x, t).  One thread per node:
-//   1. pull p(x, t+1) = p_rel(x - e_a, t) for every plane (Eq. 1, 3, 5);
+// Storage: one structure-of-arrays plane per population, x fastest.  The two
+// buffers hold the RELAXED populations, shifted by their rest value:
+// s_a(x, t) = p_rel,a(x, t) - w_a phi_ref (phi_ref = rho0, C0 or B0_k of the
+// case).  The shift keeps the stored numbers small so that FP32 and 16-bit
+// storage resolve the deviations that carry the flow, and the arithmetic below
+// works on the shifted values directly (sum_a w_a = 1, sum_a w_a e_a = 0).
+// One thread per node:
+//   1. pull s(x, t+1) = s_rel(x - e_a, t) for every plane (Eq. 1, 3, 5);
 //   2. boundary nodes replace the populations that come from solid nodes by
-//      their wall-link formulas (Sec. 3-4), evaluated from p_rel at A and E and
-//      the moments at t recovered from p_rel (mass, C and B are conserved by
-//      the relaxation, so sum_a p_rel = sum_a p);
+//      their wall-link formulas (Sec. 3-4), evaluated from the relaxed
+//      populations at A and E and the moments at t recovered from them (mass,
+//      C and B are conserved by the relaxation);
 //   3. moments, equilibria (Eq. 2, 4, 6 with the magnetic stress), BGK
-//      relaxation with the Guo source, store p_rel(x, t+1) to the other buffer.
+//      relaxation with the Guo source, store s_rel(x, t+1) to the other buffer.
 // Every step is one launch over a flat list of node tiles of all cases.
 #pragma once
 #include <cuda_bf16.h>
@@ -28,29 +33,30 @@ namespace lbm {
 template <class S> struct Codec;
 template <> struct Codec<double> {
     using T = double;
-    static constexpr bool OFFSET = false;
     LBM_DEV static double ld(const double *p) { return __ldg(p); }
+    LBM_DEV static double ld_shared(const double *p) { return *p; }
     LBM_DEV static void st(double *p, double v) { *p = v; }
 };
 template <> struct Codec<float> {
     using T = float;
-    static constexpr bool OFFSET = false;
     LBM_DEV static float ld(const float *p) { return __ldg(p); }
+    LBM_DEV static float ld_shared(const float *p) { return *p; }
     LBM_DEV static void st(float *p, float v) { *p = v; }
 };
-// 16-bit storage holds p - w_a * phi_ref, decoded to FP32 for all arithmetic.
 template <> struct Codec<__half> {
     using T = float;
-    static constexpr bool OFFSET = true;
     LBM_DEV static float ld(const __half *p) { return __half2float(__ldg(p)); }
+    LBM_DEV static float ld_shared(const __half *p) { return __half2float(*p); }
     LBM_DEV static void st(__half *p, float v) { *p = __float2half_rn(v); }
 };
 template <> struct Codec<__nv_bfloat16> {
     using T = float;
-    static constexpr bool OFFSET = true;
     LBM_DEV static float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    LBM_DEV static float ld_shared(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     LBM_DEV static void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
+
+LBM_DEV uint32_t fast_div(uint32_t n, FastDiv d) { return (__umulhi(n, d.m) + n) >> d.s; }
 
 template <class T>
 struct StepParams {
@@ -65,100 +71,94 @@ struct StepParams {
     const LinkDev<T> *links;
 };
 
-// storage offset w_q * ref(field of q) of plane q
-template <class PL, class S, class T>
-LBM_DEV T plane_off(int q, const CaseDev<T> &c) {
-    if constexpr (!Codec<S>::OFFSET) {
-        return T(0);
-    } else {
-        const int f = PL::field(q);
-        const T ref = f == 0 ? c.ref_rho : (f == 1 ? c.ref_C : c.ref_B[f - 2]);
-        return T(PL::w(q)) * ref;
-    }
-}
-
 // ------------------------------------------------------------------ equilibria
+// Shifted equilibria e_a - w_a phi_ref, written with the deviations
+// drho = rho - rho_ref, dC = C - C_ref, dB = B - B_ref so that nothing large
+// cancels.
 // Eq. 2 plus the magnetic stress w/(2 cs^4) [1/2|B|^2 (|e|^2 - D cs^2) - ((e.B)^2 - cs^2 |B|^2)]
 template <class F, bool HG, class T>
-LBM_DEV T feq_dir(int a, T rho, const T (&u)[3], T usq, const T (&B)[3], T Bsq) {
+LBM_DEV T feq_dir(int a, T drho, T rho, const T (&u)[3], T usq, const T (&B)[3], T Bsq) {
     const T ex = T(F::ex(a)), ey = T(F::ey(a)), ez = T(F::ez(a));
     const T w = T(F::w(a));
     const T eu = ex * u[0] + ey * u[1] + ez * u[2];
-    T feq = w * rho * (T(1) + T(3) * eu + T(4.5) * eu * eu - T(1.5) * usq);
+    T feq = drho + rho * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * usq);
     if constexpr (HG) {
         const T eB = ex * B[0] + ey * B[1] + ez * B[2];
         const T ee = T(F::ex(a) * F::ex(a) + F::ey(a) * F::ey(a) + F::ez(a) * F::ez(a));
-        feq += w * T(4.5) * (T(0.5) * Bsq * (ee - T(F::DIM) / T(3)) - eB * eB + Bsq / T(3));
+        feq += T(4.5) * (T(0.5) * Bsq * (ee - T(F::DIM) / T(3)) - eB * eB + Bsq / T(3));
     }
-    return feq;
+    return w * feq;
 }
 // Eq. 4 with c_h^2 = 1/4
 template <class M, class T>
-LBM_DEV T heq_dir(int a, T C, const T (&u)[3]) {
+LBM_DEV T heq_dir(int a, T dC, T C, const T (&u)[3]) {
     const T eu = T(M::ex(a)) * u[0] + T(M::ey(a)) * u[1] + T(M::ez(a)) * u[2];
-    return T(M::w(a)) * C * (T(1) + T(4) * eu);
+    return T(M::w(a)) * (dC + T(4) * C * eu);
 }
 // Eq. 6, component k, with c_g^2 = 1/4
 template <class M, class T>
-LBM_DEV T geq_dir(int a, int k, const T (&B)[3], const T (&u)[3]) {
+LBM_DEV T geq_dir(int a, int k, T dBk, const T (&B)[3], const T (&u)[3]) {
     const T ex = T(M::ex(a)), ey = T(M::ey(a)), ez = T(M::ez(a));
     const T eu = ex * u[0] + ey * u[1] + ez * u[2];
     const T eB = ex * B[0] + ey * B[1] + ez * B[2];
-    return T(M::w(a)) * (B[k] + T(4) * (eu * B[k] - eB * u[k]));
+    return T(M::w(a)) * (dBk + T(4) * (eu * B[k] - eB * u[k]));
 }
 
 // ------------------------------------------------------------------ collision
-// In place: p (populations at x, t) -> p_rel (Eq. 1, 3, 5).
+// In place: s (shifted populations at x, t) -> s_rel (Eq. 1, 3, 5).
 template <class PL, bool HH, bool HG, class T>
 LBM_DEV void collide(T (&p)[PL::P], const CaseDev<T> &c) {
     using F = typename PL::F;
     using M = typename PL::M;
     constexpr int QF = PL::QF, QM = PL::QM, NB = PL::NB, DIM = F::DIM;
-    T rho = 0, jx = 0, jy = 0, jz = 0;
+    T drho = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int a = 0; a < QF; ++a) {
-        rho += p[a];
+        drho += p[a];
         if (F::ex(a)) jx += T(F::ex(a)) * p[a];
         if (F::ey(a)) jy += T(F::ey(a)) * p[a];
         if (F::ez(a)) jz += T(F::ez(a)) * p[a];
     }
-    const T inv = T(1) / rho;
+    const T rho = drho + c.ref_rho;
     // Guo forcing: u = (sum e f + F/2) / rho with F = rho * accel
-    const T ux = jx * inv + T(0.5) * c.ax;
-    const T uy = jy * inv + T(0.5) * c.ay;
-    const T uz = DIM == 3 ? jz * inv + T(0.5) * c.az : T(0);
     const T Fx = rho * c.ax, Fy = rho * c.ay, Fz = DIM == 3 ? rho * c.az : T(0);
+    const T ux = (jx + T(0.5) * Fx) / rho;
+    const T uy = (jy + T(0.5) * Fy) / rho;
+    const T uz = DIM == 3 ? (jz + T(0.5) * Fz) / rho : T(0);
     const T usq = ux * ux + uy * uy + uz * uz;
-    T B[3] = {T(0), T(0), T(0)};
+    T B[3] = {T(0), T(0), T(0)}, dB[3] = {T(0), T(0), T(0)};
     if constexpr (HG) {
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
             T s = 0;
 #pragma unroll
             for (int a = 0; a < QM; ++a) s += p[PL::G0 + k * QM + a];
-            B[k] = s;
+            dB[k] = s;
+            B[k] = s + c.ref_B[k];
         }
     }
     const T Bsq = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
     const T u[3] = {ux, uy, uz};
+    const T uF = ux * Fx + uy * Fy + uz * Fz;
 #pragma unroll
     for (int a = 0; a < QF; ++a) {
         const T ex = T(F::ex(a)), ey = T(F::ey(a)), ez = T(F::ez(a));
         const T w = T(F::w(a));
-        const T feq = feq_dir<F, HG, T>(a, rho, u, usq, B, Bsq);
+        const T feq = feq_dir<F, HG, T>(a, drho, rho, u, usq, B, Bsq);
         const T eu = ex * ux + ey * uy + ez * uz;
         const T eF = ex * Fx + ey * Fy + ez * Fz;
         // Guo source (1 - 1/(2 tau)) w [3 (e - u).F + 9 (e.u)(e.F)]
-        const T S = c.guo * w * (T(3) * ((ex - ux) * Fx + (ey - uy) * Fy + (ez - uz) * Fz) + T(9) * eu * eF);
+        const T S = c.guo * w * (T(3) * (eF - uF) + T(9) * eu * eF);
         p[a] = p[a] + c.om_f * (feq - p[a]) + S;
     }
     if constexpr (HH) {
-        T C = 0;
+        T dC = 0;
 #pragma unroll
-        for (int a = 0; a < QM; ++a) C += p[PL::H0 + a];
+        for (int a = 0; a < QM; ++a) dC += p[PL::H0 + a];
+        const T C = dC + c.ref_C;
 #pragma unroll
         for (int a = 0; a < QM; ++a)
-            p[PL::H0 + a] = p[PL::H0 + a] + c.om_h * (heq_dir<M, T>(a, C, u) - p[PL::H0 + a]);
+            p[PL::H0 + a] = p[PL::H0 + a] + c.om_h * (heq_dir<M, T>(a, dC, C, u) - p[PL::H0 + a]);
     }
     if constexpr (HG) {
 #pragma unroll
@@ -166,14 +166,14 @@ LBM_DEV void collide(T (&p)[PL::P], const CaseDev<T> &c) {
 #pragma unroll
             for (int a = 0; a < QM; ++a) {
                 const int q = PL::G0 + k * QM + a;
-                p[q] = p[q] + c.om_g * (geq_dir<M, T>(a, k, B, u) - p[q]);
+                p[q] = p[q] + c.om_g * (geq_dir<M, T>(a, k, dB[k], B, u) - p[q]);
             }
         }
     }
 }
 
 // ------------------------------------------------------------------ wall links
-template <class PL, class S, class T>
+template <class S, class T>
 LBM_DEV T field_sum(const S *src, int64_t stride, int q0, int nq, int node) {
     T s = 0;
     for (int j = 0; j < nq; ++j) s += Codec<S>::ld(src + (int64_t)(q0 + j) * stride + node);
@@ -183,14 +183,14 @@ LBM_DEV T field_sum(const S *src, int64_t stride, int q0, int nq, int node) {
 template <class PL, class S, class T>
 LBM_DEV T eval_link(const LinkDev<T> &L, const S *src, const CaseDev<T> &c) {
     const int64_t st = c.stride;
-    const T paA = Codec<S>::ld(src + (int64_t)L.plane_a * st + L.nodeA) + L.off_a;
-    const T papA = Codec<S>::ld(src + (int64_t)L.plane_ap * st + L.nodeA) + L.off_ap;
-    const T papE = Codec<S>::ld(src + (int64_t)L.plane_ap * st + L.nodeE) + L.off_ap;
+    const T paA = Codec<S>::ld(src + (int64_t)L.plane_a * st + L.nodeA);
+    const T papA = Codec<S>::ld(src + (int64_t)L.plane_ap * st + L.nodeA);
+    const T papE = Codec<S>::ld(src + (int64_t)L.plane_ap * st + L.nodeE);
     T v = L.c0 + L.ca * paA + L.cap * papA + L.cape * papE;
     if (L.flags & LINK_NEED_PHI) {
         const int nq = L.phi_plane0 < PL::QF ? PL::QF : PL::QM;
-        const T phA = field_sum<PL, S, T>(src, st, L.phi_plane0, nq, L.nodeA) + L.ref_phi;
-        const T phE = field_sum<PL, S, T>(src, st, L.phi_plane0, nq, L.nodeE) + L.ref_phi;
+        const T phA = field_sum<S, T>(src, st, L.phi_plane0, nq, L.nodeA) + L.ref_phi;
+        const T phE = field_sum<S, T>(src, st, L.phi_plane0, nq, L.nodeE) + L.ref_phi;
         v += L.cphi * ((T(1) + L.d) * phA - L.d * phE);
     }
     if constexpr (PL::G0 < PL::P) {
@@ -198,13 +198,50 @@ LBM_DEV T eval_link(const LinkDev<T> &L, const S *src, const CaseDev<T> &c) {
 #pragma unroll
             for (int k = 0; k < PL::NB; ++k) {
                 const int q0 = PL::G0 + k * PL::QM;
-                const T bA = field_sum<PL, S, T>(src, st, q0, PL::QM, L.nodeA) + c.ref_B[k];
-                const T bE = field_sum<PL, S, T>(src, st, q0, PL::QM, L.nodeE) + c.ref_B[k];
+                const T bA = field_sum<S, T>(src, st, q0, PL::QM, L.nodeA) + c.ref_B[k];
+                const T bE = field_sum<S, T>(src, st, q0, PL::QM, L.nodeE) + c.ref_B[k];
                 v += L.cB[k] * ((T(1) + L.d) * bA - L.d * bE);
             }
         }
     }
     return v;
+}
+
+// Applies every link of boundary node n (row r of the case) to p.
+template <class PL, class S, class T>
+LBM_DEV void apply_links(T (&p)[PL::P], const StepParams<T> &prm, const CaseDev<T> &c, const S *src, int n, int r) {
+    int lo = prm.brow[c.brow_off + r];
+    const int hi0 = prm.brow[c.brow_off + r + 1];
+    int hi = hi0;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (prm.brec[mid].node < n) lo = mid + 1; else hi = mid;
+    }
+    if (lo < hi0 && prm.brec[lo].node == n) {
+        const BRec br = prm.brec[lo];
+        for (int li = br.lo; li < br.hi; ++li) {
+            const LinkDev<T> L = prm.links[li];
+            const T v = eval_link<PL, S, T>(L, src, c);
+            // select per plane (an indexed store would move p to local memory)
+            const int pa = L.plane_a;
+#pragma unroll
+            for (int q = 0; q < PL::P; ++q) p[q] = (q == pa) ? v : p[q];
+        }
+    }
+}
+
+// node coordinates of case-relative index n; r = y + ny*z is the row
+template <int DIM, class T>
+LBM_DEV void coords(const CaseDev<T> &c, int n, int &x, int &y, int &z, int &r) {
+    r = (int)fast_div((uint32_t)n, c.div_nx);
+    x = n - r * c.nx;
+    if constexpr (DIM == 3) {
+        z = (int)fast_div((uint32_t)r, c.div_ny);
+        y = r - z * c.ny;
+    } else {
+        z = 0;
+        y = r;
+    }
 }
 
 // ------------------------------------------------------------------ fused step
@@ -223,10 +260,8 @@ __global__ void __launch_bounds__(256) k_step(const StepParams<typename Codec<S>
         const S *src = static_cast<const S *>(prm.src) + c.pop_off;
         S *dst = static_cast<S *>(prm.dst) + c.pop_off;
         const int nx = c.nx, ny = c.ny;
-        const int x = n % nx;
-        const int r = n / nx;
-        const int y = r % ny;
-        const int z = r / ny;
+        int x, y, z, r;
+        coords<DIM, T>(c, n, x, y, z, r);
         // source node x - e_a with periodic wrap: index of x-1 is xi[0] (e_x = +1)
         const int xi[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
         const int yi[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};
@@ -241,39 +276,18 @@ __global__ void __launch_bounds__(256) k_step(const StepParams<typename Codec<S>
 #pragma unroll
         for (int q = 0; q < P; ++q) {
             const int src_node = xi[1 - PL::ex(q)] + yi[1 - PL::ey(q)] + zi[1 - PL::ez(q)];
-            p[q] = Codec<S>::ld(src + (int64_t)q * c.stride + src_node) + plane_off<PL, S, T>(q, c);
+            p[q] = Codec<S>::ld(src + (int64_t)q * c.stride + src_node);
         }
-        if (fl & NODE_BOUNDARY) {
-            const int row = r;
-            int lo = prm.brow[c.brow_off + row];
-            const int hi0 = prm.brow[c.brow_off + row + 1];
-            int hi = hi0;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (prm.brec[mid].node < n) lo = mid + 1; else hi = mid;
-            }
-            if (lo < hi0 && prm.brec[lo].node == n) {
-                const BRec br = prm.brec[lo];
-                for (int li = br.lo; li < br.hi; ++li) {
-                    const LinkDev<T> L = prm.links[li];
-                    const T v = eval_link<PL, S, T>(L, src, c);
-                    // select per plane (an indexed store would move p to local memory)
-                    const int pa = L.plane_a;
-#pragma unroll
-                    for (int q = 0; q < P; ++q) p[q] = (q == pa) ? v : p[q];
-                }
-            }
-        }
+        if (fl & NODE_BOUNDARY) apply_links<PL, S, T>(p, prm, c, src, n, r);
         collide<PL, HH, HG, T>(p, c);
 #pragma unroll
-        for (int q = 0; q < P; ++q)
-            Codec<S>::st(dst + (int64_t)q * c.stride + n, p[q] - plane_off<PL, S, T>(q, c));
+        for (int q = 0; q < P; ++q) Codec<S>::st(dst + (int64_t)q * c.stride + n, p[q]);
     }
 }
 
 // ------------------------------------------------------------------ initial state
-// Equilibrium (Eq. 2, 4, 6) of the given fields, relaxed once, stored as
-// p_rel(x, 0).  Fields are case-relative arrays (u, B as [N][3]); null means
+// Equilibrium (Eq. 2, 4, 6) of the given fields, relaxed once, stored shifted
+// as s_rel(x, 0).  Fields are case-relative arrays (u, B as [N][3]); null means
 // the case defaults.  Solid nodes store zero.
 template <class T, class FT>
 struct InitParams {
@@ -310,67 +324,73 @@ __global__ void __launch_bounds__(256) k_init(const InitParams<typename Codec<S>
     T p[P];
     const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const T Bsq = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const T drho = rho - c.ref_rho;
 #pragma unroll
-    for (int a = 0; a < PL::QF; ++a) p[a] = feq_dir<F, HG, T>(a, rho, u, usq, B, Bsq);
+    for (int a = 0; a < PL::QF; ++a) p[a] = feq_dir<F, HG, T>(a, drho, rho, u, usq, B, Bsq);
     if constexpr (HH) {
 #pragma unroll
-        for (int a = 0; a < PL::QM; ++a) p[PL::H0 + a] = heq_dir<M, T>(a, C, u);
+        for (int a = 0; a < PL::QM; ++a) p[PL::H0 + a] = heq_dir<M, T>(a, C - c.ref_C, C, u);
     }
     if constexpr (HG) {
 #pragma unroll
         for (int k = 0; k < PL::NB; ++k)
 #pragma unroll
-            for (int a = 0; a < PL::QM; ++a) p[PL::G0 + k * PL::QM + a] = geq_dir<M, T>(a, k, B, u);
+            for (int a = 0; a < PL::QM; ++a) p[PL::G0 + k * PL::QM + a] = geq_dir<M, T>(a, k, B[k] - c.ref_B[k], B, u);
     }
     collide<PL, HH, HG, T>(p, c);
 #pragma unroll
-    for (int q = 0; q < P; ++q)
-        Codec<S>::st(dst + (int64_t)q * c.stride + n, p[q] - plane_off<PL, S, T>(q, c));
+    for (int q = 0; q < P; ++q) Codec<S>::st(dst + (int64_t)q * c.stride + n, p[q]);
 }
 
 // ------------------------------------------------------------------ moments
-// Moments at the current time from the stored p_rel: rho = sum f_rel,
-// u = (sum e f_rel - F/2)/rho (the relaxation adds F/2 to the momentum),
-// C = sum h_rel, B = sum g_rel.
+// Moments at the current time from the stored relaxed populations:
+// rho = sum f_rel, u = (sum e f_rel - F/2)/rho (the relaxation adds F/2 to the
+// momentum), C = sum h_rel, B = sum g_rel.
 template <class PL, class S, class T>
 LBM_DEV void node_moments(const S *src, int64_t stride, int n, const CaseDev<T> &c,
                           T &rho, T (&u)[3], T &C, T (&B)[3], int &nonfinite) {
     using F = typename PL::F;
-    rho = 0;
+    T drho = 0;
     T j[3] = {T(0), T(0), T(0)};
     nonfinite = 0;
 #pragma unroll
     for (int a = 0; a < PL::QF; ++a) {
-        const T v = Codec<S>::ld(src + (int64_t)a * stride + n) + plane_off<PL, S, T>(a, c);
+        const T v = Codec<S>::ld(src + (int64_t)a * stride + n);
         nonfinite += !isfinite(v);
-        rho += v;
+        drho += v;
         j[0] += T(F::ex(a)) * v;
         j[1] += T(F::ey(a)) * v;
         j[2] += T(F::ez(a)) * v;
     }
-    u[0] = j[0] / rho - T(0.5) * c.ax;
-    u[1] = j[1] / rho - T(0.5) * c.ay;
-    u[2] = F::DIM == 3 ? j[2] / rho - T(0.5) * c.az : T(0);
+    rho = drho + c.ref_rho;
+    u[0] = (j[0] - T(0.5) * rho * c.ax) / rho;
+    u[1] = (j[1] - T(0.5) * rho * c.ay) / rho;
+    u[2] = F::DIM == 3 ? (j[2] - T(0.5) * rho * c.az) / rho : T(0);
     C = 0;
     B[0] = B[1] = B[2] = T(0);
     if constexpr (PL::G0 > PL::H0) {
+        T s = 0;
 #pragma unroll
         for (int a = 0; a < PL::QM; ++a) {
-            const T v = Codec<S>::ld(src + (int64_t)(PL::H0 + a) * stride + n) + plane_off<PL, S, T>(PL::H0 + a, c);
+            const T v = Codec<S>::ld(src + (int64_t)(PL::H0 + a) * stride + n);
             nonfinite += !isfinite(v);
-            C += v;
+            s += v;
         }
+        C = s + c.ref_C;
     }
     if constexpr (PL::P > PL::G0) {
 #pragma unroll
-        for (int k = 0; k < PL::NB; ++k)
+        for (int k = 0; k < PL::NB; ++k) {
+            T s = 0;
 #pragma unroll
             for (int a = 0; a < PL::QM; ++a) {
                 const int q = PL::G0 + k * PL::QM + a;
-                const T v = Codec<S>::ld(src + (int64_t)q * stride + n) + plane_off<PL, S, T>(q, c);
+                const T v = Codec<S>::ld(src + (int64_t)q * stride + n);
                 nonfinite += !isfinite(v);
-                B[k] += v;
+                s += v;
             }
+            B[k] = s + c.ref_B[k];
+        }
     }
 }
 
@@ -400,8 +420,8 @@ __global__ void __launch_bounds__(256) k_moments(const MomParams<typename Codec<
     int nf;
     node_moments<PL, S, T>(static_cast<const S *>(mp.src) + c.pop_off, c.stride, n, c, rho, u, C, B, nf);
     mp.rho[n] = (double)rho;
-    mp.C[n] = (double)C;
-    for (int k = 0; k < 3; ++k) { mp.u[3 * n + k] = (double)u[k]; mp.B[3 * n + k] = (double)B[k]; }
+    mp.C[n] = HH ? (double)C : 0.0;
+    for (int k = 0; k < 3; ++k) { mp.u[3 * n + k] = (double)u[k]; mp.B[3 * n + k] = HG ? (double)B[k] : 0.0; }
 }
 
 // ------------------------------------------------------------------ FP64 reductions
@@ -418,6 +438,7 @@ struct RedParams {
     const CaseDev<T> *cases;
     const int2 *tiles;
     int32_t ntiles;
+    int32_t tile_nodes;
     double *snap;
     int64_t snap_stride;
     double *part;             // [ntiles][RED_Q]
@@ -437,19 +458,20 @@ __global__ void __launch_bounds__(256) k_reduce(const RedParams<typename Codec<S
     const int t = blockIdx.x;
     const int2 tile = rp.tiles[t];
     const CaseDev<T> &c = rp.cases[tile.x];
-    const int n = tile.y + (int)threadIdx.x;
     double acc[RED_Q];
 #pragma unroll
     for (int i = 0; i < RED_Q; ++i) acc[i] = 0.0;
-    if (n < c.N && (rp.flags[c.node_off + n] & NODE_FLUID)) {
+    for (int i = threadIdx.x; i < rp.tile_nodes; i += blockDim.x) {
+        const int n = tile.y + i;
+        if (n >= c.N || !(rp.flags[c.node_off + n] & NODE_FLUID)) continue;
         T rho, u[3], C, B[3];
         int nf;
         node_moments<PL, S, T>(static_cast<const S *>(rp.src) + c.pop_off, c.stride, n, c, rho, u, C, B, nf);
         acc[0] = rho;
-        acc[1] = C;
-        acc[2] = B[0];
-        acc[3] = B[1];
-        acc[4] = B[2];
+        acc[1] = HH ? (double)C : 0.0;
+        acc[2] = HG ? (double)B[0] : 0.0;
+        acc[3] = HG ? (double)B[1] : 0.0;
+        acc[4] = HG ? (double)B[2] : 0.0;
         acc[5] = nf;
         const double phi[SNAP_Q] = {(double)u[0], (double)u[1], (double)u[2],
                                     HH ? (double)C : 0.0,

@@ -4,10 +4,17 @@
 
 namespace lbm {
 
+// Division by a run-time constant d (1 <= d, n < 2^31) with a multiply-high
+// (Granlund & Montgomery 1994, round-up magic): q = (umulhi(n, m) + n) >> s.
+struct FastDiv {
+    uint32_t m, s;
+};
+
 // Per-case descriptor, one per domain, read warp-uniformly by every tile.
 template <class T>
 struct CaseDev {
     int32_t nx, ny, nz, N;
+    FastDiv div_nx, div_ny;
     int64_t pop_off;      // element offset of the case's first plane in a population buffer
     int64_t stride;       // elements between consecutive planes of the case
     int64_t node_off;     // offset of the case's nodes in the flag / snapshot arrays
@@ -16,14 +23,15 @@ struct CaseDev {
     T om_f, om_h, om_g;   // 1/tau_nu, 1/tau_D, 1/tau_eta
     T guo;                // 1 - 1/(2 tau_nu): weight of the Guo source
     T ax, ay, az;         // body force per unit mass
-    T ref_rho, ref_C;     // 16-bit offset-storage references (0 for FP32/FP64 storage)
+    T ref_rho, ref_C;     // storage references: planes hold p - w_a * phi_ref
     T ref_B[3];
     T B0[3];              // B_ext for the residual (phi uses B - B0)
 };
 
 // Per-link record with the wall formula of the link folded into coefficients
-// (the host derives them from the link kind, d and the wall data):
-//   p_a(A, t+1) = c0 + ca p_a(A) + cap p_a'(A) + cape p_a'(E)
+// (the host derives them from the link kind, d and the wall data), acting on
+// the stored (shifted) populations s = p - w phi_ref:
+//   s_a(A, t+1) = c0 + ca s_a(A) + cap s_a'(A) + cape s_a'(E)
 //               + cphi phi_X + sum_j cB[j] B_X,j
 // with the relaxed populations at t, phi_X = -d phi(E) + (1 + d) phi(A)
 // (Eq. 13) of the link's own field (rho for f, C for h, B_k for g_k), and
@@ -40,8 +48,7 @@ struct alignas(16) LinkDev {
     uint8_t flags;        // LINK_NEED_PHI | LINK_NEED_B
     T d, c0, ca, cap, cape, cphi;
     T cB[3];
-    T off_a, off_ap;      // storage offsets w * ref of planes a and a' (16-bit storage)
-    T ref_phi;            // reference of the link's field (16-bit storage)
+    T ref_phi;            // storage reference of the link's field (phi = sum of stored + ref_phi)
 };
 
 // Boundary record of a fluid node that owns links.

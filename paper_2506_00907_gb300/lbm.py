@@ -76,8 +76,8 @@ def lib():
             "lbm_get_state": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
             "lbm_set_state": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
             "lbm_steps_done": (i64, [vp]),
-            "lbm_set_launch": (ctypes.c_int, [vp, i32, i32]),
-            "lbm_autotune": (ctypes.c_int, [vp, ctypes.c_char_p, i32, ctypes.POINTER(i32),
+            "lbm_set_launch": (ctypes.c_int, [vp, i32, i32, i32]),
+            "lbm_autotune": (ctypes.c_int, [vp, ctypes.c_char_p, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                             ctypes.POINTER(i32), dp]),
             "lbm_launches_per_step": (i32, [vp]),
             "lbm_device_state": (ctypes.c_int, [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(i32),
@@ -185,15 +185,15 @@ def lbm_steps_done(ctx):
     return lib().lbm_steps_done(ctx)
 
 
-def lbm_set_launch(ctx, block, blocks_per_sm):
-    _check(ctx, lib().lbm_set_launch(ctx, int(block), int(blocks_per_sm)))
+def lbm_set_launch(ctx, variant, block, param):
+    _check(ctx, lib().lbm_set_launch(ctx, int(variant), int(block), int(param)))
 
 
 def lbm_autotune(ctx, cache_path=None, iters=20):
-    b, p, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    v, b, p, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
     _check(ctx, lib().lbm_autotune(ctx, cache_path.encode() if cache_path else None, int(iters),
-                                   ctypes.byref(b), ctypes.byref(p), ctypes.byref(ms)))
-    return b.value, p.value, ms.value
+                                   ctypes.byref(v), ctypes.byref(b), ctypes.byref(p), ctypes.byref(ms)))
+    return v.value, b.value, p.value, ms.value
 
 
 def lbm_launches_per_step(ctx):
@@ -329,8 +329,8 @@ class Solver:
     def steps(self):
         return lbm_steps_done(self.ctx)
 
-    def set_launch(self, block, blocks_per_sm=0):
-        lbm_set_launch(self.ctx, block, blocks_per_sm)
+    def set_launch(self, variant, block, param):
+        lbm_set_launch(self.ctx, variant, block, param)
 
     def autotune(self, cache_path=None, iters=20):
         return lbm_autotune(self.ctx, cache_path, iters)

@@ -63,7 +63,9 @@ def _random_pair(dim, has_h, has_g, seed, prec=lbm.LBM_FP64, shape=None):
     r = IN.rng(seed)
     shape = shape or ((37, 29, 1) if dim == 2 else (13, 11, 9))
     solid = IN.random_solid(r, shape, fill=0.12)
-    links = LK.random_links(dim, shape, solid, r, has_h, has_g)
+    # given wall values near the bulk state (|B| well below the lattice pressure keeps the case stable)
+    phi_range = {O.H: (0.5, 1.5), O.G0: (-0.05, 0.05), O.G0 + 1: (0.25, 0.35), O.G0 + 2: (-0.05, 0.05)}
+    links = LK.random_links(dim, shape, solid, r, has_h, has_g, phi_range=phi_range)
     N = shape[0] * shape[1] * shape[2]
     fields = IN.random_fields(r, N, dim, B0=(0.0, 0.3, 0.0))
     accel = (1e-5, -2e-5, 5e-6 if dim == 3 else 0.0)
@@ -81,6 +83,8 @@ def test_fp64_random_geometry_all_link_kinds(dim, has_h, has_g):
     for k, v in p.errors().items():
         assert v < FP64_TOL, (k, v)
     p.step(39)
+    m = p.orc.moments()
+    assert np.all(np.abs(m["rho"][p.fluid] - 1.0) < 0.5)          # the case stays well posed
     for k, v in p.errors().items():
         assert v < FP64_TOL, (k, v)
 
@@ -90,7 +94,7 @@ def test_fp64_poiseuille_64x32_5000_steps():
     steps: the GPU matches the oracle and both match the analytic parabola to
     the scheme's O(dx^2) slip."""
     from oracle import analytic as AN
-    nx, ny, a = 64, 32, 1e-6
+    nx, ny, a = 64, 32, 1e-5          # steady u_max = a (2H)^2 / (8 nu) ~ 0.011
     walls = LK.channel_y(2, nx, ny, 1, 0.5, 0.5)
     solid = LK.box_solid((nx, ny, 1), walls)
     links = LK.box_links(2, (nx, ny, 1), walls, {(1, 0, O.F): dict(kind=O.VELOCITY),
@@ -130,7 +134,8 @@ def test_fp64_batched_uneven_cases():
     cases, orcs, geo = [], [], []
     for i, dr in enumerate(draws):
         shape, solid, links, B0 = _hartmann_links(dr["W"], dr["q"], dr["cw"], dr["Ha"])
-        acc = (1e-6 * (i + 1), 0.0, 0.0)
+        H = (dr["W"] - 1 + 2 * (1 - dr["q"])) / 2
+        acc = (0.02 * 0.1 * (2 + dr["Ha"]) / H ** 2, 0.0, 0.0)      # u ~ 0.01 at steady state
         o = O.OracleSim(2, shape, solid, 0.8, 1.0, 0.9, acc, False, True, 4)
         o.set_links(links)
         o.init(B0=(0, B0, 0))
@@ -151,21 +156,24 @@ def test_fp64_batched_uneven_cases():
         assert norm_rel(a["B"][fl], b["B"][fl]) < FP64_TOL
 
 
-@pytest.mark.parametrize("prec,tol_u,tol_B", [(lbm.LBM_FP32, 2e-5, 2e-6), (lbm.LBM_FP16S, 3e-2, 5e-3),
-                                              (lbm.LBM_BF16S, 2e-1, 4e-2)])
+@pytest.mark.parametrize("prec,tol_u,tol_B", [(lbm.LBM_FP32, 1e-5, 1e-5), (lbm.LBM_FP16S, 3e-2, 3e-2),
+                                              (lbm.LBM_BF16S, 2e-1, 2e-1)])
 def test_reduced_precision_against_fp64_oracle(prec, tol_u, tol_B):
-    """Hartmann channel, 300 steps from rest: FP32 arithmetic and storage,
-    and FP32 arithmetic with 16-bit offset storage, against the FP64 oracle.
-    The tolerances are the rounding of each storage format (FP32 ~ 6e-8,
-    FP16 ~ 5e-4, BF16 ~ 4e-3 per stored value relative to the offsets)
-    carried through the steps, relative to max|u| and max|B|."""
+    """Hartmann channel, 300 steps from rest: FP32 arithmetic with FP32 or
+    16-bit shifted storage against the FP64 oracle.  The tolerances follow the
+    unit roundoff of each storage format (FP32 6e-8, FP16 4.9e-4, BF16 3.9e-3)
+    applied to the stored deviations and carried through 300 steps, relative
+    to max|u| and max|B - B_ext|."""
     shape, solid, links, B0 = _hartmann_links(48, 0.3, 0.1, 8.0)
-    p = Pair(2, shape, solid, links, prec=prec, taus=(0.8, 1.0, 0.9), accel=(2e-6, 0, 0), has_g=True,
+    p = Pair(2, shape, solid, links, prec=prec, taus=(0.8, 1.0, 0.9), accel=(2e-5, 0, 0), has_g=True,
              B0=(0, B0, 0))
     p.step(300)
-    e = p.errors()
-    assert e["u"] < tol_u, e
-    assert e["B"] < tol_B, e
+    a, b = p.gpu.moments(0), p.orc.moments()
+    fl = p.fluid
+    eu = norm_rel(a["u"][fl], b["u"][fl])
+    eb = norm_rel(a["B"][fl] - [0, B0, 0], b["B"][fl] - [0, B0, 0])
+    print("precision %d: u %.3g  B %.3g" % (prec, eu, eb))
+    assert eu < tol_u and eb < tol_B, (eu, eb)
 
 
 def test_checkpoint_restore_and_graph_are_bitwise():
@@ -269,12 +277,53 @@ def test_fully_periodic_domain_and_single_node_axes():
             assert v < FP64_TOL, (shape, k, v)
 
 
+@pytest.mark.parametrize("dim,prec", [(2, lbm.LBM_FP16S), (2, lbm.LBM_FP32), (3, lbm.LBM_FP32),
+                                      (3, lbm.LBM_BF16S)])
+def test_bulk_copy_pipeline_is_bitwise_identical(dim, prec):
+    """The shared-memory pipeline (variant 1: cp.async.bulk windows + mbarrier)
+    computes exactly what the one-thread-per-node kernel computes, for several
+    tile sizes that leave ragged tails and put periodic edges inside tiles."""
+    shape = (53, 41, 1) if dim == 2 else (21, 13, 11)
+    ref = _random_pair(dim, True, True, seed=77, prec=prec, shape=shape).gpu
+    ref.set_launch(0, 128, 0)
+    ref.step(15)
+    want = ref.get_state()
+    for block, npt in ((128, 1), (256, 2), (64, 4), (192, 3)):
+        g = _random_pair(dim, True, True, seed=77, prec=prec, shape=shape).gpu
+        g.set_launch(1, block, npt)
+        g.set_graph(4)
+        g.step(15)
+        assert np.array_equal(g.get_state(), want), (block, npt)
+        g.check()
+
+
+def test_bulk_copy_pipeline_batched_cases():
+    """Variant 1 over many uneven cases equals variant 0 bit for bit."""
+    def make():
+        cases, geo = [], []
+        for i, (W, q) in enumerate(((20, 0.3), (33, 0.0), (9, 0.75), (64, 0.5), (130, 0.9))):
+            shape, solid, links, B0 = _hartmann_links(W, q, 0.3, 5.0)
+            cases.append(lbm.make_case(shape, 0.8, 1.0, 0.9, (2e-5, 0, 0), 1.0, 0.0, (0, B0, 0)))
+            geo.append((solid, links))
+        g = lbm.Solver(lbm.LBM_D2Q9, lbm.LBM_FP16S, lbm.LBM_FLOW | lbm.LBM_MHD, cases)
+        for i, (solid, links) in enumerate(geo):
+            g.set_walls(i, solid, to_abi_links(links))
+        return g
+    a = make()
+    a.set_launch(0, 256, 4)
+    a.step(30)
+    b = make()
+    b.set_launch(1, 256, 4)
+    b.step(30)
+    assert np.array_equal(a.get_state(), b.get_state())
+
+
 def test_autotune_keeps_solution():
     p = _random_pair(3, False, True, seed=9, prec=lbm.LBM_FP32, shape=(24, 20, 18))
     p.gpu.step(3)
     before = p.gpu.get_state()
-    block, bpsm, ms = p.gpu.autotune(None, iters=3)
-    assert block in (64, 128, 192, 256) and ms > 0
+    variant, block, param, ms = p.gpu.autotune(None, iters=3)
+    assert variant in (0, 1) and block in (64, 128, 192, 256) and ms > 0
     after = p.gpu.get_state()
     assert np.array_equal(before, after)
     p.gpu.step(2)   # still runs with the chosen launch shape
