@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["hartmann_batch", "pipe", "pipe_fp32", "cd"], default="hartmann_batch")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--launch", default=None,
+                    help="variant,block,blocks_per_sm,nodes_per_thread,stages,min_blocks (skips the autotuner)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-iters", type=int, default=5)
     return ap.parse_args()
@@ -276,9 +278,13 @@ def run_ours(args):
         sol.set_walls(i, s, l)
     fluid = sum(int(np.sum(np.asarray(s) == 0)) for s, _ in wl["geo"])
     tune = None
-    if not args.no_autotune:
+    if args.launch:
+        sol.set_launch(*(int(x) for x in args.launch.split(",")))
+        tune = sol.get_launch()
+    elif not args.no_autotune:
         cache = os.path.join(ROOT, "paper_2506_00907_gb300", "_build", "autotune.txt")
-        tune = sol.autotune(cache, iters=20)
+        sol.autotune(cache, iters=20)
+        tune = sol.get_launch()
     sol.set_graph(CHECK_EVERY)
     K = max(CHECK_EVERY, (args.steps // CHECK_EVERY) * CHECK_EVERY)
     W = max(3, args.warmup)
@@ -351,8 +357,7 @@ def run_ours(args):
                 "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": wl["desc"], "storage": wl["storage"], "cases": len(wl["cases"]),
-                           "fluid_nodes": fluid, "launch": {"variant": ["one thread per node", "bulk-copy pipeline"][tune[0]], "block": tune[1],
-                                      "param": tune[2]} if tune else None,
+                           "fluid_nodes": fluid, "launch": tune,
                            "graph_steps": CHECK_EVERY, "reduction_every": CHECK_EVERY,
                            "l2": "state %.0f MB > 129 MB L2, no flush" % (2 * wl["planes"] * elem * fluid / 1e6),
                            "stable": stable},
@@ -360,7 +365,8 @@ def run_ours(args):
                              "frac": achieved / peak, "traffic": traffic,
                              "peak_kind": peak_kind,
                              "bytes_per_launch": alg_bytes,
-                             "kernel": "k_step (fused step + wall links), one launch per time step"},
+                             "kernel": ("k_step_tma (bulk-copy pipeline)" if tune and tune["variant"] == 1 else
+                                        "k_step") + " (fused step + wall links), one launch per time step"},
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         if cpu:
             line["cpu_baseline"] = cpu

@@ -194,16 +194,31 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes);
 int64_t lbm_steps_done(const lbm_ctx *ctx);
 
 /* Launch shape of the fused step.
- *   variant 0: one thread per node, blocks of `block` threads over tiles of
- *              `block` nodes; param = resident blocks per SM of a persistent
- *              tile loop (0 = one block per tile, 1..64).
+ *   variant 0: one thread per node; blocks of `block` threads over tiles of
+ *              `block` nodes; blocks_per_sm = resident blocks per SM of a
+ *              persistent tile loop (0 = one block per tile, up to 64).
  *   variant 1: bulk-copy pipeline (FP32 and 16-bit storage): persistent
- *              blocks stage the next tile's source windows in shared memory
- *              with cp.async.bulk while computing the current tile; param =
- *              nodes per thread (1..8), tile = block * param nodes.
- * block: 64..256, multiple of 32.  Errors: LBM_EINVAL (out of range, or the
- * pipeline's shared memory does not fit), LBM_ECUDA. */
-lbm_status lbm_set_launch(lbm_ctx *ctx, int32_t variant, int32_t block, int32_t param);
+ *              blocks keep `stages` - 1 tiles of source windows in flight in
+ *              shared memory (cp.async.bulk on mbarriers) while computing the
+ *              current tile; tile = block * nodes_per_thread nodes (1..8);
+ *              stages 2..4; min_blocks 1, 3 or 4 selects the register budget
+ *              the kernel was compiled for.
+ * block: 64..256, multiple of 32. */
+typedef struct {
+    int32_t variant;
+    int32_t block;
+    int32_t blocks_per_sm;
+    int32_t nodes_per_thread;
+    int32_t stages;
+    int32_t min_blocks;
+} lbm_launch;
+
+/* Select the launch shape.  Errors: LBM_EINVAL (out of range, or the
+ * pipeline's shared memory does not fit on an SM), LBM_ECUDA. */
+lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *launch);
+
+/* The current launch shape. */
+lbm_status lbm_get_launch(const lbm_ctx *ctx, lbm_launch *launch);
 
 /* Autotuner: times the fused step for every candidate launch shape on this
  * context (each candidate `iters` steps after two warm-up steps, CUDA
@@ -211,9 +226,9 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, int32_t variant, int32_t block, int32_t 
  * `cache_path` (NULL = no cache) keyed by GPU name, lattice, precision,
  * physics and case sizes; a later call with the same key reads the cache
  * instead of timing.  The context's populations and step count are saved and
- * restored around the timing.  Outputs may be NULL.  Errors: LBM_ECUDA. */
-lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, int32_t *variant,
-                        int32_t *block, int32_t *param, double *best_ms);
+ * restored around the timing.  best and best_ms may be NULL.
+ * Errors: LBM_ECUDA. */
+lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm_launch *best, double *best_ms);
 
 /* Kernel launches issued per lbm_step step (for launch accounting). */
 int32_t lbm_launches_per_step(const lbm_ctx *ctx);

@@ -67,8 +67,8 @@ struct lbm_ctx {
     int cur = 0;
     uint8_t *d_flags = nullptr;
     void *d_cases = nullptr;
-    int variant = 0, block = 256, param = 0;   // see lbm_set_launch
-    int tile_nodes = 256, tma_grid = 0;
+    lbm_launch launch{0, 256, 0, 1, 2, 1};     // see lbm_set_launch
+    int tile_nodes = 256, tma_grid = 0, tma_idx = 0;
     size_t tma_smem = 0;
     int32_t *d_err = nullptr;
     int2 *d_tiles = nullptr;
@@ -374,23 +374,24 @@ StepParams<T> step_params(const lbm_ctx *c) {
 }
 
 int step_grid(const lbm_ctx *c) {
-    if (c->variant == 1) return std::max(1, std::min(c->ntiles, c->tma_grid));
-    if (c->param <= 0) return c->ntiles;
-    return std::max(1, std::min(c->ntiles, c->param * c->sm_count));
+    if (c->launch.variant == 1) return std::max(1, std::min(c->ntiles, c->tma_grid));
+    if (c->launch.blocks_per_sm <= 0) return c->ntiles;
+    return std::max(1, std::min(c->ntiles, c->launch.blocks_per_sm * c->sm_count));
 }
 
 template <class T>
 cudaError_t launch_step_t(lbm_ctx *ctx) {
     const StepParams<T> p = step_params<T>(ctx);
-    if (ctx->variant == 1) {
+    if (ctx->launch.variant == 1) {
         TmaParams tp;
         tp.tile_nodes = ctx->tile_nodes;
         const int A = 16 / (int)ctx->elem;
         tp.cap = ctx->tile_nodes + 2 * A;
+        tp.stages = ctx->launch.stages;
         tp.err = ctx->d_err;
-        return ctx->ks.step_tma(&p, tp, step_grid(ctx), ctx->block, ctx->tma_smem, ctx->stream);
+        return ctx->ks.step_tma[ctx->tma_idx](&p, tp, step_grid(ctx), ctx->launch.block, ctx->tma_smem, ctx->stream);
     }
-    return ctx->ks.step(&p, step_grid(ctx), ctx->block, ctx->stream);
+    return ctx->ks.step(&p, step_grid(ctx), ctx->launch.block, ctx->stream);
 }
 
 lbm_status launch_step(lbm_ctx *ctx) {
@@ -809,37 +810,50 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes) {
 
 int64_t lbm_steps_done(const lbm_ctx *ctx) { return ctx ? ctx->steps : 0; }
 
-lbm_status lbm_set_launch(lbm_ctx *ctx, int32_t variant, int32_t block, int32_t param) {
+lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
     if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
-    if (variant < 0 || variant > 1 || block < 64 || block > 256 || block % 32)
+    if (!lp) return fail(ctx, LBM_EINVAL, "launch is NULL");
+    const lbm_launch L = *lp;
+    if (L.variant < 0 || L.variant > 1 || L.block < 64 || L.block > 256 || L.block % 32)
         return fail(ctx, LBM_EINVAL, "variant must be 0 or 1 and block 64..256 in steps of 32");
-    int tile = block;
-    if (variant == 0) {
-        if (param < 0 || param > 64) return fail(ctx, LBM_EINVAL, "blocks per SM must be 0..64");
+    int tile = L.block;
+    int idx = 0;
+    if (L.variant == 0) {
+        if (L.blocks_per_sm < 0 || L.blocks_per_sm > 64) return fail(ctx, LBM_EINVAL, "blocks per SM must be 0..64");
     } else {
-        if (param < 1 || param > 8) return fail(ctx, LBM_EINVAL, "nodes per thread must be 1..8");
+        if (L.nodes_per_thread < 1 || L.nodes_per_thread > 8) return fail(ctx, LBM_EINVAL, "nodes per thread must be 1..8");
+        if (L.stages < 2 || L.stages > TMA_MAX_STAGES) return fail(ctx, LBM_EINVAL, "stages must be 2..%d", TMA_MAX_STAGES);
+        idx = -1;
+        for (int k = 0; k < 3; ++k)
+            if (TMA_MINB[k] == L.min_blocks) idx = k;
+        if (idx < 0) return fail(ctx, LBM_EINVAL, "min_blocks must be 1, 3 or 4");
         if (ctx->dbl) return fail(ctx, LBM_EINVAL, "the bulk-copy pipeline serves FP32 and 16-bit storage");
-        tile = block * param;
+        tile = L.block * L.nodes_per_thread;
         const int A = 16 / (int)ctx->elem;
-        const size_t smem = (size_t)tma_header_bytes(ctx->P) + 2 * (size_t)ctx->P * (tile + 2 * A) * ctx->elem;
+        const size_t smem = (size_t)tma_header_bytes(ctx->P) + (size_t)L.stages * ctx->P * (tile + 2 * A) * ctx->elem;
         int maxsm = 0;
         CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->cfg.device));
         if (smem > (size_t)maxsm) return fail(ctx, LBM_EINVAL, "tile of %d nodes needs %zu B of shared memory", tile, smem);
-        CK(cudaFuncSetAttribute(ctx->ks.step_tma_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CK(cudaFuncSetAttribute(ctx->ks.step_tma_fn[idx], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ctx->ks.step_tma_fn, block, smem));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ctx->ks.step_tma_fn[idx], L.block, smem));
         if (per_sm < 1) return fail(ctx, LBM_EINVAL, "the pipeline does not fit on an SM");
         ctx->tma_smem = smem;
         ctx->tma_grid = per_sm * ctx->sm_count;
     }
-    ctx->variant = variant;
-    ctx->param = param;
-    ctx->block = block;
+    ctx->launch = L;
+    ctx->tma_idx = idx;
     if (tile != ctx->tile_nodes) {
         ctx->tile_nodes = tile;
         return build_tiles(ctx);
     }
     drop_graphs(ctx);
+    return LBM_OK;
+}
+
+lbm_status lbm_get_launch(const lbm_ctx *ctx, lbm_launch *lp) {
+    if (!ctx || !lp) return LBM_EINVAL;
+    *lp = ctx->launch;
     return LBM_OK;
 }
 
@@ -858,14 +872,13 @@ lbm_status lbm_device_state(lbm_ctx *ctx, int32_t case_id, void **base, int32_t 
 }
 
 // ----------------------------------------------------------------------------- autotuner
-lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, int32_t *variant_out,
-                        int32_t *block_out, int32_t *param_out, double *best_ms) {
+lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm_launch *best_out, double *best_ms) {
     if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (iters < 1) iters = 20;
     cudaDeviceProp prop{};
     CK(cudaGetDeviceProperties(&prop, ctx->cfg.device));
     std::ostringstream key;
-    key << prop.name << "|v2|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
+    key << prop.name << "|v3|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
         << ctx->cases.size();
     int64_t tot = 0;
     for (auto &c : ctx->cases) tot += c.N;
@@ -879,14 +892,13 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, int
         while (std::getline(in, line)) {
             std::istringstream ls(line);
             std::string kk;
-            int v, b, p;
+            lbm_launch L{};
             double ms;
-            if (ls >> kk >> v >> b >> p >> ms && kk == k) {
-                lbm_status st = lbm_set_launch(ctx, v, b, p);
+            if (ls >> kk >> L.variant >> L.block >> L.blocks_per_sm >> L.nodes_per_thread >> L.stages >> L.min_blocks >> ms &&
+                kk == k) {
+                lbm_status st = lbm_set_launch(ctx, &L);
                 if (st != LBM_OK) return st;
-                if (variant_out) *variant_out = v;
-                if (block_out) *block_out = b;
-                if (param_out) *param_out = p;
+                if (best_out) *best_out = L;
                 if (best_ms) *best_ms = ms;
                 return LBM_OK;
             }
@@ -903,18 +915,19 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, int
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    struct Cand { int v, b, p; };
-    std::vector<Cand> cands;
+    std::vector<lbm_launch> cands;
     for (int b : {128, 256})
-        for (int p : {0, 4, 8}) cands.push_back({0, b, p});
+        for (int p : {0, 4, 8}) cands.push_back(lbm_launch{0, b, p, 1, 2, 1});
     if (!ctx->dbl)
         for (int b : {128, 256})
-            for (int p : {1, 2, 4}) cands.push_back({1, b, p});
-    int bv = ctx->variant, bb = ctx->block, bp = ctx->param;
-    double best = INFINITY;
+            for (int npt : {1, 2})
+                for (int stg : {2, 3, 4})
+                    for (int mb : {1, 3, 4}) cands.push_back(lbm_launch{1, b, 0, npt, stg, mb});
+    lbm_launch best = ctx->launch;
+    double best_t = INFINITY;
     lbm_status st = LBM_OK;
-    for (const Cand &cd : cands) {
-        if (lbm_set_launch(ctx, cd.v, cd.b, cd.p) != LBM_OK) continue;   // does not fit: skip
+    for (const lbm_launch &cd : cands) {
+        if (lbm_set_launch(ctx, &cd) != LBM_OK) continue;   // does not fit: skip
         if ((st = lbm_step(ctx, 2)) != LBM_OK) break;
         cudaEventRecord(e0, ctx->stream);
         if ((st = lbm_step(ctx, iters)) != LBM_OK) break;
@@ -923,12 +936,12 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, int
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
         const double per = ms / iters;
-        if (per < best) { best = per; bv = cd.v; bb = cd.b; bp = cd.p; }
+        if (per < best_t) { best_t = per; best = cd; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->graph_steps = saved_graph;
-    if (st == LBM_OK) st = lbm_set_launch(ctx, bv, bb, bp);
+    if (st == LBM_OK) st = lbm_set_launch(ctx, &best);
     cudaMemcpyAsync(ctx->pool[ctx->cur], save, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
     cudaFree(save);
@@ -936,12 +949,11 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, int
     if (st != LBM_OK) return st;
     if (cache_path) {
         std::ofstream o(cache_path, std::ios::app);
-        o << k << " " << bv << " " << bb << " " << bp << " " << best << "\n";
+        o << k << " " << best.variant << " " << best.block << " " << best.blocks_per_sm << " " << best.nodes_per_thread
+          << " " << best.stages << " " << best.min_blocks << " " << best_t << "\n";
     }
-    if (variant_out) *variant_out = bv;
-    if (block_out) *block_out = bb;
-    if (param_out) *param_out = bp;
-    if (best_ms) *best_ms = best;
+    if (best_out) *best_out = best;
+    if (best_ms) *best_ms = best_t;
     return LBM_OK;
 }
 

@@ -14,11 +14,14 @@ struct KernelSet {
     cudaError_t (*init_f)(const void *params, int grid, int block, cudaStream_t s);   // FP32 device fields
     cudaError_t (*moments)(const void *params, int grid, int block, cudaStream_t s);
     cudaError_t (*reduce)(const void *params, int grid, int block, cudaStream_t s);
-    cudaError_t (*step_tma)(const void *params, const TmaParams &tp, int grid, int block, size_t smem,
-                            cudaStream_t s);
+    // pipeline variants compiled for 1, 3 and 4 resident blocks per SM (register budgets)
+    cudaError_t (*step_tma[3])(const void *params, const TmaParams &tp, int grid, int block, size_t smem,
+                               cudaStream_t s);
     const void *step_fn;          // kernel symbols (occupancy queries, attributes)
-    const void *step_tma_fn;
+    const void *step_tma_fn[3];
 };
+
+constexpr int TMA_MINB[3] = {1, 3, 4};
 
 template <int DIM, bool HH, bool HG, class S>
 struct Launch {
@@ -43,14 +46,26 @@ struct Launch {
         k_reduce<DIM, HH, HG, S><<<g, b, 0, s>>>(*static_cast<const RedParams<T> *>(p));
         return cudaGetLastError();
     }
+    template <int MINB>
     static cudaError_t step_tma(const void *p, const TmaParams &tp, int g, int b, size_t smem, cudaStream_t s) {
-        k_step_tma<DIM, HH, HG, S><<<g, b, smem, s>>>(*static_cast<const StepParams<T> *>(p), tp);
+        k_step_tma<DIM, HH, HG, S, MINB><<<g, b, smem, s>>>(*static_cast<const StepParams<T> *>(p), tp);
         return cudaGetLastError();
     }
     static KernelSet make() {
-        return KernelSet{&step, &init_d, &init_f, &moments, &reduce, &step_tma,
-                         reinterpret_cast<const void *>(&k_step<DIM, HH, HG, S>),
-                         reinterpret_cast<const void *>(&k_step_tma<DIM, HH, HG, S>)};
+        KernelSet k{};
+        k.step = &step;
+        k.init_d = &init_d;
+        k.init_f = &init_f;
+        k.moments = &moments;
+        k.reduce = &reduce;
+        k.step_tma[0] = &step_tma<1>;
+        k.step_tma[1] = &step_tma<3>;
+        k.step_tma[2] = &step_tma<4>;
+        k.step_fn = reinterpret_cast<const void *>(&k_step<DIM, HH, HG, S>);
+        k.step_tma_fn[0] = reinterpret_cast<const void *>(&k_step_tma<DIM, HH, HG, S, 1>);
+        k.step_tma_fn[1] = reinterpret_cast<const void *>(&k_step_tma<DIM, HH, HG, S, 3>);
+        k.step_tma_fn[2] = reinterpret_cast<const void *>(&k_step_tma<DIM, HH, HG, S, 4>);
+        return k;
     }
 };
 

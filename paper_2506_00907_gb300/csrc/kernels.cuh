@@ -75,19 +75,27 @@ struct StepParams {
 // Shifted equilibria e_a - w_a phi_ref, written with the deviations
 // drho = rho - rho_ref, dC = C - C_ref, dB = B - B_ref so that nothing large
 // cancels.
-// Eq. 2 plus the magnetic stress w/(2 cs^4) [1/2|B|^2 (|e|^2 - D cs^2) - ((e.B)^2 - cs^2 |B|^2)]
+// Eq. 2 plus the magnetic stress w/(2 cs^4) [1/2|B|^2 (|e|^2 - D cs^2) - ((e.B)^2 - cs^2 |B|^2)].
+// mag[k] = 4.5 (1/2 |B|^2 (k - D/3) + |B|^2/3) is the isotropic part for |e|^2 = k.
 template <class F, bool HG, class T>
-LBM_DEV T feq_dir(int a, T drho, T rho, const T (&u)[3], T usq, const T (&B)[3], T Bsq) {
+LBM_DEV T feq_dir(int a, T drho, T rho, const T (&u)[3], T usq15, const T (&B)[3], const T (&mag)[3]) {
     const T ex = T(F::ex(a)), ey = T(F::ey(a)), ez = T(F::ez(a));
     const T w = T(F::w(a));
     const T eu = ex * u[0] + ey * u[1] + ez * u[2];
-    T feq = drho + rho * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * usq);
+    T feq = drho + rho * (eu * (T(3) + T(4.5) * eu) - usq15);
     if constexpr (HG) {
         const T eB = ex * B[0] + ey * B[1] + ez * B[2];
-        const T ee = T(F::ex(a) * F::ex(a) + F::ey(a) * F::ey(a) + F::ez(a) * F::ez(a));
-        feq += T(4.5) * (T(0.5) * Bsq * (ee - T(F::DIM) / T(3)) - eB * eB + Bsq / T(3));
+        const int ee = F::ex(a) * F::ex(a) + F::ey(a) * F::ey(a) + F::ez(a) * F::ez(a);
+        feq += (ee == 0 ? mag[0] : (ee == 1 ? mag[1] : mag[2])) - T(4.5) * eB * eB;
     }
     return w * feq;
+}
+
+template <class F, class T>
+LBM_DEV void mag_classes(T Bsq, T (&mag)[3]) {
+    constexpr T third = T(1) / T(3);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) mag[k] = T(4.5) * (T(0.5) * Bsq * (T(k) - T(F::DIM) * third) + Bsq * third);
 }
 // Eq. 4 with c_h^2 = 1/4
 template <class M, class T>
@@ -122,10 +130,11 @@ LBM_DEV void collide(T (&p)[PL::P], const CaseDev<T> &c) {
     const T rho = drho + c.ref_rho;
     // Guo forcing: u = (sum e f + F/2) / rho with F = rho * accel
     const T Fx = rho * c.ax, Fy = rho * c.ay, Fz = DIM == 3 ? rho * c.az : T(0);
-    const T ux = (jx + T(0.5) * Fx) / rho;
-    const T uy = (jy + T(0.5) * Fy) / rho;
-    const T uz = DIM == 3 ? (jz + T(0.5) * Fz) / rho : T(0);
-    const T usq = ux * ux + uy * uy + uz * uz;
+    const T inv = T(1) / rho;
+    const T ux = (jx + T(0.5) * Fx) * inv;
+    const T uy = (jy + T(0.5) * Fy) * inv;
+    const T uz = DIM == 3 ? (jz + T(0.5) * Fz) * inv : T(0);
+    const T usq15 = T(1.5) * (ux * ux + uy * uy + uz * uz);
     T B[3] = {T(0), T(0), T(0)}, dB[3] = {T(0), T(0), T(0)};
     if constexpr (HG) {
 #pragma unroll
@@ -137,14 +146,15 @@ LBM_DEV void collide(T (&p)[PL::P], const CaseDev<T> &c) {
             B[k] = s + c.ref_B[k];
         }
     }
-    const T Bsq = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    T mag[3] = {T(0), T(0), T(0)};
+    if constexpr (HG) mag_classes<F, T>(B[0] * B[0] + B[1] * B[1] + B[2] * B[2], mag);
     const T u[3] = {ux, uy, uz};
     const T uF = ux * Fx + uy * Fy + uz * Fz;
 #pragma unroll
     for (int a = 0; a < QF; ++a) {
         const T ex = T(F::ex(a)), ey = T(F::ey(a)), ez = T(F::ez(a));
         const T w = T(F::w(a));
-        const T feq = feq_dir<F, HG, T>(a, drho, rho, u, usq, B, Bsq);
+        const T feq = feq_dir<F, HG, T>(a, drho, rho, u, usq15, B, mag);
         const T eu = ex * ux + ey * uy + ez * uz;
         const T eF = ex * Fx + ey * Fy + ez * Fz;
         // Guo source (1 - 1/(2 tau)) w [3 (e - u).F + 9 (e.u)(e.F)]
@@ -322,11 +332,12 @@ __global__ void __launch_bounds__(256) k_init(const InitParams<typename Codec<S>
     if (DIM == 2) { u[2] = T(0); B[2] = T(0); }
     const T C = ip.C ? T(ip.C[n]) : ip.C0;
     T p[P];
-    const T usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const T Bsq = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const T usq15 = T(1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    T mag[3] = {T(0), T(0), T(0)};
+    if constexpr (HG) mag_classes<F, T>(B[0] * B[0] + B[1] * B[1] + B[2] * B[2], mag);
     const T drho = rho - c.ref_rho;
 #pragma unroll
-    for (int a = 0; a < PL::QF; ++a) p[a] = feq_dir<F, HG, T>(a, drho, rho, u, usq, B, Bsq);
+    for (int a = 0; a < PL::QF; ++a) p[a] = feq_dir<F, HG, T>(a, drho, rho, u, usq15, B, mag);
     if constexpr (HH) {
 #pragma unroll
         for (int a = 0; a < PL::QM; ++a) p[PL::H0 + a] = heq_dir<M, T>(a, C - c.ref_C, C, u);

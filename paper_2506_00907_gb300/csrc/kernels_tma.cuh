@@ -22,15 +22,19 @@
 namespace lbm {
 
 struct TmaParams {
-    int32_t tile_nodes;       // nodes per tile (= blockDim.x * nodes per thread)
+    int32_t tile_nodes;       // nodes per tile (a multiple of blockDim.x)
     int32_t cap;              // elements per plane per stage (multiple of 16 bytes)
+    int32_t stages;           // ring depth, 2..TMA_MAX_STAGES
     int32_t *err;             // error word (0 = ok)
 };
 
 constexpr uint32_t TMA_SPIN_LIMIT = 1u << 24;
+constexpr int TMA_MAX_STAGES = 4;
 
-// shared memory before the stage buffers: 2 mbarriers + the window table
-__host__ __device__ constexpr int tma_header_bytes(int P) { return ((16 + 2 * 2 * P * 4 + 127) / 128) * 128; }
+// shared memory before the stage buffers: mbarriers + the window table [stage][2P]
+__host__ __device__ constexpr int tma_header_bytes(int P) {
+    return ((8 * TMA_MAX_STAGES + TMA_MAX_STAGES * 2 * P * 4 + 127) / 128) * 128;
+}
 
 LBM_DEV uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -66,58 +70,67 @@ LBM_DEV void plane_window(int q, int start, int len, int nx, int nxy, int N, int
     const int a = start - s, b = start + len - s;
     lo = a < 0 ? 0 : (a / A) * A;
     const int top = ((N + A - 1) / A) * A;
-    int h = ((b + A - 1) / A) * A;
+    const int h = ((b + A - 1) / A) * A;
     hi = h > top ? top : h;
     if (hi < lo) hi = lo;
 }
 
-template <int DIM, bool HH, bool HG, class S>
-__global__ void __launch_bounds__(256, 1) k_step_tma(const StepParams<typename Codec<S>::T> prm, const TmaParams tp) {
+// Issued by one thread: the windows of tile t into stage st.
+template <class PL, class S, class T>
+LBM_DEV void tma_issue(const StepParams<T> &prm, const TmaParams &tp, int t, int st, uint64_t *bar, int *win,
+                       S *stage_buf) {
+    constexpr int P = PL::P;
+    const int2 tile = prm.tiles[t];
+    const CaseDev<T> &c = prm.cases[tile.x];
+    const int len = min(tp.tile_nodes, c.N - tile.y);
+    const S *src = static_cast<const S *>(prm.src) + c.pop_off;
+    int *w = win + st * 2 * P;
+    uint32_t total = 0;
+    for (int q = 0; q < P; ++q) {
+        int lo, hi;
+        plane_window<PL, S>(q, tile.y, len, c.nx, c.nx * c.ny, c.N, lo, hi);
+        w[q] = lo;
+        w[P + q] = hi;
+        total += (uint32_t)(hi - lo) * (uint32_t)sizeof(S);
+    }
+    mbar_arrive_expect_tx(&bar[st], total);
+    S *dstb = stage_buf + (size_t)st * P * tp.cap;
+    for (int q = 0; q < P; ++q) {
+        const int lo = w[q], hi = w[P + q];
+        if (hi > lo)
+            bulk_g2s(dstb + (size_t)q * tp.cap, src + (int64_t)q * c.stride + lo, (uint32_t)(hi - lo) * (uint32_t)sizeof(S),
+                     &bar[st]);
+    }
+}
+
+template <int DIM, bool HH, bool HG, class S, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_step_tma(const StepParams<typename Codec<S>::T> prm, const TmaParams tp) {
     using PL = Planes<DIM, HH, HG>;
     using T = typename Codec<S>::T;
     constexpr int P = PL::P;
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);                  // 2 barriers
-    int *win = reinterpret_cast<int *>(smem + 16);                        // [2][2P]: window lo, hi
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);                            // [stages]
+    int *win = reinterpret_cast<int *>(smem + 8 * TMA_MAX_STAGES);                  // [stages][2P]
     S *stage_buf = reinterpret_cast<S *>(smem + tma_header_bytes(P));
     const int tid = threadIdx.x;
+    const int NS = tp.stages;
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int k = 0; k < NS; ++k) mbar_init(&bar[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-
-    auto issue = [&](int t, int st) {
-        const int2 tile = prm.tiles[t];
-        const CaseDev<T> &c = prm.cases[tile.x];
-        const int len = min(tp.tile_nodes, c.N - tile.y);
-        const S *src = static_cast<const S *>(prm.src) + c.pop_off;
-        int lo[P], hi[P];
-        uint32_t total = 0;
-#pragma unroll
-        for (int q = 0; q < P; ++q) {
-            plane_window<PL, S>(q, tile.y, len, c.nx, c.nx * c.ny, c.N, lo[q], hi[q]);
-            total += (uint32_t)(hi[q] - lo[q]) * (uint32_t)sizeof(S);
-            win[st * 2 * P + q] = lo[q];
-            win[st * 2 * P + P + q] = hi[q];
+    // prologue: the first NS - 1 tiles of this block
+    if (tid == 0)
+        for (int k = 0; k < NS - 1; ++k) {
+            const int t = blockIdx.x + k * gridDim.x;
+            if (t < prm.ntiles) tma_issue<PL, S, T>(prm, tp, t, k, bar, win, stage_buf);
         }
-        mbar_arrive_expect_tx(&bar[st], total);
-        S *dstb = stage_buf + (size_t)st * P * tp.cap;
-#pragma unroll
-        for (int q = 0; q < P; ++q)
-            if (hi[q] > lo[q])
-                bulk_g2s(dstb + (size_t)q * tp.cap, src + (int64_t)q * c.stride + lo[q],
-                         (uint32_t)(hi[q] - lo[q]) * (uint32_t)sizeof(S), &bar[st]);
-    };
-
-    uint32_t phases = 0u;     // bit s = parity to wait for on stage s
-    int st = 0;
-    if (tid == 0 && (int)blockIdx.x < prm.ntiles) issue(blockIdx.x, 0);
-    for (int t = blockIdx.x; t < prm.ntiles; t += gridDim.x) {
-        const int nt = t + gridDim.x;
-        if (tid == 0 && nt < prm.ntiles) issue(nt, st ^ 1);
-        // wait for this tile's windows (bounded)
+    uint32_t phases = 0u;     // bit k = parity to wait for on stage k
+    int st = 0, k_iter = 0;
+    for (int t = blockIdx.x; t < prm.ntiles; t += gridDim.x, ++k_iter) {
+        // keep NS - 1 tiles in flight: tile k_iter + NS - 1 goes to the stage freed last iteration
+        const int ahead = t + (NS - 1) * gridDim.x;
+        if (tid == 0 && ahead < prm.ntiles) tma_issue<PL, S, T>(prm, tp, ahead, (k_iter + NS - 1) % NS, bar, win, stage_buf);
         uint32_t spins = 0;
         bool ok = true;
         while (!mbar_try_wait(&bar[st], (phases >> st) & 1u)) {
@@ -127,7 +140,7 @@ __global__ void __launch_bounds__(256, 1) k_step_tma(const StepParams<typename C
             if (tid == 0) {
                 atomicExch(tp.err, 1);
                 // let this block's copies land before the block exits (bounded)
-                for (int s2 = 0; s2 < 2; ++s2)
+                for (int s2 = 0; s2 < NS; ++s2)
                     for (uint32_t k = 0; k < TMA_SPIN_LIMIT && !mbar_try_wait(&bar[s2], (phases >> s2) & 1u); ++k) {
                     }
             }
@@ -182,7 +195,7 @@ __global__ void __launch_bounds__(256, 1) k_step_tma(const StepParams<typename C
             for (int q = 0; q < P; ++q) Codec<S>::st(dst + (int64_t)q * c.stride + n, p[q]);
         }
         __syncthreads();   // every thread is done with stage st before it is refilled
-        st ^= 1;
+        st = st + 1 == NS ? 0 : st + 1;
     }
 }
 

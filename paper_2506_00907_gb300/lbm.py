@@ -40,6 +40,14 @@ class lbm_config(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("device", ctypes.c_int32)]
 
 
+class lbm_launch(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("nodes_per_thread", ctypes.c_int32), ("stages", ctypes.c_int32), ("min_blocks", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class LbmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("lbm status %d: %s" % (status, msg))
@@ -76,9 +84,9 @@ def lib():
             "lbm_get_state": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
             "lbm_set_state": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
             "lbm_steps_done": (i64, [vp]),
-            "lbm_set_launch": (ctypes.c_int, [vp, i32, i32, i32]),
-            "lbm_autotune": (ctypes.c_int, [vp, ctypes.c_char_p, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
-                                            ctypes.POINTER(i32), dp]),
+            "lbm_set_launch": (ctypes.c_int, [vp, ctypes.POINTER(lbm_launch)]),
+            "lbm_get_launch": (ctypes.c_int, [vp, ctypes.POINTER(lbm_launch)]),
+            "lbm_autotune": (ctypes.c_int, [vp, ctypes.c_char_p, i32, ctypes.POINTER(lbm_launch), dp]),
             "lbm_launches_per_step": (i32, [vp]),
             "lbm_device_state": (ctypes.c_int, [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(i32),
                                                 ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)]),
@@ -185,15 +193,25 @@ def lbm_steps_done(ctx):
     return lib().lbm_steps_done(ctx)
 
 
-def lbm_set_launch(ctx, variant, block, param):
-    _check(ctx, lib().lbm_set_launch(ctx, int(variant), int(block), int(param)))
+def launch(variant=0, block=256, blocks_per_sm=0, nodes_per_thread=1, stages=2, min_blocks=1):
+    return lbm_launch(variant, block, blocks_per_sm, nodes_per_thread, stages, min_blocks)
+
+
+def lbm_set_launch(ctx, lp):
+    _check(ctx, lib().lbm_set_launch(ctx, ctypes.byref(lp)))
+
+
+def lbm_get_launch(ctx):
+    lp = lbm_launch()
+    _check(ctx, lib().lbm_get_launch(ctx, ctypes.byref(lp)))
+    return lp
 
 
 def lbm_autotune(ctx, cache_path=None, iters=20):
-    v, b, p, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
-    _check(ctx, lib().lbm_autotune(ctx, cache_path.encode() if cache_path else None, int(iters),
-                                   ctypes.byref(v), ctypes.byref(b), ctypes.byref(p), ctypes.byref(ms)))
-    return v.value, b.value, p.value, ms.value
+    lp, ms = lbm_launch(), ctypes.c_double()
+    _check(ctx, lib().lbm_autotune(ctx, cache_path.encode() if cache_path else None, int(iters), ctypes.byref(lp),
+                                   ctypes.byref(ms)))
+    return lp, ms.value
 
 
 def lbm_launches_per_step(ctx):
@@ -329,8 +347,11 @@ class Solver:
     def steps(self):
         return lbm_steps_done(self.ctx)
 
-    def set_launch(self, variant, block, param):
-        lbm_set_launch(self.ctx, variant, block, param)
+    def set_launch(self, variant=0, block=256, blocks_per_sm=0, nodes_per_thread=1, stages=2, min_blocks=1):
+        lbm_set_launch(self.ctx, launch(variant, block, blocks_per_sm, nodes_per_thread, stages, min_blocks))
+
+    def get_launch(self):
+        return lbm_get_launch(self.ctx).as_dict()
 
     def autotune(self, cache_path=None, iters=20):
         return lbm_autotune(self.ctx, cache_path, iters)

@@ -288,12 +288,12 @@ def test_bulk_copy_pipeline_is_bitwise_identical(dim, prec):
     ref.set_launch(0, 128, 0)
     ref.step(15)
     want = ref.get_state()
-    for block, npt in ((128, 1), (256, 2), (64, 4), (192, 3)):
+    for block, npt, stages, minb in ((128, 1, 2, 1), (256, 2, 3, 3), (64, 4, 4, 4), (192, 3, 2, 4), (256, 1, 4, 1)):
         g = _random_pair(dim, True, True, seed=77, prec=prec, shape=shape).gpu
-        g.set_launch(1, block, npt)
+        g.set_launch(1, block, nodes_per_thread=npt, stages=stages, min_blocks=minb)
         g.set_graph(4)
         g.step(15)
-        assert np.array_equal(g.get_state(), want), (block, npt)
+        assert np.array_equal(g.get_state(), want), (block, npt, stages, minb)
         g.check()
 
 
@@ -313,7 +313,7 @@ def test_bulk_copy_pipeline_batched_cases():
     a.set_launch(0, 256, 4)
     a.step(30)
     b = make()
-    b.set_launch(1, 256, 4)
+    b.set_launch(1, 256, nodes_per_thread=2, stages=3, min_blocks=3)
     b.step(30)
     assert np.array_equal(a.get_state(), b.get_state())
 
@@ -322,8 +322,8 @@ def test_autotune_keeps_solution():
     p = _random_pair(3, False, True, seed=9, prec=lbm.LBM_FP32, shape=(24, 20, 18))
     p.gpu.step(3)
     before = p.gpu.get_state()
-    variant, block, param, ms = p.gpu.autotune(None, iters=3)
-    assert variant in (0, 1) and block in (64, 128, 192, 256) and ms > 0
+    lp, ms = p.gpu.autotune(None, iters=3)
+    assert lp.variant in (0, 1) and lp.block in (64, 128, 192, 256) and ms > 0
     after = p.gpu.get_state()
     assert np.array_equal(before, after)
     p.gpu.step(2)   # still runs with the chosen launch shape
