@@ -240,6 +240,38 @@ int32_t lbm_launches_per_step(const lbm_ctx *ctx);
 lbm_status lbm_device_state(lbm_ctx *ctx, int32_t case_id, void **base, int32_t *elem_bytes,
                             int64_t *plane_stride, int64_t *case_offset, int32_t *planes);
 
+/* Allocation-free FP64 reduction of one domain (the paper has no counterpart;
+ * this is a service of the library).  It computes, for a population buffer
+ * the caller already holds, the same eight numbers lbm_check() reports for a
+ * case, but keeps its partial sums in a fixed device array inside the library
+ * instead of scratch memory that a context allocated with cudaMalloc.  It is
+ * meant for callers that cannot allocate device memory: applications that hand
+ * out every byte of the GPU through their own pool or fixed budget, and
+ * monitoring hooks that must not change the memory footprint of the job they
+ * inspect.
+ *   lattice, prec, physics: as in lbm_config.
+ *   cs:      host, the case (sizes, accel, rho0, C0, B0).
+ *   pops:    device, the case's stored populations (lbm_device_state: base +
+ *            case offset), planes of `plane_stride` elements.
+ *   flags:   device, nx*ny*nz bytes, nonzero = fluid; NULL counts every node.
+ *   snap:    device, 7 * nx*ny*nz doubles holding phi_prev = (u, C, B - B0)
+ *            plane by plane, replaced by the current phi; NULL skips the
+ *            residual (sums 6 and 7 then compare with zero).
+ *   out:     host, 8 doubles, the record of lbm_check().
+ *   stream:  cudaStream_t (NULL = legacy default stream).  Synchronises it.
+ * Limit: at most LBM_NOALLOC_MAX_NODES nodes (larger domains: LBM_EINVAL, with
+ * a message on stderr).  The first call on a device looks up the array's
+ * device address with that device current; make that first call before any
+ * stream capture.  All calls share the one array: calls that overlap on the
+ * GPU (other threads or streams) race and must be serialised by the caller.
+ * Every call overwrites what it reads, so nothing needs clearing in between.
+ * Returns LBM_EUNSTABLE (after filling out) if a population is not finite.
+ * Errors: LBM_EINVAL, LBM_ECUDA. */
+#define LBM_NOALLOC_MAX_NODES (1 << 22)
+lbm_status lbm_reduce_noalloc(int32_t lattice, int32_t prec, uint32_t physics, const lbm_case *cs,
+                              const void *pops, int64_t plane_stride, const uint8_t *flags, double *snap,
+                              double *out, void *stream);
+
 /* ------------------------------------------------------------------------
  * Wall-link builders (host only; no context and no GPU needed).
  * ------------------------------------------------------------------------ */

@@ -96,6 +96,8 @@ def lib():
                                                     ctypes.POINTER(ctypes.c_size_t)])
         sig["lbm_build_pipe"] = (ctypes.c_int, [i32, i32, i32, ctypes.c_double, ctypes.c_uint32, vp, vp, vp,
                                                 ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)])
+        sig["lbm_reduce_noalloc"] = (ctypes.c_int, [i32, i32, ctypes.c_uint32, ctypes.POINTER(lbm_case), vp, i64,
+                                                     vp, vp, dp, vp])
         for name, (res, args) in sig.items():
             f = getattr(L, name)
             f.restype = res
@@ -212,6 +214,18 @@ def lbm_autotune(ctx, cache_path=None, iters=20):
     _check(ctx, lib().lbm_autotune(ctx, cache_path.encode() if cache_path else None, int(iters), ctypes.byref(lp),
                                    ctypes.byref(ms)))
     return lp, ms.value
+
+
+def lbm_reduce_noalloc(lattice, prec, physics, case, pops, plane_stride, flags=None, snap=None, stream=None):
+    """Allocation-free FP64 reduction of one domain's stored populations (see
+    include/lbm.h): pops, flags and snap are device pointers (ints) the caller
+    owns; returns the 8-number record of lbm_check."""
+    out = np.zeros(8)
+    st = lib().lbm_reduce_noalloc(lattice, prec, physics, ctypes.byref(case), pops, int(plane_stride), flags, snap,
+                                  _dp(out), stream)
+    if st not in (LBM_OK, LBM_EUNSTABLE):
+        raise LbmError(st, "lbm_reduce_noalloc failed")
+    return out, st
 
 
 def lbm_launches_per_step(ctx):
