@@ -166,6 +166,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(ms, device=None):
+    """The slowest rank's time (ms) through the initialised process group
+    (any backend); the local value when there is no group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(units_per_rank, world, steps, ms_max):
+    """Node updates of all ranks per second (weak scaling: every rank runs the
+    same batch), in millions."""
+    return world * units_per_rank * steps / (ms_max * 1e-3) / 1e6
+
+
 # ----------------------------------------------------------------------------- oracle timing
 def oracle_sample(wl, target_nodes):
     """OracleSim objects for the first cases of the workload up to target_nodes
@@ -310,14 +328,11 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), device="cuda")
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     ms_step = ms / K
-    value = world * fluid * K / (ms * 1e-3) / 1e6
+    value = whole_job_mlups(fluid, world, K, ms)
     launches = K * lbm.lbm_launches_per_step(sol.ctx) + 2 * (K // CHECK_EVERY)
     elem = {lbm.LBM_FP64: 8, lbm.LBM_FP32: 4}.get(wl["prec"], 2)
     alg_bytes = 2.0 * wl["planes"] * elem * fluid                # one read + one write per population

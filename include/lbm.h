@@ -194,9 +194,10 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes);
 int64_t lbm_steps_done(const lbm_ctx *ctx);
 
 /* Launch shape of the fused step.
- *   variant 0: one thread per node; blocks of `block` threads over tiles of
- *              `block` nodes; blocks_per_sm = resident blocks per SM of a
- *              persistent tile loop (0 = one block per tile, up to 64).
+ *   variant 0: one thread per node at a time; tiles of block *
+ *              nodes_per_thread nodes (1..8); blocks_per_sm = resident
+ *              blocks per SM of a persistent tile loop (0 = one block per
+ *              tile, up to 64).
  *   variant 1: bulk-copy pipeline (FP32 and 16-bit storage): persistent
  *              blocks keep `stages` - 1 tiles of source windows in flight in
  *              shared memory (cp.async.bulk on mbarriers) while computing the
@@ -310,6 +311,53 @@ lbm_status lbm_build_channel(int32_t dim, int32_t nx, int32_t ny, int32_t nz, in
  * for the 5 fields.  Other arguments as lbm_build_channel. */
 lbm_status lbm_build_pipe(int32_t nx, int32_t ny, int32_t nz, double R, uint32_t physics, const lbm_wall_bc *bc,
                           uint8_t *solid, lbm_link *links, size_t cap, size_t *nlinks);
+
+/* ------------------------------------------------------------------------
+ * Warm-start network (a service of this library, not part of the paper's
+ * method): a perceptron with layer widths {4, 64, 64, 64, 2}, tanh hidden
+ * layers and a linear output, mapping (x2/R, x3/R, f_Ha, f_cw) of a pipe
+ * cross-section to the normalised steady axial velocity and induced field.
+ * It is trained on steady fields the solver produced, by this library's own
+ * forward, backward and Adam kernels; parameters are FP32 masters with an
+ * FP16 copy used by the forward and backward passes (FP32 accumulation).
+ * Parameter layout: layer by layer, W (rows = outputs, row-major) then b.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_net lbm_net;
+
+/* Number of parameters of the network. */
+int64_t lbm_net_num_params(void);
+
+/* dims must be {4, 64, 64, 64, 2} (ndims = 5).  init: host, the initial
+ * parameters (the caller draws them).  stream: cudaStream_t (NULL = legacy
+ * default).  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_net_create(const int32_t *dims, int32_t ndims, const float *init, void *stream, lbm_net **out);
+void lbm_net_destroy(lbm_net *net);
+
+/* Copy the FP32 parameters out / in (host; set also resets Adam). */
+lbm_status lbm_net_get_params(lbm_net *net, float *host);
+lbm_status lbm_net_set_params(lbm_net *net, const float *host);
+
+/* y[n][2] = net(x[n][4]); device arrays; asynchronous on the net's stream. */
+lbm_status lbm_net_forward(lbm_net *net, const float *x, float *y, int64_t n);
+
+/* Mean squared error over the n samples (device x[n][4], targets t[n][2])
+ * and its gradient, added to the net's gradient accumulator (cleared by
+ * lbm_net_adam).  loss (host, may be NULL) receives the loss; grad (host, may
+ * be NULL) a copy of the accumulated gradient.  Synchronises when either
+ * output is requested. */
+lbm_status lbm_net_loss_grad(lbm_net *net, const float *x, const float *t, int64_t n, double *loss, float *grad);
+
+/* One Adam step (bias-corrected) on the accumulated gradient, which is then
+ * cleared; refreshes the FP16 copy. */
+lbm_status lbm_net_adam(lbm_net *net, float lr, float beta1, float beta2, float eps);
+
+/* Initial fields of a pipe case (axis x, centre ((ny-1)/2, (nz-1)/2), radius
+ * R) predicted by the network with features f_ha and f_cw:
+ * u = (u_hat * u_scale, 0, 0), B = (b_hat * b_scale, B0, 0) on fluid nodes;
+ * device outputs u[N][3], B[N][3] (FP32, N = nx*ny*nz), ready for
+ * lbm_init_equilibrium_device. */
+lbm_status lbm_net_pipe_fields(lbm_net *net, int32_t nx, int32_t ny, int32_t nz, double R, double f_ha, double f_cw,
+                               double u_scale, double b_scale, double B0, float *u, float *B);
 
 #ifdef __cplusplus
 }

@@ -47,12 +47,20 @@ def hartmann_channel(W, Ha, q, cw, tau_nu=0.8, u_target=0.02):
     return case, solid, links, info
 
 
-def pipe(shape, R, Ha, wall, tau_nu=0.8, tau_eta=0.9, u_target=0.02):
+def pipe(shape, R, Ha, wall, tau_nu=0.8, tau_eta=None, u_target=0.02):
     """MHD pipe along x (Sec. 6): D3Q19 flow + D3Q7 vector B; static no-slip
     curved wall; B1 insulating ('insulating'), perfectly conducting
     ('conducting') or Shercliff (('shercliff', c_w)); B2 = B_ext,2 and B3 = 0
-    given.  Returns (lbm_case, solid, links, info)."""
-    nu, eta = (tau_nu - 0.5) / 3.0, (tau_eta - 0.5) / 4.0
+    given.  tau_eta defaults to 0.9 (the paper's value), lowered for small
+    Shercliff c_w so that eta/(c_w R) stays below SHERCLIFF_KAPPA_MAX.
+    Returns (lbm_case, solid, links, info)."""
+    nu = (tau_nu - 0.5) / 3.0
+    if tau_eta is None:
+        eta = ETA_MAX
+        if wall not in ("insulating", "conducting"):
+            eta = min(ETA_MAX, max(ETA_MIN, SHERCLIFF_KAPPA_MAX * wall[1] * R))
+        tau_eta = 0.5 + 4.0 * eta
+    eta = (tau_eta - 0.5) / 4.0
     B0 = Ha * math.sqrt(nu * eta) / R
     accel = u_target * nu * (2.0 + Ha) / (R * R)
     if wall == "insulating":

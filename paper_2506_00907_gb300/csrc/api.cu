@@ -157,6 +157,9 @@ CaseDev<T> case_dev(const lbm_ctx *c, const CaseHost &cs) {
     d.om_f = T(1.0 / cs.cfg.tau_nu);
     d.om_h = c->hh ? T(1.0 / cs.cfg.tau_D) : T(0);
     d.om_g = c->hg ? T(1.0 / cs.cfg.tau_eta) : T(0);
+    d.omc_f = T(1.0 - 1.0 / cs.cfg.tau_nu);
+    d.omc_h = c->hh ? T(1.0 - 1.0 / cs.cfg.tau_D) : T(1);
+    d.omc_g = c->hg ? T(1.0 - 1.0 / cs.cfg.tau_eta) : T(1);
     d.guo = T(1.0 - 0.5 / cs.cfg.tau_nu);
     d.ax = T(cs.cfg.accel[0]);
     d.ay = T(cs.cfg.accel[1]);
@@ -391,7 +394,7 @@ cudaError_t launch_step_t(lbm_ctx *ctx) {
         tp.err = ctx->d_err;
         return ctx->ks.step_tma[ctx->tma_idx](&p, tp, step_grid(ctx), ctx->launch.block, ctx->tma_smem, ctx->stream);
     }
-    return ctx->ks.step(&p, step_grid(ctx), ctx->launch.block, ctx->stream);
+    return ctx->ks.step(&p, ctx->launch.nodes_per_thread, step_grid(ctx), ctx->launch.block, ctx->stream);
 }
 
 lbm_status launch_step(lbm_ctx *ctx) {
@@ -519,6 +522,12 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
         }
         cs.N = (int32_t)N;
         cs.stride = round_up(N, 64);
+        if (cs.stride * ctx->P >= ((int64_t)1 << 31)) {
+            lbm_status s = fail(ctx, LBM_EINVAL, "case %d: %lld nodes x %d populations exceed 2^31 elements", c,
+                                (long long)N, ctx->P);
+            free_ctx(ctx);
+            return s;
+        }
         cs.pop_off = pool;
         cs.node_off = nodes;
         pool += cs.stride * ctx->P;
@@ -820,6 +829,8 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
     int idx = 0;
     if (L.variant == 0) {
         if (L.blocks_per_sm < 0 || L.blocks_per_sm > 64) return fail(ctx, LBM_EINVAL, "blocks per SM must be 0..64");
+        if (L.nodes_per_thread < 1 || L.nodes_per_thread > 8) return fail(ctx, LBM_EINVAL, "nodes per thread must be 1..8");
+        tile = L.block * L.nodes_per_thread;
     } else {
         if (L.nodes_per_thread < 1 || L.nodes_per_thread > 8) return fail(ctx, LBM_EINVAL, "nodes per thread must be 1..8");
         if (L.stages < 2 || L.stages > TMA_MAX_STAGES) return fail(ctx, LBM_EINVAL, "stages must be 2..%d", TMA_MAX_STAGES);
@@ -917,7 +928,8 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
     CK(cudaEventCreate(&e1));
     std::vector<lbm_launch> cands;
     for (int b : {128, 256})
-        for (int p : {0, 4, 8}) cands.push_back(lbm_launch{0, b, p, 1, 2, 1});
+        for (int p : {0, 4, 8})
+            for (int npt : {1, 2, 4}) cands.push_back(lbm_launch{0, b, p, npt, 2, 1});
     if (!ctx->dbl)
         for (int b : {128, 256})
             for (int npt : {1, 2})

@@ -9,7 +9,7 @@
 namespace lbm {
 
 struct KernelSet {
-    cudaError_t (*step)(const void *params, int grid, int block, cudaStream_t s);
+    cudaError_t (*step)(const void *params, int npt, int grid, int block, cudaStream_t s);
     cudaError_t (*init_d)(const void *params, int grid, int block, cudaStream_t s);   // FP64 host-side fields
     cudaError_t (*init_f)(const void *params, int grid, int block, cudaStream_t s);   // FP32 device fields
     cudaError_t (*moments)(const void *params, int grid, int block, cudaStream_t s);
@@ -26,8 +26,8 @@ constexpr int TMA_MINB[3] = {1, 3, 4};
 template <int DIM, bool HH, bool HG, class S>
 struct Launch {
     using T = typename Codec<S>::T;
-    static cudaError_t step(const void *p, int g, int b, cudaStream_t s) {
-        k_step<DIM, HH, HG, S><<<g, b, 0, s>>>(*static_cast<const StepParams<T> *>(p));
+    static cudaError_t step(const void *p, int npt, int g, int b, cudaStream_t s) {
+        k_step<DIM, HH, HG, S><<<g, b, 0, s>>>(*static_cast<const StepParams<T> *>(p), npt);
         return cudaGetLastError();
     }
     static cudaError_t init_d(const void *p, int g, int b, cudaStream_t s) {

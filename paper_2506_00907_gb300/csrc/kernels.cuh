@@ -58,6 +58,9 @@ template <> struct Codec<__nv_bfloat16> {
 
 LBM_DEV uint32_t fast_div(uint32_t n, FastDiv d) { return (__umulhi(n, d.m) + n) >> d.s; }
 
+LBM_DEV float fmaf_t(float a, float b, float c) { return fmaf(a, b, c); }
+LBM_DEV double fmaf_t(double a, double b, double c) { return a * b + c; }   // FP64 serves parity: no fused rounding
+
 template <class T>
 struct StepParams {
     const void *src;
@@ -159,7 +162,7 @@ LBM_DEV void collide(T (&p)[PL::P], const CaseDev<T> &c) {
         const T eF = ex * Fx + ey * Fy + ez * Fz;
         // Guo source (1 - 1/(2 tau)) w [3 (e - u).F + 9 (e.u)(e.F)]
         const T S = c.guo * w * (T(3) * (eF - uF) + T(9) * eu * eF);
-        p[a] = p[a] + c.om_f * (feq - p[a]) + S;
+        p[a] = fmaf_t(c.om_f, feq, fmaf_t(c.omc_f, p[a], S));
     }
     if constexpr (HH) {
         T dC = 0;
@@ -168,7 +171,7 @@ LBM_DEV void collide(T (&p)[PL::P], const CaseDev<T> &c) {
         const T C = dC + c.ref_C;
 #pragma unroll
         for (int a = 0; a < QM; ++a)
-            p[PL::H0 + a] = p[PL::H0 + a] + c.om_h * (heq_dir<M, T>(a, dC, C, u) - p[PL::H0 + a]);
+            p[PL::H0 + a] = fmaf_t(c.om_h, heq_dir<M, T>(a, dC, C, u), c.omc_h * p[PL::H0 + a]);
     }
     if constexpr (HG) {
 #pragma unroll
@@ -176,7 +179,7 @@ LBM_DEV void collide(T (&p)[PL::P], const CaseDev<T> &c) {
 #pragma unroll
             for (int a = 0; a < QM; ++a) {
                 const int q = PL::G0 + k * QM + a;
-                p[q] = p[q] + c.om_g * (geq_dir<M, T>(a, k, dB[k], B, u) - p[q]);
+                p[q] = fmaf_t(c.om_g, geq_dir<M, T>(a, k, dB[k], B, u), c.omc_g * p[q]);
             }
         }
     }
@@ -184,18 +187,18 @@ LBM_DEV void collide(T (&p)[PL::P], const CaseDev<T> &c) {
 
 // ------------------------------------------------------------------ wall links
 template <class S, class T>
-LBM_DEV T field_sum(const S *src, int64_t stride, int q0, int nq, int node) {
+LBM_DEV T field_sum(const S *src, int stride, int q0, int nq, int node) {
     T s = 0;
-    for (int j = 0; j < nq; ++j) s += Codec<S>::ld(src + (int64_t)(q0 + j) * stride + node);
+    for (int j = 0; j < nq; ++j) s += Codec<S>::ld(src + ((q0 + j) * stride + node));
     return s;
 }
 
 template <class PL, class S, class T>
 LBM_DEV T eval_link(const LinkDev<T> &L, const S *src, const CaseDev<T> &c) {
-    const int64_t st = c.stride;
-    const T paA = Codec<S>::ld(src + (int64_t)L.plane_a * st + L.nodeA);
-    const T papA = Codec<S>::ld(src + (int64_t)L.plane_ap * st + L.nodeA);
-    const T papE = Codec<S>::ld(src + (int64_t)L.plane_ap * st + L.nodeE);
+    const int st = (int)c.stride;
+    const T paA = Codec<S>::ld(src + ((int)L.plane_a * st + L.nodeA));
+    const T papA = Codec<S>::ld(src + ((int)L.plane_ap * st + L.nodeA));
+    const T papE = Codec<S>::ld(src + ((int)L.plane_ap * st + L.nodeE));
     T v = L.c0 + L.ca * paA + L.cap * papA + L.cape * papE;
     if (L.flags & LINK_NEED_PHI) {
         const int nq = L.phi_plane0 < PL::QF ? PL::QF : PL::QM;
@@ -256,42 +259,59 @@ LBM_DEV void coords(const CaseDev<T> &c, int n, int &x, int &y, int &z, int &r) 
 
 // ------------------------------------------------------------------ fused step
 template <int DIM, bool HH, bool HG, class S>
-__global__ void __launch_bounds__(256) k_step(const StepParams<typename Codec<S>::T> prm) {
+LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDev<typename Codec<S>::T> &c, int n,
+                       uint8_t fl) {
     using PL = Planes<DIM, HH, HG>;
     using T = typename Codec<S>::T;
     constexpr int P = PL::P;
-    for (int t = blockIdx.x; t < prm.ntiles; t += gridDim.x) {
-        const int2 tile = prm.tiles[t];
+    const S *src = static_cast<const S *>(prm.src) + c.pop_off;
+    S *dst = static_cast<S *>(prm.dst) + c.pop_off;
+    const int nx = c.nx, ny = c.ny;
+    int x, y, z, r;
+    coords<DIM, T>(c, n, x, y, z, r);
+    // source node x - e_a with periodic wrap: index of x-1 is xi[0] (e_x = +1)
+    const int xi[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
+    const int yi[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};
+    int zi[3] = {0, 0, 0};
+    if constexpr (DIM == 3) {
+        const int nz = c.nz, nxy = nx * ny;
+        zi[0] = (z == 0 ? nz - 1 : z - 1) * nxy;
+        zi[1] = z * nxy;
+        zi[2] = (z == nz - 1 ? 0 : z + 1) * nxy;
+    }
+    // in-case indices are 32-bit (the host keeps P * stride below 2^31)
+    const int st32 = (int)c.stride;
+    T p[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        const int src_node = xi[1 - PL::ex(q)] + yi[1 - PL::ey(q)] + zi[1 - PL::ez(q)];
+        p[q] = Codec<S>::ld(src + (q * st32 + src_node));
+    }
+    if (fl & NODE_BOUNDARY) apply_links<PL, S, T>(p, prm, c, src, n, r);
+    collide<PL, HH, HG, T>(p, c);
+#pragma unroll
+    for (int q = 0; q < P; ++q) Codec<S>::st(dst + (q * st32 + n), p[q]);
+}
+
+// Tiles of blockDim.x * npt nodes; each thread takes nodes tid, tid + blockDim.x, ...
+// The next tile's record and the thread's first flag are fetched one tile ahead.
+template <int DIM, bool HH, bool HG, class S>
+__global__ void __launch_bounds__(256, DIM == 2 ? 4 : 2) k_step(const StepParams<typename Codec<S>::T> prm, const int npt) {
+    using T = typename Codec<S>::T;
+    int t = blockIdx.x;
+    if (t >= prm.ntiles) return;
+    int2 tile = prm.tiles[t];
+    for (; t < prm.ntiles; t += gridDim.x) {
+        const int tn = t + gridDim.x;
+        const int2 next = tn < prm.ntiles ? prm.tiles[tn] : tile;
         const CaseDev<T> &c = prm.cases[tile.x];
-        const int n = tile.y + (int)threadIdx.x;
-        if (n >= c.N) continue;
-        const uint8_t fl = prm.flags[c.node_off + n];
-        if (!(fl & NODE_FLUID)) continue;
-        const S *src = static_cast<const S *>(prm.src) + c.pop_off;
-        S *dst = static_cast<S *>(prm.dst) + c.pop_off;
-        const int nx = c.nx, ny = c.ny;
-        int x, y, z, r;
-        coords<DIM, T>(c, n, x, y, z, r);
-        // source node x - e_a with periodic wrap: index of x-1 is xi[0] (e_x = +1)
-        const int xi[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
-        const int yi[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};
-        int zi[3] = {0, 0, 0};
-        if constexpr (DIM == 3) {
-            const int nz = c.nz, nxy = nx * ny;
-            zi[0] = (z == 0 ? nz - 1 : z - 1) * nxy;
-            zi[1] = z * nxy;
-            zi[2] = (z == nz - 1 ? 0 : z + 1) * nxy;
+        for (int k = 0; k < npt; ++k) {
+            const int n = tile.y + (int)threadIdx.x + k * (int)blockDim.x;
+            if (n >= c.N) break;
+            const uint8_t fl = prm.flags[c.node_off + n];
+            if (fl & NODE_FLUID) step_node<DIM, HH, HG, S>(prm, c, n, fl);
         }
-        T p[P];
-#pragma unroll
-        for (int q = 0; q < P; ++q) {
-            const int src_node = xi[1 - PL::ex(q)] + yi[1 - PL::ey(q)] + zi[1 - PL::ez(q)];
-            p[q] = Codec<S>::ld(src + (int64_t)q * c.stride + src_node);
-        }
-        if (fl & NODE_BOUNDARY) apply_links<PL, S, T>(p, prm, c, src, n, r);
-        collide<PL, HH, HG, T>(p, c);
-#pragma unroll
-        for (int q = 0; q < P; ++q) Codec<S>::st(dst + (int64_t)q * c.stride + n, p[q]);
+        tile = next;
     }
 }
 
@@ -320,9 +340,10 @@ __global__ void __launch_bounds__(256) k_init(const InitParams<typename Codec<S>
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= c.N) return;
     S *dst = static_cast<S *>(ip.dst) + c.pop_off;
+    const int st32 = (int)c.stride;
     if (!(ip.flags[c.node_off + n] & NODE_FLUID)) {
 #pragma unroll
-        for (int q = 0; q < P; ++q) Codec<S>::st(dst + (int64_t)q * c.stride + n, T(0));
+        for (int q = 0; q < P; ++q) Codec<S>::st(dst + (q * st32 + n), T(0));
         return;
     }
     const T rho = ip.rho ? T(ip.rho[n]) : ip.rho0;
@@ -350,7 +371,7 @@ __global__ void __launch_bounds__(256) k_init(const InitParams<typename Codec<S>
     }
     collide<PL, HH, HG, T>(p, c);
 #pragma unroll
-    for (int q = 0; q < P; ++q) Codec<S>::st(dst + (int64_t)q * c.stride + n, p[q]);
+    for (int q = 0; q < P; ++q) Codec<S>::st(dst + (q * st32 + n), p[q]);
 }
 
 // ------------------------------------------------------------------ moments

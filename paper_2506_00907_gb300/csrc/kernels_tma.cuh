@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(256, MINB) k_step_tma(const StepParams<typenam
         const int *whi = wlo + P;
         const int nx = c.nx, ny = c.ny, nz = c.nz, nxy = nx * ny;
         const int len = min(tp.tile_nodes, c.N - tile.y);
+        const int st32 = (int)c.stride;
         for (int i = tid; i < len; i += blockDim.x) {
             const int n = tile.y + i;
             const uint8_t fl = prm.flags[c.node_off + n];
@@ -186,13 +187,13 @@ __global__ void __launch_bounds__(256, MINB) k_step_tma(const StepParams<typenam
                     const int sn = xi[1 - PL::ex(q)] + yi[1 - PL::ey(q)] + zi[1 - PL::ez(q)];
                     p[q] = (sn >= wlo[q] && sn < whi[q])
                                ? (T)Codec<S>::ld_shared(sb + (size_t)q * tp.cap + (sn - wlo[q]))
-                               : Codec<S>::ld(src + (int64_t)q * c.stride + sn);
+                               : Codec<S>::ld(src + (q * st32 + sn));
                 }
             }
             if (fl & NODE_BOUNDARY) apply_links<PL, S, T>(p, prm, c, src, n, r);
             collide<PL, HH, HG, T>(p, c);
 #pragma unroll
-            for (int q = 0; q < P; ++q) Codec<S>::st(dst + (int64_t)q * c.stride + n, p[q]);
+            for (int q = 0; q < P; ++q) Codec<S>::st(dst + (q * st32 + n), p[q]);
         }
         __syncthreads();   // every thread is done with stage st before it is refilled
         st = st + 1 == NS ? 0 : st + 1;

@@ -21,6 +21,7 @@ struct CaseDev {
     int32_t brow_off;     // offset of the case's row table (ny*nz + 1 entries) in brow
     int32_t pad0;
     T om_f, om_h, om_g;   // 1/tau_nu, 1/tau_D, 1/tau_eta
+    T omc_f, omc_h, omc_g; // 1 - om (the relaxation p + om (eq - p) = (1 - om) p + om eq)
     T guo;                // 1 - 1/(2 tau_nu): weight of the Guo source
     T ax, ay, az;         // body force per unit mass
     T ref_rho, ref_C;     // storage references: planes hold p - w_a * phi_ref

@@ -57,3 +57,16 @@ def pipe_draws(n, seed=SEED, Ha=(10.0, 50.0), cw=(1e-3, 1.0)):
     h = r.uniform(Ha[0], Ha[1], n)
     c = 10.0 ** r.uniform(np.log10(cw[0]), np.log10(cw[1]), n)
     return [dict(Ha=float(h[i]), cw=float(c[i])) for i in range(n)]
+
+
+def net_init(seed=SEED, dims=(4, 64, 64, 64, 2)):
+    """Initial parameters of the warm-start network: Glorot-uniform weights,
+    zero biases, in the flat layout W_1, b_1, W_2, b_2, ... (rows = outputs)."""
+    r = rng(seed)
+    out = []
+    for i in range(len(dims) - 1):
+        fan_in, fan_out = dims[i], dims[i + 1]
+        lim = np.sqrt(6.0 / (fan_in + fan_out))
+        out.append(r.uniform(-lim, lim, fan_out * fan_in))
+        out.append(np.zeros(fan_out))
+    return np.concatenate(out).astype(np.float32)

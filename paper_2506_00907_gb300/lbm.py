@@ -96,6 +96,17 @@ def lib():
                                                     ctypes.POINTER(ctypes.c_size_t)])
         sig["lbm_build_pipe"] = (ctypes.c_int, [i32, i32, i32, ctypes.c_double, ctypes.c_uint32, vp, vp, vp,
                                                 ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)])
+        sig["lbm_net_num_params"] = (i64, [])
+        sig["lbm_net_create"] = (ctypes.c_int, [ctypes.POINTER(i32), i32, vp, vp, ctypes.POINTER(vp)])
+        sig["lbm_net_destroy"] = (None, [vp])
+        sig["lbm_net_get_params"] = (ctypes.c_int, [vp, vp])
+        sig["lbm_net_set_params"] = (ctypes.c_int, [vp, vp])
+        sig["lbm_net_forward"] = (ctypes.c_int, [vp, vp, vp, i64])
+        sig["lbm_net_loss_grad"] = (ctypes.c_int, [vp, vp, vp, i64, dp, vp])
+        sig["lbm_net_adam"] = (ctypes.c_int, [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float])
+        sig["lbm_net_pipe_fields"] = (ctypes.c_int, [vp, i32, i32, i32, ctypes.c_double, ctypes.c_double,
+                                                     ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                     ctypes.c_double, vp, vp])
         sig["lbm_reduce_noalloc"] = (ctypes.c_int, [i32, i32, ctypes.c_uint32, ctypes.POINTER(lbm_case), vp, i64,
                                                      vp, vp, dp, vp])
         for name, (res, args) in sig.items():
@@ -292,6 +303,73 @@ def lbm_build_pipe(shape, R, physics, bcs):
     if st != LBM_OK:
         raise LbmError(st, "lbm_build_pipe failed")
     return solid, links
+
+
+NET_DIMS = (4, 64, 64, 64, 2)
+
+
+def _st(st, what):
+    if st != LBM_OK:
+        raise LbmError(st, what)
+
+
+class Net:
+    """The warm-start network (include/lbm.h, lbm_net_*): device parameters,
+    the library's forward / backward / Adam kernels."""
+
+    def __init__(self, init_params, stream=None):
+        init = np.ascontiguousarray(init_params, dtype=np.float32)
+        assert init.size == lib().lbm_net_num_params()
+        dims = (ctypes.c_int32 * 5)(*NET_DIMS)
+        h = ctypes.c_void_p()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        _st(lib().lbm_net_create(dims, 5, init.ctypes.data, stream, ctypes.byref(h)), "lbm_net_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lbm_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def num_params():
+        return lib().lbm_net_num_params()
+
+    def get_params(self):
+        out = np.zeros(self.num_params(), dtype=np.float32)
+        _st(lib().lbm_net_get_params(self.h, out.ctypes.data), "lbm_net_get_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _st(lib().lbm_net_set_params(self.h, p.ctypes.data), "lbm_net_set_params")
+
+    def forward(self, x, y):
+        """x, y: torch float32 CUDA tensors [n, 4] and [n, 2]."""
+        _st(lib().lbm_net_forward(self.h, x.data_ptr(), y.data_ptr(), x.shape[0]), "lbm_net_forward")
+
+    def loss_grad(self, x, t, want_grad=False):
+        loss = ctypes.c_double()
+        g = np.zeros(self.num_params(), dtype=np.float32) if want_grad else None
+        _st(lib().lbm_net_loss_grad(self.h, x.data_ptr(), t.data_ptr(), x.shape[0], ctypes.byref(loss),
+                                    g.ctypes.data if want_grad else None), "lbm_net_loss_grad")
+        return loss.value, g
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        _st(lib().lbm_net_adam(self.h, lr, beta1, beta2, eps), "lbm_net_adam")
+
+    def pipe_fields(self, shape, R, f_ha, f_cw, u_scale, b_scale, B0, u, B):
+        nx, ny, nz = shape
+        _st(lib().lbm_net_pipe_fields(self.h, nx, ny, nz, R, f_ha, f_cw, u_scale, b_scale, B0, u.data_ptr(),
+                                      B.data_ptr()), "lbm_net_pipe_fields")
 
 
 # ----------------------------------------------------------------- convenience

@@ -288,13 +288,21 @@ def test_bulk_copy_pipeline_is_bitwise_identical(dim, prec):
     ref.set_launch(0, 128, 0)
     ref.step(15)
     want = ref.get_state()
-    for block, npt, stages, minb in ((128, 1, 2, 1), (256, 2, 3, 3), (64, 4, 4, 4), (192, 3, 2, 4), (256, 1, 4, 1)):
+    ran = 0
+    for block, npt, stages, minb in ((128, 1, 2, 1), (256, 2, 3, 3), (64, 4, 4, 4), (192, 3, 2, 4), (256, 1, 4, 1),
+                                     (64, 1, 3, 3)):
         g = _random_pair(dim, True, True, seed=77, prec=prec, shape=shape).gpu
-        g.set_launch(1, block, nodes_per_thread=npt, stages=stages, min_blocks=minb)
+        try:
+            g.set_launch(1, block, nodes_per_thread=npt, stages=stages, min_blocks=minb)
+        except lbm.LbmError as e:      # the ring of this shape does not fit in shared memory
+            assert e.status == lbm.LBM_EINVAL and "shared memory" in str(e)
+            continue
         g.set_graph(4)
         g.step(15)
         assert np.array_equal(g.get_state(), want), (block, npt, stages, minb)
         g.check()
+        ran += 1
+    assert ran >= 3
 
 
 def test_bulk_copy_pipeline_batched_cases():
