@@ -78,7 +78,7 @@ typedef struct {
     uint32_t physics;              /* LBM_FLOW | optional LBM_CD | optional LBM_MHD */
     int32_t ncases;                /* >= 1; all cases are advanced by one launch per step */
     const lbm_case *cases;         /* ncases entries, copied */
-    void *stream;                  /* cudaStream_t; NULL = legacy default stream */
+    void *stream;                  /* cudaStream_t; NULL = the context creates and owns a non-blocking stream */
     int32_t device;                /* CUDA device ordinal */
 } lbm_config;
 
@@ -142,7 +142,9 @@ lbm_status lbm_init_equilibrium(lbm_ctx *ctx, int32_t case_id, const double *rho
                                 const double *u, const double *C, const double *B);
 
 /* Same, from DEVICE fields in FP32 (u and B as [N][3], rho/C may be NULL):
- * the warm-start path.  Asynchronous on the context stream. */
+ * the warm-start path.  Asynchronous on the context stream, which reads the
+ * fields: work that writes them on another stream must be complete (or
+ * ordered before the context stream by the caller). */
 lbm_status lbm_init_equilibrium_device(lbm_ctx *ctx, int32_t case_id, const float *rho,
                                        const float *u, const float *C, const float *B);
 
@@ -170,7 +172,10 @@ lbm_status lbm_moments(lbm_ctx *ctx, int32_t case_id, double *rho, double *u,
  *                     sum |phi - phi_prev|^2, sum |phi|^2 }
  * with phi = (u, C, B - B0) (the parts the physics mask enables) and phi_prev
  * the value at the previous call (the first call compares with zero).  The
- * reduction is deterministic (fixed order).  out: host, 8*ncases doubles.
+ * per-node terms are formed in the step's arithmetic precision (FP64 storage:
+ * FP64, otherwise FP32, which also keeps phi_prev); every sum over nodes is
+ * FP64.  The reduction is deterministic (fixed order).  out: host, 8*ncases
+ * doubles.
  * Synchronises.  Returns LBM_EUNSTABLE (after filling out) if any population
  * is not finite, LBM_ETIMEOUT if a bounded device wait of an earlier step
  * gave up.  Errors: LBM_ECUDA. */
@@ -231,7 +236,9 @@ lbm_status lbm_get_launch(const lbm_ctx *ctx, lbm_launch *launch);
  * Errors: LBM_ECUDA. */
 lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm_launch *best, double *best_ms);
 
-/* Kernel launches issued per lbm_step step (for launch accounting). */
+/* Kernel launches issued per time step (for launch accounting): the bulk
+ * step over the node tiles, plus the boundary-node step when any case has
+ * wall links. */
 int32_t lbm_launches_per_step(const lbm_ctx *ctx);
 
 /* Device storage of the current populations (for zero-copy inspection):
@@ -240,6 +247,19 @@ int32_t lbm_launches_per_step(const lbm_ctx *ctx);
  * shifted by w_a * phi_ref.  Errors: LBM_EINVAL. */
 lbm_status lbm_device_state(lbm_ctx *ctx, int32_t case_id, void **base, int32_t *elem_bytes,
                             int64_t *plane_stride, int64_t *case_offset, int32_t *planes);
+
+/* Copies the state of `src` into `dst` at the precision of `dst` (a service
+ * of the library; the paper works at one precision).  Both contexts must be on
+ * the same device with the same lattice, physics and identical case list; the
+ * caller sets the same walls on both (lbm_set_walls copies are per context).
+ * Every precision stores p - w_a * phi_ref with the references of the case
+ * (rho0, C0, B0), so the stored values are rounded element-wise to the
+ * destination type (round to nearest).  The residual snapshot and the step
+ * count are copied too, so lbm_check / lbm_run_to_steady on `dst` continue
+ * the history of `src`.  Typical use: run a 16-bit storage context towards
+ * steady state, then finish in FP32 or FP64.  Synchronises both streams.
+ * Errors: LBM_EINVAL (mismatched contexts), LBM_ECUDA. */
+lbm_status lbm_convert_state(lbm_ctx *dst, lbm_ctx *src);
 
 /* Allocation-free FP64 reduction of one domain (the paper has no counterpart;
  * this is a service of the library).  It computes, for a population buffer
@@ -256,8 +276,11 @@ lbm_status lbm_device_state(lbm_ctx *ctx, int32_t case_id, void **base, int32_t 
  *            case offset), planes of `plane_stride` elements.
  *   flags:   device, nx*ny*nz bytes, nonzero = fluid; NULL counts every node.
  *   snap:    device, 7 * nx*ny*nz doubles holding phi_prev = (u, C, B - B0)
- *            plane by plane, replaced by the current phi; NULL skips the
- *            residual (sums 6 and 7 then compare with zero).
+ *            plane by plane, replaced by the current phi (the planes the
+ *            lattice and physics can make nonzero; the rest are not touched);
+ *            NULL skips the residual (sums 6 and 7 then compare with zero).
+ *            Per-node terms are formed as in lbm_check: in FP32 unless the
+ *            precision is FP64 (phi_prev is then read rounded to FP32).
  *   out:     host, 8 doubles, the record of lbm_check().
  *   stream:  cudaStream_t (NULL = legacy default stream).  Synchronises it.
  * Limit: at most LBM_NOALLOC_MAX_NODES nodes (larger domains: LBM_EINVAL, with
@@ -354,8 +377,8 @@ lbm_status lbm_net_adam(lbm_net *net, float lr, float beta1, float beta2, float 
 /* Initial fields of a pipe case (axis x, centre ((ny-1)/2, (nz-1)/2), radius
  * R) predicted by the network with features f_ha and f_cw:
  * u = (u_hat * u_scale, 0, 0), B = (b_hat * b_scale, B0, 0) on fluid nodes;
- * device outputs u[N][3], B[N][3] (FP32, N = nx*ny*nz), ready for
- * lbm_init_equilibrium_device. */
+ * device outputs u[N][3], B[N][3] (FP32, N = nx*ny*nz), written on the
+ * network's stream, for lbm_init_equilibrium_device. */
 lbm_status lbm_net_pipe_fields(lbm_net *net, int32_t nx, int32_t ny, int32_t nz, double R, double f_ha, double f_cw,
                                double u_scale, double b_scale, double B0, float *u, float *B);
 

@@ -25,7 +25,6 @@ struct CaseHost {
     lbm_case cfg;
     int32_t N = 0;
     int64_t stride = 0, pop_off = 0, node_off = 0;
-    int32_t brow_off = 0;
     std::vector<uint8_t> solid;      // empty = all fluid
     std::vector<lbm_link> links;
 };
@@ -75,14 +74,18 @@ struct lbm_ctx {
     int32_t ntiles = 0;
     int32_t *d_case_tile_lo = nullptr;
     BRec *d_brec = nullptr;
-    int32_t *d_brow = nullptr;
+    int32_t nbrec = 0;
     void *d_links = nullptr;
-    size_t cap_brec = 0, cap_brow = 0, cap_links = 0;
+    size_t cap_brec = 0, cap_links = 0;
     double *d_snap = nullptr, *d_part = nullptr, *d_red = nullptr, *h_red = nullptr;
     double *d_mom = nullptr;
     int64_t max_case_nodes = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // boundary nodes run on a side stream, forked from and joined back into
+    // `stream` every step, so that they overlap the bulk launch
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int graph_steps = 0;
     int64_t steps = 0;
@@ -92,6 +95,9 @@ struct lbm_ctx {
 };
 
 namespace {
+
+// residual snapshot entries hold phi in the step's arithmetic precision
+size_t snap_elem(const lbm_ctx *c) { return c->dbl ? sizeof(double) : sizeof(float); }
 
 lbm_status fail(lbm_ctx *c, lbm_status st, const char *fmt, ...) {
     char buf[512];
@@ -153,7 +159,6 @@ CaseDev<T> case_dev(const lbm_ctx *c, const CaseHost &cs) {
     d.pop_off = cs.pop_off;
     d.stride = cs.stride;
     d.node_off = cs.node_off;
-    d.brow_off = cs.brow_off;
     d.om_f = T(1.0 / cs.cfg.tau_nu);
     d.om_h = c->hh ? T(1.0 / cs.cfg.tau_D) : T(0);
     d.om_g = c->hg ? T(1.0 / cs.cfg.tau_eta) : T(0);
@@ -303,12 +308,10 @@ lbm_status build_tiles(lbm_ctx *ctx) {
 template <class T>
 lbm_status upload_walls_t(lbm_ctx *ctx) {
     std::vector<BRec> brec;
-    std::vector<int32_t> brow;
     std::vector<LinkDev<T>> links;
     std::vector<uint8_t> flags((size_t)ctx->total_nodes, 0);
-    for (auto &cs : ctx->cases) {
-        const int64_t rows = (int64_t)cs.cfg.ny * cs.cfg.nz;
-        cs.brow_off = (int32_t)brow.size();
+    for (size_t ci = 0; ci < ctx->cases.size(); ++ci) {
+        CaseHost &cs = ctx->cases[ci];
         std::vector<int32_t> order(cs.links.size());
         for (size_t i = 0; i < order.size(); ++i) order[i] = (int32_t)i;
         std::stable_sort(order.begin(), order.end(),
@@ -316,13 +319,11 @@ lbm_status upload_walls_t(lbm_ctx *ctx) {
         for (int32_t n = 0; n < cs.N; ++n)
             flags[cs.node_off + n] = (cs.solid.empty() || !cs.solid[n]) ? NODE_FLUID : 0;
         size_t i = 0;
-        int64_t row = 0;
         for (; i < order.size();) {
             const uint32_t node = cs.links[order[i]].node;
-            const int64_t r = node / cs.cfg.nx;
-            while (row <= r) { brow.push_back((int32_t)brec.size()); ++row; }
             BRec b{};
             b.node = (int32_t)node;
+            b.cs = (int32_t)ci;
             b.lo = (int32_t)links.size();
             while (i < order.size() && cs.links[order[i]].node == node) {
                 links.push_back(link_dev<T>(ctx, cs, cs.links[order[i]]));
@@ -332,8 +333,8 @@ lbm_status upload_walls_t(lbm_ctx *ctx) {
             brec.push_back(b);
             flags[cs.node_off + node] |= NODE_BOUNDARY;
         }
-        while (row <= rows) { brow.push_back((int32_t)brec.size()); ++row; }
     }
+    ctx->nbrec = (int32_t)brec.size();
     if (brec.empty()) brec.push_back(BRec{-1, 0, 0, 0});
     if (links.empty()) links.push_back(LinkDev<T>{});
     auto grow = [&](void **ptr, size_t &cap, size_t bytes) -> lbm_status {
@@ -347,10 +348,8 @@ lbm_status upload_walls_t(lbm_ctx *ctx) {
     };
     lbm_status st;
     if ((st = grow((void **)&ctx->d_brec, ctx->cap_brec, brec.size() * sizeof(BRec))) != LBM_OK) return st;
-    if ((st = grow((void **)&ctx->d_brow, ctx->cap_brow, brow.size() * sizeof(int32_t))) != LBM_OK) return st;
     if ((st = grow(&ctx->d_links, ctx->cap_links, links.size() * sizeof(LinkDev<T>))) != LBM_OK) return st;
     CK(cudaMemcpy(ctx->d_brec, brec.data(), brec.size() * sizeof(BRec), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ctx->d_brow, brow.data(), brow.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_links, links.data(), links.size() * sizeof(LinkDev<T>), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_flags, flags.data(), flags.size(), cudaMemcpyHostToDevice));
     drop_graphs(ctx);
@@ -371,7 +370,7 @@ StepParams<T> step_params(const lbm_ctx *c) {
     p.tiles = c->d_tiles;
     p.ntiles = c->ntiles;
     p.brec = c->d_brec;
-    p.brow = c->d_brow;
+    p.nbrec = c->nbrec;
     p.links = static_cast<const LinkDev<T> *>(c->d_links);
     return p;
 }
@@ -385,6 +384,15 @@ int step_grid(const lbm_ctx *c) {
 template <class T>
 cudaError_t launch_step_t(lbm_ctx *ctx) {
     const StepParams<T> p = step_params<T>(ctx);
+    // boundary nodes (disjoint from the bulk nodes; same source and target
+    // buffers) on the side stream, concurrently with the bulk launch
+    if (ctx->nbrec > 0) {
+        cudaError_t e = cudaEventRecord(ctx->ev_fork, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+        if (e == cudaSuccess) e = ctx->ks.boundary(&p, (ctx->nbrec + 127) / 128, 128, ctx->side);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
+        if (e != cudaSuccess) return e;
+    }
     if (ctx->launch.variant == 1) {
         TmaParams tp;
         tp.tile_nodes = ctx->tile_nodes;
@@ -392,9 +400,16 @@ cudaError_t launch_step_t(lbm_ctx *ctx) {
         tp.cap = ctx->tile_nodes + 2 * A;
         tp.stages = ctx->launch.stages;
         tp.err = ctx->d_err;
-        return ctx->ks.step_tma[ctx->tma_idx](&p, tp, step_grid(ctx), ctx->launch.block, ctx->tma_smem, ctx->stream);
+        const cudaError_t e =
+            ctx->ks.step_tma[ctx->tma_idx](&p, tp, step_grid(ctx), ctx->launch.block, ctx->tma_smem, ctx->stream);
+        if (e != cudaSuccess) return e;
+    } else {
+        const cudaError_t e =
+            ctx->ks.step(&p, ctx->launch.nodes_per_thread, step_grid(ctx), ctx->launch.block, ctx->stream);
+        if (e != cudaSuccess) return e;
     }
-    return ctx->ks.step(&p, ctx->launch.nodes_per_thread, step_grid(ctx), ctx->launch.block, ctx->stream);
+    if (ctx->nbrec > 0) return cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
+    return cudaSuccess;
 }
 
 lbm_status launch_step(lbm_ctx *ctx) {
@@ -423,9 +438,10 @@ lbm_status launch_init(lbm_ctx *ctx, int case_id, const FT *rho, const FT *u, co
     const int grid = (int)((cs.N + 255) / 256);
     CK(fn(&ip, grid, 256, ctx->stream));
     // residual history of the case starts again from zero
+    const size_t se = snap_elem(ctx);
     for (int k = 0; k < SNAP_Q; ++k)
-        CK(cudaMemsetAsync(ctx->d_snap + (int64_t)k * ctx->total_nodes + cs.node_off, 0,
-                           (size_t)cs.N * sizeof(double), ctx->stream));
+        CK(cudaMemsetAsync(reinterpret_cast<char *>(ctx->d_snap) + ((int64_t)k * ctx->total_nodes + cs.node_off) * se,
+                           0, (size_t)cs.N * se, ctx->stream));
     return LBM_OK;
 }
 
@@ -462,10 +478,13 @@ void free_ctx(lbm_ctx *c) {
     if (!c) return;
     drop_graphs(c);
     void *ptrs[] = {c->pool[0], c->pool[1], c->d_flags, c->d_cases, c->d_tiles, c->d_case_tile_lo,
-                    c->d_brec, c->d_brow, c->d_links, c->d_snap, c->d_part, c->d_red, c->d_mom, c->d_err};
+                    c->d_brec, c->d_links, c->d_snap, c->d_part, c->d_red, c->d_mom, c->d_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_red) cudaFreeHost(c->h_red);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -473,6 +492,38 @@ void free_ctx(lbm_ctx *c) {
 }  // namespace
 
 // =============================================================================
+// ----------------------------------------------------------------------------- precision conversion
+namespace {
+__device__ __forceinline__ double cv_load(const double *p, int64_t i) { return p[i]; }
+__device__ __forceinline__ double cv_load(const float *p, int64_t i) { return (double)p[i]; }
+__device__ __forceinline__ double cv_load(const __half *p, int64_t i) { return (double)__half2float(p[i]); }
+__device__ __forceinline__ double cv_load(const __nv_bfloat16 *p, int64_t i) { return (double)__bfloat162float(p[i]); }
+__device__ __forceinline__ void cv_store(double *p, int64_t i, double v) { p[i] = v; }
+__device__ __forceinline__ void cv_store(float *p, int64_t i, double v) { p[i] = (float)v; }
+__device__ __forceinline__ void cv_store(__half *p, int64_t i, double v) { p[i] = __double2half(v); }
+__device__ __forceinline__ void cv_store(__nv_bfloat16 *p, int64_t i, double v) { p[i] = __double2bfloat16(v); }
+
+// Both pools hold p - w*phi_ref with the same references (same cases), so a
+// change of precision is an element-wise rounding of the stored values.
+template <class A, class B>
+__global__ void k_convert(const A *src, B *dst, int64_t n) {
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) cv_store(dst, i, cv_load(src, i));
+}
+
+template <class A>
+cudaError_t convert_from(const A *src, void *dst, int32_t prec, int64_t n, cudaStream_t s) {
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    switch (prec) {
+        case LBM_FP64: k_convert<<<grid, 256, 0, s>>>(src, static_cast<double *>(dst), n); break;
+        case LBM_FP32: k_convert<<<grid, 256, 0, s>>>(src, static_cast<float *>(dst), n); break;
+        case LBM_FP16S: k_convert<<<grid, 256, 0, s>>>(src, static_cast<__half *>(dst), n); break;
+        default: k_convert<<<grid, 256, 0, s>>>(src, static_cast<__nv_bfloat16 *>(dst), n); break;
+    }
+    return cudaGetLastError();
+}
+}  // namespace
+
 extern "C" {
 
 const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
@@ -562,6 +613,9 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
             ctx->own_stream = st == LBM_OK;
         }
     }
+    ck(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking), "cudaStreamCreate");
+    ck(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
+    ck(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming), "cudaEventCreate");
     ck(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, cfg->device), "sm count");
     const size_t pool_bytes = (size_t)pool * ctx->elem;
     ck(cudaMalloc(&ctx->pool[0], pool_bytes), "population buffer 0");
@@ -819,6 +873,50 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes) {
 
 int64_t lbm_steps_done(const lbm_ctx *ctx) { return ctx ? ctx->steps : 0; }
 
+
+lbm_status lbm_convert_state(lbm_ctx *dst, lbm_ctx *src) {
+    lbm_ctx *ctx = dst;
+    if (!dst || !src) return fail(dst, LBM_EINVAL, "NULL context");
+    if (dst == src) return fail(dst, LBM_EINVAL, "source and destination are the same context");
+    if (dst->cfg.lattice != src->cfg.lattice || dst->cfg.physics != src->cfg.physics ||
+        dst->cfg.device != src->cfg.device || dst->cases.size() != src->cases.size())
+        return fail(dst, LBM_EINVAL, "contexts differ in lattice, physics, device or case count");
+    for (size_t c = 0; c < dst->cases.size(); ++c)
+        if (std::memcmp(&dst->cases[c].cfg, &src->cases[c].cfg, sizeof(lbm_case)) != 0)
+            return fail(dst, LBM_EINVAL, "case %zu differs between the contexts", c);
+    if (dst->pool_elems != src->pool_elems || dst->total_nodes != src->total_nodes)
+        return fail(dst, LBM_EINVAL, "pool layouts differ");
+    CK(cudaStreamSynchronize(src->stream));
+    cudaError_t e;
+    const int64_t n = src->pool_elems;
+    void *out = dst->pool[dst->cur];
+    const void *in = src->pool[src->cur];
+    switch (src->cfg.prec) {
+        case LBM_FP64: e = convert_from(static_cast<const double *>(in), out, dst->cfg.prec, n, dst->stream); break;
+        case LBM_FP32: e = convert_from(static_cast<const float *>(in), out, dst->cfg.prec, n, dst->stream); break;
+        case LBM_FP16S: e = convert_from(static_cast<const __half *>(in), out, dst->cfg.prec, n, dst->stream); break;
+        default: e = convert_from(static_cast<const __nv_bfloat16 *>(in), out, dst->cfg.prec, n, dst->stream); break;
+    }
+    CK(e);
+    const int64_t ns = src->total_nodes * SNAP_Q;
+    if (snap_elem(dst) == snap_elem(src)) {
+        CK(cudaMemcpyAsync(dst->d_snap, src->d_snap, (size_t)ns * snap_elem(src), cudaMemcpyDeviceToDevice,
+                           dst->stream));
+    } else {
+        const int grid = (int)std::min<int64_t>((ns + 255) / 256, 152 * 16);
+        if (src->dbl)
+            k_convert<<<grid, 256, 0, dst->stream>>>(reinterpret_cast<const double *>(src->d_snap),
+                                                    reinterpret_cast<float *>(dst->d_snap), ns);
+        else
+            k_convert<<<grid, 256, 0, dst->stream>>>(reinterpret_cast<const float *>(src->d_snap),
+                                                    reinterpret_cast<double *>(dst->d_snap), ns);
+        CK(cudaGetLastError());
+    }
+    CK(cudaStreamSynchronize(dst->stream));
+    dst->steps = src->steps;
+    return LBM_OK;
+}
+
 lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
     if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (!lp) return fail(ctx, LBM_EINVAL, "launch is NULL");
@@ -868,7 +966,7 @@ lbm_status lbm_get_launch(const lbm_ctx *ctx, lbm_launch *lp) {
     return LBM_OK;
 }
 
-int32_t lbm_launches_per_step(const lbm_ctx *ctx) { return ctx ? 1 : 0; }
+int32_t lbm_launches_per_step(const lbm_ctx *ctx) { return ctx ? 1 + (ctx->nbrec > 0 ? 1 : 0) : 0; }
 
 lbm_status lbm_device_state(lbm_ctx *ctx, int32_t case_id, void **base, int32_t *elem_bytes, int64_t *plane_stride,
                             int64_t *case_offset, int32_t *planes) {
@@ -889,7 +987,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
     cudaDeviceProp prop{};
     CK(cudaGetDeviceProperties(&prop, ctx->cfg.device));
     std::ostringstream key;
-    key << prop.name << "|v3|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
+    key << prop.name << "|v4|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
         << ctx->cases.size();
     int64_t tot = 0;
     for (auto &c : ctx->cases) tot += c.N;

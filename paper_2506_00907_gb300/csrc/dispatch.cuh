@@ -5,11 +5,13 @@
 
 #include "kernels.cuh"
 #include "kernels_tma.cuh"
+#include "reduce.cuh"
 
 namespace lbm {
 
 struct KernelSet {
     cudaError_t (*step)(const void *params, int npt, int grid, int block, cudaStream_t s);
+    cudaError_t (*boundary)(const void *params, int grid, int block, cudaStream_t s);
     cudaError_t (*init_d)(const void *params, int grid, int block, cudaStream_t s);   // FP64 host-side fields
     cudaError_t (*init_f)(const void *params, int grid, int block, cudaStream_t s);   // FP32 device fields
     cudaError_t (*moments)(const void *params, int grid, int block, cudaStream_t s);
@@ -28,6 +30,10 @@ struct Launch {
     using T = typename Codec<S>::T;
     static cudaError_t step(const void *p, int npt, int g, int b, cudaStream_t s) {
         k_step<DIM, HH, HG, S><<<g, b, 0, s>>>(*static_cast<const StepParams<T> *>(p), npt);
+        return cudaGetLastError();
+    }
+    static cudaError_t boundary(const void *p, int g, int b, cudaStream_t s) {
+        k_boundary<DIM, HH, HG, S><<<g, b, 0, s>>>(*static_cast<const StepParams<T> *>(p));
         return cudaGetLastError();
     }
     static cudaError_t init_d(const void *p, int g, int b, cudaStream_t s) {
@@ -54,6 +60,7 @@ struct Launch {
     static KernelSet make() {
         KernelSet k{};
         k.step = &step;
+        k.boundary = &boundary;
         k.init_d = &init_d;
         k.init_f = &init_f;
         k.moments = &moments;

@@ -69,8 +69,8 @@ struct StepParams {
     const CaseDev<T> *cases;
     const int2 *tiles;        // (case, first node) per tile of blockDim.x nodes
     int32_t ntiles;
-    const BRec *brec;
-    const int32_t *brow;
+    const BRec *brec;         // boundary nodes of all cases
+    int32_t nbrec;
     const LinkDev<T> *links;
 };
 
@@ -117,69 +117,157 @@ LBM_DEV T geq_dir(int a, int k, T dBk, const T (&B)[3], const T (&u)[3]) {
 
 // ------------------------------------------------------------------ collision
 // In place: s (shifted populations at x, t) -> s_rel (Eq. 1, 3, 5).
+//
+// The relaxed flow populations are a quadratic polynomial in e_a.  With
+// m = rho u = j + F/2 (Guo), om = 1/tau, g = 1 - 1/(2 tau), the BGK update
+// of Eq. 1 with the equilibrium of Eq. 2 plus the magnetic stress and the
+// Guo source w_a g [3 (e_a - u).F + 9 (e_a.u)(e_a.F)] collects into
+//   s_rel,a = (1 - om) s_a + w_a (A + V.e_a + e_a.Tm.e_a)
+//   A  = om (drho - 1.5 m.u + 0.75 (2 - D) |B|^2) - 3 g u.F
+//   V  = 3 (om m + g F)
+//   Tm = 4.5 [om (m u^T - B B^T) + g (u F^T + F u^T)] + 2.25 om |B|^2 I
+// (the isotropic magnetic part 4.5 (|B|^2/2 (|e|^2 - D/3) + |B|^2/3) is
+// 2.25 |B|^2 |e|^2 + 0.75 (2 - D) |B|^2).  Opposite directions share the even
+// part A + e.Tm.e and differ in the sign of V.e.  Eq. 4 and 6 are linear in
+// e_a: h_rel = (1 - om_h) h + om_h w (dC + 4 C e.u) and, per component k,
+// g_rel = (1 - om_g) g + om_g w (dB_k + 4 e.(u B_k - B u_k)).
+template <class T>
+LBM_DEV T recip(T x) { return T(1) / x; }
+template <>
+LBM_DEV float recip<float>(float x) { return __frcp_rn(x); }
+
 template <class PL, bool HH, bool HG, class T>
 LBM_DEV void collide(T (&p)[PL::P], const CaseDev<T> &c) {
     using F = typename PL::F;
     using M = typename PL::M;
     constexpr int QF = PL::QF, QM = PL::QM, NB = PL::NB, DIM = F::DIM;
-    T drho = 0, jx = 0, jy = 0, jz = 0;
+    T drho = 0, j[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int a = 0; a < QF; ++a) {
         drho += p[a];
-        if (F::ex(a)) jx += T(F::ex(a)) * p[a];
-        if (F::ey(a)) jy += T(F::ey(a)) * p[a];
-        if (F::ez(a)) jz += T(F::ez(a)) * p[a];
+        if (F::ex(a)) j[0] += T(F::ex(a)) * p[a];
+        if (F::ey(a)) j[1] += T(F::ey(a)) * p[a];
+        if (F::ez(a)) j[2] += T(F::ez(a)) * p[a];
     }
     const T rho = drho + c.ref_rho;
-    // Guo forcing: u = (sum e f + F/2) / rho with F = rho * accel
-    const T Fx = rho * c.ax, Fy = rho * c.ay, Fz = DIM == 3 ? rho * c.az : T(0);
-    const T inv = T(1) / rho;
-    const T ux = (jx + T(0.5) * Fx) * inv;
-    const T uy = (jy + T(0.5) * Fy) * inv;
-    const T uz = DIM == 3 ? (jz + T(0.5) * Fz) * inv : T(0);
-    const T usq15 = T(1.5) * (ux * ux + uy * uy + uz * uz);
+    const T inv = recip(rho);
+    const T acc[3] = {c.ax, c.ay, c.az};
+    T Fo[3], m[3], u[3];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        Fo[i] = rho * acc[i];
+        m[i] = fmaf_t(T(0.5), Fo[i], j[i]);
+        u[i] = m[i] * inv;
+    }
+    if constexpr (DIM == 2) { Fo[2] = T(0); m[2] = T(0); u[2] = T(0); }
     T B[3] = {T(0), T(0), T(0)}, dB[3] = {T(0), T(0), T(0)};
     if constexpr (HG) {
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
-            T s = 0;
+            T sum = 0;
 #pragma unroll
-            for (int a = 0; a < QM; ++a) s += p[PL::G0 + k * QM + a];
-            dB[k] = s;
-            B[k] = s + c.ref_B[k];
+            for (int a = 0; a < QM; ++a) sum += p[PL::G0 + k * QM + a];
+            dB[k] = sum;
+            B[k] = sum + c.ref_B[k];
         }
     }
-    T mag[3] = {T(0), T(0), T(0)};
-    if constexpr (HG) mag_classes<F, T>(B[0] * B[0] + B[1] * B[1] + B[2] * B[2], mag);
-    const T u[3] = {ux, uy, uz};
-    const T uF = ux * Fx + uy * Fy + uz * Fz;
+    const T om = c.om_f, g = c.guo;
+    T mu = 0, uF = 0, Bsq = 0;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        mu = fmaf_t(m[i], u[i], mu);
+        uF = fmaf_t(u[i], Fo[i], uF);
+        if constexpr (HG) Bsq = fmaf_t(B[i], B[i], Bsq);
+    }
+    T A = fmaf_t(T(-1.5), mu, drho);
+    if constexpr (HG && DIM == 2) {}                       // 0.75 (2 - D) |B|^2 vanishes in 2D
+    if constexpr (HG && DIM == 3) A = fmaf_t(T(-0.75), Bsq, A);
+    A = fmaf_t(om, A, T(-3) * g * uF);
+    T V[3], Td[3], Tc[3];                                   // Tc: 2 Tm_xy, 2 Tm_xz, 2 Tm_yz
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        V[i] = T(3) * fmaf_t(om, m[i], g * Fo[i]);
+        T t = m[i] * u[i];
+        if constexpr (HG) t = fmaf_t(-B[i], B[i], t);
+        Td[i] = fmaf_t(T(4.5), fmaf_t(om, t, T(2) * g * u[i] * Fo[i]), HG ? T(2.25) * om * Bsq : T(0));
+    }
+#pragma unroll
+    for (int pr = 0; pr < (DIM == 3 ? 3 : 1); ++pr) {
+        const int i = pr == 2 ? 1 : 0, k = pr == 0 ? 1 : 2;
+        T t = m[i] * u[k];
+        if constexpr (HG) t = fmaf_t(-B[i], B[k], t);
+        Tc[pr] = T(9) * fmaf_t(om, t, g * fmaf_t(u[i], Fo[k], Fo[i] * u[k]));
+    }
+    const T omc = c.omc_f;
 #pragma unroll
     for (int a = 0; a < QF; ++a) {
-        const T ex = T(F::ex(a)), ey = T(F::ey(a)), ez = T(F::ez(a));
+        const int b = F::opp(a);
+        if (b < a) continue;                                 // done with its pair
+        const int e[3] = {F::ex(a), F::ey(a), F::ez(a)};
+        T even = A, odd = T(0);
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+            if (e[i]) {
+                even += Td[i];
+                odd = e[i] > 0 ? odd + V[i] : odd - V[i];
+            }
+        }
+#pragma unroll
+        for (int pr = 0; pr < (DIM == 3 ? 3 : 1); ++pr) {
+            const int i = pr == 2 ? 1 : 0, k = pr == 0 ? 1 : 2;
+            const int s2 = e[i] * e[k];
+            if (s2) even = s2 > 0 ? even + Tc[pr] : even - Tc[pr];
+        }
         const T w = T(F::w(a));
-        const T feq = feq_dir<F, HG, T>(a, drho, rho, u, usq15, B, mag);
-        const T eu = ex * ux + ey * uy + ez * uz;
-        const T eF = ex * Fx + ey * Fy + ez * Fz;
-        // Guo source (1 - 1/(2 tau)) w [3 (e - u).F + 9 (e.u)(e.F)]
-        const T S = c.guo * w * (T(3) * (eF - uF) + T(9) * eu * eF);
-        p[a] = fmaf_t(c.om_f, feq, fmaf_t(c.omc_f, p[a], S));
+        if (a == b) {
+            p[a] = fmaf_t(omc, p[a], w * even);
+        } else {
+            const T we = w * even, wo = w * odd;
+            p[a] = fmaf_t(omc, p[a], we + wo);
+            p[b] = fmaf_t(omc, p[b], we - wo);
+        }
     }
+    const T w0 = T(M::w(0)), w1 = T(M::w(1));
     if constexpr (HH) {
         T dC = 0;
 #pragma unroll
         for (int a = 0; a < QM; ++a) dC += p[PL::H0 + a];
         const T C = dC + c.ref_C;
+        const T oh = c.om_h, ohc = c.omc_h;
+        const T ev = oh * w1 * dC, f4 = T(4) * oh * w1 * C;
+        p[PL::H0] = fmaf_t(ohc, p[PL::H0], oh * w0 * dC);
 #pragma unroll
-        for (int a = 0; a < QM; ++a)
-            p[PL::H0 + a] = fmaf_t(c.om_h, heq_dir<M, T>(a, dC, C, u), c.omc_h * p[PL::H0 + a]);
+        for (int a = 1; a < QM; ++a) {
+            const int b = M::opp(a);
+            if (b < a) continue;
+            const int i = M::ex(a) ? 0 : (M::ey(a) ? 1 : 2);
+            const T od = (M::ex(a) + M::ey(a) + M::ez(a) > 0) ? f4 * u[i] : -(f4 * u[i]);
+            p[PL::H0 + a] = fmaf_t(ohc, p[PL::H0 + a], ev + od);
+            p[PL::H0 + b] = fmaf_t(ohc, p[PL::H0 + b], ev - od);
+        }
     }
     if constexpr (HG) {
+        const T og = c.om_g, ogc = c.omc_g;
+        const T og1 = og * w1, og4 = T(4) * og * w1;
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
+            const int q0 = PL::G0 + k * QM;
+            const T ev = og1 * dB[k];
+            p[q0] = fmaf_t(ogc, p[q0], og * w0 * dB[k]);
 #pragma unroll
-            for (int a = 0; a < QM; ++a) {
-                const int q = PL::G0 + k * QM + a;
-                p[q] = fmaf_t(c.om_g, geq_dir<M, T>(a, k, dB[k], B, u), c.omc_g * p[q]);
+            for (int a = 1; a < QM; ++a) {
+                const int b = M::opp(a);
+                if (b < a) continue;
+                const int i = M::ex(a) ? 0 : (M::ey(a) ? 1 : 2);
+                if (i == k) {                                 // u_k B_k - B_k u_k = 0
+                    p[q0 + a] = fmaf_t(ogc, p[q0 + a], ev);
+                    p[q0 + b] = fmaf_t(ogc, p[q0 + b], ev);
+                } else {
+                    const T v = og4 * fmaf_t(u[i], B[k], -(B[i] * u[k]));
+                    const T od = (M::ex(a) + M::ey(a) + M::ez(a) > 0) ? v : -v;
+                    p[q0 + a] = fmaf_t(ogc, p[q0 + a], ev + od);
+                    p[q0 + b] = fmaf_t(ogc, p[q0 + b], ev - od);
+                }
             }
         }
     }
@@ -220,26 +308,17 @@ LBM_DEV T eval_link(const LinkDev<T> &L, const S *src, const CaseDev<T> &c) {
     return v;
 }
 
-// Applies every link of boundary node n (row r of the case) to p.
+// Replaces the populations of boundary node A that come from solid nodes by
+// the wall formulas of its links [lo, hi).
 template <class PL, class S, class T>
-LBM_DEV void apply_links(T (&p)[PL::P], const StepParams<T> &prm, const CaseDev<T> &c, const S *src, int n, int r) {
-    int lo = prm.brow[c.brow_off + r];
-    const int hi0 = prm.brow[c.brow_off + r + 1];
-    int hi = hi0;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (prm.brec[mid].node < n) lo = mid + 1; else hi = mid;
-    }
-    if (lo < hi0 && prm.brec[lo].node == n) {
-        const BRec br = prm.brec[lo];
-        for (int li = br.lo; li < br.hi; ++li) {
-            const LinkDev<T> L = prm.links[li];
-            const T v = eval_link<PL, S, T>(L, src, c);
-            // select per plane (an indexed store would move p to local memory)
-            const int pa = L.plane_a;
+LBM_DEV void apply_links(T (&p)[PL::P], const StepParams<T> &prm, const CaseDev<T> &c, const S *src, int lo, int hi) {
+    for (int li = lo; li < hi; ++li) {
+        const LinkDev<T> L = prm.links[li];
+        const T v = eval_link<PL, S, T>(L, src, c);
+        // select per plane (an indexed store would move p to local memory)
+        const int pa = L.plane_a;
 #pragma unroll
-            for (int q = 0; q < PL::P; ++q) p[q] = (q == pa) ? v : p[q];
-        }
+        for (int q = 0; q < PL::P; ++q) p[q] = (q == pa) ? v : p[q];
     }
 }
 
@@ -258,9 +337,10 @@ LBM_DEV void coords(const CaseDev<T> &c, int n, int &x, int &y, int &z, int &r) 
 }
 
 // ------------------------------------------------------------------ fused step
-template <int DIM, bool HH, bool HG, class S>
+// One node: pull, (boundary nodes: wall links [lo, hi)), collide, store.
+template <int DIM, bool HH, bool HG, class S, bool LINKS>
 LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDev<typename Codec<S>::T> &c, int n,
-                       uint8_t fl) {
+                       int lo, int hi) {
     using PL = Planes<DIM, HH, HG>;
     using T = typename Codec<S>::T;
     constexpr int P = PL::P;
@@ -287,14 +367,15 @@ LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDe
         const int src_node = xi[1 - PL::ex(q)] + yi[1 - PL::ey(q)] + zi[1 - PL::ez(q)];
         p[q] = Codec<S>::ld(src + (q * st32 + src_node));
     }
-    if (fl & NODE_BOUNDARY) apply_links<PL, S, T>(p, prm, c, src, n, r);
+    if constexpr (LINKS) apply_links<PL, S, T>(p, prm, c, src, lo, hi);
     collide<PL, HH, HG, T>(p, c);
 #pragma unroll
     for (int q = 0; q < P; ++q) Codec<S>::st(dst + (q * st32 + n), p[q]);
 }
 
-// Tiles of blockDim.x * npt nodes; each thread takes nodes tid, tid + blockDim.x, ...
-// The next tile's record and the thread's first flag are fetched one tile ahead.
+// Bulk nodes (fluid, no wall link).  Tiles of blockDim.x * npt nodes; each
+// thread takes nodes tid, tid + blockDim.x, ...  The next tile's record is
+// fetched one tile ahead.  Boundary nodes are left to k_boundary.
 template <int DIM, bool HH, bool HG, class S>
 __global__ void __launch_bounds__(256, DIM == 2 ? 4 : 2) k_step(const StepParams<typename Codec<S>::T> prm, const int npt) {
     using T = typename Codec<S>::T;
@@ -309,10 +390,20 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 4 : 2) k_step(const StepParams
             const int n = tile.y + (int)threadIdx.x + k * (int)blockDim.x;
             if (n >= c.N) break;
             const uint8_t fl = prm.flags[c.node_off + n];
-            if (fl & NODE_FLUID) step_node<DIM, HH, HG, S>(prm, c, n, fl);
+            if (fl == NODE_FLUID) step_node<DIM, HH, HG, S, false>(prm, c, n, 0, 0);
         }
         tile = next;
     }
+}
+
+// Boundary nodes: one thread per record of the compact boundary list (the
+// nodes of a wall row are consecutive records, so a warp works along a wall).
+template <int DIM, bool HH, bool HG, class S>
+__global__ void __launch_bounds__(128) k_boundary(const StepParams<typename Codec<S>::T> prm) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= prm.nbrec) return;
+    const BRec b = prm.brec[i];
+    step_node<DIM, HH, HG, S, true>(prm, prm.cases[b.cs], b.node, b.lo, b.hi);
 }
 
 // ------------------------------------------------------------------ initial state
@@ -372,188 +463,6 @@ __global__ void __launch_bounds__(256) k_init(const InitParams<typename Codec<S>
     collide<PL, HH, HG, T>(p, c);
 #pragma unroll
     for (int q = 0; q < P; ++q) Codec<S>::st(dst + (q * st32 + n), p[q]);
-}
-
-// ------------------------------------------------------------------ moments
-// Moments at the current time from the stored relaxed populations:
-// rho = sum f_rel, u = (sum e f_rel - F/2)/rho (the relaxation adds F/2 to the
-// momentum), C = sum h_rel, B = sum g_rel.
-template <class PL, class S, class T>
-LBM_DEV void node_moments(const S *src, int64_t stride, int n, const CaseDev<T> &c,
-                          T &rho, T (&u)[3], T &C, T (&B)[3], int &nonfinite) {
-    using F = typename PL::F;
-    T drho = 0;
-    T j[3] = {T(0), T(0), T(0)};
-    nonfinite = 0;
-#pragma unroll
-    for (int a = 0; a < PL::QF; ++a) {
-        const T v = Codec<S>::ld(src + (int64_t)a * stride + n);
-        nonfinite += !isfinite(v);
-        drho += v;
-        j[0] += T(F::ex(a)) * v;
-        j[1] += T(F::ey(a)) * v;
-        j[2] += T(F::ez(a)) * v;
-    }
-    rho = drho + c.ref_rho;
-    u[0] = (j[0] - T(0.5) * rho * c.ax) / rho;
-    u[1] = (j[1] - T(0.5) * rho * c.ay) / rho;
-    u[2] = F::DIM == 3 ? (j[2] - T(0.5) * rho * c.az) / rho : T(0);
-    C = 0;
-    B[0] = B[1] = B[2] = T(0);
-    if constexpr (PL::G0 > PL::H0) {
-        T s = 0;
-#pragma unroll
-        for (int a = 0; a < PL::QM; ++a) {
-            const T v = Codec<S>::ld(src + (int64_t)(PL::H0 + a) * stride + n);
-            nonfinite += !isfinite(v);
-            s += v;
-        }
-        C = s + c.ref_C;
-    }
-    if constexpr (PL::P > PL::G0) {
-#pragma unroll
-        for (int k = 0; k < PL::NB; ++k) {
-            T s = 0;
-#pragma unroll
-            for (int a = 0; a < PL::QM; ++a) {
-                const int q = PL::G0 + k * PL::QM + a;
-                const T v = Codec<S>::ld(src + (int64_t)q * stride + n);
-                nonfinite += !isfinite(v);
-                s += v;
-            }
-            B[k] = s + c.ref_B[k];
-        }
-    }
-}
-
-template <class T>
-struct MomParams {
-    const void *src;
-    const uint8_t *flags;
-    const CaseDev<T> *cases;
-    int32_t case_id;
-    double *rho, *u, *C, *B;  // case-relative device outputs (u, B as [N][3])
-};
-
-template <int DIM, bool HH, bool HG, class S>
-__global__ void __launch_bounds__(256) k_moments(const MomParams<typename Codec<S>::T> mp) {
-    using PL = Planes<DIM, HH, HG>;
-    using T = typename Codec<S>::T;
-    const CaseDev<T> &c = mp.cases[mp.case_id];
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= c.N) return;
-    if (!(mp.flags[c.node_off + n] & NODE_FLUID)) {
-        mp.rho[n] = 0;
-        mp.C[n] = 0;
-        for (int k = 0; k < 3; ++k) { mp.u[3 * n + k] = 0; mp.B[3 * n + k] = 0; }
-        return;
-    }
-    T rho, u[3], C, B[3];
-    int nf;
-    node_moments<PL, S, T>(static_cast<const S *>(mp.src) + c.pop_off, c.stride, n, c, rho, u, C, B, nf);
-    mp.rho[n] = (double)rho;
-    mp.C[n] = HH ? (double)C : 0.0;
-    for (int k = 0; k < 3; ++k) { mp.u[3 * n + k] = (double)u[k]; mp.B[3 * n + k] = HG ? (double)B[k] : 0.0; }
-}
-
-// ------------------------------------------------------------------ FP64 reductions
-// One block per tile: partial sums (rho, C, Bx, By, Bz, non-finite count,
-// |phi - phi_prev|^2, |phi|^2) in FP64, written to part[tile][8]; the previous
-// phi = (u, C, B - B0) lives in snap[7][total nodes] (FP64) and is replaced.
-constexpr int RED_Q = 8;
-constexpr int SNAP_Q = 7;
-
-template <class T>
-struct RedParams {
-    const void *src;
-    const uint8_t *flags;
-    const CaseDev<T> *cases;
-    const int2 *tiles;
-    int32_t ntiles;
-    int32_t tile_nodes;
-    double *snap;
-    int64_t snap_stride;
-    double *part;             // [ntiles][RED_Q]
-};
-
-LBM_DEV double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-template <int DIM, bool HH, bool HG, class S>
-__global__ void __launch_bounds__(256) k_reduce(const RedParams<typename Codec<S>::T> rp) {
-    using PL = Planes<DIM, HH, HG>;
-    using T = typename Codec<S>::T;
-    __shared__ double sh[RED_Q][32];
-    const int t = blockIdx.x;
-    const int2 tile = rp.tiles[t];
-    const CaseDev<T> &c = rp.cases[tile.x];
-    double acc[RED_Q];
-#pragma unroll
-    for (int i = 0; i < RED_Q; ++i) acc[i] = 0.0;
-    for (int i = threadIdx.x; i < rp.tile_nodes; i += blockDim.x) {
-        const int n = tile.y + i;
-        if (n >= c.N || !(rp.flags[c.node_off + n] & NODE_FLUID)) continue;
-        T rho, u[3], C, B[3];
-        int nf;
-        node_moments<PL, S, T>(static_cast<const S *>(rp.src) + c.pop_off, c.stride, n, c, rho, u, C, B, nf);
-        acc[0] = rho;
-        acc[1] = HH ? (double)C : 0.0;
-        acc[2] = HG ? (double)B[0] : 0.0;
-        acc[3] = HG ? (double)B[1] : 0.0;
-        acc[4] = HG ? (double)B[2] : 0.0;
-        acc[5] = nf;
-        const double phi[SNAP_Q] = {(double)u[0], (double)u[1], (double)u[2],
-                                    HH ? (double)C : 0.0,
-                                    HG ? (double)B[0] - (double)c.B0[0] : 0.0,
-                                    HG ? (double)B[1] - (double)c.B0[1] : 0.0,
-                                    HG ? (double)B[2] - (double)c.B0[2] : 0.0};
-        double *sp = rp.snap + c.node_off + n;
-#pragma unroll
-        for (int k = 0; k < SNAP_Q; ++k) {
-            const double old = sp[k * rp.snap_stride];
-            const double dd = phi[k] - old;
-            acc[6] += dd * dd;
-            acc[7] += phi[k] * phi[k];
-            sp[k * rp.snap_stride] = phi[k];
-        }
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < RED_Q; ++i) {
-        const double v = warp_sum(acc[i]);
-        if (lane == 0) sh[i][warp] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < RED_Q) {
-        const int nw = (blockDim.x + 31) >> 5;
-        double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += sh[threadIdx.x][w];
-        rp.part[(int64_t)t * RED_Q + threadIdx.x] = s;
-    }
-}
-
-// One block (256 threads) per case: sums the case's tile partials in a fixed
-// order (deterministic for a given tile list).
-inline __global__ void __launch_bounds__(256) k_reduce_final(const double *part, const int32_t *case_tile_lo,
-                                                             double *out) {
-    __shared__ double sh[256];
-    const int c = blockIdx.x;
-    const int lo = case_tile_lo[c], hi = case_tile_lo[c + 1];
-    for (int i = 0; i < RED_Q; ++i) {
-        double s = 0.0;
-        for (int t = lo + (int)threadIdx.x; t < hi; t += blockDim.x) s += part[(int64_t)t * RED_Q + i];
-        sh[threadIdx.x] = s;
-        __syncthreads();
-        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-            if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) out[c * RED_Q + i] = sh[0];
-        __syncthreads();
-    }
 }
 
 }  // namespace lbm

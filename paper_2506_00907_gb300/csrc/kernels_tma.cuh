@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(256, MINB) k_step_tma(const StepParams<typenam
         for (int i = tid; i < len; i += blockDim.x) {
             const int n = tile.y + i;
             const uint8_t fl = prm.flags[c.node_off + n];
-            if (!(fl & NODE_FLUID)) continue;
+            if (fl != NODE_FLUID) continue;         // solid, or a boundary node (k_boundary)
             int x, y, z, r;
             coords<DIM, T>(c, n, x, y, z, r);
             const bool edge = x == 0 || x == nx - 1 || y == 0 || y == ny - 1 ||
@@ -190,7 +190,6 @@ __global__ void __launch_bounds__(256, MINB) k_step_tma(const StepParams<typenam
                                : Codec<S>::ld(src + (q * st32 + sn));
                 }
             }
-            if (fl & NODE_BOUNDARY) apply_links<PL, S, T>(p, prm, c, src, n, r);
             collide<PL, HH, HG, T>(p, c);
 #pragma unroll
             for (int q = 0; q < P; ++q) Codec<S>::st(dst + (q * st32 + n), p[q]);

@@ -1,0 +1,240 @@
+// reduce.cuh -- moments at the current time and the FP64 invariant / residual
+// reductions over the stored (shifted, relaxed) populations.
+//
+// Moments: rho = sum f_rel, u = (sum e f_rel - F/2)/rho (the relaxation adds
+// F/2 to the momentum), C = sum h_rel, B = sum g_rel (mass, C and B are
+// conserved by the relaxation).
+//
+// Per node the reduction forms, in the arithmetic precision T of the step,
+// rho, C, B, a non-finite count and the residual terms
+//   r2 = |phi - phi_prev|^2,  p2 = |phi|^2,  phi = (u, C, B - B0)
+// (only the components the lattice and physics can make nonzero); sums over
+// nodes are FP64.  phi_prev is one plane per component in the snapshot
+// buffer, stored in T (FP64 storage: double, otherwise float), and is
+// replaced by phi.
+#pragma once
+#include "kernels.cuh"
+
+namespace lbm {
+
+template <class PL, class S, class T>
+LBM_DEV void node_moments(const S *src, int64_t stride, int n, const CaseDev<T> &c,
+                          T &rho, T (&u)[3], T &C, T (&B)[3], int &nonfinite) {
+    using F = typename PL::F;
+    T drho = 0;
+    T j[3] = {T(0), T(0), T(0)};
+    nonfinite = 0;
+#pragma unroll
+    for (int a = 0; a < PL::QF; ++a) {
+        const T v = Codec<S>::ld(src + (int64_t)a * stride + n);
+        nonfinite += !isfinite(v);
+        drho += v;
+        j[0] += T(F::ex(a)) * v;
+        j[1] += T(F::ey(a)) * v;
+        j[2] += T(F::ez(a)) * v;
+    }
+    rho = drho + c.ref_rho;
+    u[0] = (j[0] - T(0.5) * rho * c.ax) / rho;
+    u[1] = (j[1] - T(0.5) * rho * c.ay) / rho;
+    u[2] = F::DIM == 3 ? (j[2] - T(0.5) * rho * c.az) / rho : T(0);
+    C = 0;
+    B[0] = B[1] = B[2] = T(0);
+    if constexpr (PL::G0 > PL::H0) {
+        T s = 0;
+#pragma unroll
+        for (int a = 0; a < PL::QM; ++a) {
+            const T v = Codec<S>::ld(src + (int64_t)(PL::H0 + a) * stride + n);
+            nonfinite += !isfinite(v);
+            s += v;
+        }
+        C = s + c.ref_C;
+    }
+    if constexpr (PL::P > PL::G0) {
+#pragma unroll
+        for (int k = 0; k < PL::NB; ++k) {
+            T s = 0;
+#pragma unroll
+            for (int a = 0; a < PL::QM; ++a) {
+                const int q = PL::G0 + k * PL::QM + a;
+                const T v = Codec<S>::ld(src + (int64_t)q * stride + n);
+                nonfinite += !isfinite(v);
+                s += v;
+            }
+            B[k] = s + c.ref_B[k];
+        }
+    }
+}
+
+template <class T>
+struct MomParams {
+    const void *src;
+    const uint8_t *flags;
+    const CaseDev<T> *cases;
+    int32_t case_id;
+    double *rho, *u, *C, *B;  // case-relative device outputs (u, B as [N][3])
+};
+
+template <int DIM, bool HH, bool HG, class S>
+__global__ void __launch_bounds__(256) k_moments(const MomParams<typename Codec<S>::T> mp) {
+    using PL = Planes<DIM, HH, HG>;
+    using T = typename Codec<S>::T;
+    const CaseDev<T> &c = mp.cases[mp.case_id];
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= c.N) return;
+    if (!(mp.flags[c.node_off + n] & NODE_FLUID)) {
+        mp.rho[n] = 0;
+        mp.C[n] = 0;
+        for (int k = 0; k < 3; ++k) { mp.u[3 * n + k] = 0; mp.B[3 * n + k] = 0; }
+        return;
+    }
+    T rho, u[3], C, B[3];
+    int nf;
+    node_moments<PL, S, T>(static_cast<const S *>(mp.src) + c.pop_off, c.stride, n, c, rho, u, C, B, nf);
+    mp.rho[n] = (double)rho;
+    mp.C[n] = HH ? (double)C : 0.0;
+    for (int k = 0; k < 3; ++k) { mp.u[3 * n + k] = (double)u[k]; mp.B[3 * n + k] = HG ? (double)B[k] : 0.0; }
+}
+
+// ------------------------------------------------------------------ FP64 reductions
+// Record per case: (sum rho, sum C, sum Bx, sum By, sum Bz, non-finite count,
+// sum |phi - phi_prev|^2, sum |phi|^2).
+constexpr int RED_Q = 8;
+constexpr int SNAP_Q = 7;
+
+// Snapshot planes that can be nonzero: u (DIM components), C, B - B0 (DIM).
+template <class PL>
+LBM_HD constexpr bool snap_used(int k) {
+    constexpr int D = PL::F::DIM;
+    constexpr bool hh = PL::G0 > PL::H0, hg = PL::P > PL::G0;
+    return k < 3 ? k < D : (k == 3 ? hh : (hg && k - 4 < D));
+}
+
+// The per-node record terms; snap (may be null: phi_prev = 0) points at the
+// node's entry of plane 0, planes sstride apart.
+template <class PL, class S, class T, class SnapT>
+LBM_DEV void node_terms(const S *src, int64_t stride, int n, const CaseDev<T> &c, SnapT *snap, int64_t sstride,
+                        T &rho, T &C, T (&B)[3], int &nf, T &r2, T &p2) {
+    T u[3];
+    node_moments<PL, S, T>(src, stride, n, c, rho, u, C, B, nf);
+    const T phi[SNAP_Q] = {u[0], u[1], u[2], C, B[0] - c.B0[0], B[1] - c.B0[1], B[2] - c.B0[2]};
+    r2 = T(0);
+    p2 = T(0);
+#pragma unroll
+    for (int k = 0; k < SNAP_Q; ++k) {
+        if (!snap_used<PL>(k)) continue;
+        T dd = phi[k];
+        if (snap) {
+            dd -= T(snap[k * sstride]);
+            snap[k * sstride] = SnapT(phi[k]);
+        }
+        r2 = fmaf_t(dd, dd, r2);
+        p2 = fmaf_t(phi[k], phi[k], p2);
+    }
+}
+
+// Adds the node terms to the FP64 record acc[RED_Q] (count kept as an int).
+template <class PL, class T>
+LBM_DEV void add_terms(double (&acc)[RED_Q], int &nfc, T rho, T C, const T (&B)[3], int nf, T r2, T p2) {
+    constexpr int D = PL::F::DIM;
+    acc[0] += (double)rho;
+    if constexpr (PL::G0 > PL::H0) acc[1] += (double)C;
+    if constexpr (PL::P > PL::G0) {
+        acc[2] += (double)B[0];
+        acc[3] += (double)B[1];
+        if constexpr (D == 3) acc[4] += (double)B[2];
+    }
+    nfc += nf;
+    acc[6] += (double)r2;
+    acc[7] += (double)p2;
+}
+
+LBM_DEV double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of the record into out[RED_Q] (blockDim.x a multiple of 32,
+// at most 1024; sh holds RED_Q x 32 doubles).
+LBM_DEV void block_record(double (&acc)[RED_Q], int nfc, double (*sh)[32], double *out) {
+    acc[5] = (double)nfc;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < RED_Q; ++i) {
+        const double v = warp_sum(acc[i]);
+        if (lane == 0) sh[i][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < RED_Q) {
+        const int nw = (blockDim.x + 31) >> 5;
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += sh[threadIdx.x][w];
+        out[threadIdx.x] = s;
+    }
+}
+
+template <class T>
+struct RedParams {
+    const void *src;
+    const uint8_t *flags;
+    const CaseDev<T> *cases;
+    const int2 *tiles;
+    int32_t ntiles;
+    int32_t tile_nodes;
+    void *snap;               // SNAP_Q planes of snap_stride entries, double (FP64 storage) or float
+    int64_t snap_stride;
+    double *part;             // [ntiles][RED_Q]
+};
+
+template <class T>
+using SnapOf = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
+
+// One block per tile: partial record of the tile's fluid nodes.
+template <int DIM, bool HH, bool HG, class S>
+__global__ void __launch_bounds__(256) k_reduce(const RedParams<typename Codec<S>::T> rp) {
+    using PL = Planes<DIM, HH, HG>;
+    using T = typename Codec<S>::T;
+    using SnapT = SnapOf<T>;
+    __shared__ double sh[RED_Q][32];
+    const int t = blockIdx.x;
+    const int2 tile = rp.tiles[t];
+    const CaseDev<T> &c = rp.cases[tile.x];
+    double acc[RED_Q];
+#pragma unroll
+    for (int i = 0; i < RED_Q; ++i) acc[i] = 0.0;
+    int nfc = 0;
+    for (int i = threadIdx.x; i < rp.tile_nodes; i += blockDim.x) {
+        const int n = tile.y + i;
+        if (n >= c.N || !(rp.flags[c.node_off + n] & NODE_FLUID)) continue;
+        T rho, C, B[3], r2, p2;
+        int nf;
+        node_terms<PL, S, T, SnapT>(static_cast<const S *>(rp.src) + c.pop_off, c.stride, n, c,
+                                    static_cast<SnapT *>(rp.snap) + c.node_off + n, rp.snap_stride,
+                                    rho, C, B, nf, r2, p2);
+        add_terms<PL, T>(acc, nfc, rho, C, B, nf, r2, p2);
+    }
+    block_record(acc, nfc, sh, rp.part + (int64_t)t * RED_Q);
+}
+
+// One block (256 threads) per case: sums the case's tile partials in a fixed
+// order (deterministic for a given tile list).
+static __global__ void __launch_bounds__(256) k_reduce_final(const double *part, const int32_t *case_tile_lo,
+                                                             double *out) {
+    __shared__ double sh[256];
+    const int c = blockIdx.x;
+    const int lo = case_tile_lo[c], hi = case_tile_lo[c + 1];
+    for (int i = 0; i < RED_Q; ++i) {
+        double s = 0.0;
+        for (int t = lo + (int)threadIdx.x; t < hi; t += blockDim.x) s += part[(int64_t)t * RED_Q + i];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[c * RED_Q + i] = sh[0];
+        __syncthreads();
+    }
+}
+
+}  // namespace lbm

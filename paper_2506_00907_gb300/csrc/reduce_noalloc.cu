@@ -13,7 +13,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "kernels.cuh"
+#include "reduce.cuh"
 #include "lbm.h"
 
 namespace lbm {
@@ -33,45 +33,20 @@ __global__ void __launch_bounds__(NOALLOC_BLOCK) k_reduce_noalloc(const CaseDev<
                                                                  double *snap, double *scratch) {
     using PL = Planes<DIM, HH, HG>;
     using T = typename Codec<S>::T;
-    __shared__ double sh[RED_Q][NOALLOC_BLOCK / 32];
+    __shared__ double sh[RED_Q][32];
     const int n = blockIdx.x * NOALLOC_BLOCK + threadIdx.x;
     double acc[RED_Q];
 #pragma unroll
     for (int i = 0; i < RED_Q; ++i) acc[i] = 0.0;
+    int nfc = 0;
     if (n < c.N && (!flags || flags[n])) {
-        T rho, u[3], C, B[3];
+        T rho, C, B[3], r2, p2;
         int nf;
-        node_moments<PL, S, T>(static_cast<const S *>(pops), c.stride, n, c, rho, u, C, B, nf);
-        acc[0] = rho;
-        acc[1] = HH ? (double)C : 0.0;
-        acc[2] = HG ? (double)B[0] : 0.0;
-        acc[3] = HG ? (double)B[1] : 0.0;
-        acc[4] = HG ? (double)B[2] : 0.0;
-        acc[5] = nf;
-        const double phi[SNAP_Q] = {(double)u[0], (double)u[1], (double)u[2], HH ? (double)C : 0.0,
-                                    HG ? (double)B[0] - (double)c.B0[0] : 0.0,
-                                    HG ? (double)B[1] - (double)c.B0[1] : 0.0,
-                                    HG ? (double)B[2] - (double)c.B0[2] : 0.0};
-        for (int k = 0; k < SNAP_Q; ++k) {
-            const double old = snap ? snap[(int64_t)k * c.N + n] : 0.0;
-            const double dd = phi[k] - old;
-            acc[6] += dd * dd;
-            acc[7] += phi[k] * phi[k];
-            if (snap) snap[(int64_t)k * c.N + n] = phi[k];
-        }
+        node_terms<PL, S, T, double>(static_cast<const S *>(pops), c.stride, n, c, snap ? snap + n : nullptr, c.N,
+                                     rho, C, B, nf, r2, p2);
+        add_terms<PL, T>(acc, nfc, rho, C, B, nf, r2, p2);
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < RED_Q; ++i) {
-        const double v = warp_sum(acc[i]);
-        if (lane == 0) sh[i][warp] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < RED_Q) {
-        double s = 0.0;
-        for (int w = 0; w < NOALLOC_BLOCK / 32; ++w) s += sh[threadIdx.x][w];
-        scratch[(int64_t)blockIdx.x * RED_Q + threadIdx.x] = s;
-    }
+    block_record(acc, nfc, sh, scratch + (int64_t)blockIdx.x * RED_Q);
 }
 
 // One block sums nb partial records in a fixed order into out[RED_Q].

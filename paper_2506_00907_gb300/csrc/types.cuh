@@ -18,8 +18,7 @@ struct CaseDev {
     int64_t pop_off;      // element offset of the case's first plane in a population buffer
     int64_t stride;       // elements between consecutive planes of the case
     int64_t node_off;     // offset of the case's nodes in the flag / snapshot arrays
-    int32_t brow_off;     // offset of the case's row table (ny*nz + 1 entries) in brow
-    int32_t pad0;
+    int32_t pad0, pad1;
     T om_f, om_h, om_g;   // 1/tau_nu, 1/tau_D, 1/tau_eta
     T omc_f, omc_h, omc_g; // 1 - om (the relaxation p + om (eq - p) = (1 - om) p + om eq)
     T guo;                // 1 - 1/(2 tau_nu): weight of the Guo source
@@ -53,10 +52,12 @@ struct alignas(16) LinkDev {
 };
 
 // Boundary record of a fluid node that owns links.
+// One boundary node (a fluid node with at least one wall link): the boundary
+// kernel takes one record per thread.
 struct BRec {
     int32_t node;         // case-relative node index
     int32_t lo, hi;       // link range [lo, hi) in the global link array
-    int32_t pad;
+    int32_t cs;           // case index
 };
 
 enum : uint8_t { NODE_FLUID = 1, NODE_BOUNDARY = 2 };

@@ -96,6 +96,7 @@ def lib():
                                                     ctypes.POINTER(ctypes.c_size_t)])
         sig["lbm_build_pipe"] = (ctypes.c_int, [i32, i32, i32, ctypes.c_double, ctypes.c_uint32, vp, vp, vp,
                                                 ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)])
+        sig["lbm_convert_state"] = (ctypes.c_int, [vp, vp])
         sig["lbm_net_num_params"] = (i64, [])
         sig["lbm_net_create"] = (ctypes.c_int, [ctypes.POINTER(i32), i32, vp, vp, ctypes.POINTER(vp)])
         sig["lbm_net_destroy"] = (None, [vp])
@@ -237,6 +238,11 @@ def lbm_reduce_noalloc(lattice, prec, physics, case, pops, plane_stride, flags=N
     if st not in (LBM_OK, LBM_EUNSTABLE):
         raise LbmError(st, "lbm_reduce_noalloc failed")
     return out, st
+
+
+def lbm_convert_state(dst, src):
+    """Copy the state of context `src` into `dst` at the precision of `dst`."""
+    _check(dst, lib().lbm_convert_state(dst, src))
 
 
 def lbm_launches_per_step(ctx):
@@ -434,6 +440,10 @@ class Solver:
 
     def set_state(self, blob):
         lbm_set_state(self.ctx, blob)
+
+    def convert_from(self, other):
+        """Take the state of Solver `other` (same cases and walls), rounded to this precision."""
+        lbm_convert_state(self.ctx, other.ctx)
 
     @property
     def steps(self):

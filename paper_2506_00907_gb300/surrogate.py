@@ -34,10 +34,14 @@ def f_cw(cw):
 
 
 class Surrogate:
-    """A trained network with the (Ha, c_w) range it was trained on."""
+    """A trained network with the (Ha, c_w) range it was trained on and the
+    per-output scale of its training targets (train() fits T / scale)."""
 
-    def __init__(self, net, ha_range, cw_range):
+    def __init__(self, net, ha_range, cw_range, target_scale=None):
         self.net, self.ha_range, self.cw_range = net, tuple(ha_range), tuple(cw_range)
+        if target_scale is None:
+            target_scale = getattr(net, "target_scale", (1.0, 1.0))
+        self.target_scale = tuple(float(v) for v in target_scale)
 
     def covers(self, Ha, cw):
         return self.ha_range[0] <= Ha <= self.ha_range[1] and self.cw_range[0] <= cw <= self.cw_range[1]
@@ -61,11 +65,13 @@ def pipe_cases(draws, n, R):
     return out
 
 
-def generate(draws, n=64, R=30.0, tol=1e-7, max_steps=400000, prec=lbm.LBM_FP32, batch=64, stream=None):
+def generate(draws, n=64, R=30.0, tol=1e-7, max_steps=400000, prec=lbm.LBM_FP32, batch=64, stream=None,
+             per_case=None, seed=IN.SEED):
     """Steady fields of the drawn cases, solved in batches of `batch` cases
     (one launch per step each).  Returns (X [M, 4], T [M, 2], stats) with one
-    sample per fluid node."""
+    sample per fluid node, or per_case nodes drawn at random per case."""
     Xs, Ts, stats = [], [], []
+    r = IN.rng(seed + 3)
     for b0 in range(0, len(draws), batch):
         group = pipe_cases(draws[b0:b0 + batch], n, R)
         sol = lbm.Solver(lbm.LBM_D3Q19, prec, lbm.LBM_FLOW | lbm.LBM_MHD, [g[0] for g in group], stream=stream)
@@ -84,24 +90,33 @@ def generate(draws, n=64, R=30.0, tol=1e-7, max_steps=400000, prec=lbm.LBM_FP32,
             X = np.stack([yy.ravel()[fl] / R, zz.ravel()[fl] / R, np.full(fl.sum(), f_ha(d["Ha"])),
                           np.full(fl.sum(), f_cw(d["cw"]))], axis=1)
             T = np.stack([m["u"][fl, 0] / us, m["B"][fl, 0] / bs], axis=1)
+            if per_case and per_case < len(X):
+                keep = r.choice(len(X), per_case, replace=False)
+                X, T = X[keep], T[keep]
             Xs.append(X)
             Ts.append(T)
         sol.close()
     return np.concatenate(Xs).astype(np.float32), np.concatenate(Ts).astype(np.float32), stats
 
 
-def train(X, T, epochs=30, batch=8192, lr=3e-3, seed=IN.SEED, stream=None, log=None):
+def train(X, T, epochs=30, batch=8192, lr=3e-3, seed=IN.SEED, stream=None, log=None, normalise=True):
     """Minibatch Adam on the GPU with the library's kernels; minibatches are
-    a fixed host-side shuffle per epoch.  Returns (net, loss history)."""
+    a fixed host-side shuffle per epoch.  With normalise, each output is
+    fitted as T / rms(T) so that both outputs weigh alike in the loss (the
+    scale is kept as net.target_scale).  Returns (net, loss history)."""
     import torch
     net = lbm.Net(IN.net_init(seed), stream=stream)
+    scale = np.sqrt(np.mean(np.asarray(T, dtype=np.float64) ** 2, axis=0)) if normalise else np.ones(T.shape[1])
+    scale = np.where(scale > 0, scale, 1.0)
+    net.target_scale = tuple(float(v) for v in scale)
+    Tn = (np.asarray(T, dtype=np.float64) / scale).astype(np.float32)
     r = IN.rng(seed + 1)
     hist = []
     n = len(X)
     for ep in range(epochs):
         perm = r.permutation(n)
         Xd = torch.tensor(X[perm], device="cuda")
-        Td = torch.tensor(T[perm], device="cuda")
+        Td = torch.tensor(Tn[perm], device="cuda")
         lr_ep = lr * 0.5 * (1 + math.cos(math.pi * ep / epochs))
         tot = 0.0
         for b in range(0, n, batch):
@@ -126,7 +141,9 @@ def warm_start(sol, case_id, sur, info, shape, R, Ha, cw):
     u = torch.empty(3 * N, dtype=torch.float32, device="cuda")
     B = torch.empty(3 * N, dtype=torch.float32, device="cuda")
     us, bs = scales(info, R)
-    net.pipe_fields(shape, R, f_ha(Ha), f_cw(cw), us, bs, info["B0"], u, B)
+    su, sb = sur.target_scale
+    net.pipe_fields(shape, R, f_ha(Ha), f_cw(cw), us * su, bs * sb, info["B0"], u, B)
+    torch.cuda.synchronize()              # the network's stream wrote u, B; the solver's stream reads them
     sol.init_equilibrium_device(case_id, u=u, B=B)
     out = sol.check(raise_unstable=False)
     if out[case_id, 5] != 0:

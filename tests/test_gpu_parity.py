@@ -39,7 +39,8 @@ class Pair:
         self.orc.init(rho=f.get("rho"), u=f.get("u"), C=f.get("C"), B=f.get("B"), rho0=1.0, C0=C0, B0=B0)
         case = lbm.make_case(shape, taus[0], taus[1], taus[2], accel, 1.0, C0, B0)
         self.gpu = lbm.Solver(lbm.LBM_D2Q9 if dim == 2 else lbm.LBM_D3Q19, prec, _phys(has_h, has_g), [case])
-        self.gpu.set_walls(0, solid, to_abi_links(links))
+        self.solid, self.abi_links = solid, to_abi_links(links)
+        self.gpu.set_walls(0, solid, self.abi_links)
         if fields:
             self.gpu.init_equilibrium(0, rho=f.get("rho"), u=f.get("u"), C=f.get("C"), B=f.get("B"))
         self.has_h, self.has_g = has_h, has_g
@@ -335,3 +336,23 @@ def test_autotune_keeps_solution():
     after = p.gpu.get_state()
     assert np.array_equal(before, after)
     p.gpu.step(2)   # still runs with the chosen launch shape
+
+
+@pytest.mark.parametrize("launch", [(0, 128, 0, 1, 2, 1), (0, 256, 0, 4, 2, 1), (0, 128, 8, 2, 2, 1)])
+def test_reductions_any_launch_shape(launch):
+    """Every node of a tile enters the sums whatever the tile size (tiles of
+    up to 1024 nodes are reduced by 256-thread blocks): FP32 storage against
+    the FP64 oracle, sums at FP32 rounding of the per-node values."""
+    p = _random_pair(2, True, True, seed=37, prec=lbm.LBM_FP32, shape=(61, 47, 1))
+    p.gpu.set_launch(*launch)
+    p.step(6)
+    out = p.gpu.check()[0]
+    s = p.orc.sums()
+    assert abs(out[0] - s[0]) < 1e-6 * abs(s[0])
+    assert abs(out[1] - s[1]) < 1e-6 * abs(s[1])
+    assert np.abs(out[2:4] - s[2:4]).max() < 1e-5 * max(1.0, np.abs(s[2:4]).max())
+    assert out[5] == 0
+    m = p.orc.moments()
+    fl = p.fluid
+    phi = np.concatenate([m["u"][fl, :2], m["C"][fl, None], m["B"][fl, :2] - [0, 0.3]], axis=1)
+    assert abs(out[7] - np.sum(phi ** 2)) < 1e-5 * np.sum(phi ** 2)
