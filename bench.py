@@ -48,7 +48,9 @@ def parse():
     ap.add_argument("--train-cases", type=int, default=512)
     ap.add_argument("--train-R", type=float, default=62.0)
     ap.add_argument("--train-tol", type=float, default=1e-5)
-    ap.add_argument("--train-epochs", type=int, default=40)
+    ap.add_argument("--train-epochs", type=int, default=100)
+    ap.add_argument("--train-per-case", type=int, default=2048)
+    ap.add_argument("--train-max-steps", type=int, default=200000)
     ap.add_argument("--reference-steps", type=int, default=0,
                     help="steady_pipe reference arm: steps to project the oracle's time over (0: the "
                          "plain form's step count is unknown to that arm; it reports seconds per 1000 steps)")
@@ -505,11 +507,11 @@ def run_steady(args):
     t0 = time.perf_counter()
     draws = IN.pipe_draws(args.train_cases, seed=IN.SEED, Ha=SG.HA_RANGE, cw=SG.CW_RANGE)
     n_t = int(2 * args.train_R) + 4
-    X, T, gstats = SG.generate(draws, n=n_t, R=args.train_R, tol=args.train_tol, max_steps=args.steady_max_steps,
-                               prec=lbm.LBM_FP16S, batch=128, stream=stream.cuda_stream)
+    X, T, gstats = SG.generate(draws, n=n_t, R=args.train_R, tol=args.train_tol, max_steps=args.train_max_steps,
+                               prec=lbm.LBM_FP32, batch=128, stream=stream.cuda_stream, per_case=args.train_per_case)
     gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    net, hist = SG.train(X, T, epochs=args.train_epochs, batch=8192, lr=3e-3, stream=stream.cuda_stream)
+    net, hist = SG.train(X, T, epochs=args.train_epochs, batch=4096, lr=3e-3, stream=stream.cuda_stream)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     sur = SG.Surrogate(net, SG.HA_RANGE, SG.CW_RANGE)

@@ -132,37 +132,86 @@ LBM_DEV void node_terms(const S *src, int64_t stride, int n, const CaseDev<T> &c
     }
 }
 
-// Adds the node terms to the FP64 record acc[RED_Q] (count kept as an int).
-template <class PL, class T>
-LBM_DEV void add_terms(double (&acc)[RED_Q], int &nfc, T rho, T C, const T (&B)[3], int nf, T r2, T p2) {
-    constexpr int D = PL::F::DIM;
-    acc[0] += (double)rho;
-    if constexpr (PL::G0 > PL::H0) acc[1] += (double)C;
-    if constexpr (PL::P > PL::G0) {
-        acc[2] += (double)B[0];
-        acc[3] += (double)B[1];
-        if constexpr (D == 3) acc[4] += (double)B[2];
+// Accumulators of the record.  FP64 steps sum in double.  FP32 steps keep
+// each running sum as an unevaluated pair hi + lo of floats (Knuth's TwoSum:
+// hi + lo equals the exact sum of the added floats up to ~2^-44 relative),
+// combine pairs across the warp the same way, and form doubles only for the
+// per-block partial records, so that the FP64 units (1/70 of the FP32 rate on
+// GB300) see a few operations per block instead of several per node.
+template <class T>
+struct RecAcc {
+    double v[RED_Q];
+    LBM_DEV void zero() {
+#pragma unroll
+        for (int i = 0; i < RED_Q; ++i) v[i] = 0.0;
     }
-    nfc += nf;
-    acc[6] += (double)r2;
-    acc[7] += (double)p2;
+    LBM_DEV void add(int i, T x) { v[i] += (double)x; }
+    LBM_DEV void warp_reduce() {
+#pragma unroll
+        for (int i = 0; i < RED_Q; ++i)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+    }
+    LBM_DEV double get(int i) const { return v[i]; }
+};
+
+LBM_DEV void two_sum(float &hi, float &lo, float b) {
+    const float s = hi + b;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (b - bb);
+    hi = s;
 }
 
-LBM_DEV double warp_sum(double v) {
+template <>
+struct RecAcc<float> {
+    float hi[RED_Q], lo[RED_Q];
+    LBM_DEV void zero() {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
+        for (int i = 0; i < RED_Q; ++i) hi[i] = lo[i] = 0.f;
+    }
+    LBM_DEV void add(int i, float x) { two_sum(hi[i], lo[i], x); }
+    LBM_DEV void warp_reduce() {
+#pragma unroll
+        for (int i = 0; i < RED_Q; ++i)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float h = __shfl_down_sync(0xffffffffu, hi[i], o);
+                const float l = __shfl_down_sync(0xffffffffu, lo[i], o);
+                two_sum(hi[i], lo[i], h);
+                lo[i] += l;
+            }
+    }
+    LBM_DEV double get(int i) const { return (double)hi[i] + (double)lo[i]; }
+};
+
+// Adds the node terms to the record (non-finite count kept as an int).
+template <class PL, class T>
+LBM_DEV void add_terms(RecAcc<T> &acc, int &nfc, T rho, T C, const T (&B)[3], int nf, T r2, T p2) {
+    constexpr int D = PL::F::DIM;
+    acc.add(0, rho);
+    if constexpr (PL::G0 > PL::H0) acc.add(1, C);
+    if constexpr (PL::P > PL::G0) {
+        acc.add(2, B[0]);
+        acc.add(3, B[1]);
+        if constexpr (D == 3) acc.add(4, B[2]);
+    }
+    nfc += nf;
+    acc.add(6, r2);
+    acc.add(7, p2);
 }
 
 // Block-wide sum of the record into out[RED_Q] (blockDim.x a multiple of 32,
-// at most 1024; sh holds RED_Q x 32 doubles).
-LBM_DEV void block_record(double (&acc)[RED_Q], int nfc, double (*sh)[32], double *out) {
-    acc[5] = (double)nfc;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// at most 1024; sh holds RED_Q x 32 doubles); the warps' records are summed
+// in FP64 in a fixed order.
+template <class T>
+LBM_DEV void block_record(RecAcc<T> &acc, int nfc, double (*sh)[32], double *out) {
+    acc.warp_reduce();
 #pragma unroll
-    for (int i = 0; i < RED_Q; ++i) {
-        const double v = warp_sum(acc[i]);
-        if (lane == 0) sh[i][warp] = v;
+    for (int o = 16; o > 0; o >>= 1) nfc += __shfl_down_sync(0xffffffffu, nfc, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < RED_Q; ++i) sh[i][warp] = i == 5 ? (double)nfc : acc.get(i);
     }
     __syncthreads();
     if (threadIdx.x < RED_Q) {
@@ -199,9 +248,8 @@ __global__ void __launch_bounds__(256) k_reduce(const RedParams<typename Codec<S
     const int t = blockIdx.x;
     const int2 tile = rp.tiles[t];
     const CaseDev<T> &c = rp.cases[tile.x];
-    double acc[RED_Q];
-#pragma unroll
-    for (int i = 0; i < RED_Q; ++i) acc[i] = 0.0;
+    RecAcc<T> acc;
+    acc.zero();
     int nfc = 0;
     for (int i = threadIdx.x; i < rp.tile_nodes; i += blockDim.x) {
         const int n = tile.y + i;

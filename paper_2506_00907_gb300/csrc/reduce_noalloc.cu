@@ -35,9 +35,8 @@ __global__ void __launch_bounds__(NOALLOC_BLOCK) k_reduce_noalloc(const CaseDev<
     using T = typename Codec<S>::T;
     __shared__ double sh[RED_Q][32];
     const int n = blockIdx.x * NOALLOC_BLOCK + threadIdx.x;
-    double acc[RED_Q];
-#pragma unroll
-    for (int i = 0; i < RED_Q; ++i) acc[i] = 0.0;
+    RecAcc<T> acc;
+    acc.zero();
     int nfc = 0;
     if (n < c.N && (!flags || flags[n])) {
         T rho, C, B[3], r2, p2;

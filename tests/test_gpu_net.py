@@ -81,7 +81,7 @@ def trained():
     [0.01, 1]) that the batched solver itself produced."""
     draws = IN.pipe_draws(48, seed=2506, Ha=HA, cw=CW)
     X, T, stats = SG.generate(draws, n=N_PIPE, R=R_PIPE, tol=1e-5, batch=48, max_steps=100000)
-    net, hist = SG.train(X, T, epochs=150, batch=4096, lr=3e-3, seed=7)
+    net, hist = SG.train(X, T, epochs=300, batch=1024, lr=3e-3, seed=7)
     return SG.Surrogate(net, HA, CW), hist
 
 
