@@ -202,7 +202,9 @@ int64_t lbm_steps_done(const lbm_ctx *ctx);
  *   variant 0: one thread per node at a time; tiles of block *
  *              nodes_per_thread nodes (1..8); blocks_per_sm = resident
  *              blocks per SM of a persistent tile loop (0 = one block per
- *              tile, up to 64).
+ *              tile, up to 64); min_blocks selects the register budget the
+ *              kernel was compiled for, as resident 256-thread blocks per SM:
+ *              2D 4, 5 or 6, 3D 2, 3 or 4 (1 = the first).
  *   variant 1: bulk-copy pipeline (FP32 and 16-bit storage): persistent
  *              blocks keep `stages` - 1 tiles of source windows in flight in
  *              shared memory (cp.async.bulk on mbarriers) while computing the

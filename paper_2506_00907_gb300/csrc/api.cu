@@ -67,7 +67,7 @@ struct lbm_ctx {
     uint8_t *d_flags = nullptr;
     void *d_cases = nullptr;
     lbm_launch launch{0, 256, 0, 1, 2, 1};     // see lbm_set_launch
-    int tile_nodes = 256, tma_grid = 0, tma_idx = 0;
+    int tile_nodes = 256, tma_grid = 0, tma_idx = 0, step_idx = 0;
     size_t tma_smem = 0;
     int32_t *d_err = nullptr;
     int2 *d_tiles = nullptr;
@@ -404,8 +404,8 @@ cudaError_t launch_step_t(lbm_ctx *ctx) {
             ctx->ks.step_tma[ctx->tma_idx](&p, tp, step_grid(ctx), ctx->launch.block, ctx->tma_smem, ctx->stream);
         if (e != cudaSuccess) return e;
     } else {
-        const cudaError_t e =
-            ctx->ks.step(&p, ctx->launch.nodes_per_thread, step_grid(ctx), ctx->launch.block, ctx->stream);
+        const cudaError_t e = ctx->ks.step[ctx->step_idx](&p, ctx->launch.nodes_per_thread, step_grid(ctx),
+                                                          ctx->launch.block, ctx->stream);
         if (e != cudaSuccess) return e;
     }
     if (ctx->nbrec > 0) return cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
@@ -925,9 +925,16 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
         return fail(ctx, LBM_EINVAL, "variant must be 0 or 1 and block 64..256 in steps of 32");
     int tile = L.block;
     int idx = 0;
+    int sidx = 0;
     if (L.variant == 0) {
         if (L.blocks_per_sm < 0 || L.blocks_per_sm > 64) return fail(ctx, LBM_EINVAL, "blocks per SM must be 0..64");
         if (L.nodes_per_thread < 1 || L.nodes_per_thread > 8) return fail(ctx, LBM_EINVAL, "nodes per thread must be 1..8");
+        sidx = -1;
+        for (int k = 0; k < 3; ++k)
+            if (kstep_minb(ctx->dim, k) == L.min_blocks) sidx = k;
+        if (L.min_blocks == 1) sidx = 0;
+        if (sidx < 0)
+            return fail(ctx, LBM_EINVAL, "min_blocks must be 1 or %d..%d", kstep_minb(ctx->dim, 0), kstep_minb(ctx->dim, 2));
         tile = L.block * L.nodes_per_thread;
     } else {
         if (L.nodes_per_thread < 1 || L.nodes_per_thread > 8) return fail(ctx, LBM_EINVAL, "nodes per thread must be 1..8");
@@ -952,6 +959,7 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
     }
     ctx->launch = L;
     ctx->tma_idx = idx;
+    ctx->step_idx = sidx;
     if (tile != ctx->tile_nodes) {
         ctx->tile_nodes = tile;
         return build_tiles(ctx);
@@ -987,7 +995,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
     cudaDeviceProp prop{};
     CK(cudaGetDeviceProperties(&prop, ctx->cfg.device));
     std::ostringstream key;
-    key << prop.name << "|v4|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
+    key << prop.name << "|v5|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
         << ctx->cases.size();
     int64_t tot = 0;
     for (auto &c : ctx->cases) tot += c.N;
@@ -1025,14 +1033,13 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     std::vector<lbm_launch> cands;
-    for (int b : {128, 256})
-        for (int p : {0, 4, 8})
-            for (int npt : {1, 2, 4}) cands.push_back(lbm_launch{0, b, p, npt, 2, 1});
+    for (int r = 0; r < 3; ++r)
+        for (int b : {128, 256})
+            for (int p : {0, 8})
+                for (int npt : {1, 2, 4}) cands.push_back(lbm_launch{0, b, p, npt, 2, kstep_minb(ctx->dim, r)});
     if (!ctx->dbl)
         for (int b : {128, 256})
-            for (int npt : {1, 2})
-                for (int stg : {2, 3, 4})
-                    for (int mb : {1, 3, 4}) cands.push_back(lbm_launch{1, b, 0, npt, stg, mb});
+            for (int npt : {1, 2}) cands.push_back(lbm_launch{1, b, 0, npt, 3, 3});
     lbm_launch best = ctx->launch;
     double best_t = INFINITY;
     lbm_status st = LBM_OK;

@@ -9,8 +9,11 @@
 
 namespace lbm {
 
+// register budgets of k_step (resident 256-thread blocks per SM)
+constexpr int kstep_minb(int dim, int i) { return dim == 2 ? 4 + i : 2 + i; }
+
 struct KernelSet {
-    cudaError_t (*step)(const void *params, int npt, int grid, int block, cudaStream_t s);
+    cudaError_t (*step[3])(const void *params, int npt, int grid, int block, cudaStream_t s);
     cudaError_t (*boundary)(const void *params, int grid, int block, cudaStream_t s);
     cudaError_t (*init_d)(const void *params, int grid, int block, cudaStream_t s);   // FP64 host-side fields
     cudaError_t (*init_f)(const void *params, int grid, int block, cudaStream_t s);   // FP32 device fields
@@ -19,7 +22,7 @@ struct KernelSet {
     // pipeline variants compiled for 1, 3 and 4 resident blocks per SM (register budgets)
     cudaError_t (*step_tma[3])(const void *params, const TmaParams &tp, int grid, int block, size_t smem,
                                cudaStream_t s);
-    const void *step_fn;          // kernel symbols (occupancy queries, attributes)
+    const void *step_fn[3];       // kernel symbols (occupancy queries, attributes)
     const void *step_tma_fn[3];
 };
 
@@ -28,8 +31,9 @@ constexpr int TMA_MINB[3] = {1, 3, 4};
 template <int DIM, bool HH, bool HG, class S>
 struct Launch {
     using T = typename Codec<S>::T;
+    template <int MINB>
     static cudaError_t step(const void *p, int npt, int g, int b, cudaStream_t s) {
-        k_step<DIM, HH, HG, S><<<g, b, 0, s>>>(*static_cast<const StepParams<T> *>(p), npt);
+        k_step<DIM, HH, HG, S, MINB><<<g, b, 0, s>>>(*static_cast<const StepParams<T> *>(p), npt);
         return cudaGetLastError();
     }
     static cudaError_t boundary(const void *p, int g, int b, cudaStream_t s) {
@@ -59,7 +63,9 @@ struct Launch {
     }
     static KernelSet make() {
         KernelSet k{};
-        k.step = &step;
+        k.step[0] = &step<kstep_minb(DIM, 0)>;
+        k.step[1] = &step<kstep_minb(DIM, 1)>;
+        k.step[2] = &step<kstep_minb(DIM, 2)>;
         k.boundary = &boundary;
         k.init_d = &init_d;
         k.init_f = &init_f;
@@ -68,7 +74,9 @@ struct Launch {
         k.step_tma[0] = &step_tma<1>;
         k.step_tma[1] = &step_tma<3>;
         k.step_tma[2] = &step_tma<4>;
-        k.step_fn = reinterpret_cast<const void *>(&k_step<DIM, HH, HG, S>);
+        k.step_fn[0] = reinterpret_cast<const void *>(&k_step<DIM, HH, HG, S, kstep_minb(DIM, 0)>);
+        k.step_fn[1] = reinterpret_cast<const void *>(&k_step<DIM, HH, HG, S, kstep_minb(DIM, 1)>);
+        k.step_fn[2] = reinterpret_cast<const void *>(&k_step<DIM, HH, HG, S, kstep_minb(DIM, 2)>);
         k.step_tma_fn[0] = reinterpret_cast<const void *>(&k_step_tma<DIM, HH, HG, S, 1>);
         k.step_tma_fn[1] = reinterpret_cast<const void *>(&k_step_tma<DIM, HH, HG, S, 3>);
         k.step_tma_fn[2] = reinterpret_cast<const void *>(&k_step_tma<DIM, HH, HG, S, 4>);

@@ -376,8 +376,10 @@ LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDe
 // Bulk nodes (fluid, no wall link).  Tiles of blockDim.x * npt nodes; each
 // thread takes nodes tid, tid + blockDim.x, ...  The next tile's record is
 // fetched one tile ahead.  Boundary nodes are left to k_boundary.
-template <int DIM, bool HH, bool HG, class S>
-__global__ void __launch_bounds__(256, DIM == 2 ? 4 : 2) k_step(const StepParams<typename Codec<S>::T> prm, const int npt) {
+// MINB: resident 256-thread blocks per SM the kernel is compiled for (its
+// register budget, 65536 / (256 MINB) registers per thread).
+template <int DIM, bool HH, bool HG, class S, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_step(const StepParams<typename Codec<S>::T> prm, const int npt) {
     using T = typename Codec<S>::T;
     int t = blockIdx.x;
     if (t >= prm.ntiles) return;

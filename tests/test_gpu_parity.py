@@ -356,3 +356,18 @@ def test_reductions_any_launch_shape(launch):
     fl = p.fluid
     phi = np.concatenate([m["u"][fl, :2], m["C"][fl, None], m["B"][fl, :2] - [0, 0.3]], axis=1)
     assert abs(out[7] - np.sum(phi ** 2)) < 1e-5 * np.sum(phi ** 2)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_register_budgets_are_bitwise_identical(dim):
+    """The step compiled for each register budget (launch min_blocks) gives
+    the same state bit for bit."""
+    from paper_2506_00907_gb300.lbm import lib  # noqa: F401  (library loaded)
+    base = 4 if dim == 2 else 2
+    states = []
+    for mb in (base, base + 1, base + 2):
+        p = _random_pair(dim, True, True, seed=53 + dim, prec=lbm.LBM_FP32)
+        p.gpu.set_launch(0, 128, 0, 2, 2, mb)
+        p.gpu.step(12)
+        states.append(p.gpu.get_state()[16:])
+    assert np.array_equal(states[0], states[1]) and np.array_equal(states[0], states[2])
