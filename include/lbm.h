@@ -205,12 +205,14 @@ int64_t lbm_steps_done(const lbm_ctx *ctx);
  *              tile, up to 64); min_blocks selects the register budget the
  *              kernel was compiled for, as resident 256-thread blocks per SM:
  *              2D 4, 5 or 6, 3D 2, 3 or 4 (1 = the first).
- *   variant 1: bulk-copy pipeline (FP32 and 16-bit storage): persistent
- *              blocks keep `stages` - 1 tiles of source windows in flight in
- *              shared memory (cp.async.bulk on mbarriers) while computing the
- *              current tile; tile = block * nodes_per_thread nodes (1..8);
- *              stages 2..4; min_blocks 1, 3 or 4 selects the register budget
- *              the kernel was compiled for.
+ *   variant 1: bulk-copy loads and stores (FP32 and 16-bit storage):
+ *              persistent blocks copy each plane's source window of the next
+ *              tile (tile = block * nodes_per_thread nodes, 1..8 per thread)
+ *              into shared memory with cp.async.bulk on mbarriers while
+ *              computing the current tile, and write each finished tile back
+ *              with one cp.async.bulk store per plane; stages must be 2;
+ *              min_blocks 1, 2 or 3 selects the register budget the kernel
+ *              was compiled for.
  * block: 64..256, multiple of 32. */
 typedef struct {
     int32_t variant;

@@ -67,8 +67,8 @@ struct lbm_ctx {
     uint8_t *d_flags = nullptr;
     void *d_cases = nullptr;
     lbm_launch launch{0, 256, 0, 1, 2, 1};     // see lbm_set_launch
-    int tile_nodes = 256, tma_grid = 0, tma_idx = 0, step_idx = 0;
-    size_t tma_smem = 0;
+    int tile_nodes = 256, bulk_grid = 0, bulk_idx = 0, step_idx = 0;
+    size_t bulk_smem = 0;
     int32_t *d_err = nullptr;
     int2 *d_tiles = nullptr;
     int32_t ntiles = 0;
@@ -376,7 +376,7 @@ StepParams<T> step_params(const lbm_ctx *c) {
 }
 
 int step_grid(const lbm_ctx *c) {
-    if (c->launch.variant == 1) return std::max(1, std::min(c->ntiles, c->tma_grid));
+    if (c->launch.variant == 1) return std::max(1, std::min(c->ntiles, c->bulk_grid));
     if (c->launch.blocks_per_sm <= 0) return c->ntiles;
     return std::max(1, std::min(c->ntiles, c->launch.blocks_per_sm * c->sm_count));
 }
@@ -384,6 +384,17 @@ int step_grid(const lbm_ctx *c) {
 template <class T>
 cudaError_t launch_step_t(lbm_ctx *ctx) {
     const StepParams<T> p = step_params<T>(ctx);
+    if (ctx->launch.variant == 1) {
+        // bulk-copy variant: its output tiles cover the boundary nodes, so k_boundary follows it
+        BulkParams bp;
+        bp.tile_nodes = ctx->tile_nodes;
+        bp.cap = ctx->tile_nodes + 16 / (int)ctx->elem;
+        bp.err = ctx->d_err;
+        cudaError_t e =
+            ctx->ks.step_bulk[ctx->bulk_idx](&p, bp, step_grid(ctx), ctx->launch.block, ctx->bulk_smem, ctx->stream);
+        if (e == cudaSuccess && ctx->nbrec > 0) e = ctx->ks.boundary(&p, (ctx->nbrec + 127) / 128, 128, ctx->stream);
+        return e;
+    }
     // boundary nodes (disjoint from the bulk nodes; same source and target
     // buffers) on the side stream, concurrently with the bulk launch
     if (ctx->nbrec > 0) {
@@ -393,21 +404,9 @@ cudaError_t launch_step_t(lbm_ctx *ctx) {
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
         if (e != cudaSuccess) return e;
     }
-    if (ctx->launch.variant == 1) {
-        TmaParams tp;
-        tp.tile_nodes = ctx->tile_nodes;
-        const int A = 16 / (int)ctx->elem;
-        tp.cap = ctx->tile_nodes + 2 * A;
-        tp.stages = ctx->launch.stages;
-        tp.err = ctx->d_err;
-        const cudaError_t e =
-            ctx->ks.step_tma[ctx->tma_idx](&p, tp, step_grid(ctx), ctx->launch.block, ctx->tma_smem, ctx->stream);
-        if (e != cudaSuccess) return e;
-    } else {
-        const cudaError_t e = ctx->ks.step[ctx->step_idx](&p, ctx->launch.nodes_per_thread, step_grid(ctx),
-                                                          ctx->launch.block, ctx->stream);
-        if (e != cudaSuccess) return e;
-    }
+    const cudaError_t e = ctx->ks.step[ctx->step_idx](&p, ctx->launch.nodes_per_thread, step_grid(ctx),
+                                                      ctx->launch.block, ctx->stream);
+    if (e != cudaSuccess) return e;
     if (ctx->nbrec > 0) return cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
     return cudaSuccess;
 }
@@ -438,10 +437,8 @@ lbm_status launch_init(lbm_ctx *ctx, int case_id, const FT *rho, const FT *u, co
     const int grid = (int)((cs.N + 255) / 256);
     CK(fn(&ip, grid, 256, ctx->stream));
     // residual history of the case starts again from zero
-    const size_t se = snap_elem(ctx);
-    for (int k = 0; k < SNAP_Q; ++k)
-        CK(cudaMemsetAsync(reinterpret_cast<char *>(ctx->d_snap) + ((int64_t)k * ctx->total_nodes + cs.node_off) * se,
-                           0, (size_t)cs.N * se, ctx->stream));
+    const size_t se = snap_elem(ctx) * snap_width(ctx->dim, ctx->hh, ctx->hg);
+    CK(cudaMemsetAsync(reinterpret_cast<char *>(ctx->d_snap) + cs.node_off * se, 0, (size_t)cs.N * se, ctx->stream));
     return LBM_OK;
 }
 
@@ -627,8 +624,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
     ck(cudaMalloc(&ctx->d_flags, (size_t)nodes), "flags");
     ck(cudaMalloc(&ctx->d_cases, ctx->cases.size() * (ctx->dbl ? sizeof(CaseDev<double>) : sizeof(CaseDev<float>))),
        "case table");
-    ck(cudaMalloc(&ctx->d_snap, (size_t)nodes * SNAP_Q * sizeof(double)), "snapshot");
-    if (st == LBM_OK) ck(cudaMemset(ctx->d_snap, 0, (size_t)nodes * SNAP_Q * sizeof(double)), "memset");
+    ck(cudaMalloc(&ctx->d_snap, (size_t)nodes * 8 * sizeof(double)), "snapshot");
+    if (st == LBM_OK) ck(cudaMemset(ctx->d_snap, 0, (size_t)nodes * 8 * sizeof(double)), "memset");
     ck(cudaMalloc(&ctx->d_red, ctx->cases.size() * RED_Q * sizeof(double)), "reduction output");
     ck(cudaMallocHost(&ctx->h_red, ctx->cases.size() * RED_Q * sizeof(double)), "pinned reduction output");
     ck(cudaMalloc(&ctx->d_mom, (size_t)ctx->max_case_nodes * 8 * sizeof(double)), "moment scratch");
@@ -794,11 +791,11 @@ lbm_status lbm_check(lbm_ctx *ctx, double *out) {
     if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (ctx->dbl) {
         RedParams<double> rp{ctx->pool[ctx->cur], ctx->d_flags, static_cast<const CaseDev<double> *>(ctx->d_cases),
-                             ctx->d_tiles, ctx->ntiles, ctx->tile_nodes, ctx->d_snap, ctx->total_nodes, ctx->d_part};
+                             ctx->d_tiles, ctx->ntiles, ctx->tile_nodes, ctx->d_snap, ctx->d_part};
         CK(ctx->ks.reduce(&rp, ctx->ntiles, 256, ctx->stream));
     } else {
         RedParams<float> rp{ctx->pool[ctx->cur], ctx->d_flags, static_cast<const CaseDev<float> *>(ctx->d_cases),
-                            ctx->d_tiles, ctx->ntiles, ctx->tile_nodes, ctx->d_snap, ctx->total_nodes, ctx->d_part};
+                            ctx->d_tiles, ctx->ntiles, ctx->tile_nodes, ctx->d_snap, ctx->d_part};
         CK(ctx->ks.reduce(&rp, ctx->ntiles, 256, ctx->stream));
     }
     k_reduce_final<<<(int)ctx->cases.size(), 256, 0, ctx->stream>>>(ctx->d_part, ctx->d_case_tile_lo, ctx->d_red);
@@ -898,7 +895,7 @@ lbm_status lbm_convert_state(lbm_ctx *dst, lbm_ctx *src) {
         default: e = convert_from(static_cast<const __nv_bfloat16 *>(in), out, dst->cfg.prec, n, dst->stream); break;
     }
     CK(e);
-    const int64_t ns = src->total_nodes * SNAP_Q;
+    const int64_t ns = src->total_nodes * snap_width(src->dim, src->hh, src->hg);
     if (snap_elem(dst) == snap_elem(src)) {
         CK(cudaMemcpyAsync(dst->d_snap, src->d_snap, (size_t)ns * snap_elem(src), cudaMemcpyDeviceToDevice,
                            dst->stream));
@@ -938,27 +935,27 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
         tile = L.block * L.nodes_per_thread;
     } else {
         if (L.nodes_per_thread < 1 || L.nodes_per_thread > 8) return fail(ctx, LBM_EINVAL, "nodes per thread must be 1..8");
-        if (L.stages < 2 || L.stages > TMA_MAX_STAGES) return fail(ctx, LBM_EINVAL, "stages must be 2..%d", TMA_MAX_STAGES);
+        if (L.stages != BULK_STAGES) return fail(ctx, LBM_EINVAL, "the bulk-copy variant uses %d stages", BULK_STAGES);
         idx = -1;
         for (int k = 0; k < 3; ++k)
-            if (TMA_MINB[k] == L.min_blocks) idx = k;
-        if (idx < 0) return fail(ctx, LBM_EINVAL, "min_blocks must be 1, 3 or 4");
-        if (ctx->dbl) return fail(ctx, LBM_EINVAL, "the bulk-copy pipeline serves FP32 and 16-bit storage");
+            if (BULK_MINB[k] == L.min_blocks) idx = k;
+        if (idx < 0) return fail(ctx, LBM_EINVAL, "min_blocks must be 1, 2 or 3");
+        if (ctx->dbl) return fail(ctx, LBM_EINVAL, "the bulk-copy variant serves FP32 and 16-bit storage");
         tile = L.block * L.nodes_per_thread;
         const int A = 16 / (int)ctx->elem;
-        const size_t smem = (size_t)tma_header_bytes(ctx->P) + (size_t)L.stages * ctx->P * (tile + 2 * A) * ctx->elem;
+        const size_t smem = bulk_smem_bytes(ctx->P, tile, tile + A, (int)ctx->elem);
         int maxsm = 0;
         CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->cfg.device));
         if (smem > (size_t)maxsm) return fail(ctx, LBM_EINVAL, "tile of %d nodes needs %zu B of shared memory", tile, smem);
-        CK(cudaFuncSetAttribute(ctx->ks.step_tma_fn[idx], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CK(cudaFuncSetAttribute(ctx->ks.step_bulk_fn[idx], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ctx->ks.step_tma_fn[idx], L.block, smem));
-        if (per_sm < 1) return fail(ctx, LBM_EINVAL, "the pipeline does not fit on an SM");
-        ctx->tma_smem = smem;
-        ctx->tma_grid = per_sm * ctx->sm_count;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ctx->ks.step_bulk_fn[idx], L.block, smem));
+        if (per_sm < 1) return fail(ctx, LBM_EINVAL, "the bulk-copy variant does not fit on an SM");
+        ctx->bulk_smem = smem;
+        ctx->bulk_grid = per_sm * ctx->sm_count;
     }
     ctx->launch = L;
-    ctx->tma_idx = idx;
+    ctx->bulk_idx = idx;
     ctx->step_idx = sidx;
     if (tile != ctx->tile_nodes) {
         ctx->tile_nodes = tile;
@@ -995,7 +992,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
     cudaDeviceProp prop{};
     CK(cudaGetDeviceProperties(&prop, ctx->cfg.device));
     std::ostringstream key;
-    key << prop.name << "|v5|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
+    key << prop.name << "|v6|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
         << ctx->cases.size();
     int64_t tot = 0;
     for (auto &c : ctx->cases) tot += c.N;
@@ -1039,7 +1036,8 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
                 for (int npt : {1, 2, 4}) cands.push_back(lbm_launch{0, b, p, npt, 2, kstep_minb(ctx->dim, r)});
     if (!ctx->dbl)
         for (int b : {128, 256})
-            for (int npt : {1, 2}) cands.push_back(lbm_launch{1, b, 0, npt, 3, 3});
+            for (int npt : {1, 2, 4})
+                for (int mb : {2, 3}) cands.push_back(lbm_launch{1, b, 0, npt, BULK_STAGES, mb});
     lbm_launch best = ctx->launch;
     double best_t = INFINITY;
     lbm_status st = LBM_OK;

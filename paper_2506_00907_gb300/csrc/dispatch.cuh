@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
-#include "kernels_tma.cuh"
+#include "kernels_bulk.cuh"
 #include "reduce.cuh"
 
 namespace lbm {
@@ -19,14 +19,14 @@ struct KernelSet {
     cudaError_t (*init_f)(const void *params, int grid, int block, cudaStream_t s);   // FP32 device fields
     cudaError_t (*moments)(const void *params, int grid, int block, cudaStream_t s);
     cudaError_t (*reduce)(const void *params, int grid, int block, cudaStream_t s);
-    // pipeline variants compiled for 1, 3 and 4 resident blocks per SM (register budgets)
-    cudaError_t (*step_tma[3])(const void *params, const TmaParams &tp, int grid, int block, size_t smem,
-                               cudaStream_t s);
+    // bulk-copy variants compiled for 1, 2 and 3 resident blocks per SM (register budgets)
+    cudaError_t (*step_bulk[3])(const void *params, const BulkParams &bp, int grid, int block, size_t smem,
+                                cudaStream_t s);
     const void *step_fn[3];       // kernel symbols (occupancy queries, attributes)
-    const void *step_tma_fn[3];
+    const void *step_bulk_fn[3];
 };
 
-constexpr int TMA_MINB[3] = {1, 3, 4};
+constexpr int BULK_MINB[3] = {1, 2, 3};
 
 template <int DIM, bool HH, bool HG, class S>
 struct Launch {
@@ -57,8 +57,8 @@ struct Launch {
         return cudaGetLastError();
     }
     template <int MINB>
-    static cudaError_t step_tma(const void *p, const TmaParams &tp, int g, int b, size_t smem, cudaStream_t s) {
-        k_step_tma<DIM, HH, HG, S, MINB><<<g, b, smem, s>>>(*static_cast<const StepParams<T> *>(p), tp);
+    static cudaError_t step_bulk(const void *p, const BulkParams &bp, int g, int b, size_t smem, cudaStream_t s) {
+        k_step_bulk<DIM, HH, HG, S, MINB><<<g, b, smem, s>>>(*static_cast<const StepParams<T> *>(p), bp);
         return cudaGetLastError();
     }
     static KernelSet make() {
@@ -71,15 +71,15 @@ struct Launch {
         k.init_f = &init_f;
         k.moments = &moments;
         k.reduce = &reduce;
-        k.step_tma[0] = &step_tma<1>;
-        k.step_tma[1] = &step_tma<3>;
-        k.step_tma[2] = &step_tma<4>;
+        k.step_bulk[0] = &step_bulk<BULK_MINB[0]>;
+        k.step_bulk[1] = &step_bulk<BULK_MINB[1]>;
+        k.step_bulk[2] = &step_bulk<BULK_MINB[2]>;
         k.step_fn[0] = reinterpret_cast<const void *>(&k_step<DIM, HH, HG, S, kstep_minb(DIM, 0)>);
         k.step_fn[1] = reinterpret_cast<const void *>(&k_step<DIM, HH, HG, S, kstep_minb(DIM, 1)>);
         k.step_fn[2] = reinterpret_cast<const void *>(&k_step<DIM, HH, HG, S, kstep_minb(DIM, 2)>);
-        k.step_tma_fn[0] = reinterpret_cast<const void *>(&k_step_tma<DIM, HH, HG, S, 1>);
-        k.step_tma_fn[1] = reinterpret_cast<const void *>(&k_step_tma<DIM, HH, HG, S, 3>);
-        k.step_tma_fn[2] = reinterpret_cast<const void *>(&k_step_tma<DIM, HH, HG, S, 4>);
+        k.step_bulk_fn[0] = reinterpret_cast<const void *>(&k_step_bulk<DIM, HH, HG, S, BULK_MINB[0]>);
+        k.step_bulk_fn[1] = reinterpret_cast<const void *>(&k_step_bulk<DIM, HH, HG, S, BULK_MINB[1]>);
+        k.step_bulk_fn[2] = reinterpret_cast<const void *>(&k_step_bulk<DIM, HH, HG, S, BULK_MINB[2]>);
         return k;
     }
 };

@@ -274,10 +274,11 @@ LBM_DEV void collide(T (&p)[PL::P], const CaseDev<T> &c) {
 }
 
 // ------------------------------------------------------------------ wall links
-template <class S, class T>
-LBM_DEV T field_sum(const S *src, int stride, int q0, int nq, int node) {
+template <int NQ, class S, class T>
+LBM_DEV T field_sum(const S *src, int stride, int q0, int node) {
     T s = 0;
-    for (int j = 0; j < nq; ++j) s += Codec<S>::ld(src + ((q0 + j) * stride + node));
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) s += Codec<S>::ld(src + ((q0 + j) * stride + node));
     return s;
 }
 
@@ -289,9 +290,16 @@ LBM_DEV T eval_link(const LinkDev<T> &L, const S *src, const CaseDev<T> &c) {
     const T papE = Codec<S>::ld(src + ((int)L.plane_ap * st + L.nodeE));
     T v = L.c0 + L.ca * paA + L.cap * papA + L.cape * papE;
     if (L.flags & LINK_NEED_PHI) {
-        const int nq = L.phi_plane0 < PL::QF ? PL::QF : PL::QM;
-        const T phA = field_sum<S, T>(src, st, L.phi_plane0, nq, L.nodeA) + L.ref_phi;
-        const T phE = field_sum<S, T>(src, st, L.phi_plane0, nq, L.nodeE) + L.ref_phi;
+        T phA, phE;
+        if (L.phi_plane0 < PL::QF) {
+            phA = field_sum<PL::QF, S, T>(src, st, L.phi_plane0, L.nodeA);
+            phE = field_sum<PL::QF, S, T>(src, st, L.phi_plane0, L.nodeE);
+        } else {
+            phA = field_sum<PL::QM, S, T>(src, st, L.phi_plane0, L.nodeA);
+            phE = field_sum<PL::QM, S, T>(src, st, L.phi_plane0, L.nodeE);
+        }
+        phA += L.ref_phi;
+        phE += L.ref_phi;
         v += L.cphi * ((T(1) + L.d) * phA - L.d * phE);
     }
     if constexpr (PL::G0 < PL::P) {
@@ -299,8 +307,8 @@ LBM_DEV T eval_link(const LinkDev<T> &L, const S *src, const CaseDev<T> &c) {
 #pragma unroll
             for (int k = 0; k < PL::NB; ++k) {
                 const int q0 = PL::G0 + k * PL::QM;
-                const T bA = field_sum<S, T>(src, st, q0, PL::QM, L.nodeA) + c.ref_B[k];
-                const T bE = field_sum<S, T>(src, st, q0, PL::QM, L.nodeE) + c.ref_B[k];
+                const T bA = field_sum<PL::QM, S, T>(src, st, q0, L.nodeA) + c.ref_B[k];
+                const T bE = field_sum<PL::QM, S, T>(src, st, q0, L.nodeE) + c.ref_B[k];
                 v += L.cB[k] * ((T(1) + L.d) * bA - L.d * bE);
             }
         }
@@ -310,15 +318,27 @@ LBM_DEV T eval_link(const LinkDev<T> &L, const S *src, const CaseDev<T> &c) {
 
 // Replaces the populations of boundary node A that come from solid nodes by
 // the wall formulas of its links [lo, hi).
+// Links are taken four at a time so that their records and the populations
+// they read are all in flight together.
 template <class PL, class S, class T>
 LBM_DEV void apply_links(T (&p)[PL::P], const StepParams<T> &prm, const CaseDev<T> &c, const S *src, int lo, int hi) {
-    for (int li = lo; li < hi; ++li) {
-        const LinkDev<T> L = prm.links[li];
-        const T v = eval_link<PL, S, T>(L, src, c);
-        // select per plane (an indexed store would move p to local memory)
-        const int pa = L.plane_a;
+    constexpr int LCH = 4;
+    for (int base = lo; base < hi; base += LCH) {
+        LinkDev<T> L[LCH];
+        T v[LCH];
 #pragma unroll
-        for (int q = 0; q < PL::P; ++q) p[q] = (q == pa) ? v : p[q];
+        for (int j = 0; j < LCH; ++j)
+            if (base + j < hi) L[j] = prm.links[base + j];
+#pragma unroll
+        for (int j = 0; j < LCH; ++j) v[j] = base + j < hi ? eval_link<PL, S, T>(L[j], src, c) : T(0);
+#pragma unroll
+        for (int j = 0; j < LCH; ++j) {
+            if (base + j >= hi) break;
+            // select per plane (an indexed store would move p to local memory)
+            const int pa = L[j].plane_a;
+#pragma unroll
+            for (int q = 0; q < PL::P; ++q) p[q] = (q == pa) ? v[j] : p[q];
+        }
     }
 }
 
@@ -359,18 +379,23 @@ LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDe
         zi[1] = z * nxy;
         zi[2] = (z == nz - 1 ? 0 : z + 1) * nxy;
     }
-    // in-case indices are 32-bit (the host keeps P * stride below 2^31)
+    // in-case offsets are 32-bit (the host keeps P * stride below 2^31) and
+    // taken from one 64-bit pointer per node: the source of plane q is
+    // sp[q * stride + (wrapped neighbour offset of e_q)]
     const int st32 = (int)c.stride;
+    const S *__restrict__ sp = src + n;
+    S *__restrict__ dp = dst + n;
+    const int ox[3] = {xi[0] - x, 0, xi[2] - x};
+    const int oy[3] = {yi[0] - yi[1], 0, yi[2] - yi[1]};
+    const int oz[3] = {zi[0] - zi[1], 0, zi[2] - zi[1]};
     T p[P];
 #pragma unroll
-    for (int q = 0; q < P; ++q) {
-        const int src_node = xi[1 - PL::ex(q)] + yi[1 - PL::ey(q)] + zi[1 - PL::ez(q)];
-        p[q] = Codec<S>::ld(src + (q * st32 + src_node));
-    }
+    for (int q = 0; q < P; ++q)
+        p[q] = Codec<S>::ld(sp + (q * st32 + ox[1 - PL::ex(q)] + oy[1 - PL::ey(q)] + oz[1 - PL::ez(q)]));
     if constexpr (LINKS) apply_links<PL, S, T>(p, prm, c, src, lo, hi);
     collide<PL, HH, HG, T>(p, c);
 #pragma unroll
-    for (int q = 0; q < P; ++q) Codec<S>::st(dst + (q * st32 + n), p[q]);
+    for (int q = 0; q < P; ++q) Codec<S>::st(dp + q * st32, p[q]);
 }
 
 // Bulk nodes (fluid, no wall link).  Tiles of blockDim.x * npt nodes; each
@@ -387,7 +412,8 @@ __global__ void __launch_bounds__(256, MINB) k_step(const StepParams<typename Co
     for (; t < prm.ntiles; t += gridDim.x) {
         const int tn = t + gridDim.x;
         const int2 next = tn < prm.ntiles ? prm.tiles[tn] : tile;
-        const CaseDev<T> &c = prm.cases[tile.x];
+        // the descriptor by value: the stores below cannot alias it, so it stays in registers
+        const CaseDev<T> c = prm.cases[tile.x];
         for (int k = 0; k < npt; ++k) {
             const int n = tile.y + (int)threadIdx.x + k * (int)blockDim.x;
             if (n >= c.N) break;
@@ -405,7 +431,8 @@ __global__ void __launch_bounds__(128) k_boundary(const StepParams<typename Code
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= prm.nbrec) return;
     const BRec b = prm.brec[i];
-    step_node<DIM, HH, HG, S, true>(prm, prm.cases[b.cs], b.node, b.lo, b.hi);
+    const CaseDev<typename Codec<S>::T> c = prm.cases[b.cs];
+    step_node<DIM, HH, HG, S, true>(prm, c, b.node, b.lo, b.hi);
 }
 
 // ------------------------------------------------------------------ initial state

@@ -9,9 +9,8 @@
 // rho, C, B, a non-finite count and the residual terms
 //   r2 = |phi - phi_prev|^2,  p2 = |phi|^2,  phi = (u, C, B - B0)
 // (only the components the lattice and physics can make nonzero); sums over
-// nodes are FP64.  phi_prev is one plane per component in the snapshot
-// buffer, stored in T (FP64 storage: double, otherwise float), and is
-// replaced by phi.
+// nodes are FP64.  phi_prev is kept node by node in the snapshot buffer,
+// stored in T (FP64 storage: double, otherwise float), and is replaced by phi.
 #pragma once
 #include "kernels.cuh"
 
@@ -101,7 +100,7 @@ __global__ void __launch_bounds__(256) k_moments(const MomParams<typename Codec<
 constexpr int RED_Q = 8;
 constexpr int SNAP_Q = 7;
 
-// Snapshot planes that can be nonzero: u (DIM components), C, B - B0 (DIM).
+// Snapshot components that can be nonzero: u (DIM components), C, B - B0 (DIM).
 template <class PL>
 LBM_HD constexpr bool snap_used(int k) {
     constexpr int D = PL::F::DIM;
@@ -109,26 +108,79 @@ LBM_HD constexpr bool snap_used(int k) {
     return k < 3 ? k < D : (k == 3 ? hh : (hg && k - 4 < D));
 }
 
-// The per-node record terms; snap (may be null: phi_prev = 0) points at the
-// node's entry of plane 0, planes sstride apart.
-template <class PL, class S, class T, class SnapT>
-LBM_DEV void node_terms(const S *src, int64_t stride, int n, const CaseDev<T> &c, SnapT *snap, int64_t sstride,
-                        T &rho, T &C, T (&B)[3], int &nf, T &r2, T &p2) {
+// The context keeps phi_prev node by node: the used components packed into
+// snap_width entries (4 or 8, so that a node's entries are one or two
+// 16-byte vectors in FP32).
+LBM_HD constexpr int snap_width(int dim, bool hh, bool hg) {
+    return dim + (hh ? 1 : 0) + (hg ? dim : 0) <= 4 ? 4 : 8;
+}
+template <class PL>
+LBM_HD constexpr int snap_slot(int k) {
+    int s = 0;
+    for (int i = 0; i < k; ++i) s += snap_used<PL>(i) ? 1 : 0;
+    return s;
+}
+
+// Moments and phi = (u, C, B - B0) of node n.
+template <class PL, class S, class T>
+LBM_DEV void node_phi(const S *src, int64_t stride, int n, const CaseDev<T> &c, T &rho, T &C, T (&B)[3], int &nf,
+                      T (&phi)[SNAP_Q]) {
     T u[3];
     node_moments<PL, S, T>(src, stride, n, c, rho, u, C, B, nf);
-    const T phi[SNAP_Q] = {u[0], u[1], u[2], C, B[0] - c.B0[0], B[1] - c.B0[1], B[2] - c.B0[2]};
+    phi[0] = u[0];
+    phi[1] = u[1];
+    phi[2] = u[2];
+    phi[3] = C;
+    phi[4] = B[0] - c.B0[0];
+    phi[5] = B[1] - c.B0[1];
+    phi[6] = B[2] - c.B0[2];
+}
+
+// Residual terms r2 = |phi - phi_prev|^2 and p2 = |phi|^2 over the used components.
+template <class PL, class T>
+LBM_DEV void resid_terms(const T (&phi)[SNAP_Q], const T (&old)[SNAP_Q], T &r2, T &p2) {
     r2 = T(0);
     p2 = T(0);
 #pragma unroll
     for (int k = 0; k < SNAP_Q; ++k) {
         if (!snap_used<PL>(k)) continue;
-        T dd = phi[k];
-        if (snap) {
-            dd -= T(snap[k * sstride]);
-            snap[k * sstride] = SnapT(phi[k]);
-        }
+        const T dd = phi[k] - old[k];
         r2 = fmaf_t(dd, dd, r2);
         p2 = fmaf_t(phi[k], phi[k], p2);
+    }
+}
+
+// Packed snapshot entries of one node: read phi_prev, write phi (vector
+// accesses; p is aligned to the node's entries).
+template <class PL, class SnapT, class T>
+LBM_DEV void snap_exchange(SnapT *p, const T (&phi)[SNAP_Q], T (&old)[SNAP_Q]) {
+    constexpr int W = snap_width(PL::F::DIM, PL::G0 > PL::H0, PL::P > PL::G0);
+    SnapT v[W];
+    if constexpr (sizeof(SnapT) == 4) {
+#pragma unroll
+        for (int j = 0; j < W / 4; ++j) {
+            const float4 x = reinterpret_cast<const float4 *>(p)[j];
+            v[4 * j] = x.x; v[4 * j + 1] = x.y; v[4 * j + 2] = x.z; v[4 * j + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < W / 2; ++j) {
+            const double2 x = reinterpret_cast<const double2 *>(p)[j];
+            v[2 * j] = x.x; v[2 * j + 1] = x.y;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < SNAP_Q; ++k) {
+        old[k] = snap_used<PL>(k) ? T(v[snap_slot<PL>(k)]) : T(0);
+        if (snap_used<PL>(k)) v[snap_slot<PL>(k)] = SnapT(phi[k]);
+    }
+    if constexpr (sizeof(SnapT) == 4) {
+#pragma unroll
+        for (int j = 0; j < W / 4; ++j)
+            reinterpret_cast<float4 *>(p)[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < W / 2; ++j) reinterpret_cast<double2 *>(p)[j] = make_double2(v[2 * j], v[2 * j + 1]);
     }
 }
 
@@ -230,8 +282,7 @@ struct RedParams {
     const int2 *tiles;
     int32_t ntiles;
     int32_t tile_nodes;
-    void *snap;               // SNAP_Q planes of snap_stride entries, double (FP64 storage) or float
-    int64_t snap_stride;
+    void *snap;               // snap_width entries per node, double (FP64 storage) or float
     double *part;             // [ntiles][RED_Q]
 };
 
@@ -254,11 +305,12 @@ __global__ void __launch_bounds__(256) k_reduce(const RedParams<typename Codec<S
     for (int i = threadIdx.x; i < rp.tile_nodes; i += blockDim.x) {
         const int n = tile.y + i;
         if (n >= c.N || !(rp.flags[c.node_off + n] & NODE_FLUID)) continue;
-        T rho, C, B[3], r2, p2;
+        T rho, C, B[3], r2, p2, phi[SNAP_Q], old[SNAP_Q];
         int nf;
-        node_terms<PL, S, T, SnapT>(static_cast<const S *>(rp.src) + c.pop_off, c.stride, n, c,
-                                    static_cast<SnapT *>(rp.snap) + c.node_off + n, rp.snap_stride,
-                                    rho, C, B, nf, r2, p2);
+        node_phi<PL, S, T>(static_cast<const S *>(rp.src) + c.pop_off, c.stride, n, c, rho, C, B, nf, phi);
+        constexpr int W = snap_width(DIM, HH, HG);
+        snap_exchange<PL, SnapT, T>(static_cast<SnapT *>(rp.snap) + (c.node_off + n) * W, phi, old);
+        resid_terms<PL, T>(phi, old, r2, p2);
         add_terms<PL, T>(acc, nfc, rho, C, B, nf, r2, p2);
     }
     block_record(acc, nfc, sh, rp.part + (int64_t)t * RED_Q);

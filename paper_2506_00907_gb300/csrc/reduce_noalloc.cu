@@ -39,10 +39,16 @@ __global__ void __launch_bounds__(NOALLOC_BLOCK) k_reduce_noalloc(const CaseDev<
     acc.zero();
     int nfc = 0;
     if (n < c.N && (!flags || flags[n])) {
-        T rho, C, B[3], r2, p2;
+        T rho, C, B[3], r2, p2, phi[SNAP_Q], old[SNAP_Q];
         int nf;
-        node_terms<PL, S, T, double>(static_cast<const S *>(pops), c.stride, n, c, snap ? snap + n : nullptr, c.N,
-                                     rho, C, B, nf, r2, p2);
+        node_phi<PL, S, T>(static_cast<const S *>(pops), c.stride, n, c, rho, C, B, nf, phi);
+        // the caller's snapshot: SNAP_Q planes of N doubles
+#pragma unroll
+        for (int k = 0; k < SNAP_Q; ++k) {
+            old[k] = (snap && snap_used<PL>(k)) ? T(snap[(int64_t)k * c.N + n]) : T(0);
+            if (snap && snap_used<PL>(k)) snap[(int64_t)k * c.N + n] = (double)phi[k];
+        }
+        resid_terms<PL, T>(phi, old, r2, p2);
         add_terms<PL, T>(acc, nfc, rho, C, B, nf, r2, p2);
     }
     block_record(acc, nfc, sh, scratch + (int64_t)blockIdx.x * RED_Q);
