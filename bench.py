@@ -448,9 +448,10 @@ def run_ours(args):
                              "bytes_per_step": alg_bytes, "ms_per_step_kernels": ms_kernel,
                              "timing": "CUDA events on the solver stream around each replay of the %d-step "
                                        "graph inside the timed region (step launches only)" % CHECK_EVERY,
-                             "kernel": ("k_step_bulk (bulk-copy loads and stores)" if tune and tune["variant"] == 1
-                                        else "k_step") + " (bulk nodes) + k_boundary (wall-link nodes): one time "
-                                                         "step, %d launches" % per_step},
+                             "kernel": ("k_step_bulk (bulk-copy loads and stores, boundary nodes included)"
+                                        if tune and tune["variant"] == 1 else
+                                        "k_step (bulk nodes) + k_boundary (wall-link nodes)")
+                                       + ": one time step, %d launches" % per_step},
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         if cpu:
             line["cpu_baseline"] = cpu

@@ -206,14 +206,15 @@ int64_t lbm_steps_done(const lbm_ctx *ctx);
  *              kernel was compiled for, as resident 256-thread blocks per SM:
  *              2D 4, 5 or 6, 3D 2, 3 or 4 (1 = the first).
  *   variant 1: bulk-copy loads and stores (FP32 and 16-bit storage):
- *              persistent blocks copy each plane's source window of the next
- *              tile (tile = block * nodes_per_thread nodes, 1..8 per thread)
- *              into shared memory with cp.async.bulk on mbarriers while
- *              computing the current tile, and write each finished tile back
- *              with one cp.async.bulk store per plane; stages must be 2;
- *              min_blocks 1, 2 or 3 selects the register budget the kernel
- *              was compiled for.
- * block: 64..256, multiple of 32. */
+ *              persistent blocks of 256 threads copy each plane's source
+ *              window of the next tile into shared memory with cp.async.bulk
+ *              on mbarriers while computing the current tile, boundary nodes
+ *              included, and write each finished tile back with one
+ *              cp.async.bulk store per plane (one launch per step).  `block`
+ *              is the tile size in nodes and `min_blocks` the register budget,
+ *              one of (128, 2), (256, 2), (256, 4), (512, 1), (512, 2);
+ *              blocks_per_sm, nodes_per_thread and stages are ignored.
+ * block (variant 0): 64..256, multiple of 32. */
 typedef struct {
     int32_t variant;
     int32_t block;

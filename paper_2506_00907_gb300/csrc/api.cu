@@ -75,6 +75,9 @@ struct lbm_ctx {
     int32_t *d_case_tile_lo = nullptr;
     BRec *d_brec = nullptr;
     int32_t nbrec = 0;
+    std::vector<int2> h_tiles;         // host copies for the per-tile boundary ranges
+    std::vector<BRec> h_brec;
+    int32_t *d_tile_brec = nullptr;    // [ntiles + 1]
     void *d_links = nullptr;
     size_t cap_brec = 0, cap_links = 0;
     double *d_snap = nullptr, *d_part = nullptr, *d_red = nullptr, *h_red = nullptr;
@@ -281,6 +284,28 @@ void drop_graphs(lbm_ctx *ctx) {
         if (g) { cudaGraphExecDestroy(g); g = nullptr; }
 }
 
+// Boundary records of each tile (tiles and records are both ordered by case
+// and node): tile t owns records [r[t], r[t + 1]).
+lbm_status build_tile_brec(lbm_ctx *ctx) {
+    std::vector<int32_t> r(ctx->h_tiles.size() + 1, 0);
+    size_t b = 0;
+    for (size_t t = 0; t < ctx->h_tiles.size(); ++t) {
+        const int2 tl = ctx->h_tiles[t];
+        const int32_t end = tl.y + ctx->tile_nodes;
+        while (b < ctx->h_brec.size() && (ctx->h_brec[b].cs < tl.x ||
+                                          (ctx->h_brec[b].cs == tl.x && ctx->h_brec[b].node < tl.y)))
+            ++b;
+        r[t] = (int32_t)b;
+        while (b < ctx->h_brec.size() && ctx->h_brec[b].cs == tl.x && ctx->h_brec[b].node < end) ++b;
+    }
+    r[ctx->h_tiles.size()] = (int32_t)ctx->h_brec.size();
+    if (ctx->d_tile_brec) cudaFree(ctx->d_tile_brec);
+    ctx->d_tile_brec = nullptr;
+    CK(cudaMalloc(&ctx->d_tile_brec, r.size() * sizeof(int32_t)));
+    CK(cudaMemcpy(ctx->d_tile_brec, r.data(), r.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
 lbm_status build_tiles(lbm_ctx *ctx) {
     std::vector<int2> tiles;
     std::vector<int32_t> lo;
@@ -301,8 +326,9 @@ lbm_status build_tiles(lbm_ctx *ctx) {
     CK(cudaMalloc(&ctx->d_part, (size_t)ctx->ntiles * RED_Q * sizeof(double)));
     CK(cudaMemcpy(ctx->d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_case_tile_lo, lo.data(), lo.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    ctx->h_tiles = tiles;
     drop_graphs(ctx);
-    return LBM_OK;
+    return build_tile_brec(ctx);
 }
 
 template <class T>
@@ -335,6 +361,7 @@ lbm_status upload_walls_t(lbm_ctx *ctx) {
         }
     }
     ctx->nbrec = (int32_t)brec.size();
+    ctx->h_brec = brec;
     if (brec.empty()) brec.push_back(BRec{-1, 0, 0, 0});
     if (links.empty()) links.push_back(LinkDev<T>{});
     auto grow = [&](void **ptr, size_t &cap, size_t bytes) -> lbm_status {
@@ -353,6 +380,8 @@ lbm_status upload_walls_t(lbm_ctx *ctx) {
     CK(cudaMemcpy(ctx->d_links, links.data(), links.size() * sizeof(LinkDev<T>), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_flags, flags.data(), flags.size(), cudaMemcpyHostToDevice));
     drop_graphs(ctx);
+    const lbm_status st2 = build_tile_brec(ctx);
+    if (st2 != LBM_OK) return st2;
     return upload_cases(ctx);
 }
 
@@ -371,6 +400,7 @@ StepParams<T> step_params(const lbm_ctx *c) {
     p.ntiles = c->ntiles;
     p.brec = c->d_brec;
     p.nbrec = c->nbrec;
+    p.tile_brec = c->d_tile_brec;
     p.links = static_cast<const LinkDev<T> *>(c->d_links);
     return p;
 }
@@ -385,15 +415,10 @@ template <class T>
 cudaError_t launch_step_t(lbm_ctx *ctx) {
     const StepParams<T> p = step_params<T>(ctx);
     if (ctx->launch.variant == 1) {
-        // bulk-copy variant: its output tiles cover the boundary nodes, so k_boundary follows it
+        // bulk-copy variant: one launch, boundary nodes included
         BulkParams bp;
-        bp.tile_nodes = ctx->tile_nodes;
-        bp.cap = ctx->tile_nodes + 16 / (int)ctx->elem;
         bp.err = ctx->d_err;
-        cudaError_t e =
-            ctx->ks.step_bulk[ctx->bulk_idx](&p, bp, step_grid(ctx), ctx->launch.block, ctx->bulk_smem, ctx->stream);
-        if (e == cudaSuccess && ctx->nbrec > 0) e = ctx->ks.boundary(&p, (ctx->nbrec + 127) / 128, 128, ctx->stream);
-        return e;
+        return ctx->ks.step_bulk[ctx->bulk_idx](&p, bp, step_grid(ctx), ctx->bulk_smem, ctx->stream);
     }
     // boundary nodes (disjoint from the bulk nodes; same source and target
     // buffers) on the side stream, concurrently with the bulk launch
@@ -474,7 +499,7 @@ lbm_status init_case_host(lbm_ctx *ctx, int case_id, const double *rho, const do
 void free_ctx(lbm_ctx *c) {
     if (!c) return;
     drop_graphs(c);
-    void *ptrs[] = {c->pool[0], c->pool[1], c->d_flags, c->d_cases, c->d_tiles, c->d_case_tile_lo,
+    void *ptrs[] = {c->pool[0], c->pool[1], c->d_flags, c->d_cases, c->d_tiles, c->d_case_tile_lo, c->d_tile_brec,
                     c->d_brec, c->d_links, c->d_snap, c->d_part, c->d_red, c->d_mom, c->d_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -918,8 +943,9 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
     if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (!lp) return fail(ctx, LBM_EINVAL, "launch is NULL");
     const lbm_launch L = *lp;
-    if (L.variant < 0 || L.variant > 1 || L.block < 64 || L.block > 256 || L.block % 32)
-        return fail(ctx, LBM_EINVAL, "variant must be 0 or 1 and block 64..256 in steps of 32");
+    if (L.variant < 0 || L.variant > 1) return fail(ctx, LBM_EINVAL, "variant must be 0 or 1");
+    if (L.variant == 0 && (L.block < 64 || L.block > 256 || L.block % 32))
+        return fail(ctx, LBM_EINVAL, "block must be 64..256 in steps of 32");
     int tile = L.block;
     int idx = 0;
     int sidx = 0;
@@ -934,22 +960,21 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
             return fail(ctx, LBM_EINVAL, "min_blocks must be 1 or %d..%d", kstep_minb(ctx->dim, 0), kstep_minb(ctx->dim, 2));
         tile = L.block * L.nodes_per_thread;
     } else {
-        if (L.nodes_per_thread < 1 || L.nodes_per_thread > 8) return fail(ctx, LBM_EINVAL, "nodes per thread must be 1..8");
-        if (L.stages != BULK_STAGES) return fail(ctx, LBM_EINVAL, "the bulk-copy variant uses %d stages", BULK_STAGES);
         idx = -1;
-        for (int k = 0; k < 3; ++k)
-            if (BULK_MINB[k] == L.min_blocks) idx = k;
-        if (idx < 0) return fail(ctx, LBM_EINVAL, "min_blocks must be 1, 2 or 3");
+        for (int k = 0; k < BULK_NCFG; ++k)
+            if (BULK_TT[k] == L.block && BULK_MB[k] == L.min_blocks) idx = k;
+        if (idx < 0)
+            return fail(ctx, LBM_EINVAL, "bulk-copy variant: (block = tile nodes, min_blocks) must be one of "
+                                         "(128, 2), (256, 2), (256, 4), (512, 1), (512, 2)");
         if (ctx->dbl) return fail(ctx, LBM_EINVAL, "the bulk-copy variant serves FP32 and 16-bit storage");
-        tile = L.block * L.nodes_per_thread;
-        const int A = 16 / (int)ctx->elem;
-        const size_t smem = bulk_smem_bytes(ctx->P, tile, tile + A, (int)ctx->elem);
+        tile = L.block;
+        const size_t smem = (size_t)bulk_layout_bytes(ctx->P, tile, (int)ctx->elem);
         int maxsm = 0;
         CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->cfg.device));
         if (smem > (size_t)maxsm) return fail(ctx, LBM_EINVAL, "tile of %d nodes needs %zu B of shared memory", tile, smem);
         CK(cudaFuncSetAttribute(ctx->ks.step_bulk_fn[idx], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ctx->ks.step_bulk_fn[idx], L.block, smem));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ctx->ks.step_bulk_fn[idx], BULK_THREADS, smem));
         if (per_sm < 1) return fail(ctx, LBM_EINVAL, "the bulk-copy variant does not fit on an SM");
         ctx->bulk_smem = smem;
         ctx->bulk_grid = per_sm * ctx->sm_count;
@@ -971,7 +996,10 @@ lbm_status lbm_get_launch(const lbm_ctx *ctx, lbm_launch *lp) {
     return LBM_OK;
 }
 
-int32_t lbm_launches_per_step(const lbm_ctx *ctx) { return ctx ? 1 + (ctx->nbrec > 0 ? 1 : 0) : 0; }
+int32_t lbm_launches_per_step(const lbm_ctx *ctx) {
+    if (!ctx) return 0;
+    return ctx->launch.variant == 1 ? 1 : 1 + (ctx->nbrec > 0 ? 1 : 0);
+}
 
 lbm_status lbm_device_state(lbm_ctx *ctx, int32_t case_id, void **base, int32_t *elem_bytes, int64_t *plane_stride,
                             int64_t *case_offset, int32_t *planes) {
@@ -992,7 +1020,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
     cudaDeviceProp prop{};
     CK(cudaGetDeviceProperties(&prop, ctx->cfg.device));
     std::ostringstream key;
-    key << prop.name << "|v6|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
+    key << prop.name << "|v7|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
         << ctx->cases.size();
     int64_t tot = 0;
     for (auto &c : ctx->cases) tot += c.N;
@@ -1035,9 +1063,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
             for (int p : {0, 8})
                 for (int npt : {1, 2, 4}) cands.push_back(lbm_launch{0, b, p, npt, 2, kstep_minb(ctx->dim, r)});
     if (!ctx->dbl)
-        for (int b : {128, 256})
-            for (int npt : {1, 2, 4})
-                for (int mb : {2, 3}) cands.push_back(lbm_launch{1, b, 0, npt, BULK_STAGES, mb});
+        for (int k = 0; k < BULK_NCFG; ++k) cands.push_back(lbm_launch{1, BULK_TT[k], 0, 1, 2, BULK_MB[k]});
     lbm_launch best = ctx->launch;
     double best_t = INFINITY;
     lbm_status st = LBM_OK;

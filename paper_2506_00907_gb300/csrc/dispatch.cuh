@@ -19,14 +19,12 @@ struct KernelSet {
     cudaError_t (*init_f)(const void *params, int grid, int block, cudaStream_t s);   // FP32 device fields
     cudaError_t (*moments)(const void *params, int grid, int block, cudaStream_t s);
     cudaError_t (*reduce)(const void *params, int grid, int block, cudaStream_t s);
-    // bulk-copy variants compiled for 1, 2 and 3 resident blocks per SM (register budgets)
-    cudaError_t (*step_bulk[3])(const void *params, const BulkParams &bp, int grid, int block, size_t smem,
-                                cudaStream_t s);
+    // bulk-copy variants, one per (tile nodes, register budget) of BULK_TT / BULK_MB (null for FP64)
+    cudaError_t (*step_bulk[BULK_NCFG])(const void *params, const BulkParams &bp, int grid, size_t smem,
+                                        cudaStream_t s);
     const void *step_fn[3];       // kernel symbols (occupancy queries, attributes)
-    const void *step_bulk_fn[3];
+    const void *step_bulk_fn[BULK_NCFG];
 };
-
-constexpr int BULK_MINB[3] = {1, 2, 3};
 
 template <int DIM, bool HH, bool HG, class S>
 struct Launch {
@@ -56,10 +54,21 @@ struct Launch {
         k_reduce<DIM, HH, HG, S><<<g, b, 0, s>>>(*static_cast<const RedParams<T> *>(p));
         return cudaGetLastError();
     }
-    template <int MINB>
-    static cudaError_t step_bulk(const void *p, const BulkParams &bp, int g, int b, size_t smem, cudaStream_t s) {
-        k_step_bulk<DIM, HH, HG, S, MINB><<<g, b, smem, s>>>(*static_cast<const StepParams<T> *>(p), bp);
+    template <int I>
+    static cudaError_t step_bulk(const void *p, const BulkParams &bp, int g, size_t smem, cudaStream_t s) {
+        k_step_bulk<DIM, HH, HG, S, BULK_MB[I], BULK_TT[I]><<<g, BULK_THREADS, smem, s>>>(
+            *static_cast<const StepParams<T> *>(p), bp);
         return cudaGetLastError();
+    }
+    template <int I>
+    static void set_bulk(KernelSet &k) {
+        if constexpr (std::is_same<S, double>::value) {
+            k.step_bulk[I] = nullptr;
+            k.step_bulk_fn[I] = nullptr;
+        } else {
+            k.step_bulk[I] = &step_bulk<I>;
+            k.step_bulk_fn[I] = reinterpret_cast<const void *>(&k_step_bulk<DIM, HH, HG, S, BULK_MB[I], BULK_TT[I]>);
+        }
     }
     static KernelSet make() {
         KernelSet k{};
@@ -71,15 +80,15 @@ struct Launch {
         k.init_f = &init_f;
         k.moments = &moments;
         k.reduce = &reduce;
-        k.step_bulk[0] = &step_bulk<BULK_MINB[0]>;
-        k.step_bulk[1] = &step_bulk<BULK_MINB[1]>;
-        k.step_bulk[2] = &step_bulk<BULK_MINB[2]>;
+        set_bulk<0>(k);
+        set_bulk<1>(k);
+        set_bulk<2>(k);
+        set_bulk<3>(k);
+        set_bulk<4>(k);
+        static_assert(BULK_NCFG == 5, "one set_bulk per configuration");
         k.step_fn[0] = reinterpret_cast<const void *>(&k_step<DIM, HH, HG, S, kstep_minb(DIM, 0)>);
         k.step_fn[1] = reinterpret_cast<const void *>(&k_step<DIM, HH, HG, S, kstep_minb(DIM, 1)>);
         k.step_fn[2] = reinterpret_cast<const void *>(&k_step<DIM, HH, HG, S, kstep_minb(DIM, 2)>);
-        k.step_bulk_fn[0] = reinterpret_cast<const void *>(&k_step_bulk<DIM, HH, HG, S, BULK_MINB[0]>);
-        k.step_bulk_fn[1] = reinterpret_cast<const void *>(&k_step_bulk<DIM, HH, HG, S, BULK_MINB[1]>);
-        k.step_bulk_fn[2] = reinterpret_cast<const void *>(&k_step_bulk<DIM, HH, HG, S, BULK_MINB[2]>);
         return k;
     }
 };

@@ -72,6 +72,7 @@ struct StepParams {
     const BRec *brec;         // boundary nodes of all cases
     int32_t nbrec;
     const LinkDev<T> *links;
+    const int32_t *tile_brec; // boundary records of tile t: [tile_brec[t], tile_brec[t + 1])
 };
 
 // ------------------------------------------------------------------ equilibria
@@ -318,11 +319,10 @@ LBM_DEV T eval_link(const LinkDev<T> &L, const S *src, const CaseDev<T> &c) {
 
 // Replaces the populations of boundary node A that come from solid nodes by
 // the wall formulas of its links [lo, hi).
-// Links are taken four at a time so that their records and the populations
+// Links are taken LCH at a time so that their records and the populations
 // they read are all in flight together.
-template <class PL, class S, class T>
+template <class PL, class S, class T, int LCH>
 LBM_DEV void apply_links(T (&p)[PL::P], const StepParams<T> &prm, const CaseDev<T> &c, const S *src, int lo, int hi) {
-    constexpr int LCH = 4;
     for (int base = lo; base < hi; base += LCH) {
         LinkDev<T> L[LCH];
         T v[LCH];
@@ -357,10 +357,11 @@ LBM_DEV void coords(const CaseDev<T> &c, int n, int &x, int &y, int &z, int &r) 
 }
 
 // ------------------------------------------------------------------ fused step
-// One node: pull, (boundary nodes: wall links [lo, hi)), collide, store.
-template <int DIM, bool HH, bool HG, class S, bool LINKS>
+// One node: pull, (boundary nodes: wall links [lo, hi)), collide, store
+// plane q to out[q * ostride] (out = 0: the node's entries of the target buffer).
+template <int DIM, bool HH, bool HG, class S, bool LINKS, int LCH = 4>
 LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDev<typename Codec<S>::T> &c, int n,
-                       int lo, int hi) {
+                       int lo, int hi, S *out = nullptr, int ostride = 0) {
     using PL = Planes<DIM, HH, HG>;
     using T = typename Codec<S>::T;
     constexpr int P = PL::P;
@@ -384,7 +385,8 @@ LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDe
     // sp[q * stride + (wrapped neighbour offset of e_q)]
     const int st32 = (int)c.stride;
     const S *__restrict__ sp = src + n;
-    S *__restrict__ dp = dst + n;
+    S *__restrict__ dp = out ? out : dst + n;
+    const int os = out ? ostride : st32;
     const int ox[3] = {xi[0] - x, 0, xi[2] - x};
     const int oy[3] = {yi[0] - yi[1], 0, yi[2] - yi[1]};
     const int oz[3] = {zi[0] - zi[1], 0, zi[2] - zi[1]};
@@ -392,10 +394,10 @@ LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDe
 #pragma unroll
     for (int q = 0; q < P; ++q)
         p[q] = Codec<S>::ld(sp + (q * st32 + ox[1 - PL::ex(q)] + oy[1 - PL::ey(q)] + oz[1 - PL::ez(q)]));
-    if constexpr (LINKS) apply_links<PL, S, T>(p, prm, c, src, lo, hi);
+    if constexpr (LINKS) apply_links<PL, S, T, LCH>(p, prm, c, src, lo, hi);
     collide<PL, HH, HG, T>(p, c);
 #pragma unroll
-    for (int q = 0; q < P; ++q) Codec<S>::st(dp + q * st32, p[q]);
+    for (int q = 0; q < P; ++q) Codec<S>::st(dp + q * os, p[q]);
 }
 
 // Bulk nodes (fluid, no wall link).  Tiles of blockDim.x * npt nodes; each

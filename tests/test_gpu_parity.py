@@ -290,17 +290,16 @@ def test_bulk_copy_pipeline_is_bitwise_identical(dim, prec):
     ref.step(15)
     want = ref.get_state()
     ran = 0
-    for block, npt, stages, minb in ((128, 1, 2, 1), (256, 2, 2, 3), (64, 4, 2, 2), (192, 3, 2, 2), (256, 1, 2, 1),
-                                     (64, 1, 2, 3)):
+    for block, minb in ((128, 2), (256, 2), (256, 4), (512, 1), (512, 2)):
         g = _random_pair(dim, True, True, seed=77, prec=prec, shape=shape).gpu
         try:
-            g.set_launch(1, block, nodes_per_thread=npt, stages=stages, min_blocks=minb)
+            g.set_launch(1, block, min_blocks=minb)
         except lbm.LbmError as e:      # the tiles of this shape do not fit in shared memory
             assert e.status == lbm.LBM_EINVAL and "shared memory" in str(e)
             continue
         g.set_graph(4)
         g.step(15)
-        assert np.array_equal(g.get_state(), want), (block, npt, stages, minb)
+        assert np.array_equal(g.get_state(), want), (block, minb)
         g.check()
         ran += 1
     assert ran >= 3
@@ -322,7 +321,7 @@ def test_bulk_copy_pipeline_batched_cases():
     a.set_launch(0, 256, 4)
     a.step(30)
     b = make()
-    b.set_launch(1, 256, nodes_per_thread=2, stages=2, min_blocks=3)
+    b.set_launch(1, 256, min_blocks=2)
     b.step(30)
     assert np.array_equal(a.get_state(), b.get_state())
 
