@@ -968,7 +968,7 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
                                          "(128, 2), (256, 2), (256, 4), (512, 1), (512, 2)");
         if (ctx->dbl) return fail(ctx, LBM_EINVAL, "the bulk-copy variant serves FP32 and 16-bit storage");
         tile = L.block;
-        const size_t smem = (size_t)bulk_layout_bytes(ctx->P, tile, (int)ctx->elem);
+        const size_t smem = (size_t)bulk_layout_bytes(ctx->P, tile, (int)ctx->elem, BULK_NS[idx]);
         int maxsm = 0;
         CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->cfg.device));
         if (smem > (size_t)maxsm) return fail(ctx, LBM_EINVAL, "tile of %d nodes needs %zu B of shared memory", tile, smem);

@@ -19,7 +19,7 @@ struct KernelSet {
     cudaError_t (*init_f)(const void *params, int grid, int block, cudaStream_t s);   // FP32 device fields
     cudaError_t (*moments)(const void *params, int grid, int block, cudaStream_t s);
     cudaError_t (*reduce)(const void *params, int grid, int block, cudaStream_t s);
-    // bulk-copy variants, one per (tile nodes, register budget) of BULK_TT / BULK_MB (null for FP64)
+    // bulk-copy variants, one per configuration of BULK_TT / BULK_MB / BULK_NS (null for FP64)
     cudaError_t (*step_bulk[BULK_NCFG])(const void *params, const BulkParams &bp, int grid, size_t smem,
                                         cudaStream_t s);
     const void *step_fn[3];       // kernel symbols (occupancy queries, attributes)
@@ -56,7 +56,7 @@ struct Launch {
     }
     template <int I>
     static cudaError_t step_bulk(const void *p, const BulkParams &bp, int g, size_t smem, cudaStream_t s) {
-        k_step_bulk<DIM, HH, HG, S, BULK_MB[I], BULK_TT[I]><<<g, BULK_THREADS, smem, s>>>(
+        k_step_bulk<DIM, HH, HG, S, BULK_MB[I], BULK_TT[I], BULK_NS[I]><<<g, BULK_THREADS, smem, s>>>(
             *static_cast<const StepParams<T> *>(p), bp);
         return cudaGetLastError();
     }
@@ -67,7 +67,8 @@ struct Launch {
             k.step_bulk_fn[I] = nullptr;
         } else {
             k.step_bulk[I] = &step_bulk<I>;
-            k.step_bulk_fn[I] = reinterpret_cast<const void *>(&k_step_bulk<DIM, HH, HG, S, BULK_MB[I], BULK_TT[I]>);
+            k.step_bulk_fn[I] = reinterpret_cast<const void *>(
+                &k_step_bulk<DIM, HH, HG, S, BULK_MB[I], BULK_TT[I], BULK_NS[I]>);
         }
     }
     static KernelSet make() {

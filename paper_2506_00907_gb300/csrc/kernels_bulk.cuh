@@ -3,13 +3,13 @@
 // Same arithmetic as k_step (kernels.cuh); only the way populations move
 // between HBM and the registers differs.  Persistent blocks of 256 threads
 // walk the tile list (tiles of TT nodes).  While a block computes tile k, the
-// lanes of warp 0 have one cp.async.bulk per population plane in flight that
-// copies the plane's source window of tile k + 1 ([start - s_q, start + len -
-// s_q), s_q the flat index offset of e_q, aligned outward to 16 bytes and
-// clamped to the plane) into the other of two shared-memory stages,
-// completing on that stage's mbarrier.  Results go to one of two output tiles
-// in shared memory, which the same lanes write back with one cp.async.bulk
-// store per plane.  HBM then sees kilobytes of contiguous traffic per plane
+// lanes of warp 0 keep one cp.async.bulk per population plane in flight for
+// each of the next NS - 1 tiles, copying the plane's source window
+// ([start - s_q, start + len - s_q), s_q the flat index offset of e_q,
+// aligned outward to 16 bytes and clamped to the plane) into a ring of NS
+// shared-memory stages, each completing on its own mbarrier.  Results go to
+// one of two output tiles in shared memory, which the same lanes write back
+// with one cp.async.bulk store per plane.  HBM then sees kilobytes of contiguous traffic per plane
 // and tile instead of 2- or 4-byte accesses per thread.
 //
 // Interior nodes read their source at a fixed offset in the window; nodes on
@@ -32,27 +32,31 @@ struct BulkParams {
 constexpr uint32_t BULK_SPIN_LIMIT = 1u << 24;
 constexpr int BULK_THREADS = 256;
 
-// compiled (tile nodes, resident 256-thread blocks per SM of the register budget)
+// compiled (tile nodes, resident 256-thread blocks per SM of the register
+// budget, input stages = tiles in flight + 1)
 constexpr int BULK_NCFG = 5;
 constexpr int BULK_TT[BULK_NCFG] = {128, 256, 256, 512, 512};
 constexpr int BULK_MB[BULK_NCFG] = {2, 2, 4, 1, 2};
+constexpr int BULK_NS[BULK_NCFG] = {3, 3, 3, 2, 2};
+constexpr int BULK_MAX_NS = 4;
 
-template <int P, int TT, int ELEM>
+template <int P, int TT, int ELEM, int NS>
 struct BulkLayout {
     static constexpr int A = 16 / ELEM;             // elements per 16 bytes
     static constexpr int CAP = TT + A;              // window elements per plane and stage
-    static constexpr int BAR = 0;                   // 2 mbarriers
-    static constexpr int WLO = 16;                  // [2][P] window starts
-    static constexpr int WHI = WLO + 2 * P * 4;     // [2][P] window ends
-    static constexpr int HDR = ((WHI + 2 * P * 4 + 127) / 128) * 128;
-    static constexpr int IN = HDR;                  // [2][P][CAP] windows
-    static constexpr int OUT = IN + 2 * P * CAP * ELEM;   // [2][P][TT] output tiles
+    static constexpr int BAR = 0;                   // NS mbarriers
+    static constexpr int WLO = 8 * BULK_MAX_NS;     // [NS][P] window starts
+    static constexpr int WHI = WLO + NS * P * 4;    // [NS][P] window ends
+    static constexpr int HDR = ((WHI + NS * P * 4 + 127) / 128) * 128;
+    static constexpr int IN = HDR;                  // [NS][P][CAP] windows
+    static constexpr int OUT = IN + NS * P * CAP * ELEM;  // [2][P][TT] output tiles
     static constexpr int BYTES = OUT + 2 * P * TT * ELEM;
 };
 
 // the same total for run-time arguments (host side)
-__host__ __device__ constexpr int bulk_layout_bytes(int P, int TT, int ELEM) {
-    return ((16 + 4 * P * 4 + 127) / 128) * 128 + 2 * P * (TT + 16 / ELEM) * ELEM + 2 * P * TT * ELEM;
+__host__ __device__ constexpr int bulk_layout_bytes(int P, int TT, int ELEM, int NS) {
+    return ((8 * BULK_MAX_NS + 2 * NS * P * 4 + 127) / 128) * 128 + NS * P * (TT + 16 / ELEM) * ELEM +
+           2 * P * TT * ELEM;
 }
 
 LBM_DEV uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -90,11 +94,11 @@ LBM_DEV void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "m
 LBM_DEV void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Warp 0: the windows of tile t into stage st (lane q handles planes q, q + 32).
-template <class PL, class S, class T, int TT>
+template <class PL, class S, class T, int TT, int NS>
 LBM_DEV void bulk_issue(const StepParams<T> &prm, int t, int st, unsigned char *smem) {
     constexpr int P = PL::P;
     constexpr int NJ = (P + 31) / 32;
-    using L = BulkLayout<P, TT, (int)sizeof(S)>;
+    using L = BulkLayout<P, TT, (int)sizeof(S), NS>;
     constexpr int A = L::A;
     const int lane = threadIdx.x & 31;
     const int2 tile = prm.tiles[t];
@@ -138,45 +142,55 @@ LBM_DEV void bulk_issue(const StepParams<T> &prm, int t, int st, unsigned char *
     }
 }
 
-template <int DIM, bool HH, bool HG, class S, int MINB, int TT>
+template <int DIM, bool HH, bool HG, class S, int MINB, int TT, int NS>
 __global__ void __launch_bounds__(BULK_THREADS, MINB) k_step_bulk(const StepParams<typename Codec<S>::T> prm,
                                                                   const BulkParams bp) {
     using PL = Planes<DIM, HH, HG>;
     using T = typename Codec<S>::T;
     constexpr int P = PL::P;
-    using L = BulkLayout<P, TT, (int)sizeof(S)>;
-    static_assert(L::BYTES == bulk_layout_bytes(P, TT, (int)sizeof(S)), "layout");
+    using L = BulkLayout<P, TT, (int)sizeof(S), NS>;
+    static_assert(L::BYTES == bulk_layout_bytes(P, TT, (int)sizeof(S), NS), "layout");
+    static_assert(NS >= 2 && NS <= BULK_MAX_NS, "stages");
     constexpr int A = L::A;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L::BAR);
     const int tid = threadIdx.x;
     const bool w0 = tid < 32;
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int k = 0; k < NS; ++k) mbar_init(&bar[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (w0 && (int)blockIdx.x < prm.ntiles) bulk_issue<PL, S, T, TT>(prm, blockIdx.x, 0, smem);
+    // the first NS - 1 tiles of this block go into stages 0 .. NS - 2
+    if (w0)
+        for (int k = 0; k < NS - 1; ++k) {
+            const int t0 = blockIdx.x + k * gridDim.x;
+            if (t0 < prm.ntiles) bulk_issue<PL, S, T, TT, NS>(prm, t0, k, smem);
+        }
     int k_iter = 0;
     for (int t = blockIdx.x; t < prm.ntiles; t += gridDim.x, ++k_iter) {
-        const int st = k_iter & 1;
-        // stage st ^ 1 and output tile st were last used two iterations ago
-        const int tn = t + gridDim.x;
+        const int st = k_iter % NS;
+        const int ob = k_iter & 1;
+        // NS - 1 tiles ahead: tile k_iter + NS - 1 goes to the stage consumed in the previous iteration;
+        // output tile ob was last used two iterations ago
+        const int ta = t + (NS - 1) * gridDim.x;
         if (w0) {
-            if (tn < prm.ntiles) bulk_issue<PL, S, T, TT>(prm, tn, st ^ 1, smem);
-            bulk_wait_read_1();            // the stores of two tiles ago are done reading output tile st
+            if (ta < prm.ntiles) bulk_issue<PL, S, T, TT, NS>(prm, ta, (k_iter + NS - 1) % NS, smem);
+            bulk_wait_read_1();            // the stores of two tiles ago are done reading output tile ob
         }
         uint32_t spins = 0;
         bool ok = true;
-        while (!mbar_try_wait(&bar[st], (k_iter >> 1) & 1)) {
+        while (!mbar_try_wait(&bar[st], (k_iter / NS) & 1)) {
             if (++spins > BULK_SPIN_LIMIT) { ok = false; break; }
         }
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(bp.err, 1);
             if (w0) {
-                // let this block's copies land before the block exits (bounded)
-                for (uint32_t k = 0; k < BULK_SPIN_LIMIT && !mbar_try_wait(&bar[st ^ 1], ((k_iter + 1) >> 1) & 1); ++k) {
+                // let this block's copies in flight land before the block exits (bounded waits)
+                for (int d = 1; d < NS; ++d) {
+                    const int kk = k_iter + d;
+                    for (uint32_t k = 0; k < BULK_SPIN_LIMIT && !mbar_try_wait(&bar[kk % NS], (kk / NS) & 1); ++k) {
+                    }
                 }
                 bulk_wait_all();
             }
@@ -186,7 +200,7 @@ __global__ void __launch_bounds__(BULK_THREADS, MINB) k_step_bulk(const StepPara
         const CaseDev<T> c = prm.cases[tile.x];
         const S *src = static_cast<const S *>(prm.src) + c.pop_off;
         const S *in = reinterpret_cast<const S *>(smem + L::IN) + (size_t)st * P * L::CAP;
-        S *out = reinterpret_cast<S *>(smem + L::OUT) + (size_t)st * P * TT;
+        S *out = reinterpret_cast<S *>(smem + L::OUT) + (size_t)ob * P * TT;
         const int *wlo = reinterpret_cast<const int *>(smem + L::WLO) + st * P;
         const int *whi = reinterpret_cast<const int *>(smem + L::WHI) + st * P;
         const int nx = c.nx, ny = c.ny, nz = c.nz, nxy = nx * ny;
