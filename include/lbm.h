@@ -214,7 +214,13 @@ int64_t lbm_steps_done(const lbm_ctx *ctx);
  *              is the tile size in nodes and `min_blocks` the register budget,
  *              one of (128, 2), (256, 2), (256, 4), (512, 1), (512, 2);
  *              blocks_per_sm, nodes_per_thread and stages are ignored.
- * block (variant 0): 64..256, multiple of 32. */
+ *   variant 2: as variant 0 for 16-bit storage, each thread taking pairs of
+ *              x-adjacent nodes (nodes_per_thread 2, 4, 6 or 8): planes whose
+ *              pull offset is even are read as one 32-bit word for both
+ *              nodes and every result plane is written as one word; pairs on
+ *              a periodic edge or next to a solid or boundary node take the
+ *              one-node path.  min_blocks: 2D 2..4, 3D 1..3.
+ * block (variants 0 and 2): 64..256, multiple of 32. */
 typedef struct {
     int32_t variant;
     int32_t block;

@@ -429,8 +429,12 @@ cudaError_t launch_step_t(lbm_ctx *ctx) {
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
         if (e != cudaSuccess) return e;
     }
-    const cudaError_t e = ctx->ks.step[ctx->step_idx](&p, ctx->launch.nodes_per_thread, step_grid(ctx),
-                                                      ctx->launch.block, ctx->stream);
+    const cudaError_t e =
+        ctx->launch.variant == 2
+            ? ctx->ks.pair[ctx->step_idx](&p, ctx->launch.nodes_per_thread, step_grid(ctx), ctx->launch.block,
+                                          ctx->stream)
+            : ctx->ks.step[ctx->step_idx](&p, ctx->launch.nodes_per_thread, step_grid(ctx), ctx->launch.block,
+                                          ctx->stream);
     if (e != cudaSuccess) return e;
     if (ctx->nbrec > 0) return cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
     return cudaSuccess;
@@ -943,8 +947,8 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
     if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (!lp) return fail(ctx, LBM_EINVAL, "launch is NULL");
     const lbm_launch L = *lp;
-    if (L.variant < 0 || L.variant > 1) return fail(ctx, LBM_EINVAL, "variant must be 0 or 1");
-    if (L.variant == 0 && (L.block < 64 || L.block > 256 || L.block % 32))
+    if (L.variant < 0 || L.variant > 2) return fail(ctx, LBM_EINVAL, "variant must be 0, 1 or 2");
+    if (L.variant != 1 && (L.block < 64 || L.block > 256 || L.block % 32))
         return fail(ctx, LBM_EINVAL, "block must be 64..256 in steps of 32");
     int tile = L.block;
     int idx = 0;
@@ -958,6 +962,17 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
         if (L.min_blocks == 1) sidx = 0;
         if (sidx < 0)
             return fail(ctx, LBM_EINVAL, "min_blocks must be 1 or %d..%d", kstep_minb(ctx->dim, 0), kstep_minb(ctx->dim, 2));
+        tile = L.block * L.nodes_per_thread;
+    } else if (L.variant == 2) {
+        if (ctx->elem != 2) return fail(ctx, LBM_EINVAL, "the paired-node variant serves 16-bit storage");
+        if (L.blocks_per_sm < 0 || L.blocks_per_sm > 64) return fail(ctx, LBM_EINVAL, "blocks per SM must be 0..64");
+        if (L.nodes_per_thread < 2 || L.nodes_per_thread > 8 || L.nodes_per_thread % 2)
+            return fail(ctx, LBM_EINVAL, "nodes per thread must be 2, 4, 6 or 8");
+        sidx = -1;
+        for (int k = 0; k < 3; ++k)
+            if (kpair_minb(ctx->dim, k) == L.min_blocks) sidx = k;
+        if (sidx < 0)
+            return fail(ctx, LBM_EINVAL, "min_blocks must be %d..%d", kpair_minb(ctx->dim, 0), kpair_minb(ctx->dim, 2));
         tile = L.block * L.nodes_per_thread;
     } else {
         idx = -1;
@@ -1020,7 +1035,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
     cudaDeviceProp prop{};
     CK(cudaGetDeviceProperties(&prop, ctx->cfg.device));
     std::ostringstream key;
-    key << prop.name << "|v7|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
+    key << prop.name << "|v8|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
         << ctx->cases.size();
     int64_t tot = 0;
     for (auto &c : ctx->cases) tot += c.N;
@@ -1064,6 +1079,11 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
                 for (int npt : {1, 2, 4}) cands.push_back(lbm_launch{0, b, p, npt, 2, kstep_minb(ctx->dim, r)});
     if (!ctx->dbl)
         for (int k = 0; k < BULK_NCFG; ++k) cands.push_back(lbm_launch{1, BULK_TT[k], 0, 1, 2, BULK_MB[k]});
+    if (ctx->elem == 2)
+        for (int r = 0; r < 3; ++r)
+            for (int b : {128, 256})
+                for (int p : {0, 8})
+                    for (int npt : {2, 4}) cands.push_back(lbm_launch{2, b, p, npt, 2, kpair_minb(ctx->dim, r)});
     lbm_launch best = ctx->launch;
     double best_t = INFINITY;
     lbm_status st = LBM_OK;

@@ -11,10 +11,15 @@ namespace lbm {
 
 // register budgets of k_step (resident 256-thread blocks per SM)
 constexpr int kstep_minb(int dim, int i) { return dim == 2 ? 4 + i : 2 + i; }
+// register budgets of k_step_pair (two nodes per thread need more registers)
+constexpr int kpair_minb(int dim, int i) { return dim == 2 ? 2 + i : 1 + i; }
 
 struct KernelSet {
     cudaError_t (*step[3])(const void *params, int npt, int grid, int block, cudaStream_t s);
     cudaError_t (*boundary)(const void *params, int grid, int block, cudaStream_t s);
+    // paired-node variants (16-bit storage only; null otherwise), budgets kpair_minb(dim, 0..2)
+    cudaError_t (*pair[3])(const void *params, int npt, int grid, int block, cudaStream_t s);
+    const void *pair_fn[3];
     cudaError_t (*init_d)(const void *params, int grid, int block, cudaStream_t s);   // FP64 host-side fields
     cudaError_t (*init_f)(const void *params, int grid, int block, cudaStream_t s);   // FP32 device fields
     cudaError_t (*moments)(const void *params, int grid, int block, cudaStream_t s);
@@ -33,6 +38,25 @@ struct Launch {
     static cudaError_t step(const void *p, int npt, int g, int b, cudaStream_t s) {
         k_step<DIM, HH, HG, S, MINB><<<g, b, 0, s>>>(*static_cast<const StepParams<T> *>(p), npt);
         return cudaGetLastError();
+    }
+    template <int I>
+    static cudaError_t pair_launch(const void *p, int npt, int g, int b, cudaStream_t s) {
+        if constexpr (sizeof(S) == 2) {
+            k_step_pair<DIM, HH, HG, S, kpair_minb(DIM, I)><<<g, b, 0, s>>>(*static_cast<const StepParams<T> *>(p), npt);
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
+    template <int I>
+    static void set_pair(KernelSet &k) {
+        if constexpr (sizeof(S) == 2) {
+            k.pair[I] = &pair_launch<I>;
+            k.pair_fn[I] = reinterpret_cast<const void *>(&k_step_pair<DIM, HH, HG, S, kpair_minb(DIM, I)>);
+        } else {
+            k.pair[I] = nullptr;
+            k.pair_fn[I] = nullptr;
+        }
     }
     static cudaError_t boundary(const void *p, int g, int b, cudaStream_t s) {
         k_boundary<DIM, HH, HG, S><<<g, b, 0, s>>>(*static_cast<const StepParams<T> *>(p));
@@ -77,6 +101,9 @@ struct Launch {
         k.step[1] = &step<kstep_minb(DIM, 1)>;
         k.step[2] = &step<kstep_minb(DIM, 2)>;
         k.boundary = &boundary;
+        set_pair<0>(k);
+        set_pair<1>(k);
+        set_pair<2>(k);
         k.init_d = &init_d;
         k.init_f = &init_f;
         k.moments = &moments;

@@ -426,6 +426,99 @@ __global__ void __launch_bounds__(256, MINB) k_step(const StepParams<typename Co
     }
 }
 
+// ------------------------------------------------------------------ paired nodes (16-bit storage)
+// Two 16-bit populations of x-adjacent nodes n0 (even) and n0 + 1 share a
+// 32-bit word: planes whose pull offset is even are read as one word, the
+// others as two 16-bit loads, and every result plane is written as one word.
+template <class S> struct Pair16;
+template <> struct Pair16<__half> {
+    LBM_DEV static uint32_t ld(const __half *p) { return __ldg(reinterpret_cast<const unsigned int *>(p)); }
+    LBM_DEV static float lo(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
+    LBM_DEV static float hi(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+    LBM_DEV static void st(__half *p, float a, float b) { *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b); }
+};
+template <> struct Pair16<__nv_bfloat16> {
+    LBM_DEV static uint32_t ld(const __nv_bfloat16 *p) { return __ldg(reinterpret_cast<const unsigned int *>(p)); }
+    LBM_DEV static float lo(uint32_t w) {
+        return __bfloat162float(__ushort_as_bfloat16((unsigned short)(w & 0xffffu)));
+    }
+    LBM_DEV static float hi(uint32_t w) { return __bfloat162float(__ushort_as_bfloat16((unsigned short)(w >> 16))); }
+    LBM_DEV static void st(__nv_bfloat16 *p, float a, float b) {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+    }
+};
+
+// Nodes n0, n0 + 1 of one row, neither on a periodic edge (no wrap), both
+// bulk fluid.  PX = nx mod 2, PXY = nx ny mod 2 make the parity of each
+// plane's pull offset a compile-time fact.
+template <int DIM, bool HH, bool HG, class S, int PX, int PXY>
+LBM_DEV void pair_node(const CaseDev<float> &c, const S *src, S *dst, int n0) {
+    using PL = Planes<DIM, HH, HG>;
+    constexpr int P = PL::P;
+    const int nx = c.nx, nxy = c.nx * c.ny;
+    const int st32 = (int)c.stride;
+    const S *__restrict__ sp = src + n0;
+    S *__restrict__ dp = dst + n0;
+    float a[P], b[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        const int off = q * st32 - (PL::ex(q) + PL::ey(q) * nx + PL::ez(q) * nxy);
+        const int par = (PL::ex(q) + PL::ey(q) * PX + PL::ez(q) * PXY) & 1;
+        if (par == 0) {
+            const uint32_t w = Pair16<S>::ld(sp + off);
+            a[q] = Pair16<S>::lo(w);
+            b[q] = Pair16<S>::hi(w);
+        } else {
+            a[q] = Codec<S>::ld(sp + off);
+            b[q] = Codec<S>::ld(sp + off + 1);
+        }
+    }
+    collide<PL, HH, HG, float>(a, c);
+    collide<PL, HH, HG, float>(b, c);
+#pragma unroll
+    for (int q = 0; q < P; ++q) Pair16<S>::st(dp + q * st32, a[q], b[q]);
+}
+
+// Bulk nodes in pairs (16-bit storage).  Tiles of blockDim.x * npt nodes (npt
+// even); each thread takes the pairs tid, tid + blockDim.x, ...  Pairs that
+// touch a periodic edge, a solid or a boundary node take the one-node path.
+template <int DIM, bool HH, bool HG, class S, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_step_pair(const StepParams<float> prm, const int npt) {
+    int t = blockIdx.x;
+    if (t >= prm.ntiles) return;
+    int2 tile = prm.tiles[t];
+    for (; t < prm.ntiles; t += gridDim.x) {
+        const int tn = t + gridDim.x;
+        const int2 next = tn < prm.ntiles ? prm.tiles[tn] : tile;
+        const CaseDev<float> c = prm.cases[tile.x];
+        const S *src = static_cast<const S *>(prm.src) + c.pop_off;
+        S *dst = static_cast<S *>(prm.dst) + c.pop_off;
+        const int px = c.nx & 1, pxy = (c.nx * c.ny) & 1;
+        for (int k = 0; k < npt / 2; ++k) {
+            const int n0 = tile.y + 2 * ((int)threadIdx.x + k * (int)blockDim.x);
+            if (n0 >= c.N) break;
+            const uint8_t f0 = prm.flags[c.node_off + n0];
+            const uint8_t f1 = n0 + 1 < c.N ? prm.flags[c.node_off + n0 + 1] : uint8_t(0);
+            int x, y, z, r;
+            coords<DIM, float>(c, n0, x, y, z, r);
+            const bool interior = x >= 1 && x + 2 <= c.nx - 1 && y >= 1 && y + 1 <= c.ny - 1 &&
+                                  (DIM == 2 || (z >= 1 && z + 1 <= c.nz - 1));
+            if (f0 == NODE_FLUID && f1 == NODE_FLUID && interior) {
+                if (!px)
+                    pair_node<DIM, HH, HG, S, 0, 0>(c, src, dst, n0);
+                else if (DIM == 2 || !pxy)
+                    pair_node<DIM, HH, HG, S, 1, 0>(c, src, dst, n0);
+                else
+                    pair_node<DIM, HH, HG, S, 1, 1>(c, src, dst, n0);
+            } else {
+                if (f0 == NODE_FLUID) step_node<DIM, HH, HG, S, false>(prm, c, n0, 0, 0);
+                if (f1 == NODE_FLUID) step_node<DIM, HH, HG, S, false>(prm, c, n0 + 1, 0, 0);
+            }
+        }
+        tile = next;
+    }
+}
+
 // Boundary nodes: one thread per record of the compact boundary list (the
 // nodes of a wall row are consecutive records, so a warp works along a wall).
 template <int DIM, bool HH, bool HG, class S>

@@ -370,3 +370,60 @@ def test_register_budgets_are_bitwise_identical(dim):
         p.gpu.step(12)
         states.append(p.gpu.get_state()[16:])
     assert np.array_equal(states[0], states[1]) and np.array_equal(states[0], states[2])
+
+
+@pytest.mark.parametrize("dim,prec,shape", [
+    (2, lbm.LBM_FP16S, (53, 41, 1)), (2, lbm.LBM_BF16S, (52, 41, 1)), (2, lbm.LBM_FP16S, (36, 30, 1)),
+    (3, lbm.LBM_FP16S, (21, 13, 11)), (3, lbm.LBM_BF16S, (20, 13, 11)), (3, lbm.LBM_FP16S, (22, 14, 9))])
+def test_paired_nodes_are_bitwise_identical(dim, prec, shape):
+    """Variant 2 (two x-adjacent nodes per thread, paired 32-bit loads and
+    stores of 16-bit populations) computes exactly what one thread per node
+    computes: odd and even nx and nx*ny (which decide the word alignment of
+    each pull plane), ragged tails, periodic edges and every link kind."""
+    ref = _random_pair(dim, True, True, seed=91, prec=prec, shape=shape).gpu
+    ref.set_launch(0, 128, 0)
+    ref.step(15)
+    want = ref.get_state()
+    lo = 2 if dim == 2 else 1
+    for block, npt, mb in ((128, 2, lo), (256, 4, lo + 1), (128, 8, lo + 2)):
+        g = _random_pair(dim, True, True, seed=91, prec=prec, shape=shape).gpu
+        g.set_launch(2, block, 0, npt, 2, mb)
+        g.set_graph(4)
+        g.step(15)
+        assert np.array_equal(g.get_state(), want), (block, npt, mb)
+        g.check()
+
+
+def test_paired_nodes_batched_cases_and_flow_only():
+    """Variant 2 over uneven batched cases (odd widths, empty-link cases) and
+    for a flow-only D2Q9 lattice equals variant 0 bit for bit."""
+    def make(phys):
+        cases, geo = [], []
+        for W, q in ((20, 0.3), (33, 0.0), (9, 0.75), (64, 0.5), (131, 0.9)):
+            shape, solid, links, B0 = _hartmann_links(W, q, 0.3, 5.0)
+            if not phys & lbm.LBM_MHD:
+                links = links[links["field"] == O.F]
+            cases.append(lbm.make_case(shape, 0.8, 1.0, 0.9, (2e-5, 0, 0), 1.0, 0.0, (0, B0, 0)))
+            geo.append((solid, links))
+        g = lbm.Solver(lbm.LBM_D2Q9, lbm.LBM_BF16S, phys, cases)
+        for i, (solid, links) in enumerate(geo):
+            g.set_walls(i, solid, to_abi_links(links))
+        return g
+    for phys in (lbm.LBM_FLOW | lbm.LBM_MHD, lbm.LBM_FLOW):
+        a = make(phys)
+        a.set_launch(0, 256, 4)
+        a.step(30)
+        b = make(phys)
+        b.set_launch(2, 128, 0, 2, 2, 4)
+        b.step(30)
+        assert np.array_equal(a.get_state(), b.get_state()), phys
+
+
+def test_paired_nodes_reject_bad_shapes():
+    p = _random_pair(2, False, False, seed=5, prec=lbm.LBM_FP32)
+    with pytest.raises(lbm.LbmError):
+        p.gpu.set_launch(2, 128, 0, 2, 2, 3)       # 32-bit storage has no paired form
+    q = _random_pair(2, False, False, seed=5, prec=lbm.LBM_FP16S)
+    for bad in ((2, 128, 0, 3, 2, 3), (2, 128, 0, 2, 2, 9)):
+        with pytest.raises(lbm.LbmError):
+            q.gpu.set_launch(*bad)
