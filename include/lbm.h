@@ -220,6 +220,18 @@ int64_t lbm_steps_done(const lbm_ctx *ctx);
  *              nodes and every result plane is written as one word; pairs on
  *              a periodic edge or next to a solid or boundary node take the
  *              one-node path.  min_blocks: 2D 2..4, 3D 1..3.
+ *   variant 3: shared-memory ring (FP32 and 16-bit storage): persistent
+ *              blocks of one producer warp and 8 consumer warps.  The
+ *              producer copies each plane's source window of the block's
+ *              next tiles into a ring of `stages` (2..8) shared-memory stages
+ *              with cp.async.bulk on mbarriers; consumers relax their nodes
+ *              from the ring (2D: two x-adjacent nodes per lane with packed
+ *              FP32 arithmetic, 3D: one node per lane) and store them to
+ *              global memory.  Tiles of 512 (2D) or 256 (3D) nodes;
+ *              blocks_per_sm caps the resident blocks per SM (0 = as many as
+ *              fit); block, nodes_per_thread and min_blocks are ignored.
+ *              Boundary nodes as in variant 0.  Fails with LBM_EINVAL when
+ *              the stages do not fit in shared memory.
  * block (variants 0 and 2): 64..256, multiple of 32. */
 typedef struct {
     int32_t variant;

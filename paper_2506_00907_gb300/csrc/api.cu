@@ -406,7 +406,7 @@ StepParams<T> step_params(const lbm_ctx *c) {
 }
 
 int step_grid(const lbm_ctx *c) {
-    if (c->launch.variant == 1) return std::max(1, std::min(c->ntiles, c->bulk_grid));
+    if (c->launch.variant == 1 || c->launch.variant == 3) return std::max(1, std::min(c->ntiles, c->bulk_grid));
     if (c->launch.blocks_per_sm <= 0) return c->ntiles;
     return std::max(1, std::min(c->ntiles, c->launch.blocks_per_sm * c->sm_count));
 }
@@ -429,12 +429,18 @@ cudaError_t launch_step_t(lbm_ctx *ctx) {
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
         if (e != cudaSuccess) return e;
     }
-    const cudaError_t e =
-        ctx->launch.variant == 2
-            ? ctx->ks.pair[ctx->step_idx](&p, ctx->launch.nodes_per_thread, step_grid(ctx), ctx->launch.block,
-                                          ctx->stream)
-            : ctx->ks.step[ctx->step_idx](&p, ctx->launch.nodes_per_thread, step_grid(ctx), ctx->launch.block,
-                                          ctx->stream);
+    cudaError_t e;
+    if (ctx->launch.variant == 3) {
+        BulkParams bp;
+        bp.err = ctx->d_err;
+        e = ctx->ks.ring(&p, bp, ctx->launch.stages, step_grid(ctx), ctx->bulk_smem, ctx->stream);
+    } else if (ctx->launch.variant == 2) {
+        e = ctx->ks.pair[ctx->step_idx](&p, ctx->launch.nodes_per_thread, step_grid(ctx), ctx->launch.block,
+                                        ctx->stream);
+    } else {
+        e = ctx->ks.step[ctx->step_idx](&p, ctx->launch.nodes_per_thread, step_grid(ctx), ctx->launch.block,
+                                        ctx->stream);
+    }
     if (e != cudaSuccess) return e;
     if (ctx->nbrec > 0) return cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
     return cudaSuccess;
@@ -947,8 +953,8 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
     if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (!lp) return fail(ctx, LBM_EINVAL, "launch is NULL");
     const lbm_launch L = *lp;
-    if (L.variant < 0 || L.variant > 2) return fail(ctx, LBM_EINVAL, "variant must be 0, 1 or 2");
-    if (L.variant != 1 && (L.block < 64 || L.block > 256 || L.block % 32))
+    if (L.variant < 0 || L.variant > 3) return fail(ctx, LBM_EINVAL, "variant must be 0, 1, 2 or 3");
+    if ((L.variant == 0 || L.variant == 2) && (L.block < 64 || L.block > 256 || L.block % 32))
         return fail(ctx, LBM_EINVAL, "block must be 64..256 in steps of 32");
     int tile = L.block;
     int idx = 0;
@@ -974,6 +980,25 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
         if (sidx < 0)
             return fail(ctx, LBM_EINVAL, "min_blocks must be %d..%d", kpair_minb(ctx->dim, 0), kpair_minb(ctx->dim, 2));
         tile = L.block * L.nodes_per_thread;
+    } else if (L.variant == 3) {
+        if (ctx->dbl) return fail(ctx, LBM_EINVAL, "the ring variant serves FP32 and 16-bit storage");
+        if (L.stages < 2 || L.stages > RING_MAX_NS)
+            return fail(ctx, LBM_EINVAL, "ring variant: stages must be 2..%d", RING_MAX_NS);
+        if (L.blocks_per_sm < 0 || L.blocks_per_sm > 64) return fail(ctx, LBM_EINVAL, "blocks per SM must be 0..64");
+        const int npl = kring_npl(ctx->dim);
+        tile = ring_tile(npl);
+        const size_t smem = (size_t)ring_smem_bytes(ctx->P, npl, (int)ctx->elem, L.stages);
+        int maxsm = 0;
+        CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->cfg.device));
+        if (smem > (size_t)maxsm)
+            return fail(ctx, LBM_EINVAL, "%d ring stages need %zu B of shared memory", L.stages, smem);
+        CK(cudaFuncSetAttribute(ctx->ks.ring_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ctx->ks.ring_fn, RING_THREADS, smem));
+        if (per_sm < 1) return fail(ctx, LBM_EINVAL, "the ring variant does not fit on an SM");
+        if (L.blocks_per_sm > 0) per_sm = std::min(per_sm, L.blocks_per_sm);
+        ctx->bulk_smem = smem;
+        ctx->bulk_grid = per_sm * ctx->sm_count;
     } else {
         idx = -1;
         for (int k = 0; k < BULK_NCFG; ++k)
@@ -1035,7 +1060,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
     cudaDeviceProp prop{};
     CK(cudaGetDeviceProperties(&prop, ctx->cfg.device));
     std::ostringstream key;
-    key << prop.name << "|v8|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
+    key << prop.name << "|v9|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
         << ctx->cases.size();
     int64_t tot = 0;
     for (auto &c : ctx->cases) tot += c.N;
@@ -1084,6 +1109,8 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
             for (int b : {128, 256})
                 for (int p : {0, 8})
                     for (int npt : {2, 4}) cands.push_back(lbm_launch{2, b, p, npt, 2, kpair_minb(ctx->dim, r)});
+    if (!ctx->dbl)
+        for (int ns : {2, 3, 4, 6}) cands.push_back(lbm_launch{3, RING_CW * 32, 0, kring_npl(ctx->dim), ns, KRING_MINB});
     lbm_launch best = ctx->launch;
     double best_t = INFINITY;
     lbm_status st = LBM_OK;

@@ -5,6 +5,7 @@
 
 #include "kernels.cuh"
 #include "kernels_bulk.cuh"
+#include "kernels_ring.cuh"
 #include "reduce.cuh"
 
 namespace lbm {
@@ -13,6 +14,9 @@ namespace lbm {
 constexpr int kstep_minb(int dim, int i) { return dim == 2 ? 4 + i : 2 + i; }
 // register budgets of k_step_pair (two nodes per thread need more registers)
 constexpr int kpair_minb(int dim, int i) { return dim == 2 ? 2 + i : 1 + i; }
+// nodes per consumer lane of k_step_ring: packed pairs in 2D, one node in 3D
+constexpr int kring_npl(int dim) { return dim == 2 ? 2 : 1; }
+constexpr int KRING_MINB = 2;
 
 struct KernelSet {
     cudaError_t (*step[3])(const void *params, int npt, int grid, int block, cudaStream_t s);
@@ -29,6 +33,9 @@ struct KernelSet {
                                         cudaStream_t s);
     const void *step_fn[3];       // kernel symbols (occupancy queries, attributes)
     const void *step_bulk_fn[BULK_NCFG];
+    // shared-memory ring variant (null for FP64), ns stages
+    cudaError_t (*ring)(const void *params, const BulkParams &bp, int ns, int grid, size_t smem, cudaStream_t s);
+    const void *ring_fn;
 };
 
 template <int DIM, bool HH, bool HG, class S>
@@ -95,8 +102,27 @@ struct Launch {
                 &k_step_bulk<DIM, HH, HG, S, BULK_MB[I], BULK_TT[I], BULK_NS[I]>);
         }
     }
+    static cudaError_t ring(const void *p, const BulkParams &bp, int ns, int g, size_t smem, cudaStream_t s) {
+        if constexpr (std::is_same<S, double>::value) {
+            return cudaErrorInvalidValue;
+        } else {
+            k_step_ring<DIM, HH, HG, S, kring_npl(DIM), KRING_MINB><<<g, RING_THREADS, smem, s>>>(
+                *static_cast<const StepParams<T> *>(p), bp, ns);
+            return cudaGetLastError();
+        }
+    }
+    static void set_ring(KernelSet &k) {
+        if constexpr (std::is_same<S, double>::value) {
+            k.ring = nullptr;
+            k.ring_fn = nullptr;
+        } else {
+            k.ring = &ring;
+            k.ring_fn = reinterpret_cast<const void *>(&k_step_ring<DIM, HH, HG, S, kring_npl(DIM), KRING_MINB>);
+        }
+    }
     static KernelSet make() {
         KernelSet k{};
+        set_ring(k);
         k.step[0] = &step<kstep_minb(DIM, 0)>;
         k.step[1] = &step<kstep_minb(DIM, 1)>;
         k.step[2] = &step<kstep_minb(DIM, 2)>;

@@ -132,85 +132,154 @@ LBM_DEV T geq_dir(int a, int k, T dBk, const T (&B)[3], const T (&u)[3]) {
 // part A + e.Tm.e and differ in the sign of V.e.  Eq. 4 and 6 are linear in
 // e_a: h_rel = (1 - om_h) h + om_h w (dC + 4 C e.u) and, per component k,
 // g_rel = (1 - om_g) g + om_g w (dB_k + 4 e.(u B_k - B u_k)).
-template <class T>
-LBM_DEV T recip(T x) { return T(1) / x; }
-template <>
-LBM_DEV float recip<float>(float x) { return __frcp_rn(x); }
+// The collision is written once over an arithmetic type V:
+//   double  FP64 storage: plain operators (the FP64 translation units are
+//           compiled without multiply-add contraction, so every product rounds)
+//   F1      one node in FP32: every operation is an explicit round-to-nearest
+//           intrinsic, so a product is fused into a sum only where fma_v says so
+//   F2      two nodes in FP32 with the packed f32x2 instructions of sm_100 and
+//           later; each lane rounds exactly as F1 does, so the result of a node
+//           does not depend on which of the two forms computed it.
+// Constants of the case are scalars T; products of scalars are formed in T
+// before they meet a V.
+struct F1 {
+    float v;
+    F1() = default;
+    LBM_DEV F1(float x) : v(x) {}
+};
+LBM_DEV F1 operator+(F1 a, F1 b) { return F1(__fadd_rn(a.v, b.v)); }
+LBM_DEV F1 operator-(F1 a, F1 b) { return F1(__fsub_rn(a.v, b.v)); }
+LBM_DEV F1 operator*(F1 a, F1 b) { return F1(__fmul_rn(a.v, b.v)); }
+LBM_DEV F1 fma_v(F1 a, F1 b, F1 c) { return F1(__fmaf_rn(a.v, b.v, c.v)); }
+LBM_DEV F1 neg_v(F1 a) { return F1(-a.v); }
+LBM_DEV F1 recip_v(F1 a) { return F1(__frcp_rn(a.v)); }
 
-template <class PL, bool HH, bool HG, class T>
-LBM_DEV void collide(T (&p)[PL::P], const CaseDev<T> &c) {
+struct F2 {
+    float2 v;
+    F2() = default;
+    LBM_DEV F2(float x) : v(make_float2(x, x)) {}
+    LBM_DEV F2(float x, float y) : v(make_float2(x, y)) {}
+};
+LBM_DEV F2 operator+(F2 a, F2 b) { F2 r; r.v = __fadd2_rn(a.v, b.v); return r; }
+// a - b = fma(b, -1, a): one rounding of the exact difference, as in the scalar subtraction
+LBM_DEV F2 operator-(F2 a, F2 b) { F2 r; r.v = __ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v); return r; }
+LBM_DEV F2 operator*(F2 a, F2 b) { F2 r; r.v = __fmul2_rn(a.v, b.v); return r; }
+LBM_DEV F2 fma_v(F2 a, F2 b, F2 c) { F2 r; r.v = __ffma2_rn(a.v, b.v, c.v); return r; }
+LBM_DEV F2 neg_v(F2 a) { return F2(-a.v.x, -a.v.y); }
+LBM_DEV F2 recip_v(F2 a) { return F2(__frcp_rn(a.v.x), __frcp_rn(a.v.y)); }
+
+LBM_DEV double fma_v(double a, double b, double c) { return a * b + c; }
+LBM_DEV double neg_v(double a) { return -a; }
+LBM_DEV double recip_v(double a) { return 1.0 / a; }
+
+// sum_a e_ai s_a over a lattice with e_ai in {-1, 0, 1}: (sum over +1) - (sum over -1)
+template <class L, int Q, class V, int P>
+LBM_DEV V axis_sum(const V (&p)[P], int q0, int i) {
+    V pos, neg;
+    bool hp = false, hn = false;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int e = i == 0 ? L::ex(a) : (i == 1 ? L::ey(a) : L::ez(a));
+        if (e > 0) {
+            pos = hp ? pos + p[q0 + a] : p[q0 + a];
+            hp = true;
+        } else if (e < 0) {
+            neg = hn ? neg + p[q0 + a] : p[q0 + a];
+            hn = true;
+        }
+    }
+    return pos - neg;
+}
+
+template <class V, int P>
+LBM_DEV V plane_sum(const V (&p)[P], int q0, int n) {
+    V s = p[q0];
+#pragma unroll
+    for (int a = 1; a < n; ++a) s = s + p[q0 + a];
+    return s;
+}
+
+// first nonzero component of e_a
+template <class L>
+LBM_HD constexpr int lead_sign(int a) { return L::ex(a) ? L::ex(a) : (L::ey(a) ? L::ey(a) : L::ez(a)); }
+
+template <class PL, bool HH, bool HG, class V, class T>
+LBM_DEV void collide_v(V (&p)[PL::P], const CaseDev<T> &c) {
     using F = typename PL::F;
     using M = typename PL::M;
     constexpr int QF = PL::QF, QM = PL::QM, NB = PL::NB, DIM = F::DIM;
-    T drho = 0, j[3] = {T(0), T(0), T(0)};
+    const V drho = plane_sum(p, 0, QF);
+    V j[3];
 #pragma unroll
-    for (int a = 0; a < QF; ++a) {
-        drho += p[a];
-        if (F::ex(a)) j[0] += T(F::ex(a)) * p[a];
-        if (F::ey(a)) j[1] += T(F::ey(a)) * p[a];
-        if (F::ez(a)) j[2] += T(F::ez(a)) * p[a];
-    }
-    const T rho = drho + c.ref_rho;
-    const T inv = recip(rho);
+    for (int i = 0; i < DIM; ++i) j[i] = axis_sum<F, QF>(p, 0, i);
+    const V rho = drho + V(c.ref_rho);
+    const V inv = recip_v(rho);
     const T acc[3] = {c.ax, c.ay, c.az};
-    T Fo[3], m[3], u[3];
+    V Fo[3], m[3], u[3];
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
-        Fo[i] = rho * acc[i];
-        m[i] = fmaf_t(T(0.5), Fo[i], j[i]);
+        Fo[i] = rho * V(acc[i]);
+        m[i] = fma_v(Fo[i], V(T(0.5)), j[i]);
         u[i] = m[i] * inv;
     }
-    if constexpr (DIM == 2) { Fo[2] = T(0); m[2] = T(0); u[2] = T(0); }
-    T B[3] = {T(0), T(0), T(0)}, dB[3] = {T(0), T(0), T(0)};
+    V B[3], nB[3], dB[3];
     if constexpr (HG) {
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
-            T sum = 0;
-#pragma unroll
-            for (int a = 0; a < QM; ++a) sum += p[PL::G0 + k * QM + a];
-            dB[k] = sum;
-            B[k] = sum + c.ref_B[k];
+            dB[k] = plane_sum(p, PL::G0 + k * QM, QM);
+            B[k] = dB[k] + V(c.ref_B[k]);
+            nB[k] = neg_v(B[k]);
         }
     }
     const T om = c.om_f, g = c.guo;
-    T mu = 0, uF = 0, Bsq = 0;
+    V mu = m[0] * u[0], uF = u[0] * Fo[0], Bsq;
+    if constexpr (HG) Bsq = B[0] * B[0];
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) {
-        mu = fmaf_t(m[i], u[i], mu);
-        uF = fmaf_t(u[i], Fo[i], uF);
-        if constexpr (HG) Bsq = fmaf_t(B[i], B[i], Bsq);
+    for (int i = 1; i < DIM; ++i) {
+        mu = fma_v(m[i], u[i], mu);
+        uF = fma_v(u[i], Fo[i], uF);
+        if constexpr (HG) Bsq = fma_v(B[i], B[i], Bsq);
     }
-    T A = fmaf_t(T(-1.5), mu, drho);
-    if constexpr (HG && DIM == 2) {}                       // 0.75 (2 - D) |B|^2 vanishes in 2D
-    if constexpr (HG && DIM == 3) A = fmaf_t(T(-0.75), Bsq, A);
-    A = fmaf_t(om, A, T(-3) * g * uF);
-    T V[3], Td[3], Tc[3];                                   // Tc: 2 Tm_xy, 2 Tm_xz, 2 Tm_yz
+    V A = fma_v(mu, V(T(-1.5)), drho);
+    if constexpr (HG && DIM == 3) A = fma_v(Bsq, V(T(-0.75)), A);   // 0.75 (2 - D) |B|^2 vanishes in 2D
+    A = fma_v(A, V(om), V(T(-3) * g) * uF);
+    V Vv[3], Td[3], Tc[3];                                           // Tc: 2 Tm_xy, 2 Tm_xz, 2 Tm_yz
+    V mag;
+    if constexpr (HG) mag = V(T(2.25) * om) * Bsq;
+    const T g2 = T(2) * g;
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
-        V[i] = T(3) * fmaf_t(om, m[i], g * Fo[i]);
-        T t = m[i] * u[i];
-        if constexpr (HG) t = fmaf_t(-B[i], B[i], t);
-        Td[i] = fmaf_t(T(4.5), fmaf_t(om, t, T(2) * g * u[i] * Fo[i]), HG ? T(2.25) * om * Bsq : T(0));
+        Vv[i] = fma_v(m[i], V(om), V(g) * Fo[i]) * V(T(3));
+        V t = m[i] * u[i];
+        if constexpr (HG) t = fma_v(B[i], nB[i], t);
+        const V s = fma_v(t, V(om), (V(g2) * u[i]) * Fo[i]);
+        if constexpr (HG) Td[i] = fma_v(s, V(T(4.5)), mag);
+        else Td[i] = s * V(T(4.5));
     }
 #pragma unroll
     for (int pr = 0; pr < (DIM == 3 ? 3 : 1); ++pr) {
         const int i = pr == 2 ? 1 : 0, k = pr == 0 ? 1 : 2;
-        T t = m[i] * u[k];
-        if constexpr (HG) t = fmaf_t(-B[i], B[k], t);
-        Tc[pr] = T(9) * fmaf_t(om, t, g * fmaf_t(u[i], Fo[k], Fo[i] * u[k]));
+        V t = m[i] * u[k];
+        if constexpr (HG) t = fma_v(nB[i], B[k], t);
+        Tc[pr] = fma_v(t, V(om), V(g) * fma_v(u[i], Fo[k], Fo[i] * u[k])) * V(T(9));
     }
-    const T omc = c.omc_f;
+    const V omc = V(c.omc_f);
+    p[0] = fma_v(p[0], omc, A * V(T(F::w(0))));                      // rest: even part A only
 #pragma unroll
-    for (int a = 0; a < QF; ++a) {
+    for (int a = 1; a < QF; ++a) {
         const int b = F::opp(a);
-        if (b < a) continue;                                 // done with its pair
-        const int e[3] = {F::ex(a), F::ey(a), F::ez(a)};
-        T even = A, odd = T(0);
+        if (b < a) continue;                                         // done with its pair
+        // the member of the pair whose leading component is +1 gets even + odd
+        const int ap = lead_sign<F>(a) > 0 ? a : b, am = lead_sign<F>(a) > 0 ? b : a;
+        const int e[3] = {F::ex(ap), F::ey(ap), F::ez(ap)};
+        V even = A, odd;
+        bool first = true;
 #pragma unroll
         for (int i = 0; i < DIM; ++i) {
             if (e[i]) {
-                even += Td[i];
-                odd = e[i] > 0 ? odd + V[i] : odd - V[i];
+                even = even + Td[i];
+                odd = first ? Vv[i] : (e[i] > 0 ? odd + Vv[i] : odd - Vv[i]);
+                first = false;
             }
         }
 #pragma unroll
@@ -219,58 +288,70 @@ LBM_DEV void collide(T (&p)[PL::P], const CaseDev<T> &c) {
             const int s2 = e[i] * e[k];
             if (s2) even = s2 > 0 ? even + Tc[pr] : even - Tc[pr];
         }
-        const T w = T(F::w(a));
-        if (a == b) {
-            p[a] = fmaf_t(omc, p[a], w * even);
-        } else {
-            const T we = w * even, wo = w * odd;
-            p[a] = fmaf_t(omc, p[a], we + wo);
-            p[b] = fmaf_t(omc, p[b], we - wo);
-        }
+        const V w = V(T(F::w(ap)));
+        const V we = even * w, wo = odd * w;
+        p[ap] = fma_v(p[ap], omc, we + wo);
+        p[am] = fma_v(p[am], omc, we - wo);
     }
     const T w0 = T(M::w(0)), w1 = T(M::w(1));
     if constexpr (HH) {
-        T dC = 0;
-#pragma unroll
-        for (int a = 0; a < QM; ++a) dC += p[PL::H0 + a];
-        const T C = dC + c.ref_C;
-        const T oh = c.om_h, ohc = c.omc_h;
-        const T ev = oh * w1 * dC, f4 = T(4) * oh * w1 * C;
-        p[PL::H0] = fmaf_t(ohc, p[PL::H0], oh * w0 * dC);
+        const V dC = plane_sum(p, PL::H0, QM);
+        const V C = dC + V(c.ref_C);
+        const T oh = c.om_h;
+        const V ohc = V(c.omc_h);
+        const V ev = V(oh * w1) * dC, f4 = V(T(4) * oh * w1) * C;
+        p[PL::H0] = fma_v(p[PL::H0], ohc, V(oh * w0) * dC);
 #pragma unroll
         for (int a = 1; a < QM; ++a) {
             const int b = M::opp(a);
             if (b < a) continue;
+            const int ap = lead_sign<M>(a) > 0 ? a : b, am = lead_sign<M>(a) > 0 ? b : a;
             const int i = M::ex(a) ? 0 : (M::ey(a) ? 1 : 2);
-            const T od = (M::ex(a) + M::ey(a) + M::ez(a) > 0) ? f4 * u[i] : -(f4 * u[i]);
-            p[PL::H0 + a] = fmaf_t(ohc, p[PL::H0 + a], ev + od);
-            p[PL::H0 + b] = fmaf_t(ohc, p[PL::H0 + b], ev - od);
+            const V od = f4 * u[i];
+            p[PL::H0 + ap] = fma_v(p[PL::H0 + ap], ohc, ev + od);
+            p[PL::H0 + am] = fma_v(p[PL::H0 + am], ohc, ev - od);
         }
     }
     if constexpr (HG) {
-        const T og = c.om_g, ogc = c.omc_g;
-        const T og1 = og * w1, og4 = T(4) * og * w1;
+        const T og = c.om_g;
+        const V ogc = V(c.omc_g);
+        const V og1 = V(og * w1), og4 = V(T(4) * og * w1), og0 = V(og * w0);
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
             const int q0 = PL::G0 + k * QM;
-            const T ev = og1 * dB[k];
-            p[q0] = fmaf_t(ogc, p[q0], og * w0 * dB[k]);
+            const V ev = og1 * dB[k];
+            p[q0] = fma_v(p[q0], ogc, og0 * dB[k]);
 #pragma unroll
             for (int a = 1; a < QM; ++a) {
                 const int b = M::opp(a);
                 if (b < a) continue;
+                const int ap = lead_sign<M>(a) > 0 ? a : b, am = lead_sign<M>(a) > 0 ? b : a;
                 const int i = M::ex(a) ? 0 : (M::ey(a) ? 1 : 2);
-                if (i == k) {                                 // u_k B_k - B_k u_k = 0
-                    p[q0 + a] = fmaf_t(ogc, p[q0 + a], ev);
-                    p[q0 + b] = fmaf_t(ogc, p[q0 + b], ev);
+                if (i == k) {                                        // u_k B_k - B_k u_k = 0
+                    p[q0 + ap] = fma_v(p[q0 + ap], ogc, ev);
+                    p[q0 + am] = fma_v(p[q0 + am], ogc, ev);
                 } else {
-                    const T v = og4 * fmaf_t(u[i], B[k], -(B[i] * u[k]));
-                    const T od = (M::ex(a) + M::ey(a) + M::ez(a) > 0) ? v : -v;
-                    p[q0 + a] = fmaf_t(ogc, p[q0 + a], ev + od);
-                    p[q0 + b] = fmaf_t(ogc, p[q0 + b], ev - od);
+                    const V od = og4 * fma_v(u[i], B[k], nB[i] * u[k]);
+                    p[q0 + ap] = fma_v(p[q0 + ap], ogc, ev + od);
+                    p[q0 + am] = fma_v(p[q0 + am], ogc, ev - od);
                 }
             }
         }
+    }
+}
+
+// one node: FP64 as is, FP32 through F1
+template <class PL, bool HH, bool HG, class T>
+LBM_DEV void collide(T (&p)[PL::P], const CaseDev<T> &c) {
+    if constexpr (sizeof(T) == 8) {
+        collide_v<PL, HH, HG, T, T>(p, c);
+    } else {
+        F1 v[PL::P];
+#pragma unroll
+        for (int q = 0; q < PL::P; ++q) v[q] = F1(p[q]);
+        collide_v<PL, HH, HG, F1, float>(v, c);
+#pragma unroll
+        for (int q = 0; q < PL::P; ++q) p[q] = v[q].v;
     }
 }
 
@@ -432,19 +513,15 @@ __global__ void __launch_bounds__(256, MINB) k_step(const StepParams<typename Co
 // others as two 16-bit loads, and every result plane is written as one word.
 template <class S> struct Pair16;
 template <> struct Pair16<__half> {
-    LBM_DEV static uint32_t ld(const __half *p) { return __ldg(reinterpret_cast<const unsigned int *>(p)); }
-    LBM_DEV static float lo(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu))); }
-    LBM_DEV static float hi(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
-    LBM_DEV static void st(__half *p, float a, float b) { *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b); }
+    LBM_DEV static float2 ld(const __half *p) { return __half22float2(__ldg(reinterpret_cast<const __half2 *>(p))); }
+    LBM_DEV static void st(__half *p, float2 v) { *reinterpret_cast<__half2 *>(p) = __float22half2_rn(v); }
 };
 template <> struct Pair16<__nv_bfloat16> {
-    LBM_DEV static uint32_t ld(const __nv_bfloat16 *p) { return __ldg(reinterpret_cast<const unsigned int *>(p)); }
-    LBM_DEV static float lo(uint32_t w) {
-        return __bfloat162float(__ushort_as_bfloat16((unsigned short)(w & 0xffffu)));
+    LBM_DEV static float2 ld(const __nv_bfloat16 *p) {
+        return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162 *>(p)));
     }
-    LBM_DEV static float hi(uint32_t w) { return __bfloat162float(__ushort_as_bfloat16((unsigned short)(w >> 16))); }
-    LBM_DEV static void st(__nv_bfloat16 *p, float a, float b) {
-        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+    LBM_DEV static void st(__nv_bfloat16 *p, float2 v) {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(v);
     }
 };
 
@@ -459,24 +536,21 @@ LBM_DEV void pair_node(const CaseDev<float> &c, const S *src, S *dst, int n0) {
     const int st32 = (int)c.stride;
     const S *__restrict__ sp = src + n0;
     S *__restrict__ dp = dst + n0;
-    float a[P], b[P];
+    F2 v[P];
 #pragma unroll
     for (int q = 0; q < P; ++q) {
         const int off = q * st32 - (PL::ex(q) + PL::ey(q) * nx + PL::ez(q) * nxy);
         const int par = (PL::ex(q) + PL::ey(q) * PX + PL::ez(q) * PXY) & 1;
         if (par == 0) {
-            const uint32_t w = Pair16<S>::ld(sp + off);
-            a[q] = Pair16<S>::lo(w);
-            b[q] = Pair16<S>::hi(w);
+            const float2 w = Pair16<S>::ld(sp + off);
+            v[q] = F2(w.x, w.y);
         } else {
-            a[q] = Codec<S>::ld(sp + off);
-            b[q] = Codec<S>::ld(sp + off + 1);
+            v[q] = F2(Codec<S>::ld(sp + off), Codec<S>::ld(sp + off + 1));
         }
     }
-    collide<PL, HH, HG, float>(a, c);
-    collide<PL, HH, HG, float>(b, c);
+    collide_v<PL, HH, HG, F2, float>(v, c);
 #pragma unroll
-    for (int q = 0; q < P; ++q) Pair16<S>::st(dp + q * st32, a[q], b[q]);
+    for (int q = 0; q < P; ++q) Pair16<S>::st(dp + q * st32, v[q].v);
 }
 
 // Bulk nodes in pairs (16-bit storage).  Tiles of blockDim.x * npt nodes (npt

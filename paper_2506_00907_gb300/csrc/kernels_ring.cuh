@@ -1,0 +1,287 @@
+// kernels_ring.cuh -- the fused step fed through a ring of shared-memory stages.
+//
+// Same arithmetic as k_step (kernels.cuh); the populations reach the
+// registers differently.  A block is one producer warp and RING_CW consumer
+// warps.  The producer walks the block's tiles (t = blockIdx.x, + gridDim.x,
+// ...) and, for each, copies every population plane's source window
+// ([start - s_q, start + len - s_q), s_q the flat index offset of e_q, widened
+// to 16 bytes) into a free stage with one cp.async.bulk per plane, completing
+// on the stage's `full` mbarrier.  Consumers wait on `full`, pull their nodes
+// from the windows in shared memory, relax them and store the results
+// straight to global memory; each consumer warp then arrives on the stage's
+// `empty` mbarrier, which frees the stage for the producer.  There is no
+// block-wide barrier in the loop: the producer runs up to NS tiles ahead.
+//
+// NPL = 2: each consumer lane takes two x-adjacent nodes and relaxes them
+// together with packed f32x2 arithmetic (collide_v<F2>); planes whose window
+// shift is even are read as one 32- or 64-bit word.  NPL = 1: one node per
+// lane (F1).  Both give the bits of the one-node kernel.
+//
+// Nodes on a periodic edge, and nodes whose partner in the pair is not bulk
+// fluid, take the one-node path from global memory (step_node).  Wall-link
+// nodes are left to k_boundary, as for k_step.
+//
+// Every mbarrier wait is bounded: on timeout the warp records an error code
+// in err[0] and raises the block's abort word; the producer then stops
+// issuing, waits (bounded) for its copies in flight and returns.
+#pragma once
+#include "kernels_bulk.cuh"
+
+namespace lbm {
+
+constexpr int RING_CW = 8;                         // consumer warps per block
+constexpr int RING_THREADS = (RING_CW + 1) * 32;   // + the producer warp
+constexpr int RING_MAX_NS = 8;                     // stages
+constexpr int RING_MAX_QF = 20;                    // window shifts per stage (>= 19 lattice vectors)
+
+// shared memory: full[NS], empty[NS] mbarriers, the abort word, window shifts
+// [NS][RING_MAX_QF] (elements), then windows [NS][P][CAP]
+__host__ __device__ constexpr int ring_tile(int npl) { return RING_CW * 32 * npl; }
+__host__ __device__ constexpr int ring_cap(int npl, int elem) { return ring_tile(npl) + 16 / elem; }
+constexpr int RING_FULL = 0;
+constexpr int RING_EMPTY = 8 * RING_MAX_NS;
+constexpr int RING_ABORT = 16 * RING_MAX_NS;
+constexpr int RING_SHIFT = RING_ABORT + 16;
+constexpr int RING_WIN = ((RING_SHIFT + 4 * RING_MAX_NS * RING_MAX_QF + 127) / 128) * 128;
+__host__ __device__ constexpr int ring_smem_bytes(int P, int npl, int elem, int ns) {
+    return RING_WIN + ns * P * ring_cap(npl, elem) * elem;
+}
+
+LBM_DEV void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// bounded wait for the completion of phase `parity`; false on timeout or when
+// the block's abort word is raised
+LBM_DEV bool ring_wait(uint64_t *bar, uint32_t parity, volatile int *abort_word) {
+    for (uint32_t k = 0; k < BULK_SPIN_LIMIT; ++k) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((k & 255) == 255 && *abort_word) return false;
+    }
+    return false;
+}
+
+// the flow plane with the lattice vector of plane q (every vector of the
+// D2Q5/D3Q7 lattices is one of D2Q9/D3Q19)
+template <class PL>
+LBM_HD constexpr int flow_dir(int q) {
+    for (int a = 0; a < PL::QF; ++a)
+        if (PL::F::ex(a) == PL::ex(q) && PL::F::ey(a) == PL::ey(q) && PL::F::ez(a) == PL::ez(q)) return a;
+    return 0;
+}
+
+// two consecutive values from shared memory (aligned to their pair size) and
+// the packed store of two results
+template <class S> struct PairMem;
+template <> struct PairMem<float> {
+    LBM_DEV static float2 lds(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+    LBM_DEV static void st(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+};
+template <> struct PairMem<__half> {
+    LBM_DEV static float2 lds(const __half *p) { return __half22float2(*reinterpret_cast<const __half2 *>(p)); }
+    LBM_DEV static void st(__half *p, float2 v) { *reinterpret_cast<__half2 *>(p) = __float22half2_rn(v); }
+};
+template <> struct PairMem<__nv_bfloat16> {
+    LBM_DEV static float2 lds(const __nv_bfloat16 *p) {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+    }
+    LBM_DEV static void st(__nv_bfloat16 *p, float2 v) {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(v);
+    }
+};
+
+// Producer: windows of tile t into stage st (lane q copies planes q, q + 32).
+template <class PL, class S, int NPL>
+LBM_DEV void ring_issue(const StepParams<float> &prm, int t, int st, unsigned char *smem) {
+    constexpr int P = PL::P;
+    constexpr int NJ = (P + 31) / 32;
+    constexpr int TT = ring_tile(NPL);
+    constexpr int A = 16 / (int)sizeof(S);
+    constexpr int CAP = ring_cap(NPL, (int)sizeof(S));
+    const int lane = threadIdx.x & 31;
+    const int2 tile = prm.tiles[t];
+    const CaseDev<float> &c = prm.cases[tile.x];
+    const int len = min(TT, c.N - tile.y);
+    const int nx = c.nx, nxy = c.nx * c.ny;
+    const int top = ((c.N + A - 1) / A) * A;
+    int *shift = reinterpret_cast<int *>(smem + RING_SHIFT) + st * RING_MAX_QF;
+    int lo[NJ], hi[NJ];
+    uint32_t bytes = 0;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int q = lane + 32 * j;
+        lo[j] = hi[j] = 0;
+        if (q < P) {
+            const int s = PL::ex(q) + PL::ey(q) * nx + PL::ez(q) * nxy;
+            const int a = tile.y - s, b = tile.y + len - s;
+            lo[j] = a < 0 ? 0 : (a / A) * A;
+            const int h = ((b + A - 1) / A) * A;
+            hi[j] = h > top ? top : h;
+            if (hi[j] < lo[j]) hi[j] = lo[j];
+            if (q < PL::QF) shift[q] = a - lo[j];          // window index of the pull source of the tile's first node
+            bytes += (uint32_t)(hi[j] - lo[j]) * (uint32_t)sizeof(S);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xffffffffu, bytes, o);
+    __syncwarp();                                            // the shifts before the arrival that publishes them
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + RING_FULL) + st;
+    if (lane == 0) mbar_arrive_expect_tx(full, bytes);
+    __syncwarp();
+    const S *src = static_cast<const S *>(prm.src) + c.pop_off;
+    S *win = reinterpret_cast<S *>(smem + RING_WIN) + (size_t)st * P * CAP;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int q = lane + 32 * j;
+        if (q < P && hi[j] > lo[j])
+            bulk_g2s(win + (size_t)q * CAP, src + (int64_t)q * c.stride + lo[j],
+                     (uint32_t)(hi[j] - lo[j]) * (uint32_t)sizeof(S), full);
+    }
+}
+
+// Consumer, two nodes n0, n0 + 1 (both bulk fluid, off the periodic edges):
+// pull from the windows, relax (packed), store to global memory.
+template <int DIM, bool HH, bool HG, class S, int PX, int PXY>
+LBM_DEV void ring_pair(const CaseDev<float> &c, const S *win, const int *shift, int local, S *dst, int n0) {
+    using PL = Planes<DIM, HH, HG>;
+    constexpr int P = PL::P;
+    constexpr int CAP = ring_cap(2, (int)sizeof(S));
+    int sh[PL::QF];
+#pragma unroll
+    for (int d = 0; d < PL::QF; ++d) sh[d] = shift[d] + local;
+    F2 v[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        // the window shift of plane q has the parity of s_q (window starts are even)
+        const int par = (PL::ex(q) + PL::ey(q) * PX + PL::ez(q) * PXY) & 1;
+        const S *e = win + q * CAP + sh[flow_dir<PL>(q)];
+        if (par == 0) {
+            const float2 w = PairMem<S>::lds(e);
+            v[q] = F2(w.x, w.y);
+        } else {
+            v[q] = F2(Codec<S>::ld_shared(e), Codec<S>::ld_shared(e + 1));
+        }
+    }
+    collide_v<PL, HH, HG, F2, float>(v, c);
+    const int st32 = (int)c.stride;
+    S *__restrict__ dp = dst + n0;
+#pragma unroll
+    for (int q = 0; q < P; ++q) PairMem<S>::st(dp + q * st32, v[q].v);
+}
+
+// Consumer, one node n (bulk fluid, off the periodic edges).
+template <int DIM, bool HH, bool HG, class S>
+LBM_DEV void ring_one(const CaseDev<float> &c, const S *win, const int *shift, int local, S *dst, int n) {
+    using PL = Planes<DIM, HH, HG>;
+    constexpr int P = PL::P;
+    constexpr int CAP = ring_cap(1, (int)sizeof(S));
+    float p[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) p[q] = Codec<S>::ld_shared(win + q * CAP + shift[flow_dir<PL>(q)] + local);
+    collide<PL, HH, HG, float>(p, c);
+    const int st32 = (int)c.stride;
+    S *__restrict__ dp = dst + n;
+#pragma unroll
+    for (int q = 0; q < P; ++q) Codec<S>::st(dp + q * st32, p[q]);
+}
+
+template <int DIM, bool HH, bool HG, class S, int NPL, int MINB>
+__global__ void __launch_bounds__(RING_THREADS, MINB) k_step_ring(const StepParams<float> prm, const BulkParams bp,
+                                                                  const int ns) {
+    using PL = Planes<DIM, HH, HG>;
+    constexpr int P = PL::P;
+    constexpr int CAP = ring_cap(NPL, (int)sizeof(S));
+    static_assert(PL::QF <= RING_MAX_QF, "window shifts");
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + RING_FULL);
+    uint64_t *empty = reinterpret_cast<uint64_t *>(smem + RING_EMPTY);
+    volatile int *abort_word = reinterpret_cast<volatile int *>(smem + RING_ABORT);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < ns; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], RING_CW);
+        }
+        *abort_word = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == RING_CW) {
+        // ---------------------------------------------------------- producer
+        int k = 0;
+        bool ok = true;
+        for (;; ++k) {
+            const int t = blockIdx.x + k * gridDim.x;
+            if (t >= prm.ntiles) break;
+            const int st = k % ns;
+            if (k >= ns && !ring_wait(&empty[st], (uint32_t)((k / ns) - 1) & 1u, abort_word)) {
+                ok = false;
+                break;
+            }
+            ring_issue<PL, S, NPL>(prm, t, st, smem);
+        }
+        if (!ok && lane == 0) {
+            if (!*abort_word) atomicExch(bp.err, 1);
+            *abort_word = 1;
+        }
+        // the block stays resident until every copy it issued has landed
+        if (lane == 0)
+            for (int kk = k - 1; kk >= 0 && kk >= k - ns; --kk)
+                for (uint32_t s = 0; s < BULK_SPIN_LIMIT && !mbar_try_wait(&full[kk % ns], (uint32_t)(kk / ns) & 1u);
+                     ++s) {
+                }
+        return;
+    }
+    // -------------------------------------------------------------- consumers
+    for (int k = 0;; ++k) {
+        const int t = blockIdx.x + k * gridDim.x;
+        if (t >= prm.ntiles) break;
+        const int st = k % ns;
+        if (!ring_wait(&full[st], (uint32_t)(k / ns) & 1u, abort_word)) {
+            if (lane == 0) {
+                atomicExch(bp.err, 1);
+                *abort_word = 1;
+            }
+            return;
+        }
+        const int2 tile = prm.tiles[t];
+        const CaseDev<float> c = prm.cases[tile.x];
+        const S *win = reinterpret_cast<const S *>(smem + RING_WIN) + (size_t)st * P * CAP;
+        const int *shift = reinterpret_cast<const int *>(smem + RING_SHIFT) + st * RING_MAX_QF;
+        S *dst = static_cast<S *>(prm.dst) + c.pop_off;
+        const int local = (warp * 32 + lane) * NPL;
+        const int n0 = tile.y + local;
+        if (n0 < c.N) {
+            int x, y, z, r;
+            coords<DIM, float>(c, n0, x, y, z, r);
+            const bool yz_in = y >= 1 && y + 1 <= c.ny - 1 && (DIM == 2 || (z >= 1 && z + 1 <= c.nz - 1));
+            const uint8_t f0 = prm.flags[c.node_off + n0];
+            if constexpr (NPL == 2) {
+                const uint8_t f1 = n0 + 1 < c.N ? prm.flags[c.node_off + n0 + 1] : uint8_t(0);
+                if (f0 == NODE_FLUID && f1 == NODE_FLUID && yz_in && x >= 1 && x + 2 <= c.nx - 1) {
+                    const int px = c.nx & 1, pxy = (c.nx * c.ny) & 1;
+                    if (!px)
+                        ring_pair<DIM, HH, HG, S, 0, 0>(c, win, shift, local, dst, n0);
+                    else if (DIM == 2 || !pxy)
+                        ring_pair<DIM, HH, HG, S, 1, 0>(c, win, shift, local, dst, n0);
+                    else
+                        ring_pair<DIM, HH, HG, S, 1, 1>(c, win, shift, local, dst, n0);
+                } else {
+                    if (f0 == NODE_FLUID) step_node<DIM, HH, HG, S, false>(prm, c, n0, 0, 0);
+                    if (f1 == NODE_FLUID) step_node<DIM, HH, HG, S, false>(prm, c, n0 + 1, 0, 0);
+                }
+            } else {
+                if (f0 == NODE_FLUID) {
+                    if (yz_in && x >= 1 && x + 1 <= c.nx - 1)
+                        ring_one<DIM, HH, HG, S>(c, win, shift, local, dst, n0);
+                    else
+                        step_node<DIM, HH, HG, S, false>(prm, c, n0, 0, 0);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
+    }
+}
+
+}  // namespace lbm

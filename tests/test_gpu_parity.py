@@ -427,3 +427,99 @@ def test_paired_nodes_reject_bad_shapes():
     for bad in ((2, 128, 0, 3, 2, 3), (2, 128, 0, 2, 2, 9)):
         with pytest.raises(lbm.LbmError):
             q.gpu.set_launch(*bad)
+
+
+def _random_gpu(dim, shape, prec, seed, phys=lbm.LBM_FLOW | lbm.LBM_CD | lbm.LBM_MHD):
+    """A GPU solver on a random geometry with every link kind (no oracle:
+    for bitwise comparisons between launch variants at larger sizes)."""
+    r = IN.rng(seed)
+    has_h, has_g = bool(phys & lbm.LBM_CD), bool(phys & lbm.LBM_MHD)
+    solid = IN.random_solid(r, shape, fill=0.12)
+    phi_range = {O.H: (0.5, 1.5), O.G0: (-0.05, 0.05), O.G0 + 1: (0.25, 0.35), O.G0 + 2: (-0.05, 0.05)}
+    links = LK.random_links(dim, shape, solid, r, has_h, has_g, phi_range=phi_range)
+    N = shape[0] * shape[1] * shape[2]
+    f = IN.random_fields(r, N, dim, B0=(0.0, 0.3, 0.0))
+    case = lbm.make_case(shape, 0.8, 0.9, 0.7, (1e-5, -2e-5, 5e-6 if dim == 3 else 0.0), 1.0, 1.0, (0.0, 0.3, 0.0))
+    g = lbm.Solver(lbm.LBM_D2Q9 if dim == 2 else lbm.LBM_D3Q19, prec, phys, [case])
+    g.set_walls(0, solid, to_abi_links(links))
+    g.init_equilibrium(0, rho=f.get("rho"), u=f.get("u"), C=f.get("C") if has_h else None,
+                       B=f.get("B") if has_g else None)
+    return g
+
+
+def _ring_runs(make, steps, want):
+    ran = 0
+    for ns, bps in ((2, 1), (3, 0), (4, 1), (8, 0)):
+        g = make()
+        try:
+            g.set_launch(3, 256, bps, 1, ns, 2)
+        except lbm.LbmError as e:      # these stages do not fit in shared memory
+            assert e.status == lbm.LBM_EINVAL and "shared memory" in str(e)
+            continue
+        g.set_graph(4)
+        g.step(steps)
+        assert np.array_equal(g.get_state(), want), (ns, bps)
+        g.check()
+        ran += 1
+    return ran
+
+
+@pytest.mark.parametrize("dim,prec,shape", [
+    (2, lbm.LBM_FP16S, (53, 41, 1)), (2, lbm.LBM_BF16S, (52, 41, 1)), (2, lbm.LBM_FP32, (37, 30, 1)),
+    (3, lbm.LBM_FP16S, (21, 13, 11)), (3, lbm.LBM_BF16S, (20, 13, 11)), (3, lbm.LBM_FP32, (22, 14, 9))])
+def test_ring_pipeline_is_bitwise_identical(dim, prec, shape):
+    """Variant 3 (producer warp filling a ring of shared-memory stages with
+    cp.async.bulk windows, consumer warps relaxing from it; packed node pairs
+    in 2D) computes exactly what one thread per node computes: odd and even
+    nx, ragged tails, periodic edges, every link kind, 2..8 stages."""
+    ref = _random_pair(dim, True, True, seed=93, prec=prec, shape=shape).gpu
+    ref.set_launch(0, 128, 0)
+    ref.step(15)
+    want = ref.get_state()
+    ran = _ring_runs(lambda: _random_pair(dim, True, True, seed=93, prec=prec, shape=shape).gpu, 15, want)
+    assert ran >= 3
+
+
+@pytest.mark.parametrize("dim,prec,shape,phys", [
+    (2, lbm.LBM_FP16S, (701, 523, 1), lbm.LBM_FLOW | lbm.LBM_MHD),
+    (2, lbm.LBM_BF16S, (640, 480, 1), lbm.LBM_FLOW),
+    (3, lbm.LBM_FP16S, (97, 61, 53), lbm.LBM_FLOW | lbm.LBM_CD | lbm.LBM_MHD),
+    (3, lbm.LBM_FP32, (64, 48, 40), lbm.LBM_FLOW | lbm.LBM_MHD)])
+def test_ring_pipeline_wraps_many_tiles(dim, prec, shape, phys):
+    """Many more tiles than resident blocks: each block's ring of stages
+    wraps many times (mbarrier phases flip), still bit for bit."""
+    ref = _random_gpu(dim, shape, prec, 17, phys)
+    ref.set_launch(0, 128, 0)
+    ref.step(6)
+    want = ref.get_state()
+    assert _ring_runs(lambda: _random_gpu(dim, shape, prec, 17, phys), 6, want) >= 2
+
+
+def test_ring_pipeline_batched_cases():
+    """Variant 3 over uneven batched Hartmann channels (tiles of one block in
+    different cases) equals variant 0 bit for bit."""
+    def make():
+        cases, geo = [], []
+        for W, q in ((20, 0.3), (33, 0.0), (9, 0.75), (64, 0.5), (131, 0.9), (300, 0.2)):
+            shape, solid, links, B0 = _hartmann_links(W, q, 0.3, 5.0)
+            cases.append(lbm.make_case(shape, 0.8, 1.0, 0.9, (2e-5, 0, 0), 1.0, 0.0, (0, B0, 0)))
+            geo.append((solid, links))
+        g = lbm.Solver(lbm.LBM_D2Q9, lbm.LBM_FP16S, lbm.LBM_FLOW | lbm.LBM_MHD, cases)
+        for i, (solid, links) in enumerate(geo):
+            g.set_walls(i, solid, to_abi_links(links))
+        return g
+    a = make()
+    a.set_launch(0, 256, 4)
+    a.step(30)
+    want = a.get_state()
+    assert _ring_runs(make, 30, want) == 4
+
+
+def test_ring_rejects_fp64_and_bad_stages():
+    p = _random_pair(2, False, False, seed=5)
+    with pytest.raises(lbm.LbmError):
+        p.gpu.set_launch(3, 256, 0, 1, 3, 2)       # FP64 storage
+    q = _random_pair(2, False, False, seed=5, prec=lbm.LBM_FP16S)
+    for bad in ((3, 256, 0, 1, 1, 2), (3, 256, 0, 1, 9, 2)):
+        with pytest.raises(lbm.LbmError):
+            q.gpu.set_launch(*bad)
