@@ -243,6 +243,8 @@ LBM_DEV void collide_v(V (&p)[PL::P], const CaseDev<T> &c) {
     V A = fma_v(mu, V(T(-1.5)), drho);
     if constexpr (HG && DIM == 3) A = fma_v(Bsq, V(T(-0.75)), A);   // 0.75 (2 - D) |B|^2 vanishes in 2D
     A = fma_v(A, V(om), V(T(-3) * g) * uF);
+    // Td: Tm_ii (with the field) or Tm_ii / 4.5 (without: the even parts then
+    // accumulate 4.5 Td with one fused operation per term)
     V Vv[3], Td[3], Tc[3];                                           // Tc: 2 Tm_xy, 2 Tm_xz, 2 Tm_yz
     V mag;
     if constexpr (HG) mag = V(T(2.25) * om) * Bsq;
@@ -254,7 +256,7 @@ LBM_DEV void collide_v(V (&p)[PL::P], const CaseDev<T> &c) {
         if constexpr (HG) t = fma_v(B[i], nB[i], t);
         const V s = fma_v(t, V(om), (V(g2) * u[i]) * Fo[i]);
         if constexpr (HG) Td[i] = fma_v(s, V(T(4.5)), mag);
-        else Td[i] = s * V(T(4.5));
+        else Td[i] = s;
     }
 #pragma unroll
     for (int pr = 0; pr < (DIM == 3 ? 3 : 1); ++pr) {
@@ -277,7 +279,8 @@ LBM_DEV void collide_v(V (&p)[PL::P], const CaseDev<T> &c) {
 #pragma unroll
         for (int i = 0; i < DIM; ++i) {
             if (e[i]) {
-                even = even + Td[i];
+                if constexpr (HG) even = even + Td[i];
+                else even = fma_v(Td[i], V(T(4.5)), even);
                 odd = first ? Vv[i] : (e[i] > 0 ? odd + Vv[i] : odd - Vv[i]);
                 first = false;
             }
