@@ -97,7 +97,14 @@ def build_workload(name):
 
 
 # ----------------------------------------------------------------------------- helpers
-STEP_SOURCES = ("lattice.cuh", "types.cuh", "kernels.cuh", "kernels_bulk.cuh")   # where the step kernels live
+STEP_SOURCES = ("lattice.cuh", "types.cuh", "kernels.cuh", "kernels_bulk.cuh", "kernels_ring.cuh")   # the step kernels
+
+
+STEP_KERNEL = {
+    0: "k_step (bulk nodes) + k_boundary (wall-link nodes)",
+    1: "k_step_bulk (bulk-copy loads and stores, boundary nodes included)",
+    2: "k_step_pair (x-adjacent node pairs, packed FP32) + k_boundary (wall-link nodes)",
+    3: "k_step_ring (producer warp, bulk-copy ring of stages, consumer warps) + k_boundary (wall-link nodes)"}
 
 
 def kernel_hash():
@@ -448,9 +455,7 @@ def run_ours(args):
                              "bytes_per_step": alg_bytes, "ms_per_step_kernels": ms_kernel,
                              "timing": "CUDA events on the solver stream around each replay of the %d-step "
                                        "graph inside the timed region (step launches only)" % CHECK_EVERY,
-                             "kernel": ("k_step_bulk (bulk-copy loads and stores, boundary nodes included)"
-                                        if tune and tune["variant"] == 1 else
-                                        "k_step (bulk nodes) + k_boundary (wall-link nodes)")
+                             "kernel": STEP_KERNEL[tune["variant"] if tune else 0]
                                        + ": one time step, %d launches" % per_step},
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         if cpu:
