@@ -78,6 +78,8 @@ struct lbm_ctx {
     std::vector<int2> h_tiles;         // host copies for the per-tile boundary ranges
     std::vector<BRec> h_brec;
     int32_t *d_tile_brec = nullptr;    // [ntiles + 1]
+    std::vector<uint8_t> h_flags;      // host copy of the node flags (tile classification)
+    uint8_t *d_tile_fluid = nullptr;   // [ntiles]: 1 when every node of the tile is bulk fluid
     void *d_links = nullptr;
     size_t cap_brec = 0, cap_links = 0;
     double *d_snap = nullptr, *d_part = nullptr, *d_red = nullptr, *h_red = nullptr;
@@ -303,6 +305,21 @@ lbm_status build_tile_brec(lbm_ctx *ctx) {
     ctx->d_tile_brec = nullptr;
     CK(cudaMalloc(&ctx->d_tile_brec, r.size() * sizeof(int32_t)));
     CK(cudaMemcpy(ctx->d_tile_brec, r.data(), r.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    // tiles of bulk fluid only: the step kernel skips their per-node flag loads
+    std::vector<uint8_t> tf(ctx->h_tiles.size(), 0);
+    if (!ctx->h_flags.empty())
+        for (size_t t = 0; t < ctx->h_tiles.size(); ++t) {
+            const int2 tl = ctx->h_tiles[t];
+            const CaseHost &cs = ctx->cases[tl.x];
+            const int64_t end = std::min<int64_t>(cs.N, (int64_t)tl.y + ctx->tile_nodes);
+            bool all = true;
+            for (int64_t n = tl.y; n < end && all; ++n) all = ctx->h_flags[cs.node_off + n] == NODE_FLUID;
+            tf[t] = all ? 1 : 0;
+        }
+    if (ctx->d_tile_fluid) cudaFree(ctx->d_tile_fluid);
+    ctx->d_tile_fluid = nullptr;
+    CK(cudaMalloc(&ctx->d_tile_fluid, std::max<size_t>(1, tf.size())));
+    if (!tf.empty()) CK(cudaMemcpy(ctx->d_tile_fluid, tf.data(), tf.size(), cudaMemcpyHostToDevice));
     return LBM_OK;
 }
 
@@ -379,6 +396,7 @@ lbm_status upload_walls_t(lbm_ctx *ctx) {
     CK(cudaMemcpy(ctx->d_brec, brec.data(), brec.size() * sizeof(BRec), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_links, links.data(), links.size() * sizeof(LinkDev<T>), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_flags, flags.data(), flags.size(), cudaMemcpyHostToDevice));
+    ctx->h_flags = flags;
     drop_graphs(ctx);
     const lbm_status st2 = build_tile_brec(ctx);
     if (st2 != LBM_OK) return st2;
@@ -401,6 +419,7 @@ StepParams<T> step_params(const lbm_ctx *c) {
     p.brec = c->d_brec;
     p.nbrec = c->nbrec;
     p.tile_brec = c->d_tile_brec;
+    p.tile_fluid = c->d_tile_fluid;
     p.links = static_cast<const LinkDev<T> *>(c->d_links);
     return p;
 }
@@ -510,6 +529,7 @@ void free_ctx(lbm_ctx *c) {
     if (!c) return;
     drop_graphs(c);
     void *ptrs[] = {c->pool[0], c->pool[1], c->d_flags, c->d_cases, c->d_tiles, c->d_case_tile_lo, c->d_tile_brec,
+                    c->d_tile_fluid,
                     c->d_brec, c->d_links, c->d_snap, c->d_part, c->d_red, c->d_mom, c->d_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);

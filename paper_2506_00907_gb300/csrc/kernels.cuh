@@ -73,6 +73,7 @@ struct StepParams {
     int32_t nbrec;
     const LinkDev<T> *links;
     const int32_t *tile_brec; // boundary records of tile t: [tile_brec[t], tile_brec[t + 1])
+    const uint8_t *tile_fluid; // 1 when every node of tile t is bulk fluid
 };
 
 // ------------------------------------------------------------------ equilibria
@@ -500,11 +501,12 @@ __global__ void __launch_bounds__(256, MINB) k_step(const StepParams<typename Co
         const int2 next = tn < prm.ntiles ? prm.tiles[tn] : tile;
         // the descriptor by value: the stores below cannot alias it, so it stays in registers
         const CaseDev<T> c = prm.cases[tile.x];
+        // in a tile of bulk fluid only the pulls need not wait for a flag load
+        const bool all_fluid = prm.tile_fluid[t] != 0;
         for (int k = 0; k < npt; ++k) {
             const int n = tile.y + (int)threadIdx.x + k * (int)blockDim.x;
             if (n >= c.N) break;
-            const uint8_t fl = prm.flags[c.node_off + n];
-            if (fl == NODE_FLUID) step_node<DIM, HH, HG, S, false>(prm, c, n, 0, 0);
+            if (all_fluid || prm.flags[c.node_off + n] == NODE_FLUID) step_node<DIM, HH, HG, S, false>(prm, c, n, 0, 0);
         }
         tile = next;
     }
