@@ -1080,7 +1080,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
     cudaDeviceProp prop{};
     CK(cudaGetDeviceProperties(&prop, ctx->cfg.device));
     std::ostringstream key;
-    key << prop.name << "|v9|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
+    key << prop.name << "|v10|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
         << ctx->cases.size();
     int64_t tot = 0;
     for (auto &c : ctx->cases) tot += c.N;
@@ -1119,9 +1119,9 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
     CK(cudaEventCreate(&e1));
     std::vector<lbm_launch> cands;
     for (int r = 0; r < 3; ++r)
-        for (int b : {128, 256})
+        for (int b : {64, 128, 256})
             for (int p : {0, 8})
-                for (int npt : {1, 2, 4}) cands.push_back(lbm_launch{0, b, p, npt, 2, kstep_minb(ctx->dim, r)});
+                for (int npt : {1, 2, 3, 4}) cands.push_back(lbm_launch{0, b, p, npt, 2, kstep_minb(ctx->dim, r)});
     if (!ctx->dbl)
         for (int k = 0; k < BULK_NCFG; ++k) cands.push_back(lbm_launch{1, BULK_TT[k], 0, 1, 2, BULK_MB[k]});
     if (ctx->elem == 2)

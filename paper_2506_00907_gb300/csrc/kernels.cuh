@@ -501,12 +501,19 @@ __global__ void __launch_bounds__(256, MINB) k_step(const StepParams<typename Co
         const int2 next = tn < prm.ntiles ? prm.tiles[tn] : tile;
         // the descriptor by value: the stores below cannot alias it, so it stays in registers
         const CaseDev<T> c = prm.cases[tile.x];
-        // in a tile of bulk fluid only the pulls need not wait for a flag load
+        // in a tile of bulk fluid only the pulls need not wait for a flag load;
+        // elsewhere the flags of all npt nodes are fetched together (byte k of fw)
         const bool all_fluid = prm.tile_fluid[t] != 0;
+        uint64_t fw = 0;
+        if (!all_fluid)
+            for (int k = 0; k < npt; ++k) {
+                const int n = tile.y + (int)threadIdx.x + k * (int)blockDim.x;
+                if (n < c.N) fw |= (uint64_t)prm.flags[c.node_off + n] << (8 * k);
+            }
         for (int k = 0; k < npt; ++k) {
             const int n = tile.y + (int)threadIdx.x + k * (int)blockDim.x;
             if (n >= c.N) break;
-            if (all_fluid || prm.flags[c.node_off + n] == NODE_FLUID) step_node<DIM, HH, HG, S, false>(prm, c, n, 0, 0);
+            if (all_fluid || ((fw >> (8 * k)) & 0xffu) == NODE_FLUID) step_node<DIM, HH, HG, S, false>(prm, c, n, 0, 0);
         }
         tile = next;
     }
