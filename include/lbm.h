@@ -250,8 +250,9 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *launch);
 lbm_status lbm_get_launch(const lbm_ctx *ctx, lbm_launch *launch);
 
 /* Autotuner: times the fused step for every candidate launch shape on this
- * context (each candidate `iters` steps after two warm-up steps, CUDA
- * events), keeps the fastest, and records it in the text cache file
+ * context as it runs in production: a CUDA graph of `iters` steps (rounded
+ * up to even) is captured and replayed once untimed, then the faster of two
+ * timed replays counts (CUDA events).  It keeps the fastest shape, and records it in the text cache file
  * `cache_path` (NULL = no cache) keyed by GPU name, lattice, precision,
  * physics and case sizes; a later call with the same key reads the cache
  * instead of timing.  The context's populations and step count are saved and

@@ -1080,7 +1080,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
     cudaDeviceProp prop{};
     CK(cudaGetDeviceProperties(&prop, ctx->cfg.device));
     std::ostringstream key;
-    key << prop.name << "|v10|lat" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
+    key << prop.name << "|v11|graph" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
         << ctx->cases.size();
     int64_t tot = 0;
     for (auto &c : ctx->cases) tot += c.N;
@@ -1113,7 +1113,9 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
     CK(cudaMemcpyAsync(save, ctx->pool[ctx->cur], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
     const int64_t steps0 = ctx->steps;
     const int saved_graph = ctx->graph_steps;
-    ctx->graph_steps = 0;
+    // candidates run as they will in production: replays of a captured graph
+    const int G = std::max(2, iters + (iters & 1));
+    ctx->graph_steps = G;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1136,14 +1138,18 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
     lbm_status st = LBM_OK;
     for (const lbm_launch &cd : cands) {
         if (lbm_set_launch(ctx, &cd) != LBM_OK) continue;   // does not fit: skip
-        if ((st = lbm_step(ctx, 2)) != LBM_OK) break;
-        cudaEventRecord(e0, ctx->stream);
-        if ((st = lbm_step(ctx, iters)) != LBM_OK) break;
-        cudaEventRecord(e1, ctx->stream);
-        cudaEventSynchronize(e1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        const double per = ms / iters;
+        if ((st = lbm_step(ctx, G)) != LBM_OK) break;        // capture and first replay, untimed
+        double per = INFINITY;
+        for (int rep = 0; rep < 2 && st == LBM_OK; ++rep) {
+            cudaEventRecord(e0, ctx->stream);
+            st = lbm_step(ctx, G);
+            cudaEventRecord(e1, ctx->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            per = std::min(per, (double)ms / G);
+        }
+        if (st != LBM_OK) break;
         if (per < best_t) { best_t = per; best = cd; }
     }
     cudaEventDestroy(e0);
