@@ -72,7 +72,9 @@ struct lbm_ctx {
     int32_t *d_err = nullptr;
     int2 *d_tiles = nullptr;
     int32_t ntiles = 0;
-    int32_t *d_case_tile_lo = nullptr;
+    int32_t *d_case_tile_lo = nullptr;  // [cases + 1]: each case's range of reduction tiles
+    int2 *d_rtiles = nullptr;          // reduction tiles (RED_TILE nodes)
+    int32_t nrtiles = 0;
     BRec *d_brec = nullptr;
     int32_t nbrec = 0;
     std::vector<int2> h_tiles;         // host copies for the per-tile boundary ranges
@@ -323,26 +325,35 @@ lbm_status build_tile_brec(lbm_ctx *ctx) {
     return LBM_OK;
 }
 
+// The step's tiles (tile_nodes nodes, from the launch shape) and the
+// reduction's own tiles (RED_TILE nodes, one 256-thread block each, whatever
+// the launch shape), both flat lists over all cases.
+constexpr int32_t RED_TILE = 1024;
+
 lbm_status build_tiles(lbm_ctx *ctx) {
-    std::vector<int2> tiles;
-    std::vector<int32_t> lo;
+    std::vector<int2> tiles, rtiles;
+    std::vector<int32_t> rlo;
     for (size_t c = 0; c < ctx->cases.size(); ++c) {
-        lo.push_back((int32_t)tiles.size());
         for (int32_t s = 0; s < ctx->cases[c].N; s += ctx->tile_nodes) tiles.push_back(make_int2((int)c, s));
+        rlo.push_back((int32_t)rtiles.size());
+        for (int32_t s = 0; s < ctx->cases[c].N; s += RED_TILE) rtiles.push_back(make_int2((int)c, s));
     }
-    lo.push_back((int32_t)tiles.size());
-    if (ctx->d_tiles) cudaFree(ctx->d_tiles);
-    if (ctx->d_case_tile_lo) cudaFree(ctx->d_case_tile_lo);
-    if (ctx->d_part) cudaFree(ctx->d_part);
-    ctx->d_tiles = nullptr;
-    ctx->d_case_tile_lo = nullptr;
-    ctx->d_part = nullptr;
+    rlo.push_back((int32_t)rtiles.size());
+    void **olds[] = {(void **)&ctx->d_tiles, (void **)&ctx->d_rtiles, (void **)&ctx->d_case_tile_lo,
+                     (void **)&ctx->d_part};
+    for (void **o : olds) {
+        if (*o) cudaFree(*o);
+        *o = nullptr;
+    }
     ctx->ntiles = (int32_t)tiles.size();
-    CK(cudaMalloc(&ctx->d_tiles, tiles.size() * sizeof(int2)));
-    CK(cudaMalloc(&ctx->d_case_tile_lo, lo.size() * sizeof(int32_t)));
-    CK(cudaMalloc(&ctx->d_part, (size_t)ctx->ntiles * RED_Q * sizeof(double)));
+    ctx->nrtiles = (int32_t)rtiles.size();
+    CK(cudaMalloc(&ctx->d_tiles, std::max<size_t>(1, tiles.size()) * sizeof(int2)));
+    CK(cudaMalloc(&ctx->d_rtiles, std::max<size_t>(1, rtiles.size()) * sizeof(int2)));
+    CK(cudaMalloc(&ctx->d_case_tile_lo, rlo.size() * sizeof(int32_t)));
+    CK(cudaMalloc(&ctx->d_part, std::max<size_t>(1, rtiles.size()) * RED_Q * sizeof(double)));
     CK(cudaMemcpy(ctx->d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ctx->d_case_tile_lo, lo.data(), lo.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_rtiles, rtiles.data(), rtiles.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_case_tile_lo, rlo.data(), rlo.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     ctx->h_tiles = tiles;
     drop_graphs(ctx);
     return build_tile_brec(ctx);
@@ -529,7 +540,7 @@ void free_ctx(lbm_ctx *c) {
     if (!c) return;
     drop_graphs(c);
     void *ptrs[] = {c->pool[0], c->pool[1], c->d_flags, c->d_cases, c->d_tiles, c->d_case_tile_lo, c->d_tile_brec,
-                    c->d_tile_fluid,
+                    c->d_tile_fluid, c->d_rtiles,
                     c->d_brec, c->d_links, c->d_snap, c->d_part, c->d_red, c->d_mom, c->d_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -846,12 +857,12 @@ lbm_status lbm_check(lbm_ctx *ctx, double *out) {
     if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (ctx->dbl) {
         RedParams<double> rp{ctx->pool[ctx->cur], ctx->d_flags, static_cast<const CaseDev<double> *>(ctx->d_cases),
-                             ctx->d_tiles, ctx->ntiles, ctx->tile_nodes, ctx->d_snap, ctx->d_part};
-        CK(ctx->ks.reduce(&rp, ctx->ntiles, 256, ctx->stream));
+                             ctx->d_rtiles, ctx->nrtiles, RED_TILE, ctx->d_snap, ctx->d_part};
+        CK(ctx->ks.reduce(&rp, ctx->nrtiles, 256, ctx->stream));
     } else {
         RedParams<float> rp{ctx->pool[ctx->cur], ctx->d_flags, static_cast<const CaseDev<float> *>(ctx->d_cases),
-                            ctx->d_tiles, ctx->ntiles, ctx->tile_nodes, ctx->d_snap, ctx->d_part};
-        CK(ctx->ks.reduce(&rp, ctx->ntiles, 256, ctx->stream));
+                            ctx->d_rtiles, ctx->nrtiles, RED_TILE, ctx->d_snap, ctx->d_part};
+        CK(ctx->ks.reduce(&rp, ctx->nrtiles, 256, ctx->stream));
     }
     k_reduce_final<<<(int)ctx->cases.size(), 256, 0, ctx->stream>>>(ctx->d_part, ctx->d_case_tile_lo, ctx->d_red);
     CK(cudaGetLastError());
