@@ -173,30 +173,31 @@ LBM_DEV double fma_v(double a, double b, double c) { return a * b + c; }
 LBM_DEV double neg_v(double a) { return -a; }
 LBM_DEV double recip_v(double a) { return 1.0 / a; }
 
-// sum_a e_ai s_a over a lattice with e_ai in {-1, 0, 1}: (sum over +1) - (sum over -1)
-template <class L, int Q, class V, int P>
-LBM_DEV V axis_sum(const V (&p)[P], int q0, int i) {
+// sum_a e_ai s_a over a lattice with e_ai in {-1, 0, 1}: (sum over +1) - (sum over -1);
+// get(q) returns plane q
+template <class L, int Q, class V, class Get>
+LBM_DEV V axis_sum(Get &&get, int q0, int i) {
     V pos, neg;
     bool hp = false, hn = false;
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const int e = i == 0 ? L::ex(a) : (i == 1 ? L::ey(a) : L::ez(a));
         if (e > 0) {
-            pos = hp ? pos + p[q0 + a] : p[q0 + a];
+            pos = hp ? pos + get(q0 + a) : get(q0 + a);
             hp = true;
         } else if (e < 0) {
-            neg = hn ? neg + p[q0 + a] : p[q0 + a];
+            neg = hn ? neg + get(q0 + a) : get(q0 + a);
             hn = true;
         }
     }
     return pos - neg;
 }
 
-template <class V, int P>
-LBM_DEV V plane_sum(const V (&p)[P], int q0, int n) {
-    V s = p[q0];
+template <class V, class Get>
+LBM_DEV V plane_sum(Get &&get, int q0, int n) {
+    V s = get(q0);
 #pragma unroll
-    for (int a = 1; a < n; ++a) s = s + p[q0 + a];
+    for (int a = 1; a < n; ++a) s = s + get(q0 + a);
     return s;
 }
 
@@ -204,15 +205,18 @@ LBM_DEV V plane_sum(const V (&p)[P], int q0, int n) {
 template <class L>
 LBM_HD constexpr int lead_sign(int a) { return L::ex(a) ? L::ex(a) : (L::ey(a) ? L::ey(a) : L::ez(a)); }
 
-template <class PL, bool HH, bool HG, class V, class T>
-LBM_DEV void collide_v(V (&p)[PL::P], const CaseDev<T> &c) {
+// The collision over accessors: getm(q) reads plane q for the moments,
+// getr(q) reads it again for its relaxation, put(q, v) takes the relaxed
+// value.  Every plane is read by getr once, before put writes it.
+template <class PL, bool HH, bool HG, class V, class T, class GetM, class GetR, class Put>
+LBM_DEV void collide_g(GetM &&getm, GetR &&getr, Put &&put, const CaseDev<T> &c) {
     using F = typename PL::F;
     using M = typename PL::M;
     constexpr int QF = PL::QF, QM = PL::QM, NB = PL::NB, DIM = F::DIM;
-    const V drho = plane_sum(p, 0, QF);
+    const V drho = plane_sum<V>(getm, 0, QF);
     V j[3];
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) j[i] = axis_sum<F, QF>(p, 0, i);
+    for (int i = 0; i < DIM; ++i) j[i] = axis_sum<F, QF, V>(getm, 0, i);
     const V rho = drho + V(c.ref_rho);
     const V inv = recip_v(rho);
     const T acc[3] = {c.ax, c.ay, c.az};
@@ -227,7 +231,7 @@ LBM_DEV void collide_v(V (&p)[PL::P], const CaseDev<T> &c) {
     if constexpr (HG) {
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
-            dB[k] = plane_sum(p, PL::G0 + k * QM, QM);
+            dB[k] = plane_sum<V>(getm, PL::G0 + k * QM, QM);
             B[k] = dB[k] + V(c.ref_B[k]);
             nB[k] = neg_v(B[k]);
         }
@@ -267,7 +271,7 @@ LBM_DEV void collide_v(V (&p)[PL::P], const CaseDev<T> &c) {
         Tc[pr] = fma_v(t, V(om), V(g) * fma_v(u[i], Fo[k], Fo[i] * u[k])) * V(T(9));
     }
     const V omc = V(c.omc_f);
-    p[0] = fma_v(p[0], omc, A * V(T(F::w(0))));                      // rest: even part A only
+    put(0, fma_v(getr(0), omc, A * V(T(F::w(0)))));                      // rest: even part A only
 #pragma unroll
     for (int a = 1; a < QF; ++a) {
         const int b = F::opp(a);
@@ -294,17 +298,17 @@ LBM_DEV void collide_v(V (&p)[PL::P], const CaseDev<T> &c) {
         }
         const V w = V(T(F::w(ap)));
         const V we = even * w, wo = odd * w;
-        p[ap] = fma_v(p[ap], omc, we + wo);
-        p[am] = fma_v(p[am], omc, we - wo);
+        put(ap, fma_v(getr(ap), omc, we + wo));
+        put(am, fma_v(getr(am), omc, we - wo));
     }
     const T w0 = T(M::w(0)), w1 = T(M::w(1));
     if constexpr (HH) {
-        const V dC = plane_sum(p, PL::H0, QM);
+        const V dC = plane_sum<V>(getm, PL::H0, QM);
         const V C = dC + V(c.ref_C);
         const T oh = c.om_h;
         const V ohc = V(c.omc_h);
         const V ev = V(oh * w1) * dC, f4 = V(T(4) * oh * w1) * C;
-        p[PL::H0] = fma_v(p[PL::H0], ohc, V(oh * w0) * dC);
+        put(PL::H0, fma_v(getr(PL::H0), ohc, V(oh * w0) * dC));
 #pragma unroll
         for (int a = 1; a < QM; ++a) {
             const int b = M::opp(a);
@@ -312,8 +316,8 @@ LBM_DEV void collide_v(V (&p)[PL::P], const CaseDev<T> &c) {
             const int ap = lead_sign<M>(a) > 0 ? a : b, am = lead_sign<M>(a) > 0 ? b : a;
             const int i = M::ex(a) ? 0 : (M::ey(a) ? 1 : 2);
             const V od = f4 * u[i];
-            p[PL::H0 + ap] = fma_v(p[PL::H0 + ap], ohc, ev + od);
-            p[PL::H0 + am] = fma_v(p[PL::H0 + am], ohc, ev - od);
+            put(PL::H0 + ap, fma_v(getr(PL::H0 + ap), ohc, ev + od));
+            put(PL::H0 + am, fma_v(getr(PL::H0 + am), ohc, ev - od));
         }
     }
     if constexpr (HG) {
@@ -324,7 +328,7 @@ LBM_DEV void collide_v(V (&p)[PL::P], const CaseDev<T> &c) {
         for (int k = 0; k < NB; ++k) {
             const int q0 = PL::G0 + k * QM;
             const V ev = og1 * dB[k];
-            p[q0] = fma_v(p[q0], ogc, og0 * dB[k]);
+            put(q0, fma_v(getr(q0), ogc, og0 * dB[k]));
 #pragma unroll
             for (int a = 1; a < QM; ++a) {
                 const int b = M::opp(a);
@@ -332,16 +336,24 @@ LBM_DEV void collide_v(V (&p)[PL::P], const CaseDev<T> &c) {
                 const int ap = lead_sign<M>(a) > 0 ? a : b, am = lead_sign<M>(a) > 0 ? b : a;
                 const int i = M::ex(a) ? 0 : (M::ey(a) ? 1 : 2);
                 if (i == k) {                                        // u_k B_k - B_k u_k = 0
-                    p[q0 + ap] = fma_v(p[q0 + ap], ogc, ev);
-                    p[q0 + am] = fma_v(p[q0 + am], ogc, ev);
+                    put(q0 + ap, fma_v(getr(q0 + ap), ogc, ev));
+                    put(q0 + am, fma_v(getr(q0 + am), ogc, ev));
                 } else {
                     const V od = og4 * fma_v(u[i], B[k], nB[i] * u[k]);
-                    p[q0 + ap] = fma_v(p[q0 + ap], ogc, ev + od);
-                    p[q0 + am] = fma_v(p[q0 + am], ogc, ev - od);
+                    put(q0 + ap, fma_v(getr(q0 + ap), ogc, ev + od));
+                    put(q0 + am, fma_v(getr(q0 + am), ogc, ev - od));
                 }
             }
         }
     }
+}
+
+// in place on a register array
+template <class PL, bool HH, bool HG, class V, class T>
+LBM_DEV void collide_v(V (&p)[PL::P], const CaseDev<T> &c) {
+    auto get = [&](int q) -> V { return p[q]; };
+    auto put = [&](int q, V v) { p[q] = v; };
+    collide_g<PL, HH, HG, V, T>(get, get, put, c);
 }
 
 // one node: FP64 as is, FP32 through F1
@@ -441,6 +453,22 @@ LBM_DEV void coords(const CaseDev<T> &c, int n, int &x, int &y, int &z, int &r) 
     }
 }
 
+// 16-bit populations two to a 32-bit register: plane q in half (q & 1) of word q >> 1
+template <class S> struct Pack16;
+template <> struct Pack16<__half> {
+    LBM_DEV static uint32_t raw(const __half *p) { return __ldg(reinterpret_cast<const unsigned short *>(p)); }
+    LBM_DEV static float get(uint32_t w, int hi) {
+        const __half2 h = *reinterpret_cast<const __half2 *>(&w);
+        return hi ? __high2float(h) : __low2float(h);
+    }
+};
+template <> struct Pack16<__nv_bfloat16> {
+    LBM_DEV static uint32_t raw(const __nv_bfloat16 *p) {
+        return __ldg(reinterpret_cast<const unsigned short *>(p));
+    }
+    LBM_DEV static float get(uint32_t w, int hi) { return __uint_as_float(hi ? (w & 0xffff0000u) : (w << 16)); }
+};
+
 // ------------------------------------------------------------------ fused step
 // One node: pull, (boundary nodes: wall links [lo, hi)), collide, store
 // plane q to out[q * ostride] (out = 0: the node's entries of the target buffer).
@@ -475,6 +503,28 @@ LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDe
     const int ox[3] = {xi[0] - x, 0, xi[2] - x};
     const int oy[3] = {yi[0] - yi[1], 0, yi[2] - yi[1]};
     const int oz[3] = {zi[0] - zi[1], 0, zi[2] - zi[1]};
+    if constexpr (!LINKS && sizeof(S) == 2 && P > 24) {
+        // many 16-bit planes (3D with fields): the pulled values stay packed two
+        // to a register; the moments and then the relaxation each convert them
+        // (the empty asm keeps the second conversion from reusing the first),
+        // and every relaxed value is stored as soon as it is formed.  Same
+        // arithmetic as the array path below.
+        uint32_t pk[(P + 1) / 2];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const uint32_t w = Pack16<S>::raw(sp + (q * st32 + ox[1 - PL::ex(q)] + oy[1 - PL::ey(q)] + oz[1 - PL::ez(q)]));
+            pk[q >> 1] = (q & 1) ? (pk[q >> 1] | (w << 16)) : w;
+        }
+        auto getm = [&](int q) -> F1 { return F1(Pack16<S>::get(pk[q >> 1], q & 1)); };
+        auto getr = [&](int q) -> F1 {
+            uint32_t w = pk[q >> 1];
+            asm("" : "+r"(w));
+            return F1(Pack16<S>::get(w, q & 1));
+        };
+        auto put = [&](int q, F1 v) { Codec<S>::st(dp + q * os, v.v); };
+        collide_g<PL, HH, HG, F1, float>(getm, getr, put, c);
+        return;
+    }
     T p[P];
 #pragma unroll
     for (int q = 0; q < P; ++q)
