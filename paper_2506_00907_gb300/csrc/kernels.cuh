@@ -657,18 +657,22 @@ __global__ void __launch_bounds__(256, MINB) k_step_pair(const StepParams<float>
 
 // Boundary nodes: one thread per record of the compact boundary list (the
 // nodes of a wall row are consecutive records, so a warp works along a wall).
-// It runs beside the bulk step on a side stream, so it is built lean (links
-// one at a time, a small register budget): its blocks then take few of the
-// registers that the bulk step's blocks would otherwise use.  FP64 keeps the
-// full budget (its link arithmetic would spill).
+// It runs beside the bulk step on a side stream.  In 2D and for 16-bit 3D
+// storage it is built lean (links one at a time, a small register budget), so
+// that its blocks take few of the registers the bulk step's blocks would use;
+// 3D FP32 walls (many links per node, on curved walls) run faster with four
+// links evaluated together and the full budget, and FP64 needs that budget.
+// (Measured on GB300: Hartmann batch, MHD pipe FP32 and FP16.)
+template <class S, int DIM>
+constexpr bool boundary_lean() { return sizeof(S) == 2 || (DIM == 2 && sizeof(S) == 4); }
 template <int DIM, bool HH, bool HG, class S>
-__global__ void __launch_bounds__(128, sizeof(S) == 8 ? 1 : (DIM == 2 ? 8 : 6))
+__global__ void __launch_bounds__(128, boundary_lean<S, DIM>() ? (DIM == 2 ? 8 : 6) : 1)
     k_boundary(const StepParams<typename Codec<S>::T> prm) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= prm.nbrec) return;
     const BRec b = prm.brec[i];
     const CaseDev<typename Codec<S>::T> c = prm.cases[b.cs];
-    step_node<DIM, HH, HG, S, true, 1>(prm, c, b.node, b.lo, b.hi);
+    step_node<DIM, HH, HG, S, true, boundary_lean<S, DIM>() ? 1 : 4>(prm, c, b.node, b.lo, b.hi);
 }
 
 // ------------------------------------------------------------------ initial state
