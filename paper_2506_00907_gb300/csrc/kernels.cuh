@@ -664,7 +664,7 @@ __global__ void __launch_bounds__(256, MINB) k_step_pair(const StepParams<float>
 // links evaluated together and the full budget, and FP64 needs that budget.
 // (Measured on GB300: Hartmann batch, MHD pipe FP32 and FP16.)
 template <class S, int DIM>
-constexpr bool boundary_lean() { return sizeof(S) == 2 || (DIM == 2 && sizeof(S) == 4); }
+LBM_HD constexpr bool boundary_lean() { return sizeof(S) == 2 || (DIM == 2 && sizeof(S) == 4); }
 template <int DIM, bool HH, bool HG, class S>
 __global__ void __launch_bounds__(128, boundary_lean<S, DIM>() ? (DIM == 2 ? 8 : 6) : 1)
     k_boundary(const StepParams<typename Codec<S>::T> prm) {
