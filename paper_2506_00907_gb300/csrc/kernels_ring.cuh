@@ -3,13 +3,14 @@
 // Same arithmetic as k_step (kernels.cuh); the populations reach the
 // registers differently.  A block is one producer warp and RING_CW consumer
 // warps.  The producer walks the block's tiles (t = blockIdx.x, + gridDim.x,
-// ...) and, for each, copies every population plane's source window
-// ([start - s_q, start + len - s_q), s_q the flat index offset of e_q, widened
-// to 16 bytes) into a free stage with one cp.async.bulk per plane, completing
-// on the stage's `full` mbarrier.  Consumers wait on `full`, pull their nodes
-// from the windows in shared memory, relax them and store the results
-// straight to global memory; each consumer warp then arrives on the stage's
-// `empty` mbarrier, which frees the stage for the producer.  There is no
+// ...) and, for each, fills a free stage: every population plane's source
+// window ([start - s_q, start + len - s_q), s_q the flat index offset of e_q,
+// widened to 16 bytes) and the tile's node flags with one cp.async.bulk each,
+// completing on the stage's `full` mbarrier, and the tile record and its case
+// descriptor (fetched one tile ahead) written by its lanes.  Consumers wait on
+// `full`, read everything they need from the stage into registers, arrive on
+// the stage's `empty` mbarrier (which frees it for the producer), then relax
+// their nodes and store the results straight to global memory.  There is no
 // block-wide barrier in the loop: the producer runs up to NS tiles ahead.
 //
 // NPL = 2: each consumer lane takes two x-adjacent nodes and relaxes them
