@@ -32,6 +32,8 @@ LINK_DTYPE = np.dtype([
 # fields and link kinds (values are part of the link interface)
 F, H, G0 = 0, 1, 2
 VELOCITY, GIVEN, FLUX, NEUMANN_BFL = 0, 1, 2, 3
+# variants the paper compares against (Eq. 15/16 for every d; simplified flux wall, Eq. 33)
+VELOCITY_EQ15, FLUX_SIMPLIFIED = 4, 5
 
 _lib = None
 

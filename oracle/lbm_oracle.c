@@ -14,7 +14,9 @@
  *   2. equilibria and relaxation                     (Eq. 1-6)
  *   3. propagation to x + e_a for fluid targets      (Eq. 1, 3, 5)
  *   4. every wall link writes the unknown population at its node A
- *      (Sec. 3-4, Eq. 11-29, 34-35, 43), each link independently (pair-wise).
+ *      (Sec. 3-4, Eq. 11-29, 34-35, 43), each link independently (pair-wise);
+ *      two comparison schemes of the paper are selectable per link: Eq. 15/16
+ *      for every d (Sec. 5.1) and the simplified flux wall of Eq. 33 (Sec. 5.4).
  *
  * Readings where the paper is silent (each is listed with its reason in the
  * design notes of the repository):
@@ -28,6 +30,9 @@
  *     phi(E) := phi(A), which needs no E.
  *   - the fluid velocity entering boundary equilibria is the wall velocity u_w
  *     stored in the link (walls are never extrapolated for u).
+ *   - simplified flux wall for d != 1 (Eq. 33 is printed for d = 1 only): the
+ *     increments join the bounced population in the interpolation of Eq. 11/12,
+ *     which is Eq. 33 at d = 1 and Eq. 28 at d = 1/2.
  * Lattice units throughout: dx = dt = 1, c = 1.
  */
 #include <math.h>
@@ -158,7 +163,9 @@ int orc_lattice(int dim, int scalar, int *q, int *e /* q*3 */, double *w) {
 /* Wall links                                                                 */
 /* ------------------------------------------------------------------------- */
 enum { ORC_F = 0, ORC_H = 1, ORC_G0 = 2 };              /* field: f, h, g_k = 2 + k */
-enum { ORC_VELOCITY = 0, ORC_GIVEN = 1, ORC_FLUX = 2, ORC_NEUMANN_BFL = 3 };
+enum { ORC_VELOCITY = 0, ORC_GIVEN = 1, ORC_FLUX = 2, ORC_NEUMANN_BFL = 3,
+       ORC_VELOCITY_EQ15 = 4,   /* Eq. 15 with Eq. 16 for every d (the paper's own scheme before Eq. 43) */
+       ORC_FLUX_SIMPLIFIED = 5  /* flux and move increments added to the bounced population at X (Eq. 33) */ };
 
 typedef struct {
     int32_t node;        /* first fluid node A */
@@ -200,6 +207,11 @@ double orc_eval_link(int dim, const orc_link *lk, const orc_link_in *in) {
          * with Eq. 2 (magnetic terms are even in e and cancel). */
         double rhoX = extrap_X(d, in->phi_E, in->phi_A);
         double incr = orc_feq(dim, a, rhoX, lk->u_wall, NULL) - orc_feq(dim, ap, rhoX, lk->u_wall, NULL);
+        if (lk->kind == ORC_VELOCITY_EQ15) {
+            /* Eq. 15 with Eq. 16 for every d in (0, 1]: extrapolation to Y for
+             * d >= 0.5, which Sec. 5.1 reports unstable for d above about 0.8 */
+            return incr + at_Y(d, in->p_ap_E, in->p_ap_A);
+        }
         if (lk->kind != ORC_VELOCITY) return NAN;
         if (d < 0.5) {
             /* Eq. 15 with Eq. 16 */
@@ -244,6 +256,26 @@ double orc_eval_link(int dim, const orc_link *lk, const orc_link_in *in) {
         double pM_new = pM_rel + dflux + dmove;                              /* Eq. 26 */
         double pE_new = in->p_a_A;                 /* p_a(E,t+1) = p_rel,a(A,t) */
         return ((d - 0.5) * pE_new + pM_new) / (d + 0.5);                    /* Eq. 27 */
+    }
+    case ORC_FLUX_SIMPLIFIED: {
+        /* Eq. 33: the flux increment (Eq. 23) and the moving-wall correction
+         * (Eq. 24), both at phi_X of Eq. 13, are added to the population bounced
+         * at the wall point X, and A is reached by the interpolation of Eq. 11/12
+         * (Eq. 21/22 without flux).  At d = 1 this is Eq. 33 as printed; at d = 1/2
+         * it is Eq. 28. */
+        double phiX = extrap_X(d, in->phi_E, in->phi_A);
+        double dflux = lk->k0 + lk->k1 * phiX;
+        double minus_u[3] = {-uw[0], -uw[1], -uw[2]};
+        double dmove;
+        if (!is_g) {
+            dmove = orc_heq(dim, ap, phiX, minus_u) - orc_heq(dim, a, phiX, minus_u);
+        } else {
+            double BX[3];
+            for (int c = 0; c < 3; ++c) BX[c] = extrap_X(d, in->B_E[c], in->B_A[c]);
+            dmove = orc_geq(dim, ap, k, BX, minus_u) - orc_geq(dim, a, k, BX, minus_u);
+        }
+        if (d < 0.5) return at_Y(d, in->p_ap_E, in->p_ap_A) + dflux + dmove;
+        return ((2.0 * d - 1.0) * in->p_a_A + in->p_ap_A + dflux + dmove) / (2.0 * d);
     }
     case ORC_NEUMANN_BFL:
         if (d < 0.5) return at_Y(d, in->p_ap_E, in->p_ap_A);                 /* Eq. 21 */
@@ -364,11 +396,11 @@ int orc_set_links(orc_sim *s, const orc_link *links, long n) {
         const orc_link *lk = &links[i];
         int field = lk->field;
         if (field == ORC_F) {
-            if (lk->kind != ORC_VELOCITY || lk->dir <= 0 || lk->dir >= qf) { free(seen); return -1; }
+            if ((lk->kind != ORC_VELOCITY && lk->kind != ORC_VELOCITY_EQ15) || lk->dir <= 0 || lk->dir >= qf) { free(seen); return -1; }
         } else if (field == ORC_H) {
-            if (!s->has_h || lk->kind == ORC_VELOCITY || lk->kind > ORC_NEUMANN_BFL || lk->dir <= 0 || lk->dir >= qm) { free(seen); return -1; }
+            if (!s->has_h || (lk->kind != ORC_GIVEN && lk->kind != ORC_FLUX && lk->kind != ORC_NEUMANN_BFL && lk->kind != ORC_FLUX_SIMPLIFIED) || lk->dir <= 0 || lk->dir >= qm) { free(seen); return -1; }
         } else if (field >= ORC_G0 && field < ORC_G0 + s->nB) {
-            if (!s->has_g || lk->kind == ORC_VELOCITY || lk->kind > ORC_NEUMANN_BFL || lk->dir <= 0 || lk->dir >= qm) { free(seen); return -1; }
+            if (!s->has_g || (lk->kind != ORC_GIVEN && lk->kind != ORC_FLUX && lk->kind != ORC_NEUMANN_BFL && lk->kind != ORC_FLUX_SIMPLIFIED) || lk->dir <= 0 || lk->dir >= qm) { free(seen); return -1; }
         } else { free(seen); return -1; }
         if (lk->node < 0 || lk->node >= s->N || s->solid[lk->node]) { free(seen); return -2; }
         lattice L = field == ORC_F ? flow_lattice(s->dim) : scalar_lattice(s->dim);

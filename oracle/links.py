@@ -21,7 +21,7 @@ import math
 
 import numpy as np
 
-from . import LINK_DTYPE, F, H, G0, VELOCITY, GIVEN, FLUX, NEUMANN_BFL, lattice
+from . import LINK_DTYPE, F, H, G0, VELOCITY, GIVEN, FLUX, NEUMANN_BFL, VELOCITY_EQ15, FLUX_SIMPLIFIED, lattice
 
 
 def _fields(dim, has_h, has_g):
@@ -202,7 +202,7 @@ def pipe_links(shape, R, params, has_g=True, center=None):
             e_solid += int(np.sum(solid[En]))
             k0 = np.zeros(nodes.size)
             k1 = np.zeros(nodes.size)
-            if p["kind"] == FLUX:
+            if p["kind"] in (FLUX, FLUX_SIMPLIFIED):
                 bx, by, bz = (x[nodes] - e[a][0]) % nx, (y[nodes] - e[a][1]) % ny, (z[nodes] - e[a][2]) % nz
                 Bn = bx + nx * (by + ny * bz)
                 for i in range(nodes.size):
@@ -225,17 +225,22 @@ def pipe_links(shape, R, params, has_g=True, center=None):
 # ---------------------------------------------------------------------------
 # Random links for parity fuzzing
 # ---------------------------------------------------------------------------
-def random_links(dim, shape, solid, rng, has_h=False, has_g=False, kinds=None, phi_range=None):
+def random_links(dim, shape, solid, rng, has_h=False, has_g=False, kinds=None, phi_range=None, variants=False):
     """Every required link of a given solid mask, with kind, d and wall data
     drawn from ``rng`` (numpy Generator).  d in (0, 1]; both branches of every
     scheme occur.  phi_range maps a field to the (lo, hi) range of its given
-    wall values (default (-0.5, 1.5))."""
+    wall values (default (-0.5, 1.5)).  variants=True also draws the two
+    comparison schemes (Eq. 15/16 for every d, the simplified flux wall)."""
     nx, ny, nz = shape
     solid3 = np.asarray(solid, dtype=np.uint8).reshape(nz, ny, nx)
     out = []
     for field in _fields(dim, has_h, has_g):
         e, _ = lattice(dim, scalar=(field != F))
-        allowed = np.array([VELOCITY] if field == F else (kinds or [GIVEN, FLUX, NEUMANN_BFL]))
+        if field == F:
+            allowed = np.array([VELOCITY, VELOCITY_EQ15] if variants else [VELOCITY])
+        else:
+            allowed = np.array(kinds or ([GIVEN, FLUX, NEUMANN_BFL, FLUX_SIMPLIFIED] if variants
+                                         else [GIVEN, FLUX, NEUMANN_BFL]))
         for a in range(1, len(e)):
             nodes = np.flatnonzero(((solid3 == 0) & (_upstream_solid(solid3, e[a]) == 1)).ravel())
             m = nodes.size
