@@ -91,7 +91,15 @@ typedef enum {
                               step, Eq. 23, 48) with the moving-wall correction Eq. 24,
                               imposed by the M scheme, Eq. 25-27 (Robin, Shercliff Eq. 30,
                               zero gradient with k0 = k1 = 0) */
-    LBM_W_NEUMANN_BFL = 3  /* h or g_k.  Zero gradient by interpolated bounce-back, Eq. 21/22 */
+    LBM_W_NEUMANN_BFL = 3, /* h or g_k.  Zero gradient by interpolated bounce-back, Eq. 21/22 */
+    /* The two comparison schemes the paper evaluates beside its own (selectable
+     * per link; not used by the builders' defaults): */
+    LBM_W_VELOCITY_EQ15 = 4,   /* field f.  Eq. 15 with Eq. 16 for every d, Y extrapolated for
+                                  d > 1/2; Sec. 5.1 replaces it there by Eq. 43 because it is
+                                  unstable (it diverges on walls for every d > 1/2 tried) */
+    LBM_W_FLUX_SIMPLIFIED = 5  /* h or g_k.  Flux and move increments as LBM_W_FLUX, added to the
+                                  population bounced at X and interpolated as in Eq. 11/12: Eq. 33
+                                  at d = 1 (inaccurate at small c_w, Sec. 5.4), Eq. 28 at d = 1/2 */
 } lbm_wall_kind;
 
 /* One wall link: the unknown population of direction dir (pointing from the

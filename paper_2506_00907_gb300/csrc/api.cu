@@ -213,6 +213,12 @@ LinkDev<T> link_dev(const lbm_ctx *c, const CaseHost &cs, const lbm_link &lk) {
         else { ca = (2 * d - 1) / (2 * d); cap = 1 / (2 * d); cphi = inc / (2 * d); }  // Eq. 43
         break;
     }
+    case LBM_W_VELOCITY_EQ15: {
+        // Eq. 15 with Eq. 16 for every d (extrapolated Y for d > 1/2)
+        const double inc = 6.0 * w * eu;
+        cap = 2 * d; cape = 1 - 2 * d; cphi = inc;
+        break;
+    }
     case LBM_W_GIVEN:
         // Eq. 19/34 with Eq. 20/35: p^eq_a(X) + p^eq_a'(X) = 2 w phi_w
         c0 = 2 * w * lk.phi_wall;
@@ -223,13 +229,28 @@ LinkDev<T> link_dev(const lbm_ctx *c, const CaseHost &cs, const lbm_link &lk) {
         if (d < 0.5) { cap = 2 * d; cape = 1 - 2 * d; }                       // Eq. 21
         else { ca = (2 * d - 1) / (2 * d); cap = 1 / (2 * d); }               // Eq. 22
         break;
-    case LBM_W_FLUX: {
-        // M scheme, Eq. 25-27: [ (d - 1/2) p_a(A) + (1/2 - d) p_a'(E) + (1/2 + d) p_a'(A)
-        //                        + dflux + dmove ] / (d + 1/2)
-        const double s = 1.0 / (d + 0.5);
-        ca = (d - 0.5) * s;
-        cap = (0.5 + d) * s;
-        cape = (0.5 - d) * s;
+    case LBM_W_FLUX:
+    case LBM_W_FLUX_SIMPLIFIED: {
+        double s;
+        if (lk.kind == LBM_W_FLUX) {
+            // M scheme, Eq. 25-27: [ (d - 1/2) p_a(A) + (1/2 - d) p_a'(E) + (1/2 + d) p_a'(A)
+            //                        + dflux + dmove ] / (d + 1/2)
+            s = 1.0 / (d + 0.5);
+            ca = (d - 0.5) * s;
+            cap = (0.5 + d) * s;
+            cape = (0.5 - d) * s;
+        } else if (d < 0.5) {
+            // simplified wall, Eq. 11 form: (1 - 2d) p_a'(E) + 2d p_a'(A) + dflux + dmove
+            s = 1.0;
+            cap = 2 * d;
+            cape = 1 - 2 * d;
+        } else {
+            // simplified wall, Eq. 12 form (Eq. 33 at d = 1):
+            // [ (2d - 1) p_a(A) + p_a'(A) + dflux + dmove ] / (2d)
+            s = 1.0 / (2 * d);
+            ca = (2 * d - 1) * s;
+            cap = s;
+        }
         c0 = lk.k0 * s;
         if (lk.field == 1) {
             // dmove = h^eq_a'(-u) - h^eq_a(-u) = 2 w C_X (e.u)/c_h^2 (Eq. 24)
@@ -732,8 +753,9 @@ lbm_status lbm_set_walls(lbm_ctx *ctx, int32_t case_id, const uint8_t *solid, co
         if (!ok_field) return fail(ctx, LBM_EINVAL, "link %zu: field %d not enabled", i, f);
         const Lat &L = f == 0 ? ctx->latf : ctx->latm;
         if (lk.dir < 1 || lk.dir >= L.q) return fail(ctx, LBM_EINVAL, "link %zu: bad direction %d", i, lk.dir);
-        const bool ok_kind = f == 0 ? lk.kind == LBM_W_VELOCITY
-                                    : (lk.kind == LBM_W_GIVEN || lk.kind == LBM_W_FLUX || lk.kind == LBM_W_NEUMANN_BFL);
+        const bool ok_kind = f == 0 ? (lk.kind == LBM_W_VELOCITY || lk.kind == LBM_W_VELOCITY_EQ15)
+                                    : (lk.kind == LBM_W_GIVEN || lk.kind == LBM_W_FLUX || lk.kind == LBM_W_NEUMANN_BFL ||
+                                       lk.kind == LBM_W_FLUX_SIMPLIFIED);
         if (!ok_kind) return fail(ctx, LBM_EINVAL, "link %zu: kind %d not valid for field %d", i, lk.kind, f);
         if (lk.node >= (uint64_t)N || sol[lk.node]) return fail(ctx, LBM_EINVAL, "link %zu: node %u not fluid", i, lk.node);
         if (!(lk.d > 0.0 && lk.d <= 1.0)) return fail(ctx, LBM_EINVAL, "link %zu: d = %g outside (0, 1]", i, lk.d);

@@ -171,7 +171,7 @@ lbm_status lbm_build_pipe(int32_t nx, int32_t ny, int32_t nz, double R, uint32_t
                 double d = (ae + std::sqrt(ae * ae + ee * (R * R - (ay * ay + az * az)))) / ee;
                 d = std::min(1.0, std::max(d, 1e-12));
                 double k0 = 0.0, k1 = 0.0;
-                if (w.kind == LBM_W_FLUX && field != 0) {
+                if ((w.kind == LBM_W_FLUX || w.kind == LBM_W_FLUX_SIMPLIFIED) && field != 0) {
                     const double proj = ey * nrm_y[b] + ez * nrm_z[b];
                     double tot = 0.0;
                     const int bx = (int)(b % nx), by = (int)((b / nx) % ny), bz = (int)(b / ((int64_t)nx * ny));

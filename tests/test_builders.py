@@ -57,25 +57,28 @@ def test_channel_builder_matches_oracle(dim, shape, axis, d_lo, d_hi):
 
 
 @pytest.mark.parametrize("R,shape", [(17.3, (2, 40, 40)), (12.0, (1, 27, 26))])
-@pytest.mark.parametrize("b1", ["insulating", "conducting", "shercliff"])
+@pytest.mark.parametrize("b1", ["insulating", "conducting", "shercliff", "shercliff_simplified"])
 def test_pipe_builder_matches_oracle(R, shape, b1):
+    """Product and oracle pipe builders give the same links (the simplified
+    case also takes the comparison velocity scheme, Eq. 15/16 for every d)."""
     eta = 0.1
+    fkind = O.VELOCITY_EQ15 if b1 == "shercliff_simplified" else O.VELOCITY
     if b1 == "insulating":
         g0 = dict(kind=O.GIVEN, phi_wall=0.0)
     elif b1 == "conducting":
         g0 = dict(kind=O.FLUX)
     else:
-        g0 = dict(kind=O.FLUX, kappa1=-eta / (0.1 * R))
-    params = {O.F: dict(kind=O.VELOCITY), O.G0: g0, O.G0 + 1: dict(kind=O.GIVEN, phi_wall=0.04),
+        g0 = dict(kind=O.FLUX if b1 == "shercliff" else O.FLUX_SIMPLIFIED, kappa1=-eta / (0.1 * R))
+    params = {O.F: dict(kind=fkind), O.G0: g0, O.G0 + 1: dict(kind=O.GIVEN, phi_wall=0.04),
               O.G0 + 2: dict(kind=O.GIVEN, phi_wall=0.0)}
     orc, info = LK.pipe_links(shape, R, params)
-    bcs = [lbm.wall_bc(lbm.LBM_W_VELOCITY), None,
+    bcs = [lbm.wall_bc(fkind), None,
            lbm.wall_bc(g0["kind"], phi_wall=g0.get("phi_wall", 0.0), kappa1=g0.get("kappa1", 0.0)),
            lbm.wall_bc(lbm.LBM_W_GIVEN, phi_wall=0.04), lbm.wall_bc(lbm.LBM_W_GIVEN)]
     solid, prod = lbm.lbm_build_pipe(shape, R, lbm.LBM_FLOW | lbm.LBM_MHD, bcs)
     assert np.array_equal(solid, LK.pipe_solid(shape, R).reshape(-1))
     _compare(prod, orc)
-    if b1 == "shercliff":
+    if b1.startswith("shercliff"):
         # conservative splitting: the flux coefficients of a slice add up to kappa1 * 2 pi R
         fl = prod[prod["field"] == 2]
         for x in range(shape[0]):

@@ -60,13 +60,13 @@ class Pair:
         return out
 
 
-def _random_pair(dim, has_h, has_g, seed, prec=lbm.LBM_FP64, shape=None):
+def _random_pair(dim, has_h, has_g, seed, prec=lbm.LBM_FP64, shape=None, variants=False):
     r = IN.rng(seed)
     shape = shape or ((37, 29, 1) if dim == 2 else (13, 11, 9))
     solid = IN.random_solid(r, shape, fill=0.12)
     # given wall values near the bulk state (|B| well below the lattice pressure keeps the case stable)
     phi_range = {O.H: (0.5, 1.5), O.G0: (-0.05, 0.05), O.G0 + 1: (0.25, 0.35), O.G0 + 2: (-0.05, 0.05)}
-    links = LK.random_links(dim, shape, solid, r, has_h, has_g, phi_range=phi_range)
+    links = LK.random_links(dim, shape, solid, r, has_h, has_g, phi_range=phi_range, variants=variants)
     N = shape[0] * shape[1] * shape[2]
     fields = IN.random_fields(r, N, dim, B0=(0.0, 0.3, 0.0))
     accel = (1e-5, -2e-5, 5e-6 if dim == 3 else 0.0)
@@ -86,6 +86,23 @@ def test_fp64_random_geometry_all_link_kinds(dim, has_h, has_g):
     p.step(39)
     m = p.orc.moments()
     assert np.all(np.abs(m["rho"][p.fluid] - 1.0) < 0.5)          # the case stays well posed
+    for k, v in p.errors().items():
+        assert v < FP64_TOL, (k, v)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fp64_comparison_schemes(dim):
+    """The paper's comparison schemes (Eq. 15/16 for every d, the simplified
+    flux wall of Eq. 33) drawn beside the default kinds on random geometry with
+    every field: FP64 parity with the oracle.  Few steps, because Eq. 15/16
+    beyond d = 1/2 is unstable by design."""
+    p = _random_pair(dim, True, True, seed=300 + dim, variants=True)
+    kinds = set(p.abi_links["kind"].tolist())
+    assert {lbm.LBM_W_VELOCITY_EQ15, lbm.LBM_W_FLUX_SIMPLIFIED} <= kinds
+    p.step(1)
+    for k, v in p.errors().items():
+        assert v < FP64_TOL, (k, v)
+    p.step(15)
     for k, v in p.errors().items():
         assert v < FP64_TOL, (k, v)
 
