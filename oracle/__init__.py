@@ -34,6 +34,8 @@ F, H, G0 = 0, 1, 2
 VELOCITY, GIVEN, FLUX, NEUMANN_BFL = 0, 1, 2, 3
 # variants the paper compares against (Eq. 15/16 for every d; simplified flux wall, Eq. 33)
 VELOCITY_EQ15, FLUX_SIMPLIFIED = 4, 5
+# open boundary of given density (pressure), Eq. 42/44; the inlet is VELOCITY with a normal u (Eq. 41/43)
+PRESSURE = 6
 
 _lib = None
 

@@ -16,7 +16,9 @@
  *   4. every wall link writes the unknown population at its node A
  *      (Sec. 3-4, Eq. 11-29, 34-35, 43), each link independently (pair-wise);
  *      two comparison schemes of the paper are selectable per link: Eq. 15/16
- *      for every d (Sec. 5.1) and the simplified flux wall of Eq. 33 (Sec. 5.4).
+ *      for every d (Sec. 5.1) and the simplified flux wall of Eq. 33 (Sec. 5.4);
+ *      open boundaries (Sec. 5.1): given velocity is the velocity kind with a
+ *      normal u (Eq. 41, 43), given pressure its own kind (Eq. 42, 44).
  *
  * Readings where the paper is silent (each is listed with its reason in the
  * design notes of the repository):
@@ -33,6 +35,9 @@
  *   - simplified flux wall for d != 1 (Eq. 33 is printed for d = 1 only): the
  *     increments join the bounced population in the interpolation of Eq. 11/12,
  *     which is Eq. 33 at d = 1 and Eq. 28 at d = 1/2.
+ *   - given pressure for d < 1/2 (Eq. 42/44 are printed for d = 1/2 and d >= 1/2):
+ *     the interpolation of Eq. 16 to Y, as for a given C (Eq. 19/20); u(X) is
+ *     extrapolated by Eq. 13; a case with a magnetic field has no pressure kind.
  * Lattice units throughout: dx = dt = 1, c = 1.
  */
 #include <math.h>
@@ -165,7 +170,8 @@ int orc_lattice(int dim, int scalar, int *q, int *e /* q*3 */, double *w) {
 enum { ORC_F = 0, ORC_H = 1, ORC_G0 = 2 };              /* field: f, h, g_k = 2 + k */
 enum { ORC_VELOCITY = 0, ORC_GIVEN = 1, ORC_FLUX = 2, ORC_NEUMANN_BFL = 3,
        ORC_VELOCITY_EQ15 = 4,   /* Eq. 15 with Eq. 16 for every d (the paper's own scheme before Eq. 43) */
-       ORC_FLUX_SIMPLIFIED = 5  /* flux and move increments added to the bounced population at X (Eq. 33) */ };
+       ORC_FLUX_SIMPLIFIED = 5, /* flux and move increments added to the bounced population at X (Eq. 33) */
+       ORC_PRESSURE = 6         /* given density (pressure) of an open boundary, Eq. 42 and 44 */ };
 
 typedef struct {
     int32_t node;        /* first fluid node A */
@@ -185,6 +191,7 @@ typedef struct {
     double p_ap_E;       /* p_rel,a'(E,t)                              */
     double phi_A, phi_E; /* rho (f), C (h) or B_k (g_k) at A and E     */
     double B_A[3], B_E[3]; /* full B at A and E (g fields only)        */
+    double u_A[3], u_E[3]; /* fluid velocity at A and E (f field only)  */
 } orc_link_in;
 
 /* Eq. 13: extrapolation of an unknown macroscopic quantity to the wall point X */
@@ -207,6 +214,19 @@ double orc_eval_link(int dim, const orc_link *lk, const orc_link_in *in) {
          * with Eq. 2 (magnetic terms are even in e and cancel). */
         double rhoX = extrap_X(d, in->phi_E, in->phi_A);
         double incr = orc_feq(dim, a, rhoX, lk->u_wall, NULL) - orc_feq(dim, ap, rhoX, lk->u_wall, NULL);
+        if (lk->kind == ORC_PRESSURE) {
+            /* Given density rho_w = phi_wall (pressure rho_w c_s^2) on an open
+             * boundary.  Zeroth-moment pair conservation (the flow form of
+             * Eq. 18-19): p_a(A) = f^eq_a(X) + f^eq_a'(X) - f_rel,a'(Y), with
+             * u(X,t) extrapolated by Eq. 13 (the outlet velocity is unknown) and
+             * Y by Eq. 16 for d < 1/2; Eq. 44 for d >= 1/2; both are Eq. 42 at
+             * d = 1/2. */
+            double uX[3];
+            for (int c = 0; c < 3; ++c) uX[c] = extrap_X(d, in->u_E[c], in->u_A[c]);
+            double sum_eq = orc_feq(dim, a, lk->phi_wall, uX, NULL) + orc_feq(dim, ap, lk->phi_wall, uX, NULL);
+            if (d < 0.5) return sum_eq - at_Y(d, in->p_ap_E, in->p_ap_A);
+            return ((2.0 * d - 1.0) * in->p_a_A - in->p_ap_A + sum_eq) / (2.0 * d);
+        }
         if (lk->kind == ORC_VELOCITY_EQ15) {
             /* Eq. 15 with Eq. 16 for every d in (0, 1]: extrapolation to Y for
              * d >= 0.5, which Sec. 5.1 reports unstable for d above about 0.8 */
@@ -396,7 +416,8 @@ int orc_set_links(orc_sim *s, const orc_link *links, long n) {
         const orc_link *lk = &links[i];
         int field = lk->field;
         if (field == ORC_F) {
-            if ((lk->kind != ORC_VELOCITY && lk->kind != ORC_VELOCITY_EQ15) || lk->dir <= 0 || lk->dir >= qf) { free(seen); return -1; }
+            if ((lk->kind != ORC_VELOCITY && lk->kind != ORC_VELOCITY_EQ15 && !(lk->kind == ORC_PRESSURE && !s->has_g))
+                || lk->dir <= 0 || lk->dir >= qf) { free(seen); return -1; }
         } else if (field == ORC_H) {
             if (!s->has_h || (lk->kind != ORC_GIVEN && lk->kind != ORC_FLUX && lk->kind != ORC_NEUMANN_BFL && lk->kind != ORC_FLUX_SIMPLIFIED) || lk->dir <= 0 || lk->dir >= qm) { free(seen); return -1; }
         } else if (field >= ORC_G0 && field < ORC_G0 + s->nB) {
@@ -557,6 +578,7 @@ static void link_inputs(const orc_sim *s, const orc_link *lk, orc_link *eff, orc
         in->phi_A = s->B[3 * A + k]; in->phi_E = s->B[3 * E + k];
     }
     for (int c = 0; c < 3; ++c) { in->B_A[c] = s->B[3 * A + c]; in->B_E[c] = s->B[3 * E + c]; }
+    for (int c = 0; c < 3; ++c) { in->u_A[c] = s->u[3 * A + c]; in->u_E[c] = s->u[3 * E + c]; }
 }
 
 /* Step 4: every link sets its unknown population at t+1 */
