@@ -97,9 +97,15 @@ typedef enum {
     LBM_W_VELOCITY_EQ15 = 4,   /* field f.  Eq. 15 with Eq. 16 for every d, Y extrapolated for
                                   d > 1/2; Sec. 5.1 replaces it there by Eq. 43 because it is
                                   unstable (it diverges on walls for every d > 1/2 tried) */
-    LBM_W_FLUX_SIMPLIFIED = 5  /* h or g_k.  Flux and move increments as LBM_W_FLUX, added to the
+    LBM_W_FLUX_SIMPLIFIED = 5, /* h or g_k.  Flux and move increments as LBM_W_FLUX, added to the
                                   population bounced at X and interpolated as in Eq. 11/12: Eq. 33
                                   at d = 1 (inaccurate at small c_w, Sec. 5.4), Eq. 28 at d = 1/2 */
+    /* Open boundaries (Sec. 5.1): a given inlet velocity is LBM_W_VELOCITY with
+     * u_wall normal to the boundary (Eq. 41, 43). */
+    LBM_W_PRESSURE = 6         /* field f, cases without LBM_MHD.  Given density rho_w = phi_wall
+                                  (pressure rho_w c_s^2): f^eq_a(X) + f^eq_a'(X) - f_rel,a'(Y) with
+                                  Y by Eq. 16 for d < 1/2, Eq. 44 for d >= 1/2 (Eq. 42 at d = 1/2);
+                                  u(X) extrapolated by Eq. 13 from the fluid velocities at A and E */
 } lbm_wall_kind;
 
 /* One wall link: the unknown population of direction dir (pointing from the
@@ -114,7 +120,7 @@ typedef struct {
     uint8_t reserved;
     double d;
     double u_wall[3];              /* wall velocity (never extrapolated) */
-    double phi_wall;               /* LBM_W_GIVEN: C or B_k on the wall */
+    double phi_wall;               /* LBM_W_GIVEN: C or B_k on the wall; LBM_W_PRESSURE: density */
     double k0, k1;                 /* LBM_W_FLUX: increment k0 + k1 * phi_X per step */
 } lbm_link;
 

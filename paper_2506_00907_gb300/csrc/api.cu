@@ -219,6 +219,18 @@ LinkDev<T> link_dev(const lbm_ctx *c, const CaseHost &cs, const lbm_link &lk) {
         cap = 2 * d; cape = 1 - 2 * d; cphi = inc;
         break;
     }
+    case LBM_W_PRESSURE: {
+        // given density rho_w on an open boundary: f^eq_a(X) + f^eq_a'(X) - f_rel,a'(Y) for
+        // d < 1/2 (Y by Eq. 16), Eq. 44 for d >= 1/2 (Eq. 42 at d = 1/2), with
+        // f^eq_a + f^eq_a' = 2 w rho_w [1 + 4.5 (e.u_X)^2 - 1.5 |u_X|^2] and u_X by Eq. 13
+        const double s = d < 0.5 ? 1.0 : 1.0 / (2 * d);
+        c0 = 2 * w * lk.phi_wall * s;
+        cphi = 2 * w * lk.phi_wall * s;        // coefficient of the quadratic u terms (LINK_NEED_U)
+        if (d < 0.5) { cap = -2 * d; cape = -(1 - 2 * d); }
+        else { ca = (2 * d - 1) * s; cap = -s; }
+        for (int j = 0; j < 3; ++j) cB[j] = e[j];   // direction of the unknown population
+        break;
+    }
     case LBM_W_GIVEN:
         // Eq. 19/34 with Eq. 20/35: p^eq_a(X) + p^eq_a'(X) = 2 w phi_w
         c0 = 2 * w * lk.phi_wall;
@@ -273,8 +285,11 @@ LinkDev<T> link_dev(const lbm_ctx *c, const CaseHost &cs, const lbm_link &lk) {
     r.plane_a = (uint8_t)(base + a);
     r.plane_ap = (uint8_t)(base + ap);
     r.phi_plane0 = (uint8_t)base;
-    r.flags = (uint8_t)((cphi != 0.0 ? LINK_NEED_PHI : 0) |
-                        ((cB[0] != 0.0 || cB[1] != 0.0 || cB[2] != 0.0) ? LINK_NEED_B : 0));
+    if (lk.kind == LBM_W_PRESSURE)
+        r.flags = LINK_NEED_U;
+    else
+        r.flags = (uint8_t)((cphi != 0.0 ? LINK_NEED_PHI : 0) |
+                            ((cB[0] != 0.0 || cB[1] != 0.0 || cB[2] != 0.0) ? LINK_NEED_B : 0));
     r.d = T(d);
     r.ca = T(ca);
     r.cap = T(cap);
@@ -753,7 +768,8 @@ lbm_status lbm_set_walls(lbm_ctx *ctx, int32_t case_id, const uint8_t *solid, co
         if (!ok_field) return fail(ctx, LBM_EINVAL, "link %zu: field %d not enabled", i, f);
         const Lat &L = f == 0 ? ctx->latf : ctx->latm;
         if (lk.dir < 1 || lk.dir >= L.q) return fail(ctx, LBM_EINVAL, "link %zu: bad direction %d", i, lk.dir);
-        const bool ok_kind = f == 0 ? (lk.kind == LBM_W_VELOCITY || lk.kind == LBM_W_VELOCITY_EQ15)
+        const bool ok_kind = f == 0 ? (lk.kind == LBM_W_VELOCITY || lk.kind == LBM_W_VELOCITY_EQ15 ||
+                                       (lk.kind == LBM_W_PRESSURE && !ctx->hg))
                                     : (lk.kind == LBM_W_GIVEN || lk.kind == LBM_W_FLUX || lk.kind == LBM_W_NEUMANN_BFL ||
                                        lk.kind == LBM_W_FLUX_SIMPLIFIED);
         if (!ok_kind) return fail(ctx, LBM_EINVAL, "link %zu: kind %d not valid for field %d", i, lk.kind, f);

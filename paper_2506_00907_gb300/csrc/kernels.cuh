@@ -400,6 +400,33 @@ LBM_DEV T eval_link(const LinkDev<T> &L, const S *src, const CaseDev<T> &c) {
         phE += L.ref_phi;
         v += L.cphi * ((T(1) + L.d) * phA - L.d * phE);
     }
+    // given-pressure links exist only in cases without a magnetic field
+    if constexpr (PL::G0 == PL::P) if (L.flags & LINK_NEED_U) {
+        // fluid velocity at A and E from the relaxed populations:
+        // u = (sum e s_rel - F/2) / rho, with F = rho * accel
+        T rA = 0, rE = 0, jA[3] = {0, 0, 0}, jE[3] = {0, 0, 0};
+#pragma unroll
+        for (int q = 0; q < PL::QF; ++q) {
+            const T vA = Codec<S>::ld(src + (q * st + L.nodeA));
+            const T vE = Codec<S>::ld(src + (q * st + L.nodeE));
+            rA += vA;
+            rE += vE;
+            if (PL::ex(q)) { jA[0] += T(PL::ex(q)) * vA; jE[0] += T(PL::ex(q)) * vE; }
+            if (PL::ey(q)) { jA[1] += T(PL::ey(q)) * vA; jE[1] += T(PL::ey(q)) * vE; }
+            if (PL::ez(q)) { jA[2] += T(PL::ez(q)) * vA; jE[2] += T(PL::ez(q)) * vE; }
+        }
+        rA += L.ref_phi;
+        rE += L.ref_phi;
+        const T acc[3] = {c.ax, c.ay, c.az};
+        T eu = 0, uu = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const T uX = (T(1) + L.d) * (jA[k] / rA - T(0.5) * acc[k]) - L.d * (jE[k] / rE - T(0.5) * acc[k]);
+            eu += L.cB[k] * uX;
+            uu += uX * uX;
+        }
+        v += L.cphi * (T(4.5) * eu * eu - T(1.5) * uu);
+    }
     if constexpr (PL::G0 < PL::P) {
         if (L.flags & LINK_NEED_B) {
 #pragma unroll

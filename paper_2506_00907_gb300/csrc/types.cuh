@@ -36,7 +36,9 @@ struct CaseDev {
 // with the relaxed populations at t, phi_X = -d phi(E) + (1 + d) phi(A)
 // (Eq. 13) of the link's own field (rho for f, C for h, B_k for g_k), and
 // B_X the extrapolated magnetic field vector (moving flux walls of g, Eq. 24).
-enum : uint8_t { LINK_NEED_PHI = 1, LINK_NEED_B = 2 };
+// Given-pressure links (open boundaries, Eq. 42/44) add cphi * (4.5 (e.u_X)^2 -
+// 1.5 |u_X|^2) with u_X = -d u(E) + (1 + d) u(A) (Eq. 13) and e = cB (LINK_NEED_U).
+enum : uint8_t { LINK_NEED_PHI = 1, LINK_NEED_B = 2, LINK_NEED_U = 4 };
 
 template <class T>
 struct alignas(16) LinkDev {
@@ -45,7 +47,7 @@ struct alignas(16) LinkDev {
     uint8_t plane_a;      // plane of the unknown direction a
     uint8_t plane_ap;     // plane of the opposite direction a'
     uint8_t phi_plane0;   // first plane of the link's field
-    uint8_t flags;        // LINK_NEED_PHI | LINK_NEED_B
+    uint8_t flags;        // LINK_NEED_PHI | LINK_NEED_B | LINK_NEED_U
     T d, c0, ca, cap, cape, cphi;
     T cB[3];
     T ref_phi;            // storage reference of the link's field (phi = sum of stored + ref_phi)

@@ -18,6 +18,7 @@ LBM_FP64, LBM_FP32, LBM_FP16S, LBM_BF16S = 0, 1, 2, 3
 LBM_FLOW, LBM_CD, LBM_MHD = 1, 2, 4
 LBM_W_VELOCITY, LBM_W_GIVEN, LBM_W_FLUX, LBM_W_NEUMANN_BFL = 0, 1, 2, 3
 LBM_W_VELOCITY_EQ15, LBM_W_FLUX_SIMPLIFIED = 4, 5      # the paper's comparison schemes
+LBM_W_PRESSURE = 6                                      # open boundary of given density (Eq. 42, 44)
 FIELD_F, FIELD_H, FIELD_G = 0, 1, 2
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S, "bf16s": LBM_BF16S}
 

@@ -107,6 +107,89 @@ def test_fp64_comparison_schemes(dim):
         assert v < FP64_TOL, (k, v)
 
 
+def _open_channel_pair(dim, d, prec=lbm.LBM_FP64, has_h=False, steps_shape=None):
+    """Channel open along x (Sec. 5.1): inlet of given velocity, outlet of
+    given density (Eq. 42/44), static walls at random distances along y (and z),
+    body force, and a concentration with a given inlet value and a zero-gradient
+    outlet when has_h."""
+    shape = steps_shape or ((45, 14, 1) if dim == 2 else (23, 9, 8))
+    walls = {1: (0.3, shape[1] - 1.6)}
+    if dim == 3:
+        walls[2] = (0.55, shape[2] - 1.1)
+    walls[0] = (1 - d, shape[0] - 2 + d)
+    U = (0.03, 0.004, -0.002 if dim == 3 else 0.0)
+    p = {(0, 0, O.F): dict(kind=O.VELOCITY, u_wall=U), (0, 1, O.F): dict(kind=O.PRESSURE, phi_wall=1.01)}
+    for ax in walls:
+        if ax != 0:
+            p[(ax, 0, O.F)] = dict(kind=O.VELOCITY)
+            p[(ax, 1, O.F)] = dict(kind=O.VELOCITY, u_wall=(0.01, 0, 0))
+    if has_h:
+        p[(0, 0, O.H)] = dict(kind=O.GIVEN, phi_wall=1.5, u_wall=U)
+        p[(0, 1, O.H)] = dict(kind=O.NEUMANN_BFL)
+        for ax in walls:
+            if ax != 0:
+                p[(ax, 0, O.H)] = dict(kind=O.FLUX, kappa0=0.002, kappa1=-0.01)
+                p[(ax, 1, O.H)] = dict(kind=O.GIVEN, phi_wall=0.8)
+    solid = LK.box_solid(shape, walls)
+    links = LK.box_links(dim, shape, walls, p, has_h=has_h)
+    r = IN.rng(400 + dim)
+    N = shape[0] * shape[1] * shape[2]
+    fields = IN.random_fields(r, N, dim, B0=(0.0, 0.0, 0.0))
+    accel = (2e-5, 0.0, 0.0)
+    return Pair(dim, shape, solid, links, prec=prec, accel=accel, has_h=has_h, fields=fields, C0=1.0)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("d", [0.3, 0.5, 1.0])
+@pytest.mark.parametrize("has_h", [False, True])
+def test_fp64_open_boundaries(dim, d, has_h):
+    """Given inlet velocity and given outlet pressure (Sec. 5.1, Eq. 41-44):
+    FP64 parity with the oracle over 200 steps from a random initial field."""
+    p = _open_channel_pair(dim, d, has_h=has_h)
+    assert np.any(p.abi_links["kind"] == lbm.LBM_W_PRESSURE)
+    p.step(1)
+    for k, v in p.errors().items():
+        assert v < FP64_TOL, (k, v)
+    p.step(199)
+    for k, v in p.errors().items():
+        assert v < FP64_TOL, (k, v)
+
+
+@pytest.mark.parametrize("prec", [lbm.LBM_FP32, lbm.LBM_FP16S])
+def test_open_boundaries_every_launch_variant(prec):
+    """The pressure links' velocity extrapolation runs in every launch variant
+    with the same arithmetic: variants 1 and 3 (FP32 and 16-bit storage) equal
+    variant 0 bit for bit on an open 2D channel with concentration."""
+    ref = _open_channel_pair(2, 0.7, prec=prec, has_h=True).gpu
+    ref.set_launch(0, 128, 0)
+    ref.step(30)
+    want = ref.get_state()
+    for variant, kw in ((1, dict(min_blocks=2)), (3, dict(blocks_per_sm=1, stages=4, min_blocks=2))):
+        g = _open_channel_pair(2, 0.7, prec=prec, has_h=True).gpu
+        g.set_launch(variant, 256, **kw)
+        g.step(30)
+        assert np.array_equal(g.get_state(), want), variant
+
+
+def test_pressure_kind_is_refused_with_a_magnetic_field():
+    """The C ABI refuses given-pressure links in a case with a magnetic field."""
+    shape = (12, 10, 1)
+    walls = {1: (0.5, 8.5), 0: (0.5, 10.5)}
+    p = {(0, 0, O.F): dict(kind=O.VELOCITY, u_wall=(0.01, 0, 0)), (0, 1, O.F): dict(kind=O.PRESSURE, phi_wall=1.0)}
+    for side in (0, 1):
+        p[(1, side, O.F)] = dict(kind=O.VELOCITY)
+        for k in range(2):
+            p[(0, side, O.G0 + k)] = dict(kind=O.GIVEN, phi_wall=0.0)
+            p[(1, side, O.G0 + k)] = dict(kind=O.GIVEN, phi_wall=0.0)
+    solid = LK.box_solid(shape, walls)
+    links = to_abi_links(LK.box_links(2, shape, walls, p, has_g=True))
+    g = lbm.Solver(lbm.LBM_D2Q9, lbm.LBM_FP64, lbm.LBM_FLOW | lbm.LBM_MHD,
+                   [lbm.make_case(shape, 0.8, 0.9, 0.9, (0, 0, 0), 1.0, 1.0, (0, 0, 0))])
+    with pytest.raises(lbm.LbmError) as ei:
+        g.set_walls(0, solid, links)
+    assert ei.value.status == lbm.LBM_EINVAL
+
+
 def test_fp64_poiseuille_64x32_5000_steps():
     """Body-force channel, 64 x 32 nodes, tau = 0.8, half-grid walls, 5000
     steps: the GPU matches the oracle and both match the analytic parabola to
