@@ -60,6 +60,8 @@ def lib():
         L.orc_populations.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, ctypes.c_int]
         L.orc_steps.restype = ctypes.c_long
         L.orc_steps.argtypes = [ctypes.c_void_p]
+        L.orc_set_wall_motion.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]
+        L.orc_set_wall_motion.restype = ctypes.c_int
         L.orc_sums.argtypes = [ctypes.c_void_p, dp]
         L.orc_feq.restype = ctypes.c_double
         L.orc_feq.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp]
@@ -176,6 +178,11 @@ class OracleSim:
         rc = lib().orc_set_links(self._h, links.ctypes.data_as(ctypes.c_void_p), len(links))
         if rc != 0:
             raise ValueError("oracle rejected the link list (code %d)" % rc)
+
+    def set_wall_motion(self, omega, phase=0.0):
+        """Oscillating velocity walls: u_wall * cos(omega t + phase) (Eq. 45)."""
+        if lib().orc_set_wall_motion(self._h, omega, phase) != 0:
+            raise ValueError("wall motion needs static flux walls for h and g")
 
     def init(self, rho=None, u=None, C=None, B=None, rho0=1.0, C0=0.0, B0=(0.0, 0.0, 0.0)):
         def flat(a, k):

@@ -17,6 +17,17 @@ def couette(y, y0, y1, u0, u1):
     return u0 + (u1 - u0) * (y - y0) / (y1 - y0)
 
 
+def stokes_oscillating(y, t, y0, y1, U, omega, nu, phase=0.0):
+    """Stokes' second problem in a channel (Sec. 5.2, Eq. 45): the wall at y1
+    moves with U cos(omega t + phase), the wall at y0 is at rest.  The periodic
+    state of u_t = nu u_yy is Re[U e^{i(omega t + phase)} sinh(k (y - y0)) /
+    sinh(k (y1 - y0))] with k = (1 + i) sqrt(omega / (2 nu)), the solution of
+    the boundary-value problem nu w'' = i omega w, w(y0) = 0, w(y1) = U."""
+    k = (1 + 1j) * np.sqrt(omega / (2 * nu))
+    w = U * np.sinh(k * (np.asarray(y, dtype=np.float64) - y0)) / np.sinh(k * (y1 - y0))
+    return np.real(w * np.exp(1j * (omega * t + phase)))
+
+
 def poiseuille(y, y0, y1, accel, nu):
     """Body-force-driven channel flow nu u'' + a = 0, u(y0) = u(y1) = 0."""
     y = np.asarray(y, dtype=np.float64)

@@ -322,6 +322,8 @@ typedef struct {
     orc_link *links;
     long nlinks;
     long steps;
+    int motion;                /* wall motion (Sec. 5.2): velocity links of f move with u_wall cos(omega t + phase) */
+    double omega, phase;
     int nthreads;
 } orc_sim;
 
@@ -579,6 +581,12 @@ static void link_inputs(const orc_sim *s, const orc_link *lk, orc_link *eff, orc
     }
     for (int c = 0; c < 3; ++c) { in->B_A[c] = s->B[3 * A + c]; in->B_E[c] = s->B[3 * E + c]; }
     for (int c = 0; c < 3; ++c) { in->u_A[c] = s->u[3 * A + c]; in->u_E[c] = s->u[3 * E + c]; }
+    if (s->motion && lk->field == ORC_F && (lk->kind == ORC_VELOCITY || lk->kind == ORC_VELOCITY_EQ15)) {
+        /* oscillating wall, Eq. 45: the wall velocity of the step t -> t+1 is
+         * taken at t, the time of f^eq(X, t) in Eq. 41 and 43 */
+        double sc = cos(s->omega * (double)s->steps + s->phase);
+        for (int c = 0; c < 3; ++c) eff->u_wall[c] = lk->u_wall[c] * sc;
+    }
 }
 
 /* Step 4: every link sets its unknown population at t+1 */
@@ -642,6 +650,24 @@ long orc_populations(orc_sim *s, int which, double *out, int set) {
 }
 
 long orc_steps(const orc_sim *s) { return s->steps; }
+
+/* Oscillating walls (Sec. 5.2, Eq. 45): from now on every velocity link of f
+ * uses u_wall * cos(omega * t + phase) in the step from t to t + 1, t counting
+ * the steps since the last initialisation.  The moving-wall term of flux links
+ * of h or g would need the same motion, so a link list holding such a link with
+ * a nonzero wall velocity is refused (-1).  Set the links first. */
+int orc_set_wall_motion(orc_sim *s, double omega, double phase) {
+    for (long i = 0; i < s->nlinks; ++i) {
+        const orc_link *lk = &s->links[i];
+        if (lk->field != ORC_F && (lk->kind == ORC_FLUX || lk->kind == ORC_FLUX_SIMPLIFIED) &&
+            (lk->u_wall[0] != 0.0 || lk->u_wall[1] != 0.0 || lk->u_wall[2] != 0.0))
+            return -1;
+    }
+    s->motion = 1;
+    s->omega = omega;
+    s->phase = phase;
+    return 0;
+}
 
 /* FP64 sums over fluid nodes of rho, C and B_k at the current time (reduction row):
  * out[0] = sum rho, out[1] = sum C, out[2..4] = sum B_k, out[5] = number of
