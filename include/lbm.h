@@ -173,6 +173,19 @@ lbm_status lbm_step(lbm_ctx *ctx, int32_t nsteps);
  * graph that lbm_step replays.  Errors: LBM_EINVAL, LBM_ECUDA. */
 lbm_status lbm_set_graph(lbm_ctx *ctx, int32_t steps_per_graph);
 
+/* Oscillating velocity walls of one case (Stokes' second problem, Sec. 5.2,
+ * Eq. 45): from now on every velocity link of field f in the case (kinds
+ * LBM_W_VELOCITY and LBM_W_VELOCITY_EQ15) uses u_wall * cos(omega * t + phase)
+ * in the step from t to t + 1, the wall velocity taken at t as f^eq(X, t) in
+ * Eq. 41/43.  t counts the context's steps since the latest call of this
+ * function (for any case); a one-block kernel refreshes the cases' factors
+ * ahead of every step, also inside captured graphs (existing graphs are
+ * dropped).  Flux walls of h or g with a nonzero wall velocity would need the
+ * same motion in their moving-wall term: a case holding one is refused, here
+ * and in later lbm_set_walls calls.  Synchronises.  Errors: LBM_EINVAL (case id,
+ * non-finite omega or phase, moving flux wall), LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_set_wall_motion(lbm_ctx *ctx, int32_t case_id, double omega, double phase);
+
 /* Macroscopic fields of one case at the current time, FP64, host arrays of N
  * (rho, C) or 3N (u, B) entries; NULL skips.  Solid nodes report 0.
  * Synchronises.  Errors: LBM_EINVAL, LBM_ECUDA. */

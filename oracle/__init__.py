@@ -180,7 +180,8 @@ class OracleSim:
             raise ValueError("oracle rejected the link list (code %d)" % rc)
 
     def set_wall_motion(self, omega, phase=0.0):
-        """Oscillating velocity walls: u_wall * cos(omega t + phase) (Eq. 45)."""
+        """Oscillating velocity walls: u_wall * cos(omega t + phase) (Eq. 45),
+        t counting the steps from this call on."""
         if lib().orc_set_wall_motion(self._h, omega, phase) != 0:
             raise ValueError("wall motion needs static flux walls for h and g")
 

@@ -324,6 +324,7 @@ typedef struct {
     long steps;
     int motion;                /* wall motion (Sec. 5.2): velocity links of f move with u_wall cos(omega t + phase) */
     double omega, phase;
+    long motion_t;             /* t: steps since the motion was set */
     int nthreads;
 } orc_sim;
 
@@ -584,7 +585,7 @@ static void link_inputs(const orc_sim *s, const orc_link *lk, orc_link *eff, orc
     if (s->motion && lk->field == ORC_F && (lk->kind == ORC_VELOCITY || lk->kind == ORC_VELOCITY_EQ15)) {
         /* oscillating wall, Eq. 45: the wall velocity of the step t -> t+1 is
          * taken at t, the time of f^eq(X, t) in Eq. 41 and 43 */
-        double sc = cos(s->omega * (double)s->steps + s->phase);
+        double sc = cos(s->omega * (double)s->motion_t + s->phase);
         for (int c = 0; c < 3; ++c) eff->u_wall[c] = lk->u_wall[c] * sc;
     }
 }
@@ -621,6 +622,7 @@ void orc_step(orc_sim *s, int nsteps) {
         t = s->h; s->h = s->hn; s->hn = t;
         t = s->g; s->g = s->gn; s->gn = t;
         s->steps++;
+        s->motion_t++;
     }
 }
 
@@ -653,7 +655,7 @@ long orc_steps(const orc_sim *s) { return s->steps; }
 
 /* Oscillating walls (Sec. 5.2, Eq. 45): from now on every velocity link of f
  * uses u_wall * cos(omega * t + phase) in the step from t to t + 1, t counting
- * the steps since the last initialisation.  The moving-wall term of flux links
+ * the steps since this call.  The moving-wall term of flux links
  * of h or g would need the same motion, so a link list holding such a link with
  * a nonzero wall velocity is refused (-1).  Set the links first. */
 int orc_set_wall_motion(orc_sim *s, double omega, double phase) {
@@ -666,6 +668,7 @@ int orc_set_wall_motion(orc_sim *s, double omega, double phase) {
     s->motion = 1;
     s->omega = omega;
     s->phase = phase;
+    s->motion_t = 0;
     return 0;
 }
 

@@ -96,6 +96,11 @@ struct lbm_ctx {
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int graph_steps = 0;
     int64_t steps = 0;
+    // oscillating velocity walls (lbm_set_wall_motion): per case omega, phase, on
+    bool motion = false;
+    std::vector<double> h_motion;
+    double *d_motion = nullptr;
+    long long *d_clock = nullptr;      // steps since the last lbm_set_wall_motion
     int sm_count = 1;
     KernelSet ks{};
     std::string err;
@@ -128,6 +133,13 @@ lbm_status fail(lbm_ctx *c, lbm_status st, const char *fmt, ...) {
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 bool finite3(const double *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+// A flux wall of h or g whose wall moves would need the same oscillation in
+// its moving-wall term; such links and wall motion exclude each other.
+bool moving_flux_link(const lbm_link &lk) {
+    return lk.field != 0 && (lk.kind == LBM_W_FLUX || lk.kind == LBM_W_FLUX_SIMPLIFIED) &&
+           (lk.u_wall[0] != 0.0 || lk.u_wall[1] != 0.0 || lk.u_wall[2] != 0.0);
+}
 
 // base plane of a field: 0 f, 1 h, 2 + k g_k
 int field_base(const lbm_ctx *c, int field) {
@@ -184,6 +196,7 @@ CaseDev<T> case_dev(const lbm_ctx *c, const CaseHost &cs) {
         d.B0[k] = T(cs.cfg.B0[k]);
     }
     if (c->dim == 2) { d.ref_B[2] = T(0); d.B0[2] = T(0); }
+    d.wall_scale = T(1);
     return d;
 }
 
@@ -290,6 +303,8 @@ LinkDev<T> link_dev(const lbm_ctx *c, const CaseHost &cs, const lbm_link &lk) {
     else
         r.flags = (uint8_t)((cphi != 0.0 ? LINK_NEED_PHI : 0) |
                             ((cB[0] != 0.0 || cB[1] != 0.0 || cB[2] != 0.0) ? LINK_NEED_B : 0));
+    // the velocity term of a moving velocity wall follows the case's wall motion (Eq. 45)
+    if ((lk.kind == LBM_W_VELOCITY || lk.kind == LBM_W_VELOCITY_EQ15) && cphi != 0.0) r.flags |= LINK_WALL_T;
     r.d = T(d);
     r.ca = T(ca);
     r.cap = T(cap);
@@ -477,9 +492,28 @@ int step_grid(const lbm_ctx *c) {
     return std::max(1, std::min(c->ntiles, c->launch.blocks_per_sm * c->sm_count));
 }
 
+// Wall motion of the coming step (Eq. 45): wall_scale = cos(omega t + phase) of
+// every moving case at t = the device clock, which then advances by one.  One
+// block; launched ahead of each step (also inside captured graphs) only when a
+// case has wall motion.
+template <class T>
+__global__ void k_wall_clock(CaseDev<T> *cases, const double *motion, int ncases, long long *clock) {
+    const long long t = *clock;
+    for (int i = threadIdx.x; i < ncases; i += blockDim.x)
+        if (motion[3 * i + 2] != 0.0) cases[i].wall_scale = T(cos(motion[3 * i] * (double)t + motion[3 * i + 1]));
+    __syncthreads();
+    if (threadIdx.x == 0) *clock = t + 1;
+}
+
 template <class T>
 cudaError_t launch_step_t(lbm_ctx *ctx) {
     const StepParams<T> p = step_params<T>(ctx);
+    if (ctx->motion) {
+        k_wall_clock<T><<<1, 256, 0, ctx->stream>>>(static_cast<CaseDev<T> *>(ctx->d_cases), ctx->d_motion,
+                                                     (int)ctx->cases.size(), ctx->d_clock);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     if (ctx->launch.variant == 1) {
         // bulk-copy variant: one launch, boundary nodes included
         BulkParams bp;
@@ -577,7 +611,8 @@ void free_ctx(lbm_ctx *c) {
     drop_graphs(c);
     void *ptrs[] = {c->pool[0], c->pool[1], c->d_flags, c->d_cases, c->d_tiles, c->d_case_tile_lo, c->d_tile_brec,
                     c->d_tile_fluid, c->d_rtiles,
-                    c->d_brec, c->d_links, c->d_snap, c->d_part, c->d_red, c->d_mom, c->d_err};
+                    c->d_brec, c->d_links, c->d_snap, c->d_part, c->d_red, c->d_mom, c->d_err,
+                    c->d_motion, c->d_clock};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_red) cudaFreeHost(c->h_red);
@@ -773,6 +808,8 @@ lbm_status lbm_set_walls(lbm_ctx *ctx, int32_t case_id, const uint8_t *solid, co
                                     : (lk.kind == LBM_W_GIVEN || lk.kind == LBM_W_FLUX || lk.kind == LBM_W_NEUMANN_BFL ||
                                        lk.kind == LBM_W_FLUX_SIMPLIFIED);
         if (!ok_kind) return fail(ctx, LBM_EINVAL, "link %zu: kind %d not valid for field %d", i, lk.kind, f);
+        if (ctx->motion && ctx->h_motion[3 * case_id + 2] != 0.0 && moving_flux_link(lk))
+            return fail(ctx, LBM_EINVAL, "link %zu: a moving flux wall in a case with wall motion", i);
         if (lk.node >= (uint64_t)N || sol[lk.node]) return fail(ctx, LBM_EINVAL, "link %zu: node %u not fluid", i, lk.node);
         if (!(lk.d > 0.0 && lk.d <= 1.0)) return fail(ctx, LBM_EINVAL, "link %zu: d = %g outside (0, 1]", i, lk.d);
         if (!finite3(lk.u_wall) || !std::isfinite(lk.phi_wall) || !std::isfinite(lk.k0) || !std::isfinite(lk.k1))
@@ -841,6 +878,31 @@ static lbm_status capture_graph(lbm_ctx *ctx) {
     e = cudaGraphInstantiate(&ctx->gexec[parity], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(ctx, LBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_wall_motion(lbm_ctx *ctx, int32_t case_id, double omega, double phase) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (case_id < 0 || case_id >= (int32_t)ctx->cases.size()) return fail(ctx, LBM_EINVAL, "bad case id %d", case_id);
+    if (!std::isfinite(omega) || !std::isfinite(phase)) return fail(ctx, LBM_EINVAL, "non-finite omega or phase");
+    for (const lbm_link &lk : ctx->cases[case_id].links)
+        if (moving_flux_link(lk))
+            return fail(ctx, LBM_EINVAL, "case %d has a flux wall of field %d with a wall velocity", case_id, lk.field);
+    const size_t n = ctx->cases.size();
+    if (!ctx->d_motion) {
+        CK(cudaMalloc(&ctx->d_motion, 3 * n * sizeof(double)));
+        CK(cudaMalloc(&ctx->d_clock, sizeof(long long)));
+        ctx->h_motion.assign(3 * n, 0.0);
+    }
+    ctx->h_motion[3 * case_id] = omega;
+    ctx->h_motion[3 * case_id + 1] = phase;
+    ctx->h_motion[3 * case_id + 2] = 1.0;
+    CK(cudaMemcpyAsync(ctx->d_motion, ctx->h_motion.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_clock, 0, sizeof(long long), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->motion = true;
+    drop_graphs(ctx);          // graphs captured before hold no clock launch
     return LBM_OK;
 }
 

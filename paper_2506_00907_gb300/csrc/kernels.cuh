@@ -398,7 +398,8 @@ LBM_DEV T eval_link(const LinkDev<T> &L, const S *src, const CaseDev<T> &c) {
         }
         phA += L.ref_phi;
         phE += L.ref_phi;
-        v += L.cphi * ((T(1) + L.d) * phA - L.d * phE);
+        const T cp = (L.flags & LINK_WALL_T) ? L.cphi * c.wall_scale : L.cphi;
+        v += cp * ((T(1) + L.d) * phA - L.d * phE);
     }
     // given-pressure links exist only in cases without a magnetic field
     if constexpr (PL::G0 == PL::P) if (L.flags & LINK_NEED_U) {

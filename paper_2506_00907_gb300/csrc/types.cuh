@@ -26,6 +26,7 @@ struct CaseDev {
     T ref_rho, ref_C;     // storage references: planes hold p - w_a * phi_ref
     T ref_B[3];
     T B0[3];              // B_ext for the residual (phi uses B - B0)
+    T wall_scale;         // oscillating velocity walls (Eq. 45): u_wall * wall_scale in this step; 1 without motion
 };
 
 // Per-link record with the wall formula of the link folded into coefficients
@@ -38,7 +39,8 @@ struct CaseDev {
 // B_X the extrapolated magnetic field vector (moving flux walls of g, Eq. 24).
 // Given-pressure links (open boundaries, Eq. 42/44) add cphi * (4.5 (e.u_X)^2 -
 // 1.5 |u_X|^2) with u_X = -d u(E) + (1 + d) u(A) (Eq. 13) and e = cB (LINK_NEED_U).
-enum : uint8_t { LINK_NEED_PHI = 1, LINK_NEED_B = 2, LINK_NEED_U = 4 };
+// Velocity links of a moving wall (LINK_WALL_T) scale cphi by the case's wall_scale.
+enum : uint8_t { LINK_NEED_PHI = 1, LINK_NEED_B = 2, LINK_NEED_U = 4, LINK_WALL_T = 8 };
 
 template <class T>
 struct alignas(16) LinkDev {
@@ -47,7 +49,7 @@ struct alignas(16) LinkDev {
     uint8_t plane_a;      // plane of the unknown direction a
     uint8_t plane_ap;     // plane of the opposite direction a'
     uint8_t phi_plane0;   // first plane of the link's field
-    uint8_t flags;        // LINK_NEED_PHI | LINK_NEED_B | LINK_NEED_U
+    uint8_t flags;        // LINK_NEED_PHI | LINK_NEED_B | LINK_NEED_U | LINK_WALL_T
     T d, c0, ca, cap, cape, cphi;
     T cB[3];
     T ref_phi;            // storage reference of the link's field (phi = sum of stored + ref_phi)

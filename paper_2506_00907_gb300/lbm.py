@@ -78,6 +78,7 @@ def lib():
             "lbm_init_equilibrium_device": (ctypes.c_int, [vp, i32, fp, fp, fp, fp]),
             "lbm_step": (ctypes.c_int, [vp, i32]),
             "lbm_set_graph": (ctypes.c_int, [vp, i32]),
+            "lbm_set_wall_motion": (ctypes.c_int, [vp, i32, ctypes.c_double, ctypes.c_double]),
             "lbm_moments": (ctypes.c_int, [vp, i32, dp, dp, dp, dp]),
             "lbm_check": (ctypes.c_int, [vp, dp]),
             "lbm_run_to_steady": (ctypes.c_int, [vp, i64, i32, ctypes.c_double,
@@ -169,6 +170,10 @@ def lbm_step(ctx, nsteps):
 
 def lbm_set_graph(ctx, steps_per_graph):
     _check(ctx, lib().lbm_set_graph(ctx, int(steps_per_graph)))
+
+
+def lbm_set_wall_motion(ctx, case_id, omega, phase=0.0):
+    _check(ctx, lib().lbm_set_wall_motion(ctx, int(case_id), float(omega), float(phase)))
 
 
 def lbm_moments(ctx, case_id, N):
@@ -427,6 +432,9 @@ class Solver:
 
     def set_graph(self, k):
         lbm_set_graph(self.ctx, k)
+
+    def set_wall_motion(self, case_id, omega, phase=0.0):
+        lbm_set_wall_motion(self.ctx, case_id, omega, phase)
 
     def moments(self, case_id=0):
         return lbm_moments(self.ctx, case_id, self.N[case_id])

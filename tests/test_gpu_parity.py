@@ -190,6 +190,109 @@ def test_pressure_kind_is_refused_with_a_magnetic_field():
     assert ei.value.status == lbm.LBM_EINVAL
 
 
+def _stokes_geometry(nx, ny, d, U):
+    walls = LK.channel_y(2, nx, ny, 1, d, d)
+    p = {(1, 0, O.F): dict(kind=O.VELOCITY), (1, 1, O.F): dict(kind=O.VELOCITY, u_wall=(U, 0, 0))}
+    shape = (nx, ny, 1)
+    return shape, LK.box_solid(shape, walls), LK.box_links(2, shape, walls, p)
+
+
+@pytest.mark.parametrize("d", [0.25, 0.5, 1.0])
+@pytest.mark.parametrize("graph", [0, 4])
+def test_fp64_oscillating_wall(d, graph):
+    """Stokes' second problem (Sec. 5.2, Eq. 45): the top wall moves with
+    U cos(omega t + phase).  FP64 parity with the oracle over 600 steps (1.5
+    periods), stepping eagerly or by graph replays that advance the device
+    clock themselves."""
+    shape, solid, links = _stokes_geometry(3, 22, d, 0.01)
+    p = Pair(2, shape, solid, links)
+    omega, phase = 2 * math.pi / 400, 0.4
+    p.orc.set_wall_motion(omega, phase)
+    p.gpu.set_wall_motion(0, omega, phase)
+    if graph:
+        p.gpu.set_graph(graph)
+    for _ in range(6):
+        p.step(100)
+        for k, v in p.errors().items():
+            assert v < FP64_TOL, (k, v)
+    u = p.gpu.moments(0)["u"].reshape(shape[1], shape[0], 3)[1:-1, 0, 0]
+    assert np.abs(u).max() > 1e-3                     # the wall did drive the flow
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fp64_wall_motion_random_geometry(dim):
+    """Random solids with randomly moving velocity walls (every direction of
+    u_wall, both velocity kinds) and static scalar walls, under wall motion and
+    graphs: FP64 parity with the oracle."""
+    r = IN.rng(500 + dim)
+    shape = (29, 23, 1) if dim == 2 else (13, 11, 9)
+    solid = IN.random_solid(r, shape, fill=0.12)
+    links = LK.random_links(dim, shape, solid, r, has_h=True, kinds=[O.GIVEN, O.NEUMANN_BFL],
+                            phi_range={O.H: (0.5, 1.5)})
+    links["kind"][(links["field"] == O.F) & (links["d"] < 0.5)] = O.VELOCITY_EQ15
+    fields = IN.random_fields(r, shape[0] * shape[1] * shape[2], dim)
+    p = Pair(dim, shape, solid, links, accel=(1e-5, 0, 0), has_h=True, fields=fields)
+    p.orc.set_wall_motion(0.05, -1.0)
+    p.gpu.set_wall_motion(0, 0.05, -1.0)
+    p.gpu.set_graph(2)
+    p.step(40)
+    for k, v in p.errors().items():
+        assert v < FP64_TOL, (k, v)
+
+
+def test_fp64_wall_motion_per_case():
+    """One launch over three cases: two oscillate at different frequencies and
+    phases, one keeps its steady moving wall.  Each matches its own oracle."""
+    geo = [_stokes_geometry(2, ny, d, 0.01) for ny, d in ((14, 0.5), (19, 0.75), (11, 0.3))]
+    motion = [(2 * math.pi / 150, 0.0), None, (2 * math.pi / 70, 1.2)]
+    cases = [lbm.make_case(g[0], 0.8, 0.9, 0.7, (0, 0, 0), 1.0, 1.0, (0, 0, 0)) for g in geo]
+    gpu = lbm.Solver(lbm.LBM_D2Q9, lbm.LBM_FP64, lbm.LBM_FLOW, cases)
+    orcs = []
+    for i, (shape, solid, links) in enumerate(geo):
+        gpu.set_walls(i, solid, to_abi_links(links))
+        o = O.OracleSim(2, shape, solid, 0.8)
+        o.set_links(links)
+        o.init()
+        if motion[i]:
+            o.set_wall_motion(*motion[i])
+        orcs.append(o)
+    for i, m in enumerate(motion):
+        if m:
+            gpu.set_wall_motion(i, *m)
+    gpu.set_graph(4)
+    gpu.step(300)
+    for i, o in enumerate(orcs):
+        o.step(300)
+        fl = np.asarray(geo[i][1]).reshape(-1) == 0
+        a, b = gpu.moments(i), o.moments()
+        assert norm_rel(a["u"][fl], b["u"][fl]) < FP64_TOL
+        assert norm_rel(a["rho"][fl], b["rho"][fl]) < FP64_TOL
+
+
+def test_wall_motion_refuses_moving_flux_walls():
+    """A case with a flux wall of h whose wall moves is refused, and so is a
+    later link list with such a wall in a moving case."""
+    walls = LK.channel_y(2, 1, 10, 1, 0.5, 0.5)
+    shape = (1, 10, 1)
+    solid = LK.box_solid(shape, walls)
+
+    def links(u):
+        p = {(1, 0, O.F): dict(kind=O.VELOCITY), (1, 1, O.F): dict(kind=O.VELOCITY, u_wall=(0.01, 0, 0)),
+             (1, 0, O.H): dict(kind=O.GIVEN, phi_wall=1.0), (1, 1, O.H): dict(kind=O.FLUX, u_wall=(u, 0, 0))}
+        return to_abi_links(LK.box_links(2, shape, walls, p, has_h=True))
+    g = lbm.Solver(lbm.LBM_D2Q9, lbm.LBM_FP64, lbm.LBM_FLOW | lbm.LBM_CD,
+                   [lbm.make_case(shape, 0.8, 0.9, 0.7, (0, 0, 0), 1.0, 1.0, (0, 0, 0))])
+    g.set_walls(0, solid, links(0.01))
+    with pytest.raises(lbm.LbmError) as ei:
+        g.set_wall_motion(0, 1e-3)
+    assert ei.value.status == lbm.LBM_EINVAL
+    g.set_walls(0, solid, links(0.0))
+    g.set_wall_motion(0, 1e-3)
+    with pytest.raises(lbm.LbmError) as ei:
+        g.set_walls(0, solid, links(0.01))
+    assert ei.value.status == lbm.LBM_EINVAL
+
+
 def test_fp64_poiseuille_64x32_5000_steps():
     """Body-force channel, 64 x 32 nodes, tau = 0.8, half-grid walls, 5000
     steps: the GPU matches the oracle and both match the analytic parabola to
