@@ -367,8 +367,10 @@ def run_ours(args):
 
     kernel_ev = []                  # (start, end, steps) around each replay of the step graph
 
-    def run(nsteps, timed=False):
-        done = 0
+    def run(nsteps, timed=False, collect_last=True):
+        # the check of each block of steps is collected only after the next
+        # block has been enqueued, so the GPU never waits for the host
+        done, pending = 0, False
         while done < nsteps:
             k = min(CHECK_EVERY, nsteps - done)
             if timed:
@@ -380,8 +382,14 @@ def run_ours(args):
             else:
                 sol.step(k)
             done += k
+            if pending:
+                sol.check_wait(raise_unstable=False)
+                pending = False
             if done % CHECK_EVERY == 0:
-                sol.check(raise_unstable=False)
+                sol.check_async()
+                pending = True
+        if pending and collect_last:
+            sol.check_wait(raise_unstable=False)
     run(W)
     torch.cuda.synchronize()
     if world > 1:
@@ -391,8 +399,9 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    run(K, timed=True)
+    run(K, timed=True, collect_last=False)
     e1.record(stream)
+    sol.check_wait(raise_unstable=False)          # the last block's check (its kernels precede e1)
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1), device="cuda")

@@ -205,8 +205,19 @@ lbm_status lbm_moments(lbm_ctx *ctx, int32_t case_id, double *rho, double *u,
  * doubles.
  * Synchronises.  Returns LBM_EUNSTABLE (after filling out) if any population
  * is not finite, LBM_ETIMEOUT if a bounded device wait of an earlier step
- * gave up.  Errors: LBM_ECUDA. */
+ * gave up.  Errors: LBM_ESTATE (an asynchronous check is in flight), LBM_ECUDA. */
 lbm_status lbm_check(lbm_ctx *ctx, double *out);
+
+/* lbm_check in two halves, so that the host need not hold the GPU idle while
+ * the result travels back: lbm_check_async enqueues the same reductions and
+ * the copy of their record into pinned host memory on the context's stream and
+ * returns at once; steps may be enqueued behind it; lbm_check_wait waits for
+ * that check only (not for later work) and returns what lbm_check would have
+ * returned for it, filling out (host, 8*ncases doubles, may be NULL).  One
+ * check may be in flight per context: lbm_check_async and lbm_check refuse a
+ * second with LBM_ESTATE, and lbm_check_wait refuses when none is in flight. */
+lbm_status lbm_check_async(lbm_ctx *ctx);
+lbm_status lbm_check_wait(lbm_ctx *ctx, double *out);
 
 /* Step until every case's relative residual sqrt(sum|phi-phi_prev|^2 / sum|phi|^2)
  * over `interval` steps is below tol, or max_steps are done.  *steps_done and

@@ -85,6 +85,9 @@ struct lbm_ctx {
     void *d_links = nullptr;
     size_t cap_brec = 0, cap_links = 0;
     double *d_snap = nullptr, *d_part = nullptr, *d_red = nullptr, *h_red = nullptr;
+    int32_t *h_err = nullptr;          // pinned copy of the device error word
+    cudaEvent_t ev_check = nullptr;    // completion of the latest enqueued check
+    bool check_pending = false;        // lbm_check_async issued, lbm_check_wait not yet called
     double *d_mom = nullptr;
     int64_t max_case_nodes = 0;
     cudaStream_t stream = nullptr;
@@ -616,6 +619,8 @@ void free_ctx(lbm_ctx *c) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_red) cudaFreeHost(c->h_red);
+    if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->ev_check) cudaEventDestroy(c->ev_check);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->side) cudaStreamDestroy(c->side);
@@ -765,6 +770,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
     if (st == LBM_OK) ck(cudaMemset(ctx->d_snap, 0, (size_t)nodes * 8 * sizeof(double)), "memset");
     ck(cudaMalloc(&ctx->d_red, ctx->cases.size() * RED_Q * sizeof(double)), "reduction output");
     ck(cudaMallocHost(&ctx->h_red, ctx->cases.size() * RED_Q * sizeof(double)), "pinned reduction output");
+    ck(cudaMallocHost(&ctx->h_err, sizeof(int32_t)), "pinned error word");
+    ck(cudaEventCreateWithFlags(&ctx->ev_check, cudaEventDisableTiming), "cudaEventCreate");
     ck(cudaMalloc(&ctx->d_mom, (size_t)ctx->max_case_nodes * 8 * sizeof(double)), "moment scratch");
     ck(cudaMalloc(&ctx->d_err, sizeof(int32_t)), "error word");
     if (st == LBM_OK) ck(cudaMemset(ctx->d_err, 0, sizeof(int32_t)), "memset");
@@ -953,8 +960,9 @@ lbm_status lbm_moments(lbm_ctx *ctx, int32_t case_id, double *rho, double *u, do
     return LBM_OK;
 }
 
-lbm_status lbm_check(lbm_ctx *ctx, double *out) {
-    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+// Enqueue the reductions and the copies of their record and of the error word
+// into pinned host memory; ev_check marks their completion.
+static lbm_status check_enqueue(lbm_ctx *ctx) {
     if (ctx->dbl) {
         RedParams<double> rp{ctx->pool[ctx->cur], ctx->d_flags, static_cast<const CaseDev<double> *>(ctx->d_cases),
                              ctx->d_rtiles, ctx->nrtiles, RED_TILE, ctx->d_snap, ctx->d_part};
@@ -968,15 +976,42 @@ lbm_status lbm_check(lbm_ctx *ctx, double *out) {
     CK(cudaGetLastError());
     const size_t bytes = ctx->cases.size() * RED_Q * sizeof(double);
     CK(cudaMemcpyAsync(ctx->h_red, ctx->d_red, bytes, cudaMemcpyDeviceToHost, ctx->stream));
-    int32_t err = 0;
-    CK(cudaMemcpyAsync(&err, ctx->d_err, sizeof(err), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    if (out) std::memcpy(out, ctx->h_red, bytes);
-    if (err) return fail(ctx, LBM_ETIMEOUT, "a bounded device wait gave up (code %d)", err);
+    CK(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaEventRecord(ctx->ev_check, ctx->stream));
+    ctx->check_pending = true;
+    return LBM_OK;
+}
+
+// Wait for the enqueued check, hand out its record and report its findings.
+static lbm_status check_collect(lbm_ctx *ctx, double *out) {
+    ctx->check_pending = false;
+    CK(cudaEventSynchronize(ctx->ev_check));
+    if (out) std::memcpy(out, ctx->h_red, ctx->cases.size() * RED_Q * sizeof(double));
+    if (*ctx->h_err) return fail(ctx, LBM_ETIMEOUT, "a bounded device wait gave up (code %d)", *ctx->h_err);
     for (size_t c = 0; c < ctx->cases.size(); ++c)
         if (ctx->h_red[c * RED_Q + 5] != 0.0)
             return fail(ctx, LBM_EUNSTABLE, "case %zu: %g non-finite populations", c, ctx->h_red[c * RED_Q + 5]);
     return LBM_OK;
+}
+
+lbm_status lbm_check(lbm_ctx *ctx, double *out) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (ctx->check_pending) return fail(ctx, LBM_ESTATE, "an asynchronous check is in flight (lbm_check_wait)");
+    const lbm_status st = check_enqueue(ctx);
+    if (st != LBM_OK) return st;
+    return check_collect(ctx, out);
+}
+
+lbm_status lbm_check_async(lbm_ctx *ctx) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (ctx->check_pending) return fail(ctx, LBM_ESTATE, "an asynchronous check is in flight (lbm_check_wait)");
+    return check_enqueue(ctx);
+}
+
+lbm_status lbm_check_wait(lbm_ctx *ctx, double *out) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (!ctx->check_pending) return fail(ctx, LBM_ESTATE, "no asynchronous check in flight (lbm_check_async)");
+    return check_collect(ctx, out);
 }
 
 lbm_status lbm_run_to_steady(lbm_ctx *ctx, int64_t max_steps, int32_t interval, double tol, int64_t *steps_done,

@@ -81,6 +81,8 @@ def lib():
             "lbm_set_wall_motion": (ctypes.c_int, [vp, i32, ctypes.c_double, ctypes.c_double]),
             "lbm_moments": (ctypes.c_int, [vp, i32, dp, dp, dp, dp]),
             "lbm_check": (ctypes.c_int, [vp, dp]),
+            "lbm_check_async": (ctypes.c_int, [vp]),
+            "lbm_check_wait": (ctypes.c_int, [vp, dp]),
             "lbm_run_to_steady": (ctypes.c_int, [vp, i64, i32, ctypes.c_double,
                                                  ctypes.POINTER(i64), dp]),
             "lbm_state_bytes": (ctypes.c_size_t, [vp]),
@@ -185,6 +187,18 @@ def lbm_moments(ctx, case_id, N):
 def lbm_check(ctx, ncases, raise_unstable=True):
     out = np.zeros(8 * ncases)
     st = lib().lbm_check(ctx, _dp(out))
+    if st != LBM_OK and (st != LBM_EUNSTABLE or raise_unstable):
+        _check(ctx, st)
+    return out.reshape(ncases, 8)
+
+
+def lbm_check_async(ctx):
+    _check(ctx, lib().lbm_check_async(ctx))
+
+
+def lbm_check_wait(ctx, ncases, raise_unstable=True):
+    out = np.zeros(8 * ncases)
+    st = lib().lbm_check_wait(ctx, _dp(out))
     if st != LBM_OK and (st != LBM_EUNSTABLE or raise_unstable):
         _check(ctx, st)
     return out.reshape(ncases, 8)
@@ -441,6 +455,12 @@ class Solver:
 
     def check(self, raise_unstable=True):
         return lbm_check(self.ctx, len(self.cases), raise_unstable)
+
+    def check_async(self):
+        lbm_check_async(self.ctx)
+
+    def check_wait(self, raise_unstable=True):
+        return lbm_check_wait(self.ctx, len(self.cases), raise_unstable)
 
     def run_to_steady(self, max_steps, interval=100, tol=1e-8):
         return lbm_run_to_steady(self.ctx, max_steps, interval, tol)

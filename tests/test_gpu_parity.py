@@ -426,6 +426,33 @@ def test_fp64_reductions_match_oracle():
     assert abs(out[7] - np.sum(phi1 ** 2)) < 1e-12 * np.sum(phi1 ** 2)
 
 
+@pytest.mark.parametrize("prec", [lbm.LBM_FP64, lbm.LBM_FP32])
+def test_async_check_returns_the_check_record(prec):
+    """lbm_check_async + lbm_check_wait give the record lbm_check gives for the
+    same state, bit for bit, although more steps were enqueued behind the
+    check before its result was collected; one check may be in flight."""
+    a = _random_pair(2, True, True, seed=61, prec=prec).gpu
+    b = _random_pair(2, True, True, seed=61, prec=prec).gpu
+    a.step(20)
+    b.step(20)
+    want = a.check(raise_unstable=False)
+    b.check_async()
+    with pytest.raises(lbm.LbmError) as ei:
+        b.check_async()
+    assert ei.value.status == lbm.LBM_ESTATE
+    with pytest.raises(lbm.LbmError) as ei:
+        b.check()
+    assert ei.value.status == lbm.LBM_ESTATE
+    b.step(10)
+    got = b.check_wait(raise_unstable=False)
+    assert np.array_equal(got, want)
+    with pytest.raises(lbm.LbmError) as ei:
+        b.check_wait()
+    assert ei.value.status == lbm.LBM_ESTATE
+    a.step(10)
+    assert np.array_equal(a.check(raise_unstable=False), b.check(raise_unstable=False))
+
+
 def test_nonfinite_population_is_reported():
     """A NaN planted in the initial field is found by the FP64 check
     (LBM_EUNSTABLE) without any device fault."""
