@@ -36,6 +36,8 @@ VELOCITY, GIVEN, FLUX, NEUMANN_BFL = 0, 1, 2, 3
 VELOCITY_EQ15, FLUX_SIMPLIFIED = 4, 5
 # open boundary of given density (pressure), Eq. 42/44; the inlet is VELOCITY with a normal u (Eq. 41/43)
 PRESSURE = 6
+# M-scheme flux wall of C with the reaction flux (kappa0 + kappa1 C_X) / (1 + K C_X), K = phi_wall
+FLUX_RATIONAL = 7
 
 _lib = None
 

@@ -17,6 +17,23 @@ def couette(y, y0, y1, u0, u1):
     return u0 + (u1 - u0) * (y - y0) / (y1 - y0)
 
 
+def reactive_channel_rational(y, y0, y1, D, kappa0, kappa1, K, C_top):
+    """Steady C(y) of a channel with given C_top at y1 and a reacting wall at y0
+    whose flux into the fluid is F(C) = (kappa0 + kappa1 C) / (1 + K C): the
+    profile is linear, and the wall value C_b solves the flux balance
+    D (C_top - C_b) / (y1 - y0) = -F(C_b), a quadratic once multiplied by
+    (1 + K C_b); the root with 1 + K C_b > 0 nearest C_top is taken."""
+    L = y1 - y0
+    # D (C_top - C) (1 + K C) + L (kappa0 + kappa1 C) = 0
+    a = -D * K
+    b = D * K * C_top - D + L * kappa1
+    c = D * C_top + L * kappa0
+    roots = np.roots([a, b, c]) if a != 0 else np.array([-c / b])
+    roots = np.real(roots[np.isreal(roots) & (1 + K * np.real(roots) > 0)])
+    Cb = roots[np.argmin(np.abs(roots - C_top))]
+    return Cb + (C_top - Cb) * (np.asarray(y, dtype=np.float64) - y0) / L
+
+
 def stokes_oscillating(y, t, y0, y1, U, omega, nu, phase=0.0):
     """Stokes' second problem in a channel (Sec. 5.2, Eq. 45): the wall at y1
     moves with U cos(omega t + phase), the wall at y0 is at rest.  The periodic

@@ -18,7 +18,8 @@
  *      two comparison schemes of the paper are selectable per link: Eq. 15/16
  *      for every d (Sec. 5.1) and the simplified flux wall of Eq. 33 (Sec. 5.4);
  *      open boundaries (Sec. 5.1): given velocity is the velocity kind with a
- *      normal u (Eq. 41, 43), given pressure its own kind (Eq. 42, 44).
+ *      normal u (Eq. 41, 43), given pressure its own kind (Eq. 42, 44);
+ *      a reaction flux of C nonlinear in C_X (rational form) by the M scheme.
  *
  * Readings where the paper is silent (each is listed with its reason in the
  * design notes of the repository):
@@ -171,7 +172,8 @@ enum { ORC_F = 0, ORC_H = 1, ORC_G0 = 2 };              /* field: f, h, g_k = 2 
 enum { ORC_VELOCITY = 0, ORC_GIVEN = 1, ORC_FLUX = 2, ORC_NEUMANN_BFL = 3,
        ORC_VELOCITY_EQ15 = 4,   /* Eq. 15 with Eq. 16 for every d (the paper's own scheme before Eq. 43) */
        ORC_FLUX_SIMPLIFIED = 5, /* flux and move increments added to the bounced population at X (Eq. 33) */
-       ORC_PRESSURE = 6         /* given density (pressure) of an open boundary, Eq. 42 and 44 */ };
+       ORC_PRESSURE = 6,        /* given density (pressure) of an open boundary, Eq. 42 and 44 */
+       ORC_FLUX_RATIONAL = 7    /* M scheme with the nonlinear flux (k0 + k1 phi_X) / (1 + phi_wall phi_X) */ };
 
 typedef struct {
     int32_t node;        /* first fluid node A */
@@ -258,11 +260,15 @@ double orc_eval_link(int dim, const orc_link *lk, const orc_link_in *in) {
         BX[k] = lk->phi_wall;
         return orc_geq(dim, a, k, BX, uw) + orc_geq(dim, ap, k, BX, uw) - pY;
     }
-    case ORC_FLUX: {
+    case ORC_FLUX:
+    case ORC_FLUX_RATIONAL: {
         /* M scheme, Eq. 25-27, with the flux increment (Eq. 23) and the
-         * moving-wall correction (Eq. 24) evaluated at X (Eq. 13). */
+         * moving-wall correction (Eq. 24) evaluated at X (Eq. 13).  A reaction
+         * flux nonlinear in C is evaluated explicitly at C_X (Sec. 4.2.2): here
+         * the rational form (k0 + k1 C_X) / (1 + K C_X), K = phi_wall. */
         double phiX = extrap_X(d, in->phi_E, in->phi_A);
-        double dflux = lk->k0 + lk->k1 * phiX;
+        double dflux = lk->kind == ORC_FLUX_RATIONAL ? (lk->k0 + lk->k1 * phiX) / (1.0 + lk->phi_wall * phiX)
+                                                     : lk->k0 + lk->k1 * phiX;
         double minus_u[3] = {-uw[0], -uw[1], -uw[2]};
         double dmove;
         if (!is_g) {
@@ -422,7 +428,7 @@ int orc_set_links(orc_sim *s, const orc_link *links, long n) {
             if ((lk->kind != ORC_VELOCITY && lk->kind != ORC_VELOCITY_EQ15 && !(lk->kind == ORC_PRESSURE && !s->has_g))
                 || lk->dir <= 0 || lk->dir >= qf) { free(seen); return -1; }
         } else if (field == ORC_H) {
-            if (!s->has_h || (lk->kind != ORC_GIVEN && lk->kind != ORC_FLUX && lk->kind != ORC_NEUMANN_BFL && lk->kind != ORC_FLUX_SIMPLIFIED) || lk->dir <= 0 || lk->dir >= qm) { free(seen); return -1; }
+            if (!s->has_h || (lk->kind != ORC_GIVEN && lk->kind != ORC_FLUX && lk->kind != ORC_NEUMANN_BFL && lk->kind != ORC_FLUX_SIMPLIFIED && lk->kind != ORC_FLUX_RATIONAL) || lk->dir <= 0 || lk->dir >= qm) { free(seen); return -1; }
         } else if (field >= ORC_G0 && field < ORC_G0 + s->nB) {
             if (!s->has_g || (lk->kind != ORC_GIVEN && lk->kind != ORC_FLUX && lk->kind != ORC_NEUMANN_BFL && lk->kind != ORC_FLUX_SIMPLIFIED) || lk->dir <= 0 || lk->dir >= qm) { free(seen); return -1; }
         } else { free(seen); return -1; }
@@ -661,7 +667,7 @@ long orc_steps(const orc_sim *s) { return s->steps; }
 int orc_set_wall_motion(orc_sim *s, double omega, double phase) {
     for (long i = 0; i < s->nlinks; ++i) {
         const orc_link *lk = &s->links[i];
-        if (lk->field != ORC_F && (lk->kind == ORC_FLUX || lk->kind == ORC_FLUX_SIMPLIFIED) &&
+        if (lk->field != ORC_F && (lk->kind == ORC_FLUX || lk->kind == ORC_FLUX_SIMPLIFIED || lk->kind == ORC_FLUX_RATIONAL) &&
             (lk->u_wall[0] != 0.0 || lk->u_wall[1] != 0.0 || lk->u_wall[2] != 0.0))
             return -1;
     }

@@ -21,7 +21,7 @@ import math
 
 import numpy as np
 
-from . import LINK_DTYPE, F, H, G0, VELOCITY, GIVEN, FLUX, NEUMANN_BFL, VELOCITY_EQ15, FLUX_SIMPLIFIED, lattice
+from . import LINK_DTYPE, F, H, G0, VELOCITY, GIVEN, FLUX, NEUMANN_BFL, VELOCITY_EQ15, FLUX_SIMPLIFIED, FLUX_RATIONAL, lattice
 
 
 def _fields(dim, has_h, has_g):
@@ -202,7 +202,7 @@ def pipe_links(shape, R, params, has_g=True, center=None):
             e_solid += int(np.sum(solid[En]))
             k0 = np.zeros(nodes.size)
             k1 = np.zeros(nodes.size)
-            if p["kind"] in (FLUX, FLUX_SIMPLIFIED):
+            if p["kind"] in (FLUX, FLUX_SIMPLIFIED, FLUX_RATIONAL):
                 bx, by, bz = (x[nodes] - e[a][0]) % nx, (y[nodes] - e[a][1]) % ny, (z[nodes] - e[a][2]) % nz
                 Bn = bx + nx * (by + ny * bz)
                 for i in range(nodes.size):
