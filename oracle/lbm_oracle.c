@@ -38,7 +38,8 @@
  *     which is Eq. 33 at d = 1 and Eq. 28 at d = 1/2.
  *   - given pressure for d < 1/2 (Eq. 42/44 are printed for d = 1/2 and d >= 1/2):
  *     the interpolation of Eq. 16 to Y, as for a given C (Eq. 19/20); u(X) is
- *     extrapolated by Eq. 13; a case with a magnetic field has no pressure kind.
+ *     extrapolated by Eq. 13; the pressure kind belongs to flow-only cases (the
+ *     paper's open channel), not to cases with a concentration or a magnetic field.
  * Lattice units throughout: dx = dt = 1, c = 1.
  */
 #include <math.h>
@@ -425,7 +426,7 @@ int orc_set_links(orc_sim *s, const orc_link *links, long n) {
         const orc_link *lk = &links[i];
         int field = lk->field;
         if (field == ORC_F) {
-            if ((lk->kind != ORC_VELOCITY && lk->kind != ORC_VELOCITY_EQ15 && !(lk->kind == ORC_PRESSURE && !s->has_g))
+            if ((lk->kind != ORC_VELOCITY && lk->kind != ORC_VELOCITY_EQ15 && !(lk->kind == ORC_PRESSURE && !s->has_g && !s->has_h))
                 || lk->dir <= 0 || lk->dir >= qf) { free(seen); return -1; }
         } else if (field == ORC_H) {
             if (!s->has_h || (lk->kind != ORC_GIVEN && lk->kind != ORC_FLUX && lk->kind != ORC_NEUMANN_BFL && lk->kind != ORC_FLUX_SIMPLIFIED && lk->kind != ORC_FLUX_RATIONAL) || lk->dir <= 0 || lk->dir >= qm) { free(seen); return -1; }

@@ -94,10 +94,13 @@ def test_open_poiseuille_channel(d):
     assert abs(-grad / (8 * nu * U / (y1 - y0) ** 2) - 1) < 0.03
 
 
-def test_pressure_kind_is_refused_with_a_magnetic_field():
-    """The given-pressure kind is defined for cases without a magnetic field."""
+@pytest.mark.parametrize("field", ["h", "g"])
+def test_pressure_kind_is_refused_beside_other_fields(field):
+    """The given-pressure kind belongs to flow-only cases (the paper's open
+    channel): a case with a concentration or a magnetic field refuses it."""
     shape = (8, 3, 1)
     s, links, _, _ = _open_x(shape, 0.5, 0.01, 1.0)
-    g = O.OracleSim(2, shape, LK.box_solid(shape, {0: (0.5, 6.5)}), 0.8, has_g=True)
+    g = O.OracleSim(2, shape, LK.box_solid(shape, {0: (0.5, 6.5)}), 0.8,
+                    has_h=(field == "h"), has_g=(field == "g"))
     with pytest.raises(ValueError):
         g.set_links(links)
