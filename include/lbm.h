@@ -102,7 +102,7 @@ typedef enum {
                                   at d = 1 (inaccurate at small c_w, Sec. 5.4), Eq. 28 at d = 1/2 */
     /* Open boundaries (Sec. 5.1): a given inlet velocity is LBM_W_VELOCITY with
      * u_wall normal to the boundary (Eq. 41, 43). */
-    LBM_W_PRESSURE = 6         /* field f, cases without LBM_MHD.  Given density rho_w = phi_wall
+    LBM_W_PRESSURE = 6         /* field f, flow-only contexts.  Given density rho_w = phi_wall
                                   (pressure rho_w c_s^2): f^eq_a(X) + f^eq_a'(X) - f_rel,a'(Y) with
                                   Y by Eq. 16 for d < 1/2, Eq. 44 for d >= 1/2 (Eq. 42 at d = 1/2);
                                   u(X) extrapolated by Eq. 13 from the fluid velocities at A and E */

@@ -104,6 +104,8 @@ struct lbm_ctx {
     std::vector<double> h_motion;
     double *d_motion = nullptr;
     long long *d_clock = nullptr;      // steps since the last lbm_set_wall_motion
+    int2 *d_wall_links = nullptr;      // (link index, case) of every velocity link of an oscillating wall
+    int32_t n_wall_links = 0;
     int sm_count = 1;
     KernelSet ks{};
     std::string err;
@@ -199,7 +201,6 @@ CaseDev<T> case_dev(const lbm_ctx *c, const CaseHost &cs) {
         d.B0[k] = T(cs.cfg.B0[k]);
     }
     if (c->dim == 2) { d.ref_B[2] = T(0); d.B0[2] = T(0); }
-    d.wall_scale = T(1);
     return d;
 }
 
@@ -306,14 +307,21 @@ LinkDev<T> link_dev(const lbm_ctx *c, const CaseHost &cs, const lbm_link &lk) {
     else
         r.flags = (uint8_t)((cphi != 0.0 ? LINK_NEED_PHI : 0) |
                             ((cB[0] != 0.0 || cB[1] != 0.0 || cB[2] != 0.0) ? LINK_NEED_B : 0));
-    // the velocity term of a moving velocity wall follows the case's wall motion (Eq. 45)
-    if ((lk.kind == LBM_W_VELOCITY || lk.kind == LBM_W_VELOCITY_EQ15) && cphi != 0.0) r.flags |= LINK_WALL_T;
+    // the velocity term of a moving wall of an oscillating case (Eq. 45): the
+    // clock kernel scales cphi from its steady value kept in cB[0] (unused by f links)
+    const size_t ci = (size_t)(&cs - c->cases.data());
+    if ((lk.kind == LBM_W_VELOCITY || lk.kind == LBM_W_VELOCITY_EQ15) && cphi != 0.0 && !c->h_motion.empty() &&
+        c->h_motion[3 * ci + 2] != 0.0) {
+        r.flags |= LINK_WALL_T;
+        r.cB[0] = T(cphi);
+    }
     r.d = T(d);
     r.ca = T(ca);
     r.cap = T(cap);
     r.cape = T(cape);
     r.cphi = T(cphi);
-    for (int j = 0; j < 3; ++j) r.cB[j] = T(cB[j]);
+    for (int j = 0; j < 3; ++j)
+        if (!(r.flags & LINK_WALL_T)) r.cB[j] = T(cB[j]);
     // the planes store s = p - w phi_ref (w_a = w_a'): the formula on s gains
     // the constant (ca + cap + cape - 1) w phi_ref
     const double ref = lk.field == 0 ? cs.cfg.rho0 : (lk.field == 1 ? cs.cfg.C0 : cs.cfg.B0[lk.field - 2]);
@@ -444,6 +452,17 @@ lbm_status upload_walls_t(lbm_ctx *ctx) {
     }
     ctx->nbrec = (int32_t)brec.size();
     ctx->h_brec = brec;
+    // velocity links of oscillating walls, for the clock kernel
+    std::vector<int2> wl;
+    for (const BRec &b : brec)
+        for (int32_t l = b.lo; l < b.hi; ++l)
+            if (links[l].flags & LINK_WALL_T) wl.push_back(make_int2(l, b.cs));
+    ctx->n_wall_links = (int32_t)wl.size();
+    if (ctx->d_wall_links) { cudaFree(ctx->d_wall_links); ctx->d_wall_links = nullptr; }
+    if (!wl.empty()) {
+        CK(cudaMalloc(&ctx->d_wall_links, wl.size() * sizeof(int2)));
+        CK(cudaMemcpy(ctx->d_wall_links, wl.data(), wl.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    }
     if (brec.empty()) brec.push_back(BRec{-1, 0, 0, 0});
     if (links.empty()) links.push_back(LinkDev<T>{});
     auto grow = [&](void **ptr, size_t &cap, size_t bytes) -> lbm_status {
@@ -495,15 +514,20 @@ int step_grid(const lbm_ctx *c) {
     return std::max(1, std::min(c->ntiles, c->launch.blocks_per_sm * c->sm_count));
 }
 
-// Wall motion of the coming step (Eq. 45): wall_scale = cos(omega t + phase) of
-// every moving case at t = the device clock, which then advances by one.  One
-// block; launched ahead of each step (also inside captured graphs) only when a
-// case has wall motion.
+// Wall motion of the coming step (Eq. 45): every velocity link of an oscillating
+// wall gets cphi = (steady cphi, kept in cB[0]) * cos(omega t + phase) of its
+// case at t = the device clock, which then advances by one.  One block;
+// launched ahead of each step (also inside captured graphs) only when a case
+// has wall motion, so the step kernels carry no cost for it.
 template <class T>
-__global__ void k_wall_clock(CaseDev<T> *cases, const double *motion, int ncases, long long *clock) {
+__global__ void k_wall_clock(LinkDev<T> *links, const int2 *wall_links, int n, const double *motion,
+                             long long *clock) {
     const long long t = *clock;
-    for (int i = threadIdx.x; i < ncases; i += blockDim.x)
-        if (motion[3 * i + 2] != 0.0) cases[i].wall_scale = T(cos(motion[3 * i] * (double)t + motion[3 * i + 1]));
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int2 w = wall_links[i];
+        const double sc = cos(motion[3 * w.y] * (double)t + motion[3 * w.y + 1]);
+        links[w.x].cphi = T((double)links[w.x].cB[0] * sc);
+    }
     __syncthreads();
     if (threadIdx.x == 0) *clock = t + 1;
 }
@@ -512,8 +536,8 @@ template <class T>
 cudaError_t launch_step_t(lbm_ctx *ctx) {
     const StepParams<T> p = step_params<T>(ctx);
     if (ctx->motion) {
-        k_wall_clock<T><<<1, 256, 0, ctx->stream>>>(static_cast<CaseDev<T> *>(ctx->d_cases), ctx->d_motion,
-                                                     (int)ctx->cases.size(), ctx->d_clock);
+        k_wall_clock<T><<<1, 256, 0, ctx->stream>>>(static_cast<LinkDev<T> *>(ctx->d_links), ctx->d_wall_links,
+                                                     ctx->n_wall_links, ctx->d_motion, ctx->d_clock);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -615,7 +639,7 @@ void free_ctx(lbm_ctx *c) {
     void *ptrs[] = {c->pool[0], c->pool[1], c->d_flags, c->d_cases, c->d_tiles, c->d_case_tile_lo, c->d_tile_brec,
                     c->d_tile_fluid, c->d_rtiles,
                     c->d_brec, c->d_links, c->d_snap, c->d_part, c->d_red, c->d_mom, c->d_err,
-                    c->d_motion, c->d_clock};
+                    c->d_motion, c->d_clock, c->d_wall_links};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_red) cudaFreeHost(c->h_red);
@@ -811,7 +835,7 @@ lbm_status lbm_set_walls(lbm_ctx *ctx, int32_t case_id, const uint8_t *solid, co
         const Lat &L = f == 0 ? ctx->latf : ctx->latm;
         if (lk.dir < 1 || lk.dir >= L.q) return fail(ctx, LBM_EINVAL, "link %zu: bad direction %d", i, lk.dir);
         const bool ok_kind = f == 0 ? (lk.kind == LBM_W_VELOCITY || lk.kind == LBM_W_VELOCITY_EQ15 ||
-                                       (lk.kind == LBM_W_PRESSURE && !ctx->hg))
+                                       (lk.kind == LBM_W_PRESSURE && !ctx->hg && !ctx->hh))
                                     : (lk.kind == LBM_W_GIVEN || lk.kind == LBM_W_FLUX || lk.kind == LBM_W_NEUMANN_BFL ||
                                        lk.kind == LBM_W_FLUX_SIMPLIFIED);
         if (!ok_kind) return fail(ctx, LBM_EINVAL, "link %zu: kind %d not valid for field %d", i, lk.kind, f);
@@ -909,8 +933,9 @@ lbm_status lbm_set_wall_motion(lbm_ctx *ctx, int32_t case_id, double omega, doub
     CK(cudaMemsetAsync(ctx->d_clock, 0, sizeof(long long), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->motion = true;
-    drop_graphs(ctx);          // graphs captured before hold no clock launch
-    return LBM_OK;
+    // refold the links (marks the moving ones, keeps their steady velocity
+    // term) and drop the graphs captured without a clock launch
+    return upload_walls(ctx);
 }
 
 lbm_status lbm_step(lbm_ctx *ctx, int32_t nsteps) {

@@ -398,11 +398,10 @@ LBM_DEV T eval_link(const LinkDev<T> &L, const S *src, const CaseDev<T> &c) {
         }
         phA += L.ref_phi;
         phE += L.ref_phi;
-        const T cp = (L.flags & LINK_WALL_T) ? L.cphi * c.wall_scale : L.cphi;
-        v += cp * ((T(1) + L.d) * phA - L.d * phE);
+        v += L.cphi * ((T(1) + L.d) * phA - L.d * phE);
     }
-    // given-pressure links exist only in cases without a magnetic field
-    if constexpr (PL::G0 == PL::P) if (L.flags & LINK_NEED_U) {
+    // given-pressure links exist only in flow-only cases
+    if constexpr (PL::P == PL::QF) if (L.flags & LINK_NEED_U) {
         // fluid velocity at A and E from the relaxed populations:
         // u = (sum e s_rel - F/2) / rho, with F = rho * accel
         T rA = 0, rE = 0, jA[3] = {0, 0, 0}, jE[3] = {0, 0, 0};

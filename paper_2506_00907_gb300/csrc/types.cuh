@@ -26,7 +26,6 @@ struct CaseDev {
     T ref_rho, ref_C;     // storage references: planes hold p - w_a * phi_ref
     T ref_B[3];
     T B0[3];              // B_ext for the residual (phi uses B - B0)
-    T wall_scale;         // oscillating velocity walls (Eq. 45): u_wall * wall_scale in this step; 1 without motion
 };
 
 // Per-link record with the wall formula of the link folded into coefficients
@@ -39,7 +38,8 @@ struct CaseDev {
 // B_X the extrapolated magnetic field vector (moving flux walls of g, Eq. 24).
 // Given-pressure links (open boundaries, Eq. 42/44) add cphi * (4.5 (e.u_X)^2 -
 // 1.5 |u_X|^2) with u_X = -d u(E) + (1 + d) u(A) (Eq. 13) and e = cB (LINK_NEED_U).
-// Velocity links of a moving wall (LINK_WALL_T) scale cphi by the case's wall_scale.
+// Velocity links of an oscillating wall (LINK_WALL_T) keep their steady cphi in
+// cB[0]; a clock kernel writes cphi = cB[0] cos(omega t + phase) before each step.
 enum : uint8_t { LINK_NEED_PHI = 1, LINK_NEED_B = 2, LINK_NEED_U = 4, LINK_WALL_T = 8 };
 
 template <class T>

@@ -141,11 +141,10 @@ def _open_channel_pair(dim, d, prec=lbm.LBM_FP64, has_h=False, steps_shape=None)
 
 @pytest.mark.parametrize("dim", [2, 3])
 @pytest.mark.parametrize("d", [0.3, 0.5, 1.0])
-@pytest.mark.parametrize("has_h", [False, True])
-def test_fp64_open_boundaries(dim, d, has_h):
+def test_fp64_open_boundaries(dim, d):
     """Given inlet velocity and given outlet pressure (Sec. 5.1, Eq. 41-44):
     FP64 parity with the oracle over 200 steps from a random initial field."""
-    p = _open_channel_pair(dim, d, has_h=has_h)
+    p = _open_channel_pair(dim, d)
     assert np.any(p.abi_links["kind"] == lbm.LBM_W_PRESSURE)
     p.step(1)
     for k, v in p.errors().items():
@@ -159,31 +158,35 @@ def test_fp64_open_boundaries(dim, d, has_h):
 def test_open_boundaries_every_launch_variant(prec):
     """The pressure links' velocity extrapolation runs in every launch variant
     with the same arithmetic: variants 1 and 3 (FP32 and 16-bit storage) equal
-    variant 0 bit for bit on an open 2D channel with concentration."""
-    ref = _open_channel_pair(2, 0.7, prec=prec, has_h=True).gpu
+    variant 0 bit for bit on an open 2D channel."""
+    ref = _open_channel_pair(2, 0.7, prec=prec).gpu
     ref.set_launch(0, 128, 0)
     ref.step(30)
     want = ref.get_state()
     for variant, kw in ((1, dict(min_blocks=2)), (3, dict(blocks_per_sm=1, stages=4, min_blocks=2))):
-        g = _open_channel_pair(2, 0.7, prec=prec, has_h=True).gpu
+        g = _open_channel_pair(2, 0.7, prec=prec).gpu
         g.set_launch(variant, 256, **kw)
         g.step(30)
         assert np.array_equal(g.get_state(), want), variant
 
 
-def test_pressure_kind_is_refused_with_a_magnetic_field():
-    """The C ABI refuses given-pressure links in a case with a magnetic field."""
+@pytest.mark.parametrize("phys", [lbm.LBM_FLOW | lbm.LBM_MHD, lbm.LBM_FLOW | lbm.LBM_CD])
+def test_pressure_kind_is_refused_beside_other_fields(phys):
+    """The C ABI refuses given-pressure links in a case with a magnetic field
+    or a concentration (the kind belongs to flow-only cases)."""
     shape = (12, 10, 1)
     walls = {1: (0.5, 8.5), 0: (0.5, 10.5)}
+    has_h, has_g = bool(phys & lbm.LBM_CD), bool(phys & lbm.LBM_MHD)
     p = {(0, 0, O.F): dict(kind=O.VELOCITY, u_wall=(0.01, 0, 0)), (0, 1, O.F): dict(kind=O.PRESSURE, phi_wall=1.0)}
+    fields = [O.H] if has_h else [O.G0, O.G0 + 1]
     for side in (0, 1):
         p[(1, side, O.F)] = dict(kind=O.VELOCITY)
-        for k in range(2):
-            p[(0, side, O.G0 + k)] = dict(kind=O.GIVEN, phi_wall=0.0)
-            p[(1, side, O.G0 + k)] = dict(kind=O.GIVEN, phi_wall=0.0)
+        for fld in fields:
+            p[(0, side, fld)] = dict(kind=O.GIVEN, phi_wall=0.0)
+            p[(1, side, fld)] = dict(kind=O.GIVEN, phi_wall=0.0)
     solid = LK.box_solid(shape, walls)
-    links = to_abi_links(LK.box_links(2, shape, walls, p, has_g=True))
-    g = lbm.Solver(lbm.LBM_D2Q9, lbm.LBM_FP64, lbm.LBM_FLOW | lbm.LBM_MHD,
+    links = to_abi_links(LK.box_links(2, shape, walls, p, has_h=has_h, has_g=has_g))
+    g = lbm.Solver(lbm.LBM_D2Q9, lbm.LBM_FP64, phys,
                    [lbm.make_case(shape, 0.8, 0.9, 0.9, (0, 0, 0), 1.0, 1.0, (0, 0, 0))])
     with pytest.raises(lbm.LbmError) as ei:
         g.set_walls(0, solid, links)
