@@ -66,3 +66,20 @@ def test_create_without_gpu_fails_loudly():
     case = lbm.make_case((4, 4, 1), 0.8)
     with pytest.raises(lbm.LbmError):
         lbm.lbm_create(lbm.LBM_D2Q9, lbm.LBM_FP32, lbm.LBM_FLOW, [case], None, 0)
+
+
+def test_wall_kind_values_agree_with_the_header():
+    """The link-kind and field values are part of the link interface: the
+    header's enum, the binding's constants and the oracle's constants (which
+    shares no code with the product) must name the same numbers."""
+    import oracle as O
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef enum \{(.*?)\} lbm_wall_kind;", text, flags=re.S).group(1)
+    header = {name: int(v) for name, v in re.findall(r"(LBM_W_[A-Z0-9_]+)\s*=\s*(\d+)", body)}
+    assert header == {k: getattr(lbm, k) for k in header}
+    oracle_names = {"LBM_W_VELOCITY": O.VELOCITY, "LBM_W_GIVEN": O.GIVEN, "LBM_W_FLUX": O.FLUX,
+                    "LBM_W_NEUMANN_BFL": O.NEUMANN_BFL, "LBM_W_VELOCITY_EQ15": O.VELOCITY_EQ15,
+                    "LBM_W_FLUX_SIMPLIFIED": O.FLUX_SIMPLIFIED, "LBM_W_PRESSURE": O.PRESSURE}
+    assert set(oracle_names) == set(header)
+    for k, v in oracle_names.items():
+        assert header[k] == v, k
