@@ -84,3 +84,21 @@ def test_pipe_builder_matches_oracle(R, shape, b1):
         for x in range(shape[0]):
             tot = fl["k1"][fl["node"] % shape[0] == x].sum()
             assert abs(tot - g0["kappa1"] * 2 * math.pi * R) < 1e-10
+
+
+@pytest.mark.parametrize("dim,shape", [(2, (14, 5, 1)), (3, (9, 4, 3))])
+@pytest.mark.parametrize("d", [0.5, 0.3, 1.0])
+def test_open_channel_builder_matches_oracle(dim, shape, d):
+    """A domain open along x (Sec. 5.1): inlet of given velocity (the velocity
+    kind with a normal u) and outlet of given density, built by the product's
+    channel builder, equals the oracle's links."""
+    walls = {0: (1.0 - d, shape[0] - 2.0 + d)}
+    U = (0.03, 0.002, 0.0)
+    params = {(0, 0, O.F): dict(kind=O.VELOCITY, u_wall=U), (0, 1, O.F): dict(kind=O.PRESSURE, phi_wall=1.01)}
+    orc = LK.box_links(dim, shape, walls, params)
+    lo = [lbm.wall_bc(lbm.LBM_W_VELOCITY, u_wall=U), None, None, None, None]
+    hi = [lbm.wall_bc(lbm.LBM_W_PRESSURE, phi_wall=1.01), None, None, None, None]
+    solid, prod = lbm.lbm_build_channel(dim, shape, 0, d, d, lbm.LBM_FLOW, lo, hi)
+    assert np.array_equal(solid, LK.box_solid(shape, walls).reshape(-1))
+    assert np.any(prod["kind"] == lbm.LBM_W_PRESSURE)
+    _compare(prod, orc)
