@@ -178,9 +178,11 @@ lbm_status lbm_set_graph(lbm_ctx *ctx, int32_t steps_per_graph);
  * LBM_W_VELOCITY and LBM_W_VELOCITY_EQ15) uses u_wall * cos(omega * t + phase)
  * in the step from t to t + 1, the wall velocity taken at t as f^eq(X, t) in
  * Eq. 41/43.  t counts the context's steps since the latest call of this
- * function (for any case); a one-block kernel refreshes the cases' factors
- * ahead of every step, also inside captured graphs (existing graphs are
- * dropped).  Flux walls of h or g with a nonzero wall velocity would need the
+ * function (for any case).  The call refolds the wall links of every case
+ * (as lbm_set_walls does) and drops existing graphs; from then on a one-block
+ * kernel rewrites the velocity coefficient of each oscillating link ahead of
+ * every step, also inside captured graphs, so the step kernels themselves
+ * carry no term for the motion.  Flux walls of h or g with a nonzero wall velocity would need the
  * same motion in their moving-wall term: a case holding one is refused, here
  * and in later lbm_set_walls calls.  Synchronises.  Errors: LBM_EINVAL (case id,
  * non-finite omega or phase, moving flux wall), LBM_ENOMEM, LBM_ECUDA. */
