@@ -920,11 +920,9 @@ lbm_status lbm_set_wall_motion(lbm_ctx *ctx, int32_t case_id, double omega, doub
         if (moving_flux_link(lk))
             return fail(ctx, LBM_EINVAL, "case %d has a flux wall of field %d with a wall velocity", case_id, lk.field);
     const size_t n = ctx->cases.size();
-    if (!ctx->d_motion) {
-        CK(cudaMalloc(&ctx->d_motion, 3 * n * sizeof(double)));
-        CK(cudaMalloc(&ctx->d_clock, sizeof(long long)));
-        ctx->h_motion.assign(3 * n, 0.0);
-    }
+    if (!ctx->d_motion) CK(cudaMalloc(&ctx->d_motion, 3 * n * sizeof(double)));
+    if (!ctx->d_clock) CK(cudaMalloc(&ctx->d_clock, sizeof(long long)));
+    if (ctx->h_motion.empty()) ctx->h_motion.assign(3 * n, 0.0);
     ctx->h_motion[3 * case_id] = omega;
     ctx->h_motion[3 * case_id + 1] = phase;
     ctx->h_motion[3 * case_id + 2] = 1.0;
