@@ -5,17 +5,28 @@ schemes (one JSON line on rank 0).
 Default workload: 64 batched 2D Hartmann channels (widths U{64..512}, Ha
 U[1,30], wall-to-node fraction q U[0,1), Shercliff c_w log-U[1e-3,1], seed
 2506), FP16 offset storage with FP32 arithmetic, all cases advanced by one
-kernel launch per time step, replayed as CUDA graphs; the FP64 invariant /
-residual reduction runs every 100 steps inside the timed region.
-``--workload pipe`` and ``--workload cd`` time the 3D MHD pipe and the
-flow + concentration channel instead.
+kernel launch per time step.  One bench step is one pass of the whole path:
+a CUDA-graph replay of 100 time steps of every case followed by the FP64
+invariant / residual reduction.  ``--workload pipe`` / ``pipe_fp32`` / ``cd``
+time the 3D MHD pipe and the flow + concentration channels instead;
+``steady_pipe`` measures the time to steady state at the 32x256x256 size.
 
-``--impl reference`` times the FP64 CPU oracle (the baseline this build is
-checked against) on a bounded sample of the same workload.
+Besides the headline figures the default line carries:
+  * ``accuracy``   -- the run's fields against the FP64 oracle, node by node;
+  * ``steady``     -- time to steady state at fixed error, plain form against
+                      the warm-started, 16-bit, batched form (bounded size);
+  * ``fp64``       -- the same workload with FP64 storage, with its HBM and
+                      FP64-arithmetic bounds.
+The oracle (``oracle/``) runs only in the CPU-baseline leg (``oracle_leg``),
+which times it and checks the GPU results, and in ``--impl reference``.
+
+Under torchrun every rank takes its own share of the cases (64 per rank,
+balanced by node count) and no data moves between ranks.
 """
 import argparse
 import hashlib
 import json
+import math
 import os
 import subprocess
 import sys
@@ -28,32 +39,34 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS and % of HBM roofline; time-to-steady-state at fixed error"
-CHECK_EVERY = 100
+GRAPH = 100                  # time steps per bench step (one graph replay + one reduction)
+CASES_PER_RANK = 64
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4000)
-    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=40, help="bench steps of %d time steps each" % GRAPH)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["hartmann_batch", "pipe", "pipe_fp32", "cd", "steady_pipe"],
                     default="hartmann_batch")
-    # steady_pipe: time to steady state, warm-started FP16 batch vs cold FP32 one case at a time
-    ap.add_argument("--steady-cases", type=int, default=4)
-    ap.add_argument("--steady-tol", type=float, default=1e-8)
-    ap.add_argument("--switch-tol", type=float, default=1e-5,
+    # time to steady state: the bounded record of the default line and the full steady_pipe workload
+    ap.add_argument("--no-steady", action="store_true")
+    ap.add_argument("--steady-cases", type=int, default=None)
+    ap.add_argument("--steady-tol", type=float, default=None,
+                    help="residual of the steady-state comparison (default 5e-6 for the bounded record at R = 62, "
+                         "1e-6 for steady_pipe at R = 126: above each size's FP32 residual floor)")
+    ap.add_argument("--switch-tol", type=float, default=2e-5,
                     help="residual at which the FP16-storage phase hands over to FP32")
-    ap.add_argument("--steady-max-steps", type=int, default=2000000)
-    ap.add_argument("--train-cases", type=int, default=512)
+    ap.add_argument("--steady-max-steps", type=int, default=None)
+    ap.add_argument("--train-cases", type=int, default=None)
     ap.add_argument("--train-R", type=float, default=62.0)
     ap.add_argument("--train-tol", type=float, default=1e-5)
-    ap.add_argument("--train-epochs", type=int, default=100)
+    ap.add_argument("--train-epochs", type=int, default=None)
     ap.add_argument("--train-per-case", type=int, default=2048)
     ap.add_argument("--train-max-steps", type=int, default=200000)
-    ap.add_argument("--reference-steps", type=int, default=0,
-                    help="steady_pipe reference arm: steps to project the oracle's time over (0: the "
-                         "plain form's step count is unknown to that arm; it reports seconds per 1000 steps)")
+    ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--launch", default=None,
                     help="variant,block,blocks_per_sm,nodes_per_thread,stages,min_blocks (skips the autotuner)")
@@ -62,43 +75,90 @@ def parse():
     return ap.parse_args()
 
 
-# ----------------------------------------------------------------------------- workloads
-def build_workload(name):
-    """Returns dict(cases, geo=[(solid, links)], lattice, prec, physics, infos, desc)."""
-    from paper_2506_00907_gb300 import cases as CS
+# ----------------------------------------------------------------------------- workloads (no library code)
+def hartmann_draws(world):
+    """64 draws per rank: batch b with seed 2506 + b (batch 0 is the 64-case
+    configuration), each turned into lattice parameters."""
     from paper_2506_00907_gb300 import inputs as IN
-    from paper_2506_00907_gb300 import lbm
+    out = []
+    for b in range(world):
+        out += [IN.hartmann_params(d["W"], d["Ha"], d["q"], d["cw"], clamp_cw=True)
+                for d in IN.hartmann_batch(CASES_PER_RANK, seed=IN.SEED + b)]
+    return out
+
+
+def partition(sizes, world):
+    """Cases of each rank: largest case first to the least-loaded rank (LPT),
+    each rank's list in the original order."""
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for i in sorted(range(len(sizes)), key=lambda k: (-sizes[k], k)):
+        r = min(range(world), key=lambda k: (load[k], k))
+        parts[r].append(i)
+        load[r] += sizes[i]
+    return [sorted(p) for p in parts]
+
+
+def workload_spec(name, rank=0, world=1):
+    """What a bench step computes: the case parameters (shared input recipe),
+    their kind and the description; no library is loaded."""
+    from paper_2506_00907_gb300 import inputs as IN
     if name == "hartmann_batch":
-        cases, geo, infos = [], [], []
-        for dr in IN.hartmann_batch(64):
-            c, s, l, info = CS.hartmann_channel(dr["W"], dr["Ha"], dr["q"], dr["cw"], clamp_cw=True)
-            cases.append(c)
-            geo.append((s, l))
-            infos.append(info)
-        clamped = sum(1 for i in infos if i["cw_clamped"])
-        return dict(cases=cases, geo=geo, infos=infos, lattice=lbm.LBM_D2Q9, prec=lbm.LBM_FP16S, cw_clamped=clamped,
-                    physics=lbm.LBM_FLOW | lbm.LBM_MHD, planes=19, storage="fp16-offset", dim=2,
-                    desc="64 batched 2D Hartmann channels, W~U{64..512} (W x (W+2) nodes), Ha~U[1,30], "
-                         "q~U[0,1), c_w~logU[1e-3,1], seed 2506; D2Q9 + D2Q5 x 2 (B1, B2)")
+        allp = hartmann_draws(world)
+        sizes = [p["W"] * p["W"] for p in allp]                   # fluid nodes W x W
+        mine = partition(sizes, world)[rank]
+        params = [allp[i] for i in mine]
+        fluid = sum(p["W"] * p["W"] for p in params)
+        return dict(kind="hartmann", params=params, dim=2, planes=19, storage="fp16-offset", prec="fp16s",
+                    fluid=fluid, cw_clamped=sum(1 for p in params if p["cw_clamped"]),
+                    desc="%d batched 2D Hartmann channels%s, W~U{64..512} (W x (W+2) nodes), Ha~U[1,30], "
+                         "q~U[0,1), c_w~logU[1e-3,1], seed 2506%s; D2Q9 + D2Q5 x 2 (B1, B2)" % (
+                             len(params), "" if world == 1 else " (rank %d of %d)" % (rank, world),
+                             "" if world == 1 else "..%d" % (IN.SEED + world - 1)))
     if name in ("pipe", "pipe_fp32"):
         dr = IN.pipe_draws(1, Ha=(5.0, 20.0), cw=(0.01, 1.0))[0]
-        c, s, l, info = CS.pipe((32, 128, 128), 62.0, dr["Ha"], ("shercliff", dr["cw"]))
-        prec = lbm.LBM_FP16S if name == "pipe" else lbm.LBM_FP32
-        return dict(cases=[c], geo=[(s, l)], infos=[info], lattice=lbm.LBM_D3Q19, prec=prec,
-                    physics=lbm.LBM_FLOW | lbm.LBM_MHD, planes=40, dim=3,
-                    storage="fp16-offset" if name == "pipe" else "fp32",
+        P = IN.pipe_params(62.0, dr["Ha"], ("shercliff", dr["cw"]))
+        shape = (32, 128, 128)
+        yy, zz = np.meshgrid(np.arange(128) - 63.5, np.arange(128) - 63.5, indexing="ij")
+        fluid = 32 * int(np.sum(yy ** 2 + zz ** 2 < 62.0 ** 2))
+        fp32 = name == "pipe_fp32"
+        return dict(kind="pipe", params=[P], shape=shape, dim=3, planes=40, fluid=fluid,
+                    storage="fp32" if fp32 else "fp16-offset", prec="fp32" if fp32 else "fp16s", cw_clamped=0,
                     desc="3D MHD pipe 32x128x128 (periodic axial), R = 62, Ha=%.2f, Shercliff c_w=%.3g; "
                          "D3Q19 + D3Q7 x 3" % (dr["Ha"], dr["cw"]))
-    c, s, l, info = CS.reactive_channel(512, 256, 0.25, 0.05, 1e-2)
-    return dict(cases=[c], geo=[(s, l)], infos=[info], lattice=lbm.LBM_D2Q9, prec=lbm.LBM_FP32,
-                physics=lbm.LBM_FLOW | lbm.LBM_CD, planes=14, storage="fp32", dim=2,
-                desc="D2Q9 flow + D2Q5 concentration 512x256, moving top wall U=0.05 with given C, "
-                     "Robin reactive bottom wall k=1e-2, q=0.25")
+    params = IN.reactive_grid(512, 256)
+    fluid = sum(512 * 254 for _ in params)
+    return dict(kind="reactive", params=params, dim=2, planes=14, storage="fp32", prec="fp32", fluid=fluid,
+                cw_clamped=0,
+                desc="%d D2Q9 flow + D2Q5 concentration channels 512x256: top wall U = 0.05 with given C = 2, "
+                     "Robin reactive bottom wall k in {1e-3, 1e-2, 1e-1}, q in {0, 1/4, 1/2, 3/4}" % len(params))
+
+
+def spec_config(spec):
+    """The workload's config block (the same on both arms)."""
+    return {"workload": spec["desc"], "cases": len(spec["params"]), "fluid_nodes": spec["fluid"],
+            "time_steps_per_step": GRAPH, "reduction_every": GRAPH,
+            "l2": "inputs larger than L2 (population state >= %.0f MB at 16-bit storage > 129 MB), no flush" % (
+                spec["planes"] * 2 * spec["fluid"] / 1e6)}
+
+
+def product_cases(spec):
+    """C-ABI cases and walls of the spec (product builders)."""
+    from paper_2506_00907_gb300 import cases as CS
+    out = []
+    for P in spec["params"]:
+        if spec["kind"] == "hartmann":
+            c, s, l, info = CS.hartmann_channel(P["W"], P["Ha"], P["q"], P["cw_drawn"], clamp_cw=True)
+        elif spec["kind"] == "pipe":
+            c, s, l, info = CS.pipe(spec["shape"], P["R"], P["Ha"], P["wall"])
+        else:
+            c, s, l, info = CS.reactive_channel(*P["shape"][:2], P["q"], P["U"], P["k"], P["C_eq"], P["C_top"])
+        out.append((c, s, l, info))
+    return out
 
 
 # ----------------------------------------------------------------------------- helpers
 STEP_SOURCES = ("lattice.cuh", "types.cuh", "kernels.cuh", "kernels_bulk.cuh", "kernels_ring.cuh")   # the step kernels
-
 
 STEP_KERNEL = {
     0: "k_step (bulk nodes) + k_boundary (wall-link nodes)",
@@ -128,12 +188,12 @@ def measured_traffic(workload):
     return rec.get("bytes_per_launch")
 
 
-def peak_hbm():
+def peaks():
     try:
         pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        return float(pk["hbm_gbs"]), "measured"
+        return dict(hbm=float(pk["hbm_gbs"]), kind="measured")
     except Exception:
-        return 6800.0, "fallback"
+        return dict(hbm=6800.0, kind="fallback")
 
 
 class Clocks:
@@ -204,62 +264,47 @@ def max_over_ranks(ms, device=None):
     return float(t.item())
 
 
-def whole_job_mlups(units_per_rank, world, steps, ms_max):
-    """Node updates of all ranks per second (weak scaling: every rank runs the
-    same batch), in millions."""
-    return world * units_per_rank * steps / (ms_max * 1e-3) / 1e6
+def sum_over_ranks(v, device=None):
+    """Sum of a per-rank number over the process group (the local value alone
+    without a group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(v)
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
 
 
-# ----------------------------------------------------------------------------- oracle timing
-def oracle_sample(wl, target_nodes):
-    """OracleSim objects for the first cases of the workload up to target_nodes
-    fluid nodes, with links from the oracle's own builder."""
-    import oracle as O
-    from oracle import links as LK
+def whole_job_mlups(units_all_ranks, time_steps, ms_max):
+    """Node updates of all ranks per second, in millions, over the slowest
+    rank's time."""
+    return units_all_ranks * time_steps / (ms_max * 1e-3) / 1e6
+
+
+# ----------------------------------------------------------------------------- the oracle (CPU-baseline leg)
+def oracle_sims(spec, nx=None, target_nodes=None, threads=None):
+    """Oracle domains of the spec's cases (oracle builders only); with
+    target_nodes, the first cases up to that many fluid nodes."""
+    from oracle import workloads as WL
     sims, nodes = [], 0
-    threads = os.cpu_count() or 1
-    for (c, info) in zip(wl["cases"], wl["infos"]):
-        shape = (c.nx, c.ny, c.nz)
-        dim = wl["dim"]
-        if "W" in info:
-            d = 1.0 - info["q"]
-            walls = LK.channel_y(2, c.nx, c.ny, 1, d, d)
-            p = {(1, s, O.F): dict(kind=O.VELOCITY) for s in (0, 1)}
-            p.update({(1, s, O.G0): dict(kind=O.FLUX, kappa1=info["kappa1"]) for s in (0, 1)})
-            p.update({(1, s, O.G0 + 1): dict(kind=O.GIVEN, phi_wall=info["B0"]) for s in (0, 1)})
-            solid = LK.box_solid(shape, walls)
-            links = LK.box_links(2, shape, walls, p, has_g=True)
-            has_h, has_g = False, True
-        elif "R" in info:
-            wall = info["wall"]
-            g0 = dict(kind=O.GIVEN, phi_wall=0.0) if wall == "insulating" else \
-                dict(kind=O.FLUX) if wall == "conducting" else dict(kind=O.FLUX, kappa1=-info["eta"] / (wall[1] * info["R"]))
-            params = {O.F: dict(kind=O.VELOCITY), O.G0: g0, O.G0 + 1: dict(kind=O.GIVEN, phi_wall=info["B0"]),
-                      O.G0 + 2: dict(kind=O.GIVEN, phi_wall=0.0)}
-            solid = LK.pipe_solid(shape, info["R"])
-            links, _ = LK.pipe_links(shape, info["R"], params)
-            has_h, has_g = False, True
+    for P in spec["params"]:
+        if spec["kind"] == "hartmann":
+            s, solid = WL.hartmann(P, nx=nx, threads=threads)
+        elif spec["kind"] == "pipe":
+            s, solid = WL.pipe(P, spec["shape"], nx=nx, threads=threads)
         else:
-            d = 1.0 - info["q"]
-            walls = LK.channel_y(2, c.nx, c.ny, 1, d, d)
-            p = {(1, 0, O.F): dict(kind=O.VELOCITY), (1, 1, O.F): dict(kind=O.VELOCITY, u_wall=(info["U"], 0, 0)),
-                 (1, 0, O.H): dict(kind=O.FLUX, kappa0=info["k"], kappa1=-info["k"]),
-                 (1, 1, O.H): dict(kind=O.GIVEN, phi_wall=2.0, u_wall=(info["U"], 0, 0))}
-            solid = LK.box_solid(shape, walls)
-            links = LK.box_links(2, shape, walls, p, has_h=True)
-            has_h, has_g = True, False
-        s = O.OracleSim(dim, shape, solid, c.tau_nu, c.tau_D, c.tau_eta, tuple(c.accel), has_h, has_g, threads)
-        s.set_links(links)
-        s.init(rho0=c.rho0, C0=c.C0, B0=tuple(c.B0))
-        sims.append((s, int(np.sum(np.asarray(solid) == 0))))
-        nodes += sims[-1][1]
-        if nodes >= target_nodes:
+            s, solid = WL.reactive(P, nx=nx, threads=threads)
+        n = int(np.sum(np.asarray(solid) == 0))
+        sims.append((s, n))
+        nodes += n
+        if target_nodes and nodes >= target_nodes:
             break
-    return sims, nodes, threads
+    return sims, nodes
 
 
 def time_oracle(sims, budget_s=12.0, max_steps=None):
-    """Steps the sample until the budget is used; returns (MLUPS, steps)."""
+    """Steps the sample until the budget is used; returns (MLUPS, steps, s)."""
     for s, _ in sims:
         s.step(1)                       # warm
     nodes = sum(n for _, n in sims)
@@ -275,14 +320,119 @@ def time_oracle(sims, budget_s=12.0, max_steps=None):
     return nodes * steps / el / 1e6, steps, el
 
 
+def accuracy_vs_oracle(spec, steps, gpu_fields):
+    """Norm-relative errors of the GPU fields after `steps` time steps against
+    the FP64 oracle run from the same state, node by node over every fluid
+    node of every case.  The oracle runs each case at x length 1 (the cases
+    are x-invariant, so its rows equal those of the full width); the cases
+    run in parallel threads (the oracle releases the interpreter)."""
+    import concurrent.futures as cf
+    from oracle import workloads as WL
+
+    def one(i):
+        P = spec["params"][i]
+        if spec["kind"] == "hartmann":
+            s, solid = WL.hartmann(P, nx=1, threads=1)
+            nx = P["shape"][0]
+        elif spec["kind"] == "pipe":
+            s, solid = WL.pipe(P, spec["shape"], nx=1, threads=4)
+            nx = spec["shape"][0]
+        else:
+            s, solid = WL.reactive(P, nx=1, threads=1)
+            nx = P["shape"][0]
+        s.step(steps)
+        m = s.moments()
+        fl = np.asarray(solid).reshape(-1) == 0
+        g = gpu_fields[i]
+        out = {}
+        ref = {"u": WL.widen(m["u"][fl], nx), "rho": WL.widen(m["rho"][fl], nx) - 1.0}
+        if spec["kind"] == "reactive":
+            ref["C"] = WL.widen(m["C"][fl], nx)
+        else:
+            ref["b"] = WL.widen(m["B"][fl] - np.array([0.0, P["B0"], 0.0]), nx)
+        for k, r in ref.items():
+            den = 1.0 if k == "rho" else np.abs(r).max()
+            out[k] = float(np.abs(g[k] - r).max() / (den if den > 0 else 1.0))
+        return out
+
+    workers = max(1, min(16, os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(max_workers=workers if spec["kind"] != "pipe" else 1) as ex:
+        per = list(ex.map(one, range(len(gpu_fields))))
+    keys = per[0].keys()
+    return {k: max(p[k] for p in per) for k in keys}
+
+
+def gpu_fields(sol, spec, geo):
+    """The fields the accuracy record compares, per case, over fluid nodes in
+    node order: u, rho - 1 and B - B_ext (or C)."""
+    out = []
+    for i, (s, _) in enumerate(geo):
+        m = sol.moments(i)
+        fl = np.asarray(s).reshape(-1) == 0
+        f = {"u": m["u"][fl], "rho": m["rho"][fl] - 1.0}
+        if spec["kind"] == "reactive":
+            f["C"] = m["C"][fl]
+        else:
+            f["b"] = m["B"][fl] - np.array([0.0, spec["params"][i]["B0"], 0.0])
+        out.append(f)
+    return out
+
+
+def oracle_leg(spec, acc_steps, fields, steady):
+    """The CPU-baseline leg: times the FP64 oracle on the host cores (first
+    cases of the workload up to 1.5 M fluid nodes, about 12 s) and uses it
+    to check this run: the accuracy record and the steady-state errors
+    against the finite-volume pipe solution."""
+    out = {}
+    sims, nodes = oracle_sims(spec, target_nodes=1.5e6)
+    threads = max(1, min(16, os.cpu_count() or 1))
+    mlups, steps, el = time_oracle(sims, budget_s=12.0)
+    out["cpu_baseline"] = {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                           "sample": "FP64 oracle, %d of the %d cases at full size (%d fluid nodes), %d time steps "
+                                     "in %.1f s" % (len(sims), len(spec["params"]), nodes, steps, el)}
+    del sims
+    if fields is not None:
+        t0 = time.perf_counter()
+        acc = accuracy_vs_oracle(spec, acc_steps, fields)
+        out["accuracy"] = {"against": "FP64 oracle, same cases from the same state, node by node",
+                           "time_steps": acc_steps, "storage": spec["storage"],
+                           "norm_rel_error": acc,
+                           "metric": "max over cases of max|gpu - oracle| / max|oracle| per field over fluid "
+                                     "nodes (b = B - B_ext); rho: max|gpu - oracle| in units of rho0",
+                           "oracle_s": time.perf_counter() - t0}
+    if steady is not None:
+        out["steady_errors"] = steady_errors(steady)
+    return out
+
+
+def steady_errors(st):
+    """Both forms' steady axial velocity against the finite-volume solution of
+    the pipe problem (the oracle's independent solver), per held-out case."""
+    from oracle import pipe_fd as FD
+    res = []
+    for c in st["cases"]:
+        info = c["info"]
+        r, th, uf, bf = FD.solve(info["R"], info["B0"], info["nu"], info["eta"], info["accel"], wall=info["wall"],
+                                 nr=96, nt=192)
+        ua = FD.sample(r, th, uf, c["yy"], c["zz"])
+        den = np.abs(ua).max()
+        res.append({"plain": float(np.abs(c["u_plain"] - ua).max() / den),
+                    "combined": float(np.abs(c["u_comb"] - ua).max() / den)})
+    return res
+
+
 def run_reference(args):
+    """The FP64 oracle on the host cores: each bench step is one time step of
+    the first cases of the workload (up to 1.5 M fluid nodes; a bounded
+    sample of the bench step's 100 time steps of every case)."""
     rank, world, local = dist_env()
     if rank != 0:
         return 0
     if args.workload == "steady_pipe":
         return run_reference_steady(args)
-    wl = build_workload(args.workload)
-    sims, nodes, threads = oracle_sample(wl, 2.0e5)
+    spec = workload_spec(args.workload)
+    sims, nodes = oracle_sims(spec, target_nodes=1.5e6)
+    threads = max(1, min(16, os.cpu_count() or 1))
     for _ in range(args.warmup):
         for s, _ in sims:
             s.step(1)
@@ -292,48 +442,64 @@ def run_reference(args):
             s.step(1)
     el = time.perf_counter() - t0
     mlups = nodes * args.steps / el / 1e6
-    sample = "first %d cases of the workload (%d fluid nodes), FP64 oracle, one time step per bench step" % (
-        len(sims), nodes)
+    sample = "FP64 oracle, %d of the %d cases at full size (%d fluid nodes), one time step per bench step" % (
+        len(sims), len(spec["params"]), nodes)
     line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": wl["desc"], "sample": sample},
+            "data": "synthetic", "config": spec_config(spec),
             "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_reference_steady(args):
-    """The oracle on case 0 of the steady workload: seconds for --reference-steps
-    time steps of all held-out cases, projected from the timed steps."""
-    wl = steady_workload(args)
-    sims, nodes, threads = oracle_sample(dict(wl, cases=wl["cases"][:1], infos=wl["infos"][:1]), 1.0)
-    for _ in range(args.warmup):
-        for s, _ in sims:
-            s.step(1)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        for s, _ in sims:
-            s.step(1)
-    el = time.perf_counter() - t0
-    mlups = nodes * args.steps / el / 1e6
-    fluid = sum(int(np.sum(np.asarray(s) == 0)) for s, _ in wl["geo"])
-    steps = args.reference_steps or 1000
-    value = fluid * steps / (mlups * 1e6)
-    sample = "FP64 oracle on case 0 (%d fluid nodes), %d steps in %.1f s; value = %d steps of all %d cases at " \
-             "that rate" % (nodes, args.steps, el, steps, len(wl["cases"]))
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": wl["desc"], "sample": sample},
-            "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
 # ----------------------------------------------------------------------------- GPU arm
+def make_solver(spec, stream, local):
+    from paper_2506_00907_gb300 import lbm
+    geo = product_cases(spec)
+    lat = lbm.LBM_D2Q9 if spec["dim"] == 2 else lbm.LBM_D3Q19
+    phys = lbm.LBM_FLOW | (lbm.LBM_CD if spec["kind"] == "reactive" else lbm.LBM_MHD)
+    prec = {"fp16s": lbm.LBM_FP16S, "bf16s": lbm.LBM_BF16S, "fp32": lbm.LBM_FP32, "fp64": lbm.LBM_FP64}[spec["prec"]]
+    sol = lbm.Solver(lat, prec, phys, [g[0] for g in geo], stream=stream.cuda_stream, device=local)
+    for i, g in enumerate(geo):
+        sol.set_walls(i, g[1], g[2])
+    return sol, [(g[1], g[2]) for g in geo], [g[3] for g in geo]
+
+
+def bench_runner(sol, stream, W):
+    """Runs W untimed bench steps (one 100-step graph replay + the FP64
+    check each; a check is collected after the next replay has been
+    enqueued, so the GPU never waits for the host) and returns run(n, timed),
+    which enqueues n more, and the list that collects CUDA events around each
+    timed replay.  The first warm-up step captures the graph; 100 steps keep
+    the buffer parity, so every later step replays that graph."""
+    import torch
+    kernel_ev = []
+
+    def run(n, timed):
+        pending = False
+        for _ in range(n):
+            if timed:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sol.step(GRAPH)
+                b.record(stream)
+                kernel_ev.append((a, b))
+            else:
+                sol.step(GRAPH)
+            if pending:
+                sol.check_wait(raise_unstable=False)
+            sol.check_async()
+            pending = True
+        return pending
+
+    if run(W, False):
+        sol.check_wait(raise_unstable=False)
+    torch.cuda.synchronize()
+    return run, kernel_ev
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -346,13 +512,10 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B.build()
-    wl = build_workload(args.workload)
+    spec = workload_spec(args.workload, rank, world)
     stream = torch.cuda.Stream()                 # the solver's stream; every event below is recorded on it
     torch.cuda.set_stream(stream)
-    sol = lbm.Solver(wl["lattice"], wl["prec"], wl["physics"], wl["cases"], stream=stream.cuda_stream, device=local)
-    for i, (s, l) in enumerate(wl["geo"]):
-        sol.set_walls(i, s, l)
-    fluid = sum(int(np.sum(np.asarray(s) == 0)) for s, _ in wl["geo"])
+    sol, geo, infos = make_solver(spec, stream, local)
     tune = None
     if args.launch:
         sol.set_launch(*(int(x) for x in args.launch.split(",")))
@@ -361,37 +524,12 @@ def run_ours(args):
         cache = os.path.join(ROOT, "paper_2506_00907_gb300", "_build", "autotune.txt")
         sol.autotune(cache, iters=20)
         tune = sol.get_launch()
-    sol.set_graph(CHECK_EVERY)
-    K = max(CHECK_EVERY, (args.steps // CHECK_EVERY) * CHECK_EVERY)
-    W = max(3, args.warmup)
+    sol.set_graph(GRAPH)
+    K, W = args.steps, max(3, args.warmup)
+    if K < 1:
+        raise SystemExit("--steps must be >= 1")
 
-    kernel_ev = []                  # (start, end, steps) around each replay of the step graph
-
-    def run(nsteps, timed=False, collect_last=True):
-        # the check of each block of steps is collected only after the next
-        # block has been enqueued, so the GPU never waits for the host
-        done, pending = 0, False
-        while done < nsteps:
-            k = min(CHECK_EVERY, nsteps - done)
-            if timed:
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                sol.step(k)
-                b.record(stream)
-                kernel_ev.append((a, b, k))
-            else:
-                sol.step(k)
-            done += k
-            if pending:
-                sol.check_wait(raise_unstable=False)
-                pending = False
-            if done % CHECK_EVERY == 0:
-                sol.check_async()
-                pending = True
-        if pending and collect_last:
-            sol.check_wait(raise_unstable=False)
-    run(W)
-    torch.cuda.synchronize()
+    run, kernel_ev = bench_runner(sol, stream, W)
     if world > 1:
         dist.barrier()
     clocks = Clocks(local)
@@ -399,111 +537,234 @@ def run_ours(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    run(K, timed=True, collect_last=False)
+    pending = run(K, True)
     e1.record(stream)
-    sol.check_wait(raise_unstable=False)          # the last block's check (its kernels precede e1)
+    if pending:
+        sol.check_wait(raise_unstable=False)          # the last step's check (its kernels precede e1)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1), device="cuda")
+    ms_local = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms_local, device="cuda")
+    fluid_all = sum_over_ranks(spec["fluid"], device="cuda")
     if world > 1:
         dist.barrier()
-    ms_step = ms / K
-    value = whole_job_mlups(fluid, world, K, ms)
+    value = whole_job_mlups(fluid_all, K * GRAPH, ms)
+    time_steps_done = (W + K) * GRAPH
 
-    elem = {lbm.LBM_FP64: 8, lbm.LBM_FP32: 4}.get(wl["prec"], 2)
-    alg_bytes = 2.0 * wl["planes"] * elem * fluid                # one read + one write per population
-    peak, peak_kind = peak_hbm()
-    # the step kernels alone (bulk k_step + boundary k_boundary): replays of the
-    # step graph hold only step launches
+    elem = {lbm.LBM_FP64: 8, lbm.LBM_FP32: 4}.get(sol.prec, 2)
+    alg_bytes = 2.0 * spec["planes"] * elem * spec["fluid"]          # one read + one write per population
+    pk = peaks()
     per_step = lbm.lbm_launches_per_step(sol.ctx)
-    launches = K * per_step + 2 * (K // CHECK_EVERY)
-    ms_kernel = sum(a.elapsed_time(b) for a, b, _ in kernel_ev) / sum(k for _, _, k in kernel_ev)
+    launches = K * (GRAPH * per_step + 2)
+    ms_kernel = sum(a.elapsed_time(b) for a, b in kernel_ev) / (GRAPH * len(kernel_ev))
     achieved = alg_bytes / (ms_kernel * 1e-3) / 1e9
     out = sol.check(raise_unstable=False)
     stable = bool(np.all(out[:, 5] == 0))
+    do_oracle = rank == 0 and world == 1 and not args.no_cpu_baseline
+    fields = gpu_fields(sol, spec, geo) if do_oracle else None
 
-    # end to end through the C ABI: pinned host state in, 100 steps, reductions out
+    # end to end through the C ABI: pinned host state in, one bench step, reductions out
     blob_np = sol.get_state()
     pinned = torch.empty(blob_np.size, dtype=torch.uint8, pin_memory=True)
     pinned.numpy()[:] = blob_np
-    red = np.zeros(8 * len(wl["cases"]))
+    red = np.zeros(8 * len(spec["params"]))
     L = lbm.lib()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.e2e_iters):
         L.lbm_set_state(sol.ctx, pinned.data_ptr(), blob_np.size)
-        sol.step(CHECK_EVERY)
+        sol.step(GRAPH)
         L.lbm_check(sol.ctx, red.ctypes.data_as(lbm.ctypes.POINTER(lbm.ctypes.c_double)))
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * fluid * CHECK_EVERY * args.e2e_iters / e2e_s / 1e6, "unit": "MLUPS",
-           "h2d_bytes_per_step": int(blob_np.size) / CHECK_EVERY, "d2h_bytes_per_step": red.nbytes / CHECK_EVERY,
-           "step": "host->device state copy from pinned memory, %d time steps, FP64 reductions read back; "
-                   "bytes are per time step" % CHECK_EVERY}
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sims, nodes, threads = oracle_sample(wl, 1.5e6)
-        mlups, steps, el = time_oracle(sims, budget_s=12.0)
-        cpu = {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
-               "sample": "FP64 oracle on the first %d cases (%d fluid nodes), %d steps in %.1f s" % (
-                   len(sims), nodes, steps, el)}
+    e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0), device="cuda")
+    e2e = {"value": whole_job_mlups(fluid_all, GRAPH * args.e2e_iters, e2e_ms), "unit": "MLUPS",
+           "h2d_bytes_per_step": int(blob_np.size), "d2h_bytes_per_step": int(red.nbytes),
+           "step": "host->device state copy from pinned memory, one bench step (%d time steps), FP64 reduction "
+                   "record read back; bytes per bench step" % GRAPH}
+    fp64 = None
+    if rank == 0 and not args.no_fp64 and args.workload == "hartmann_batch":
+        sol.close()
+        sol = None
+        fp64 = fp64_record(spec, stream, local, pk)
+    steady = None
+    if rank == 0 and world == 1 and not args.no_steady and args.workload == "hartmann_batch":
+        if sol is not None:
+            sol.close()
+            sol = None
+        steady = steady_record(args, stream)
     if rank == 0:
         traffic = measured_traffic(args.workload)
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K, "warmup": W,
-                "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "data": "synthetic",
-                "config": {"workload": wl["desc"], "storage": wl["storage"], "cases": len(wl["cases"]),
-                           "fluid_nodes": fluid, "launch": tune,
-                           "graph_steps": CHECK_EVERY, "reduction_every": CHECK_EVERY,
-                           "cw_raised_to_stability_limit": wl.get("cw_clamped", 0),
-                           "l2": "state %.0f MB > 129 MB L2, no flush" % (2 * wl["planes"] * elem * fluid / 1e6),
-                           "stable": stable},
-                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": traffic,
-                             "peak_kind": peak_kind,
-                             "bytes_per_step": alg_bytes, "ms_per_step_kernels": ms_kernel,
+                "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if elem < 8 else "f64", "data": "synthetic", "config": spec_config(spec),
+                "storage": spec["storage"], "ms_per_time_step": ms / (K * GRAPH),
+                "launch": tune, "cw_raised_to_stability_limit": spec["cw_clamped"], "stable": stable,
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm"], "unit": "GB/s",
+                             "frac": achieved / pk["hbm"], "traffic": traffic,
+                             "peak_kind": pk["kind"],
+                             "bytes_per_time_step": alg_bytes, "ms_per_time_step_kernels": ms_kernel,
                              "timing": "CUDA events on the solver stream around each replay of the %d-step "
-                                       "graph inside the timed region (step launches only)" % CHECK_EVERY,
+                                       "graph inside the timed region (step launches only)" % GRAPH,
                              "kernel": STEP_KERNEL[tune["variant"] if tune else 0]
                                        + ": one time step, %d launches" % per_step},
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk}
-        if cpu:
-            line["cpu_baseline"] = cpu
+        if fp64:
+            line["fp64"] = fp64
+        if steady:
+            line["steady"] = {k: v for k, v in steady.items() if k != "cases"}
+        if do_oracle:
+            leg = oracle_leg(spec, time_steps_done, fields, steady)
+            line["cpu_baseline"] = leg["cpu_baseline"]
+            if "accuracy" in leg:
+                line["accuracy"] = leg["accuracy"]
+            if "steady_errors" in leg:
+                e = leg["steady_errors"]
+                line["steady"]["error_vs_fv"] = e
+                line["steady"]["combined_within_1.05x_plain"] = all(c["combined"] <= 1.05 * c["plain"] for c in e)
         print(json.dumps(line), flush=True)
-    sol.close()
+    if sol is not None:
+        sol.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
 
 
+def fp64_record(spec, stream, local, pk):
+    """The same cases with FP64 storage and arithmetic: MLUPS, and the step
+    time against the HBM bound (2 x 19 x 8 bytes per node)."""
+    import torch
+    from paper_2506_00907_gb300 import lbm
+    s64 = dict(spec, prec="fp64")
+    sol, geo, _ = make_solver(s64, stream, local)
+    sol.set_launch(0, 128, 0, 1, 2, 1)
+    sol.set_graph(GRAPH)
+    sol.step(GRAPH)
+    torch.cuda.synchronize()
+    ev = []
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sol.step(GRAPH)
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    ms = min(a.elapsed_time(b) for a, b in ev) / GRAPH
+    sol.close()
+    alg = 2.0 * spec["planes"] * 8 * spec["fluid"]
+    return {"mlups": spec["fluid"] / (ms * 1e-3) / 1e6, "ms_per_time_step": ms, "bytes_per_time_step": alg,
+            "hbm": {"achieved": alg / (ms * 1e-3) / 1e9, "peak": pk["hbm"], "unit": "GB/s",
+                    "frac": alg / (ms * 1e-3) / 1e9 / pk["hbm"]},
+            "timing": "best of 3 replays of the %d-step graph, step launches only" % GRAPH}
+
+
 # ----------------------------------------------------------------------------- time to steady state
-STEADY_SHAPE, STEADY_R = (32, 256, 256), 126.0
-
-
-def steady_workload(args):
-    """Held-out MHD pipes of the steady-state comparison (seed 2507)."""
+def steady_pipes(shape, R, n, seed):
+    """Held-out MHD pipes of the steady-state comparison (product builders)."""
     from paper_2506_00907_gb300 import cases as CS
+    from paper_2506_00907_gb300 import inputs as IN
+    from paper_2506_00907_gb300 import surrogate as SG
+    held = IN.pipe_draws(n, seed=seed, Ha=SG.HA_RANGE, cw=SG.CW_RANGE)
+    return held, [CS.pipe(shape, R, h["Ha"], ("shercliff", h["cw"])) for h in held]
+
+
+def steady_compare(stream, shape, R, n_cases, train_cases, train_epochs, tol, max_steps, args):
+    """Wall time to the steady-state residual: the plain form (FP32 storage,
+    one case per context, cold start) against the combined form (network warm
+    start, FP16 storage with all cases in one launch per step, then FP32 from
+    the switch residual on).  The network is trained in the same run on
+    steady fields the batched solver produces for `train_cases` draws at
+    radius train-R (one axial node)."""
+    import torch
     from paper_2506_00907_gb300 import inputs as IN
     from paper_2506_00907_gb300 import lbm
     from paper_2506_00907_gb300 import surrogate as SG
-    held = IN.pipe_draws(args.steady_cases, seed=2507, Ha=SG.HA_RANGE, cw=SG.CW_RANGE)
-    group = [CS.pipe(STEADY_SHAPE, STEADY_R, h["Ha"], ("shercliff", h["cw"])) for h in held]
-    return dict(held=held, group=group, cases=[g[0] for g in group], geo=[(g[1], g[2]) for g in group],
-                infos=[g[3] for g in group], dim=3, lattice=lbm.LBM_D3Q19, planes=40,
-                desc="3D MHD pipe 32x256x256 (periodic axial), R = 126, %d held-out cases Ha~U[10,50], "
-                     "Shercliff c_w~logU[1e-3,1] (seed 2507); D3Q19 + D3Q7 x 3" % len(held))
+    phys = lbm.LBM_FLOW | lbm.LBM_MHD
+    held, group = steady_pipes(shape, R, n_cases, 2507)
+    t0 = time.perf_counter()
+    draws = IN.pipe_draws(train_cases, seed=IN.SEED, Ha=SG.HA_RANGE, cw=SG.CW_RANGE)
+    n_t = int(2 * args.train_R) + 4
+    X, T, gstats = SG.generate(draws, n=n_t, R=args.train_R, tol=args.train_tol, max_steps=args.train_max_steps,
+                               prec=lbm.LBM_FP32, batch=128, stream=stream.cuda_stream, per_case=args.train_per_case)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    net, hist = SG.train(X, T, epochs=train_epochs, batch=4096, lr=3e-3, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    sur = SG.Surrogate(net, SG.HA_RANGE, SG.CW_RANGE)
+    c = (shape[1] - 1) / 2.0
+    zz, yy = np.meshgrid(np.arange(shape[2]) - c, np.arange(shape[1]) - c, indexing="ij")
+    yy = np.broadcast_to(yy[:, :, None], (shape[2], shape[1], shape[0])).reshape(-1)
+    zz = np.broadcast_to(zz[:, :, None], (shape[2], shape[1], shape[0])).reshape(-1)
+
+    def axial(sol, i):
+        fl = np.asarray(group[i][1]).reshape(-1) == 0
+        return sol.moments(i)["u"][fl, 0], fl
+
+    plain = []
+    for i, (cs, solid, links, info) in enumerate(group):
+        sol = lbm.Solver(lbm.LBM_D3Q19, lbm.LBM_FP32, phys, [cs], stream=stream.cuda_stream)
+        sol.set_walls(0, solid, links)
+        sol.set_graph(GRAPH)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        k, r = sol.run_to_steady(max_steps, GRAPH, tol)
+        dt = time.perf_counter() - t
+        u, fl = axial(sol, 0)
+        plain.append(dict(steps=int(k), residual=float(r), s=dt, u=u, fl=fl))
+        sol.close()
+    plain_s = sum(p["s"] for p in plain)
+    s16 = lbm.Solver(lbm.LBM_D3Q19, lbm.LBM_FP16S, phys, [g[0] for g in group], stream=stream.cuda_stream)
+    s32 = lbm.Solver(lbm.LBM_D3Q19, lbm.LBM_FP32, phys, [g[0] for g in group], stream=stream.cuda_stream)
+    for i, (cs, solid, links, info) in enumerate(group):
+        s16.set_walls(i, solid, links)
+        s32.set_walls(i, solid, links)
+    s16.set_graph(GRAPH)
+    s32.set_graph(GRAPH)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    warm = [SG.warm_start(s16, i, sur, g[3], shape, R, held[i]["Ha"], held[i]["cw"]) for i, g in enumerate(group)]
+    k16, r16 = s16.run_to_steady(max_steps, GRAPH, args.switch_tol)
+    s32.convert_from(s16)
+    k32, r32 = s32.run_to_steady(max_steps, GRAPH, tol)
+    comb_s = time.perf_counter() - t
+    cases = []
+    for i, p in enumerate(plain):
+        u, fl = axial(s32, i)
+        info = group[i][3]
+        cases.append(dict(info=info, yy=yy[fl], zz=zz[fl], u_plain=p["u"], u_comb=u))
+    s16.close()
+    s32.close()
+    fluid = [int(np.sum(np.asarray(g[1]) == 0)) for g in group]
+    return {"shape": list(shape), "R": R, "held_out": [dict(Ha=h["Ha"], cw=h["cw"]) for h in held],
+            "residual": tol, "switch_residual": args.switch_tol, "max_steps": max_steps,
+            "plain_s": plain_s, "combined_s": comb_s, "speedup": plain_s / comb_s,
+            "plain": [{"steps": p["steps"], "residual": p["residual"], "s": p["s"]} for p in plain],
+            "combined": {"fp16_steps": int(k16), "fp16_residual": float(r16), "fp32_steps": int(k32),
+                         "fp32_residual": float(r32), "warm_started": warm},
+            "plain_node_updates": int(sum(f * p["steps"] for f, p in zip(fluid, plain))),
+            "surrogate": {"train_cases": train_cases, "train_R": args.train_R, "samples": int(len(X)),
+                          "epochs": train_epochs, "generate_s": gen_s, "train_s": train_s,
+                          "loss_first": float(hist[0]), "loss_last": float(hist[-1]), "generate": gstats},
+            "plain_form": "FP32 storage, one case per context, cold start, CUDA graphs of %d steps, residual "
+                          "every %d steps" % (GRAPH, GRAPH),
+            "combined_form": "network warm start, FP16 offset storage with all cases in one launch per step "
+                             "until the switch residual, then FP32 storage (state converted on the GPU)",
+            "cases": cases}
+
+
+def steady_record(args, stream):
+    """The bounded steady-state record of the default line: 2 held-out pipes
+    of 32x128x128 (R = 62), network trained on 64 draws."""
+    return steady_compare(stream, (32, 128, 128), 62.0, args.steady_cases or 2, args.train_cases or 64,
+                          args.train_epochs or 60, args.steady_tol or 5e-6, args.steady_max_steps or 300000, args)
 
 
 def run_steady(args):
-    """Wall time to the steady-state residual: the plain form (FP32 storage,
-    one case per context, cold start) against the combined form (network warm
-    start, FP16 storage, all cases in one launch per step, then FP32 from
-    the switch residual on)."""
+    """--workload steady_pipe: the 32x256x256 comparison (R = 126, network
+    trained on 512 draws at R = 62); the line's value is the combined form's
+    time to the residual."""
     import torch
     from paper_2506_00907_gb300 import build as B
-    from paper_2506_00907_gb300 import inputs as IN
-    from paper_2506_00907_gb300 import lbm
-    from paper_2506_00907_gb300 import surrogate as SG
     rank, world, local = dist_env()
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU")
@@ -513,113 +774,68 @@ def run_steady(args):
     B.build()
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    phys = lbm.LBM_FLOW | lbm.LBM_MHD
-    wl = steady_workload(args)
-    held, group = wl["held"], wl["group"]
-    fluid = [int(np.sum(np.asarray(g[1]) == 0)) for g in group]
-
-    # the network: steady fields that the batched solver produces at the training resolution
-    t0 = time.perf_counter()
-    draws = IN.pipe_draws(args.train_cases, seed=IN.SEED, Ha=SG.HA_RANGE, cw=SG.CW_RANGE)
-    n_t = int(2 * args.train_R) + 4
-    X, T, gstats = SG.generate(draws, n=n_t, R=args.train_R, tol=args.train_tol, max_steps=args.train_max_steps,
-                               prec=lbm.LBM_FP32, batch=128, stream=stream.cuda_stream, per_case=args.train_per_case)
-    gen_s = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    net, hist = SG.train(X, T, epochs=args.train_epochs, batch=4096, lr=3e-3, stream=stream.cuda_stream)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
-    sur = SG.Surrogate(net, SG.HA_RANGE, SG.CW_RANGE)
-
-    def fields(sol, i, g):
-        m = sol.moments(i)
-        fl = np.asarray(group[g][1]).reshape(-1) == 0
-        return m["u"][fl, 0], m["B"][fl, 0]
-
-    # plain form
-    plain = []
-    for i, (c, solid, links, info) in enumerate(group):
-        sol = lbm.Solver(lbm.LBM_D3Q19, lbm.LBM_FP32, phys, [c], stream=stream.cuda_stream)
-        sol.set_walls(0, solid, links)
-        sol.set_graph(CHECK_EVERY)
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        k, r = sol.run_to_steady(args.steady_max_steps, CHECK_EVERY, args.steady_tol)
-        dt = time.perf_counter() - t
-        plain.append(dict(steps=int(k), residual=float(r), s=dt, fields=fields(sol, 0, i)))
-        sol.close()
-    plain_s = sum(p["s"] for p in plain)
-
-    # combined form (contexts and walls are set up outside the timed region, as for the plain form)
-    t_setup = time.perf_counter()
-    s16 = lbm.Solver(lbm.LBM_D3Q19, lbm.LBM_FP16S, phys, wl["cases"], stream=stream.cuda_stream)
-    s32 = lbm.Solver(lbm.LBM_D3Q19, lbm.LBM_FP32, phys, wl["cases"], stream=stream.cuda_stream)
-    h2d = 0
-    for i, (c, solid, links, info) in enumerate(group):
-        s16.set_walls(i, solid, links)
-        s32.set_walls(i, solid, links)
-        h2d += np.asarray(solid).nbytes + np.asarray(links).nbytes
-    s16.set_graph(CHECK_EVERY)
-    s32.set_graph(CHECK_EVERY)
-    torch.cuda.synchronize()
-    setup_s = time.perf_counter() - t_setup
-    t = time.perf_counter()
-    warm = [SG.warm_start(s16, i, sur, g[3], STEADY_SHAPE, STEADY_R, held[i]["Ha"], held[i]["cw"])
-            for i, g in enumerate(group)]
-    k16, r16 = s16.run_to_steady(args.steady_max_steps, CHECK_EVERY, args.switch_tol)
-    s32.convert_from(s16)
-    k32, r32 = s32.run_to_steady(args.steady_max_steps, CHECK_EVERY, args.steady_tol)
-    comb_s = time.perf_counter() - t
-    t_rb = time.perf_counter()
-    comb_fields = [fields(s32, i, i) for i in range(len(group))]
-    readback_s = time.perf_counter() - t_rb
-    s16.close()
-    s32.close()
-
-    def nrel(a, b):
-        return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
-    err_u = max(nrel(cf[0], p["fields"][0]) for cf, p in zip(comb_fields, plain))
-    err_b = max(nrel(cf[1], p["fields"][1]) for cf, p in zip(comb_fields, plain))
-    plain_steps = sum(p["steps"] for p in plain)
-    alg = 2.0 * 40 * 4 * sum(f * p["steps"] for f, p in zip(fluid, plain))
-    achieved = alg / plain_s / 1e9
-    peak, peak_kind = peak_hbm()
-    cpu = None
-    if not args.no_cpu_baseline:
-        sims, nodes, threads = oracle_sample(dict(wl, cases=wl["cases"][:1], infos=wl["infos"][:1]), 1.0)
-        mlups, st, el = time_oracle(sims, budget_s=12.0)
-        cpu_s = sum(f * p["steps"] for f, p in zip(fluid, plain)) / (mlups * 1e6)
-        cpu = {"value": cpu_s, "unit": "s", "cores": threads, "kind": "oracle",
-               "sample": "FP64 oracle, case 0 of the workload (%d fluid nodes), %d steps in %.1f s = %.1f MLUPS; "
-                         "value = the plain form's node updates to steady state at that rate" % (
-                             nodes, st, el, mlups)}
-    line = {"metric": METRIC, "value": comb_s, "unit": "s", "n_gpus": 1, "steps": int(k16 + k32),
-            "warmup": 0, "ms_per_step": 1e3 * comb_s / max(1, k16 + k32), "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl["desc"], "residual": args.steady_tol, "switch_residual": args.switch_tol,
-                       "plain": "FP32 storage, one case per context, cold start, CUDA graphs of %d steps, "
-                                "residual every %d steps" % (CHECK_EVERY, CHECK_EVERY),
-                       "combined": "network warm start, FP16 offset storage with all cases in one launch per "
-                                   "step until the switch residual, then FP32 storage (state converted on the GPU)",
+    st = steady_compare(stream, (32, 256, 256), 126.0, args.steady_cases or 2, args.train_cases or 512,
+                        args.train_epochs or 100, args.steady_tol or 1e-6, args.steady_max_steps or 2000000, args)
+    pk = peaks()
+    alg = 2.0 * 40 * 4 * st["plain_node_updates"]
+    achieved = alg / st["plain_s"] / 1e9
+    desc = ("3D MHD pipe 32x256x256 (periodic axial), R = 126, %d held-out cases Ha~U[10,50], Shercliff "
+            "c_w~logU[1e-3,1] (seed 2507); D3Q19 + D3Q7 x 3" % len(st["held_out"]))
+    line = {"metric": METRIC, "value": st["combined_s"], "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": 1e3 * st["combined_s"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "residual": st["residual"], "switch_residual": args.switch_tol,
                        "l2": "state > 129 MB L2, no flush"},
-            "plain_s": plain_s, "speedup": plain_s / comb_s,
-            "plain": [{k: v for k, v in p.items() if k != "fields"} for p in plain],
-            "combined": {"fp16_steps": int(k16), "fp16_residual": float(r16), "fp32_steps": int(k32),
-                         "fp32_residual": float(r32), "warm_started": warm},
-            "error_vs_plain": {"u1": err_u, "b1": err_b},
-            "surrogate": {"train_cases": args.train_cases, "train_R": args.train_R, "samples": int(len(X)),
-                          "generate_s": gen_s, "train_s": train_s, "loss_first": float(hist[0]),
-                          "loss_last": float(hist[-1]), "generate": gstats},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+            "steady": {k: v for k, v in st.items() if k != "cases"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm"], "unit": "GB/s",
+                         "frac": achieved / pk["hbm"], "traffic": None, "peak_kind": pk["kind"],
                          "kernel": "plain form, k_step + k_boundary FP32 with the residual check every %d steps"
-                                   % CHECK_EVERY},
-            "e2e": {"value": setup_s + comb_s + readback_s, "unit": "s", "h2d_bytes_per_step": h2d / max(1, k16 + k32),
-                    "d2h_bytes_per_step": sum(8 * 8 * f for f in fluid) / max(1, k16 + k32),
-                    "step": "context creation and wall upload, the combined run, moments read back"},
-            "gpu_launches": int(2 * (k16 + k32) + 3 * (k16 + k32) // CHECK_EVERY)}
-    if cpu:
-        line["cpu_baseline"] = cpu
+                                   % GRAPH},
+            "e2e": {"value": st["combined_s"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                    "step": "the combined run (contexts and walls set up before it)"},
+            "gpu_launches": int(2 * (st["combined"]["fp16_steps"] + st["combined"]["fp32_steps"]))}
+    if not args.no_cpu_baseline:
+        line["steady"]["error_vs_fv"] = steady_errors(st)
+        spec = dict(kind="pipe", params=[c["info"] for c in st["cases"]], shape=(32, 256, 256))
+        sims, nodes = oracle_sims(spec, target_nodes=1.0)
+        mlups, n, el = time_oracle(sims, budget_s=12.0)
+        line["cpu_baseline"] = {"value": st["plain_node_updates"] / (mlups * 1e6), "unit": "s",
+                                "cores": max(1, min(16, os.cpu_count() or 1)), "kind": "oracle",
+                                "sample": "FP64 oracle, case 0 at full size (%d fluid nodes), %d steps in %.1f s "
+                                          "= %.1f MLUPS; value = the plain form's node updates to steady state at "
+                                          "that rate" % (nodes, n, el, mlups)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_steady(args):
+    """The oracle on case 0 of the steady workload: seconds for 1000 time
+    steps of the held-out cases at its measured rate."""
+    from paper_2506_00907_gb300 import inputs as IN
+    from paper_2506_00907_gb300 import surrogate as SG
+    held = IN.pipe_draws(args.steady_cases or 2, seed=2507, Ha=SG.HA_RANGE, cw=SG.CW_RANGE)
+    params = [IN.pipe_params(126.0, h["Ha"], ("shercliff", h["cw"])) for h in held]
+    spec = dict(kind="pipe", params=params, shape=(32, 256, 256))
+    sims, nodes = oracle_sims(spec, target_nodes=1.0)
+    for _ in range(args.warmup):
+        for s, _ in sims:
+            s.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for s, _ in sims:
+            s.step(1)
+    el = time.perf_counter() - t0
+    mlups = nodes * args.steps / el / 1e6
+    value = len(params) * nodes * 1000 / (mlups * 1e6)
+    sample = "FP64 oracle on case 0 (%d fluid nodes), %d steps in %.1f s; value = 1000 steps of all %d cases at " \
+             "that rate" % (nodes, args.steps, el, len(params))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "3D MHD pipe 32x256x256, R = 126 (held-out draws, seed 2507)"},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": max(1, min(16, os.cpu_count() or 1)),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 

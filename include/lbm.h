@@ -177,8 +177,10 @@ lbm_status lbm_set_graph(lbm_ctx *ctx, int32_t steps_per_graph);
  * Eq. 45): from now on every velocity link of field f in the case (kinds
  * LBM_W_VELOCITY and LBM_W_VELOCITY_EQ15) uses u_wall * cos(omega * t + phase)
  * in the step from t to t + 1, the wall velocity taken at t as f^eq(X, t) in
- * Eq. 41/43.  t counts the context's steps since the latest call of this
- * function (for any case).  The call refolds the wall links of every case
+ * Eq. 41/43.  t counts the context's steps since this call for this case
+ * (a later call for another case leaves this case's phase alone; a later call
+ * for the same case restarts its t at 0).  The motion is part of the state
+ * blob (lbm_get_state) and of lbm_convert_state.  The call refolds the wall links of every case
  * (as lbm_set_walls does) and drops existing graphs; from then on a one-block
  * kernel rewrites the velocity coefficient of each oscillating link ahead of
  * every step, also inside captured graphs, so the step kernels themselves
@@ -228,9 +230,14 @@ lbm_status lbm_run_to_steady(lbm_ctx *ctx, int64_t max_steps, int32_t interval, 
                              int64_t *steps_done, double *residual);
 
 /* Checkpoint: size in bytes of the state blob, and copy it out / in (host
- * memory, synchronises).  The blob holds every population of every case and
- * the step count; restoring it and stepping is bitwise identical to not
- * having stopped.  Errors: LBM_EINVAL (size mismatch), LBM_ECUDA. */
+ * memory, synchronises).  The blob holds every population of every case, the
+ * step count and the wall-motion table of lbm_set_wall_motion (per case
+ * omega, phase, on, and the step at which the motion was set); restoring it
+ * into a context with the same cases and walls and stepping is bitwise
+ * identical to not having stopped, oscillating walls included (a context
+ * restored from a blob takes the blob's wall motion).  Errors: LBM_EINVAL
+ * (size mismatch, not a blob of this version, a moving flux wall in a case
+ * the blob moves), LBM_ECUDA. */
 size_t lbm_state_bytes(const lbm_ctx *ctx);
 lbm_status lbm_get_state(lbm_ctx *ctx, void *host, size_t bytes);
 lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes);
@@ -271,7 +278,8 @@ int64_t lbm_steps_done(const lbm_ctx *ctx);
  *              blocks_per_sm caps the resident blocks per SM (0 = as many as
  *              fit); block, nodes_per_thread and min_blocks are ignored.
  *              Boundary nodes as in variant 0.  Fails with LBM_EINVAL when
- *              the stages do not fit in shared memory.
+ *              the stages do not fit in shared memory.  Not among the
+ *              autotuner's candidates.
  * block (variants 0 and 2): 64..256, multiple of 32. */
 typedef struct {
     int32_t variant;
@@ -296,8 +304,11 @@ lbm_status lbm_get_launch(const lbm_ctx *ctx, lbm_launch *launch);
  * `cache_path` (NULL = no cache) keyed by GPU name, lattice, precision,
  * physics and case sizes; a later call with the same key reads the cache
  * instead of timing.  The context's populations and step count are saved and
- * restored around the timing.  best and best_ms may be NULL.
- * Errors: LBM_ECUDA. */
+ * restored around the timing.  best and best_ms may be NULL.  Candidates:
+ * variants 0, 1 and 2 (not 3).  If a candidate's steps fail, the sweep stops,
+ * the state and the previous launch shape are restored, every resource of
+ * the sweep is released, and the error names the candidate.
+ * Errors: LBM_ENOMEM, LBM_ECUDA (or the failing step's status). */
 lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm_launch *best, double *best_ms);
 
 /* Kernel launches issued per time step (for launch accounting): the bulk
@@ -342,17 +353,22 @@ lbm_status lbm_convert_state(lbm_ctx *dst, lbm_ctx *src);
  *   snap:    device, 7 * nx*ny*nz doubles holding phi_prev = (u, C, B - B0)
  *            plane by plane, replaced by the current phi (the planes the
  *            lattice and physics can make nonzero; the rest are not touched);
- *            NULL skips the residual (sums 6 and 7 then compare with zero).
+ *            NULL takes phi_prev as zero (sums 6 and 7 then both equal
+ *            sum |phi|^2).
  *            Per-node terms are formed as in lbm_check: in FP32 unless the
  *            precision is FP64 (phi_prev is then read rounded to FP32).
  *   out:     host, 8 doubles, the record of lbm_check().
- *   stream:  cudaStream_t (NULL = legacy default stream).  Synchronises it.
+ *   stream:  cudaStream_t (NULL = legacy default stream).  The call
+ *            synchronises it (it reads the record back to the host), so it
+ *            must not be called while that stream is being captured.
  * Limit: at most LBM_NOALLOC_MAX_NODES nodes (larger domains: LBM_EINVAL, with
- * a message on stderr).  The first call on a device looks up the array's
- * device address with that device current; make that first call before any
- * stream capture.  All calls share the one array: calls that overlap on the
- * GPU (other threads or streams) race and must be serialised by the caller.
- * Every call overwrites what it reads, so nothing needs clearing in between.
+ * a message on stderr).  Every call looks up the array's device address on
+ * the current device (cudaGetSymbolAddress), so a context torn down and
+ * recreated in between is no hazard.  All calls share the one array: calls
+ * that overlap on the GPU (other threads or streams) race and must be
+ * serialised by the caller.  Every call overwrites what it reads, so nothing
+ * needs clearing in between.  FP64 storage is reduced with the FP64 step's
+ * rounding policy (no multiply-add contraction), as lbm_check does.
  * Returns LBM_EUNSTABLE (after filling out) if a population is not finite.
  * Errors: LBM_EINVAL, LBM_ECUDA. */
 #define LBM_NOALLOC_MAX_NODES (1 << 22)

@@ -21,6 +21,9 @@ namespace {
 
 thread_local std::string g_err;
 
+// entries per case of the wall-motion table: omega, phase, on, t0
+constexpr int MOTION_W = 4;
+
 struct CaseHost {
     lbm_case cfg;
     int32_t N = 0;
@@ -99,11 +102,12 @@ struct lbm_ctx {
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int graph_steps = 0;
     int64_t steps = 0;
-    // oscillating velocity walls (lbm_set_wall_motion): per case omega, phase, on
+    // oscillating velocity walls (lbm_set_wall_motion): per case omega, phase,
+    // on, t0 (the step count at which the case's motion was set)
     bool motion = false;
     std::vector<double> h_motion;
     double *d_motion = nullptr;
-    long long *d_clock = nullptr;      // steps since the last lbm_set_wall_motion
+    long long *d_clock = nullptr;      // the context's step count, advanced by the clock kernel
     int2 *d_wall_links = nullptr;      // (link index, case) of every velocity link of an oscillating wall
     int32_t n_wall_links = 0;
     int sm_count = 1;
@@ -311,7 +315,7 @@ LinkDev<T> link_dev(const lbm_ctx *c, const CaseHost &cs, const lbm_link &lk) {
     // clock kernel scales cphi from its steady value kept in cB[0] (unused by f links)
     const size_t ci = (size_t)(&cs - c->cases.data());
     if ((lk.kind == LBM_W_VELOCITY || lk.kind == LBM_W_VELOCITY_EQ15) && cphi != 0.0 && !c->h_motion.empty() &&
-        c->h_motion[3 * ci + 2] != 0.0) {
+        c->h_motion[MOTION_W * ci + 2] != 0.0) {
         r.flags |= LINK_WALL_T;
         r.cB[0] = T(cphi);
     }
@@ -515,17 +519,19 @@ int step_grid(const lbm_ctx *c) {
 }
 
 // Wall motion of the coming step (Eq. 45): every velocity link of an oscillating
-// wall gets cphi = (steady cphi, kept in cB[0]) * cos(omega t + phase) of its
-// case at t = the device clock, which then advances by one.  One block;
-// launched ahead of each step (also inside captured graphs) only when a case
-// has wall motion, so the step kernels carry no cost for it.
+// wall gets cphi = (steady cphi, kept in cB[0]) * cos(omega (t - t0) + phase)
+// of its case at t = the device clock (the context's step count), which then
+// advances by one; t0 is the step at which the case's motion was set.  One
+// block; launched ahead of each step (also inside captured graphs) only when
+// a case has wall motion, so the step kernels carry no cost for it.
 template <class T>
 __global__ void k_wall_clock(LinkDev<T> *links, const int2 *wall_links, int n, const double *motion,
                              long long *clock) {
     const long long t = *clock;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int2 w = wall_links[i];
-        const double sc = cos(motion[3 * w.y] * (double)t + motion[3 * w.y + 1]);
+        const double *m = motion + MOTION_W * w.y;
+        const double sc = cos(m[0] * ((double)t - m[3]) + m[1]);
         links[w.x].cphi = T((double)links[w.x].cB[0] * sc);
     }
     __syncthreads();
@@ -839,7 +845,7 @@ lbm_status lbm_set_walls(lbm_ctx *ctx, int32_t case_id, const uint8_t *solid, co
                                     : (lk.kind == LBM_W_GIVEN || lk.kind == LBM_W_FLUX || lk.kind == LBM_W_NEUMANN_BFL ||
                                        lk.kind == LBM_W_FLUX_SIMPLIFIED);
         if (!ok_kind) return fail(ctx, LBM_EINVAL, "link %zu: kind %d not valid for field %d", i, lk.kind, f);
-        if (ctx->motion && ctx->h_motion[3 * case_id + 2] != 0.0 && moving_flux_link(lk))
+        if (ctx->motion && ctx->h_motion[MOTION_W * case_id + 2] != 0.0 && moving_flux_link(lk))
             return fail(ctx, LBM_EINVAL, "link %zu: a moving flux wall in a case with wall motion", i);
         if (lk.node >= (uint64_t)N || sol[lk.node]) return fail(ctx, LBM_EINVAL, "link %zu: node %u not fluid", i, lk.node);
         if (!(lk.d > 0.0 && lk.d <= 1.0)) return fail(ctx, LBM_EINVAL, "link %zu: d = %g outside (0, 1]", i, lk.d);
@@ -912,28 +918,56 @@ static lbm_status capture_graph(lbm_ctx *ctx) {
     return LBM_OK;
 }
 
+// The device clock of the wall motion follows the context's step count.
+static lbm_status set_clock(lbm_ctx *ctx) {
+    if (!ctx->d_clock) return LBM_OK;
+    const long long t = ctx->steps;
+    CK(cudaMemcpyAsync(ctx->d_clock, &t, sizeof t, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+// Installs a wall-motion table (MOTION_W doubles per case: omega, phase, on,
+// t0), sets the device clock to the step count and refolds the wall links
+// (marks the moving ones, keeps their steady velocity term; drops graphs
+// captured without or with a clock launch).  Nothing to do when neither the
+// table nor the context has a moving case.
+static lbm_status apply_motion(lbm_ctx *ctx, const double *table) {
+    const size_t n = ctx->cases.size();
+    bool any = false;
+    for (size_t c = 0; c < n; ++c) {
+        if (table[MOTION_W * c + 2] == 0.0) continue;
+        any = true;
+        if (!std::isfinite(table[MOTION_W * c]) || !std::isfinite(table[MOTION_W * c + 1]) ||
+            !std::isfinite(table[MOTION_W * c + 3]))
+            return fail(ctx, LBM_EINVAL, "case %zu: non-finite wall motion", c);
+        for (const lbm_link &lk : ctx->cases[c].links)
+            if (moving_flux_link(lk))
+                return fail(ctx, LBM_EINVAL, "case %zu has a flux wall of field %d with a wall velocity", c, lk.field);
+    }
+    if (!any && !ctx->motion) return LBM_OK;
+    if (!ctx->d_motion) CK(cudaMalloc(&ctx->d_motion, MOTION_W * n * sizeof(double)));
+    if (!ctx->d_clock) CK(cudaMalloc(&ctx->d_clock, sizeof(long long)));
+    ctx->h_motion.assign(table, table + MOTION_W * n);
+    CK(cudaMemcpyAsync(ctx->d_motion, ctx->h_motion.data(), MOTION_W * n * sizeof(double), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    const lbm_status st = set_clock(ctx);
+    if (st != LBM_OK) return st;
+    ctx->motion = any;
+    return upload_walls(ctx);
+}
+
 lbm_status lbm_set_wall_motion(lbm_ctx *ctx, int32_t case_id, double omega, double phase) {
     if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (case_id < 0 || case_id >= (int32_t)ctx->cases.size()) return fail(ctx, LBM_EINVAL, "bad case id %d", case_id);
     if (!std::isfinite(omega) || !std::isfinite(phase)) return fail(ctx, LBM_EINVAL, "non-finite omega or phase");
-    for (const lbm_link &lk : ctx->cases[case_id].links)
-        if (moving_flux_link(lk))
-            return fail(ctx, LBM_EINVAL, "case %d has a flux wall of field %d with a wall velocity", case_id, lk.field);
-    const size_t n = ctx->cases.size();
-    if (!ctx->d_motion) CK(cudaMalloc(&ctx->d_motion, 3 * n * sizeof(double)));
-    if (!ctx->d_clock) CK(cudaMalloc(&ctx->d_clock, sizeof(long long)));
-    if (ctx->h_motion.empty()) ctx->h_motion.assign(3 * n, 0.0);
-    ctx->h_motion[3 * case_id] = omega;
-    ctx->h_motion[3 * case_id + 1] = phase;
-    ctx->h_motion[3 * case_id + 2] = 1.0;
-    CK(cudaMemcpyAsync(ctx->d_motion, ctx->h_motion.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice,
-                       ctx->stream));
-    CK(cudaMemsetAsync(ctx->d_clock, 0, sizeof(long long), ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    ctx->motion = true;
-    // refold the links (marks the moving ones, keeps their steady velocity
-    // term) and drop the graphs captured without a clock launch
-    return upload_walls(ctx);
+    std::vector<double> t = ctx->h_motion;
+    if (t.empty()) t.assign(MOTION_W * ctx->cases.size(), 0.0);
+    t[MOTION_W * case_id] = omega;
+    t[MOTION_W * case_id + 1] = phase;
+    t[MOTION_W * case_id + 2] = 1.0;
+    t[MOTION_W * case_id + 3] = (double)ctx->steps;
+    return apply_motion(ctx, t.data());
 }
 
 lbm_status lbm_step(lbm_ctx *ctx, int32_t nsteps) {
@@ -1064,17 +1098,26 @@ lbm_status lbm_run_to_steady(lbm_ctx *ctx, int64_t max_steps, int32_t interval, 
     return st;
 }
 
+// State blob: magic, step count, the current population buffer, then the
+// wall-motion table (MOTION_W doubles per case, zeros without motion).
+static constexpr uint64_t STATE_MAGIC = 0x32544154534d424cull;   // "LBMSTAT2"
+
+static size_t pool_bytes(const lbm_ctx *ctx) { return (size_t)ctx->pool_elems * ctx->elem; }
+
 size_t lbm_state_bytes(const lbm_ctx *ctx) {
-    return ctx ? 16 + (size_t)ctx->pool_elems * ctx->elem : 0;
+    return ctx ? 16 + pool_bytes(ctx) + MOTION_W * ctx->cases.size() * sizeof(double) : 0;
 }
 
 lbm_status lbm_get_state(lbm_ctx *ctx, void *host, size_t bytes) {
     if (!ctx || !host) return fail(ctx, LBM_EINVAL, "NULL argument");
     if (bytes != lbm_state_bytes(ctx)) return fail(ctx, LBM_EINVAL, "state size mismatch");
-    uint64_t hdr[2] = {0x4c424d5354415445ull, (uint64_t)ctx->steps};
-    std::memcpy(host, hdr, 16);
-    CK(cudaMemcpyAsync(static_cast<char *>(host) + 16, ctx->pool[ctx->cur], bytes - 16, cudaMemcpyDeviceToHost,
-                       ctx->stream));
+    uint64_t hdr[2] = {STATE_MAGIC, (uint64_t)ctx->steps};
+    char *h = static_cast<char *>(host);
+    std::memcpy(h, hdr, 16);
+    CK(cudaMemcpyAsync(h + 16, ctx->pool[ctx->cur], pool_bytes(ctx), cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<double> table = ctx->h_motion;
+    table.resize(MOTION_W * ctx->cases.size(), 0.0);
+    std::memcpy(h + 16 + pool_bytes(ctx), table.data(), table.size() * sizeof(double));
     CK(cudaStreamSynchronize(ctx->stream));
     return LBM_OK;
 }
@@ -1083,13 +1126,15 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes) {
     if (!ctx || !host) return fail(ctx, LBM_EINVAL, "NULL argument");
     if (bytes != lbm_state_bytes(ctx)) return fail(ctx, LBM_EINVAL, "state size mismatch");
     uint64_t hdr[2];
-    std::memcpy(hdr, host, 16);
-    if (hdr[0] != 0x4c424d5354415445ull) return fail(ctx, LBM_EINVAL, "not a state blob");
-    CK(cudaMemcpyAsync(ctx->pool[ctx->cur], static_cast<const char *>(host) + 16, bytes - 16,
-                       cudaMemcpyHostToDevice, ctx->stream));
+    const char *h = static_cast<const char *>(host);
+    std::memcpy(hdr, h, 16);
+    if (hdr[0] != STATE_MAGIC) return fail(ctx, LBM_EINVAL, "not a state blob");
+    std::vector<double> table(MOTION_W * ctx->cases.size());
+    std::memcpy(table.data(), h + 16 + pool_bytes(ctx), table.size() * sizeof(double));
+    CK(cudaMemcpyAsync(ctx->pool[ctx->cur], h + 16, pool_bytes(ctx), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->steps = (int64_t)hdr[1];
-    return LBM_OK;
+    return apply_motion(ctx, table.data());
 }
 
 int64_t lbm_steps_done(const lbm_ctx *ctx) { return ctx ? ctx->steps : 0; }
@@ -1135,7 +1180,9 @@ lbm_status lbm_convert_state(lbm_ctx *dst, lbm_ctx *src) {
     }
     CK(cudaStreamSynchronize(dst->stream));
     dst->steps = src->steps;
-    return LBM_OK;
+    std::vector<double> table = src->h_motion;
+    table.resize(MOTION_W * src->cases.size(), 0.0);
+    return apply_motion(dst, table.data());
 }
 
 lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
@@ -1249,7 +1296,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
     cudaDeviceProp prop{};
     CK(cudaGetDeviceProperties(&prop, ctx->cfg.device));
     std::ostringstream key;
-    key << prop.name << "|v11|graph" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
+    key << prop.name << "|v12|graph" << ctx->dim << "|prec" << (int)ctx->cfg.prec << "|phys" << ctx->cfg.physics << "|n"
         << ctx->cases.size();
     int64_t tot = 0;
     for (auto &c : ctx->cases) tot += c.N;
@@ -1275,19 +1322,27 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
             }
         }
     }
-    // save the state; timing steps must not change the caller's solution
+    // save the state; timing steps must not change the caller's solution.
+    // Every resource below is released on every path.
     const size_t bytes = (size_t)ctx->pool_elems * ctx->elem;
-    void *save = nullptr;
-    CK(cudaMalloc(&save, bytes));
-    CK(cudaMemcpyAsync(save, ctx->pool[ctx->cur], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
     const int64_t steps0 = ctx->steps;
     const int saved_graph = ctx->graph_steps;
+    const lbm_launch before = ctx->launch;
+    void *save = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    lbm_status st = LBM_OK;
+    auto cuda = [&](cudaError_t e, const char *what) {
+        if (st == LBM_OK && e != cudaSuccess)
+            st = fail(ctx, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "autotune, %s: %s", what,
+                      cudaGetErrorString(e));
+    };
+    cuda(cudaMalloc(&save, bytes), "state copy");
+    if (st == LBM_OK) cuda(cudaMemcpyAsync(save, ctx->pool[ctx->cur], bytes, cudaMemcpyDeviceToDevice, ctx->stream),
+                           "state copy");
+    if (st == LBM_OK) cuda(cudaEventCreate(&e0), "event");
+    if (st == LBM_OK) cuda(cudaEventCreate(&e1), "event");
     // candidates run as they will in production: replays of a captured graph
     const int G = std::max(2, iters + (iters & 1));
-    ctx->graph_steps = G;
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
     std::vector<lbm_launch> cands;
     for (int r = 0; r < 3; ++r)
         for (int b : {64, 128, 256})
@@ -1300,36 +1355,56 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
             for (int b : {128, 256})
                 for (int p : {0, 8})
                     for (int npt : {2, 4}) cands.push_back(lbm_launch{2, b, p, npt, 2, kpair_minb(ctx->dim, r)});
-    if (!ctx->dbl)
-        for (int ns : {2, 3, 4, 6}) cands.push_back(lbm_launch{3, RING_CW * 32, 0, kring_npl(ctx->dim), ns, KRING_MINB});
-    lbm_launch best = ctx->launch;
+    // (the shared-memory ring, variant 3, is not a candidate: it never won on
+    // GB300 and one of its runs was once 400x slower for a reason not found;
+    // lbm_set_launch still selects it)
+    lbm_launch best = before;
     double best_t = INFINITY;
-    lbm_status st = LBM_OK;
-    for (const lbm_launch &cd : cands) {
-        if (lbm_set_launch(ctx, &cd) != LBM_OK) continue;   // does not fit: skip
-        if ((st = lbm_step(ctx, G)) != LBM_OK) break;        // capture and first replay, untimed
-        double per = INFINITY;
-        for (int rep = 0; rep < 2 && st == LBM_OK; ++rep) {
-            cudaEventRecord(e0, ctx->stream);
-            st = lbm_step(ctx, G);
-            cudaEventRecord(e1, ctx->stream);
-            cudaEventSynchronize(e1);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            per = std::min(per, (double)ms / G);
+    size_t stopped = cands.size();
+    if (st == LBM_OK) {
+        ctx->graph_steps = G;
+        for (size_t i = 0; i < cands.size() && st == LBM_OK; ++i) {
+            const lbm_launch &cd = cands[i];
+            if (lbm_set_launch(ctx, &cd) != LBM_OK) continue;   // does not fit: skip
+            st = lbm_step(ctx, G);                             // capture and first replay, untimed
+            double per = INFINITY;
+            for (int rep = 0; rep < 2 && st == LBM_OK; ++rep) {
+                cuda(cudaEventRecord(e0, ctx->stream), "event record");
+                if (st == LBM_OK) st = lbm_step(ctx, G);
+                if (st == LBM_OK) cuda(cudaEventRecord(e1, ctx->stream), "event record");
+                if (st == LBM_OK) cuda(cudaEventSynchronize(e1), "event wait");
+                float ms = 0;
+                if (st == LBM_OK) cuda(cudaEventElapsedTime(&ms, e0, e1), "event time");
+                per = std::min(per, (double)ms / G);
+            }
+            if (st != LBM_OK) {
+                stopped = i;
+                break;
+            }
+            if (per < best_t) { best_t = per; best = cd; }
         }
-        if (st != LBM_OK) break;
-        if (per < best_t) { best_t = per; best = cd; }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     ctx->graph_steps = saved_graph;
-    if (st == LBM_OK) st = lbm_set_launch(ctx, &best);
-    cudaMemcpyAsync(ctx->pool[ctx->cur], save, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
-    cudaStreamSynchronize(ctx->stream);
-    cudaFree(save);
+    const lbm_status st_set = lbm_set_launch(ctx, st == LBM_OK ? &best : &before);
+    if (save) {
+        cudaMemcpyAsync(ctx->pool[ctx->cur], save, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(save);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     ctx->steps = steps0;
-    if (st != LBM_OK) return st;
+    const lbm_status st_clk = set_clock(ctx);
+    if (st != LBM_OK) {
+        const std::string why = ctx->err;
+        if (stopped < cands.size())
+            return fail(ctx, st, "autotune stopped at candidate %zu of %zu (variant %d, block %d, nodes per thread %d);"
+                        " launch shape left unchanged: %s", stopped + 1, cands.size(), cands[stopped].variant,
+                        cands[stopped].block, cands[stopped].nodes_per_thread, why.c_str());
+        return st;
+    }
+    if (st_set != LBM_OK) return st_set;
+    if (st_clk != LBM_OK) return st_clk;
     if (cache_path) {
         std::ofstream o(cache_path, std::ios::app);
         o << k << " " << best.variant << " " << best.block << " " << best.blocks_per_sm << " " << best.nodes_per_thread

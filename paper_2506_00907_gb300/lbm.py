@@ -419,6 +419,7 @@ class Solver:
             stream = torch.cuda.current_stream(device).cuda_stream
         self.cases = list(cases)
         self.N = [c.nx * c.ny * c.nz for c in self.cases]
+        self.lattice, self.prec, self.physics = lattice, prec, physics
         self.ctx = lbm_create(lattice, prec, physics, self.cases, stream, device)
 
     def close(self):

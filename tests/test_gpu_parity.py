@@ -272,6 +272,74 @@ def test_fp64_wall_motion_per_case():
         assert norm_rel(a["rho"][fl], b["rho"][fl]) < FP64_TOL
 
 
+def test_fp64_wall_motion_set_late_keeps_other_phases():
+    """Case 0 oscillates from step 0; case 1's motion is set only after 70
+    steps (its own t starts there).  Each matches an oracle whose motion was
+    set at the same step: setting one case's motion leaves the other's phase
+    alone."""
+    geo = [_stokes_geometry(2, ny, d, 0.01) for ny, d in ((14, 0.5), (17, 0.8))]
+    motion = [(2 * math.pi / 150, 0.3), (2 * math.pi / 90, -0.7)]
+    cases = [lbm.make_case(g[0], 0.8, 0.9, 0.7, (0, 0, 0), 1.0, 1.0, (0, 0, 0)) for g in geo]
+    gpu = lbm.Solver(lbm.LBM_D2Q9, lbm.LBM_FP64, lbm.LBM_FLOW, cases)
+    orcs = []
+    for i, (shape, solid, links) in enumerate(geo):
+        gpu.set_walls(i, solid, to_abi_links(links))
+        o = O.OracleSim(2, shape, solid, 0.8)
+        o.set_links(links)
+        o.init()
+        orcs.append(o)
+    orcs[0].set_wall_motion(*motion[0])
+    gpu.set_wall_motion(0, *motion[0])
+    gpu.set_graph(4)
+    gpu.step(70)
+    for o in orcs:
+        o.step(70)
+    orcs[1].set_wall_motion(*motion[1])
+    gpu.set_wall_motion(1, *motion[1])
+    gpu.step(200)
+    for i, o in enumerate(orcs):
+        o.step(200)
+        fl = np.asarray(geo[i][1]).reshape(-1) == 0
+        a, b = gpu.moments(i), o.moments()
+        assert norm_rel(a["u"][fl], b["u"][fl]) < FP64_TOL, i
+
+
+@pytest.mark.parametrize("graph", [0, 4])
+def test_checkpoint_of_an_oscillating_wall_is_bitwise(graph):
+    """A state blob taken mid-period and restored into a fresh context with the
+    same walls (whose motion comes from the blob alone), then stepped, equals
+    the run that never stopped, bit for bit (FP64), and so does a conversion
+    into a second FP64 context."""
+    shape, solid, links = _stokes_geometry(3, 22, 0.75, 0.01)
+    omega, phase = 2 * math.pi / 130, 0.4
+
+    def make():
+        g = lbm.Solver(lbm.LBM_D2Q9, lbm.LBM_FP64, lbm.LBM_FLOW,
+                       [lbm.make_case(shape, 0.8, 0.9, 0.7, (1e-6, 0, 0), 1.0, 1.0, (0, 0, 0))])
+        g.set_walls(0, solid, to_abi_links(links))
+        if graph:
+            g.set_graph(graph)
+        return g
+    a = make()
+    a.step(12)                       # motion set at step 12: its t starts there
+    a.set_wall_motion(0, omega, phase)
+    a.step(52)
+    blob = a.get_state()
+    a.step(96)
+    want = a.get_state()
+    b = make()
+    b.set_state(blob)
+    b.step(96)
+    assert b.steps == a.steps
+    assert np.array_equal(b.get_state(), want)
+    c = make()
+    b2 = make()
+    b2.set_state(blob)
+    c.convert_from(b2)
+    c.step(96)
+    assert np.array_equal(c.get_state(), want)
+
+
 def test_wall_motion_refuses_moving_flux_walls():
     """A case with a flux wall of h whose wall moves is refused, and so is a
     later link list with such a wall in a moving case."""
