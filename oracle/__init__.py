@@ -38,6 +38,14 @@ VELOCITY_EQ15, FLUX_SIMPLIFIED = 4, 5
 PRESSURE = 6
 # M-scheme flux wall of C with the reaction flux (kappa0 + kappa1 C_X) / (1 + K C_X), K = phi_wall
 FLUX_RATIONAL = 7
+# M-scheme flux wall of species i with k0 + k1 R_i(C_X) of the surface reaction network (several species)
+REACTION = 8
+MAX_SPECIES, MAX_REACT = 4, 4
+
+
+def species_field(k):
+    """Field code of concentration species k: 1 for species 0, 4 + k for k >= 1."""
+    return H if k == 0 else 4 + k
 
 _lib = None
 
@@ -78,6 +86,14 @@ def lib():
         L.orc_lattice.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_int), dp]
         L.orc_sizeof_link.restype = ctypes.c_int
+        L.orc_set_species.restype = ctypes.c_int
+        L.orc_set_species.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, dp]
+        L.orc_set_network.restype = ctypes.c_int
+        L.orc_set_network.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int), dp]
+        L.orc_species.restype = ctypes.c_double
+        L.orc_species.argtypes = [ctypes.c_void_p, ctypes.c_int, dp]
+        L.orc_network_rate.restype = ctypes.c_double
+        L.orc_network_rate.argtypes = [ctypes.c_void_p, ctypes.c_int, dp]
         assert L.orc_sizeof_link() == LINK_DTYPE.itemsize
         _lib = L
     return _lib
@@ -130,7 +146,10 @@ class _LinkIn(ctypes.Structure):
     _fields_ = [("p_a_A", ctypes.c_double), ("p_ap_A", ctypes.c_double),
                 ("p_ap_E", ctypes.c_double), ("phi_A", ctypes.c_double),
                 ("phi_E", ctypes.c_double), ("B_A", ctypes.c_double * 3),
-                ("B_E", ctypes.c_double * 3)]
+                ("B_E", ctypes.c_double * 3), ("u_A", ctypes.c_double * 3),
+                ("u_E", ctypes.c_double * 3), ("C_A", ctypes.c_double * 4),
+                ("C_E", ctypes.c_double * 4), ("nspecies", ctypes.c_int),
+                ("net", ctypes.c_void_p)]
 
 
 def eval_link(dim, link, p_a_A, p_ap_A, p_ap_E, phi_A=1.0, phi_E=1.0,
@@ -180,6 +199,45 @@ class OracleSim:
         rc = lib().orc_set_links(self._h, links.ctypes.data_as(ctypes.c_void_p), len(links))
         if rc != 0:
             raise ValueError("oracle rejected the link list (code %d)" % rc)
+
+    def set_species(self, tau_D, C0):
+        """Several concentration species (before the links and the initial
+        state): tau_D[k] and the initial C0[k] of species k (species 0's C0 is
+        init's)."""
+        t = np.ascontiguousarray(tau_D, dtype=np.float64)
+        c = np.ascontiguousarray(C0, dtype=np.float64)
+        if len(t) != len(c) or lib().orc_set_species(self._h, len(t), _dp(t), _dp(c)) != 0:
+            raise ValueError("bad species")
+        self.nspecies = len(t)
+
+    def set_network(self, reactions):
+        """Surface reactions of REACTION links: a list of dicts with rate,
+        order (per species, 0..2) and stoich (per species)."""
+        n = len(reactions)
+        rate = np.zeros(max(1, n))
+        order = np.zeros(max(1, n) * MAX_SPECIES, dtype=np.int32)
+        stoich = np.zeros(max(1, n) * MAX_SPECIES)
+        for j, r in enumerate(reactions):
+            rate[j] = r["rate"]
+            for m, o in enumerate(r.get("order", ())):
+                order[j * MAX_SPECIES + m] = o
+            for m, v in enumerate(r.get("stoich", ())):
+                stoich[j * MAX_SPECIES + m] = v
+        if lib().orc_set_network(self._h, n, _dp(rate), order.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                 _dp(stoich)) != 0:
+            raise ValueError("bad reaction network")
+
+    def species(self, k):
+        """C[N] of species k at the current time (solid nodes 0)."""
+        C = np.zeros(self.N)
+        lib().orc_species(self._h, k, _dp(C))
+        return C
+
+    def network_rate(self, i, C):
+        """The production rate R_i of the network at concentrations C."""
+        c = np.zeros(MAX_SPECIES)
+        c[:len(C)] = C
+        return lib().orc_network_rate(self._h, i, _dp(c))
 
     def set_wall_motion(self, omega, phase=0.0):
         """Oscillating velocity walls: u_wall * cos(omega t + phase) (Eq. 45),

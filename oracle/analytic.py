@@ -145,3 +145,23 @@ def reaction_diffusion_series(x, y, L, W, D, k, C_bc, C_eq, nterms=400):
         ratio = np.exp(-lam * x) * (1 + np.exp(-2 * lam * (L - x))) / (1 + math.exp(-2 * lam * L))
         out += An * np.cos(lam * y) * ratio
     return C_eq + out
+
+
+def reactive_channel_two_species(y, y0, y1, DA, DB, k, A_top, B_top):
+    """Steady 1-D diffusion of two species A and B between a wall at y0 where
+    they react, A + B -> products at the rate k A B per unit area (each
+    species' flux into the fluid is -k A B, Sec. 4.2.2), and a wall at y1 with
+    given A_top, B_top.  Both profiles are linear; the wall values satisfy
+    D_A (A_top - A_b) / L = D_B (B_top - B_b) / L = k A_b B_b.  Eliminating B_b
+    leaves k (D_A/D_B) a^2 + (k B_top - k (D_A/D_B) A_top + D_A/L) a - D_A A_top/L
+    = 0 for a = A_b, whose positive root is taken.  Returns (A(y), B(y))."""
+    L = y1 - y0
+    r = DA / DB
+    alpha = k * r
+    beta = k * B_top - k * r * A_top + DA / L
+    gamma = -DA * A_top / L
+    a = (-beta + math.sqrt(beta * beta - 4.0 * alpha * gamma)) / (2.0 * alpha)
+    b = B_top - r * (A_top - a)
+    y = np.asarray(y, dtype=np.float64)
+    t = (y - y0) / L
+    return a + (A_top - a) * t, b + (B_top - b) * t

@@ -19,7 +19,12 @@
  *      for every d (Sec. 5.1) and the simplified flux wall of Eq. 33 (Sec. 5.4);
  *      open boundaries (Sec. 5.1): given velocity is the velocity kind with a
  *      normal u (Eq. 41, 43), given pressure its own kind (Eq. 42, 44);
- *      a reaction flux of C nonlinear in C_X (rational form) by the M scheme.
+ *      a reaction flux of C nonlinear in C_X (rational form) by the M scheme;
+ *      several concentration species (Sec. 4.2.2, text after Eq. 23): each
+ *      species' C_i(X) by Eq. 13, the surface reaction fluxes F_i(C_1, C_2, ..)
+ *      of a mass-action network evaluated explicitly from them, and each F_i
+ *      added to its own species by the M scheme (Eq. 23-27), with no coupled
+ *      (Newton) solve.
  *
  * Readings where the paper is silent (each is listed with its reason in the
  * design notes of the repository):
@@ -169,12 +174,44 @@ int orc_lattice(int dim, int scalar, int *q, int *e /* q*3 */, double *w) {
 /* ------------------------------------------------------------------------- */
 /* Wall links                                                                 */
 /* ------------------------------------------------------------------------- */
-enum { ORC_F = 0, ORC_H = 1, ORC_G0 = 2 };              /* field: f, h, g_k = 2 + k */
+enum { ORC_F = 0, ORC_H = 1, ORC_G0 = 2,               /* field: f, h (species 0), g_k = 2 + k */
+       ORC_HS1 = 5 };                                   /* species k >= 1 of C: field 4 + k (5, 6, 7) */
+#define ORC_MAX_SPECIES 4
+#define ORC_MAX_REACT 4
+/* species index of a concentration field, or -1 */
+static int species_of(int field) {
+    if (field == ORC_H) return 0;
+    if (field >= ORC_HS1 && field < ORC_HS1 + ORC_MAX_SPECIES - 1) return field - ORC_HS1 + 1;
+    return -1;
+}
 enum { ORC_VELOCITY = 0, ORC_GIVEN = 1, ORC_FLUX = 2, ORC_NEUMANN_BFL = 3,
        ORC_VELOCITY_EQ15 = 4,   /* Eq. 15 with Eq. 16 for every d (the paper's own scheme before Eq. 43) */
        ORC_FLUX_SIMPLIFIED = 5, /* flux and move increments added to the bounced population at X (Eq. 33) */
        ORC_PRESSURE = 6,        /* given density (pressure) of an open boundary, Eq. 42 and 44 */
-       ORC_FLUX_RATIONAL = 7    /* M scheme with the nonlinear flux (k0 + k1 phi_X) / (1 + phi_wall phi_X) */ };
+       ORC_FLUX_RATIONAL = 7,   /* M scheme with the nonlinear flux (k0 + k1 phi_X) / (1 + phi_wall phi_X) */
+       ORC_REACTION = 8         /* M scheme with k0 + k1 R_i(C_X) of the surface reaction network */ };
+
+/* Mass-action surface reactions: reaction j runs at rate_j prod_m C_m^order[j][m]
+ * per unit wall area and time; species i is produced at
+ * R_i = sum_j stoich[j][i] rate_j prod_m C_m^order[j][m]. */
+typedef struct {
+    int n;
+    double rate[ORC_MAX_REACT];
+    int order[ORC_MAX_REACT][ORC_MAX_SPECIES];
+    double stoich[ORC_MAX_REACT][ORC_MAX_SPECIES];
+} orc_network;
+
+/* R_i at the concentrations C[0 .. nspecies-1] */
+static double network_rate(const orc_network *net, int nspecies, int i, const double *C) {
+    double R = 0.0;
+    for (int j = 0; j < net->n; ++j) {
+        double r = net->rate[j];
+        for (int m = 0; m < nspecies; ++m)
+            for (int o = 0; o < net->order[j][m]; ++o) r *= C[m];
+        R += net->stoich[j][i] * r;
+    }
+    return R;
+}
 
 typedef struct {
     int32_t node;        /* first fluid node A */
@@ -195,6 +232,9 @@ typedef struct {
     double phi_A, phi_E; /* rho (f), C (h) or B_k (g_k) at A and E     */
     double B_A[3], B_E[3]; /* full B at A and E (g fields only)        */
     double u_A[3], u_E[3]; /* fluid velocity at A and E (f field only)  */
+    double C_A[ORC_MAX_SPECIES], C_E[ORC_MAX_SPECIES]; /* every species' C at A and E (reaction links) */
+    int nspecies;
+    const orc_network *net;
 } orc_link_in;
 
 /* Eq. 13: extrapolation of an unknown macroscopic quantity to the wall point X */
@@ -245,7 +285,7 @@ double orc_eval_link(int dim, const orc_link *lk, const orc_link_in *in) {
     }
     lattice L = scalar_lattice(dim);
     int a = lk->dir, ap = opposite(L, a);
-    int is_g = lk->field >= ORC_G0;
+    int is_g = species_of(lk->field) < 0;
     int k = is_g ? lk->field - ORC_G0 : 0;
     const double *uw = lk->u_wall;
     switch (lk->kind) {
@@ -262,14 +302,26 @@ double orc_eval_link(int dim, const orc_link *lk, const orc_link_in *in) {
         return orc_geq(dim, a, k, BX, uw) + orc_geq(dim, ap, k, BX, uw) - pY;
     }
     case ORC_FLUX:
-    case ORC_FLUX_RATIONAL: {
+    case ORC_FLUX_RATIONAL:
+    case ORC_REACTION: {
         /* M scheme, Eq. 25-27, with the flux increment (Eq. 23) and the
          * moving-wall correction (Eq. 24) evaluated at X (Eq. 13).  A reaction
-         * flux nonlinear in C is evaluated explicitly at C_X (Sec. 4.2.2): here
-         * the rational form (k0 + k1 C_X) / (1 + K C_X), K = phi_wall. */
+         * flux nonlinear in C is evaluated explicitly at C_X (Sec. 4.2.2): the
+         * rational form (k0 + k1 C_X) / (1 + K C_X), K = phi_wall, or the
+         * network's R_i of every species' C_X (each by Eq. 13 from its own C at
+         * A and E). */
         double phiX = extrap_X(d, in->phi_E, in->phi_A);
-        double dflux = lk->kind == ORC_FLUX_RATIONAL ? (lk->k0 + lk->k1 * phiX) / (1.0 + lk->phi_wall * phiX)
-                                                     : lk->k0 + lk->k1 * phiX;
+        double dflux;
+        if (lk->kind == ORC_FLUX_RATIONAL) {
+            dflux = (lk->k0 + lk->k1 * phiX) / (1.0 + lk->phi_wall * phiX);
+        } else if (lk->kind == ORC_REACTION) {
+            double CX[ORC_MAX_SPECIES];
+            for (int m = 0; m < in->nspecies; ++m) CX[m] = extrap_X(d, in->C_E[m], in->C_A[m]);
+            if (!in->net || is_g) return NAN;
+            dflux = lk->k0 + lk->k1 * network_rate(in->net, in->nspecies, species_of(lk->field), CX);
+        } else {
+            dflux = lk->k0 + lk->k1 * phiX;
+        }
         double minus_u[3] = {-uw[0], -uw[1], -uw[2]};
         double dmove;
         if (!is_g) {
@@ -317,14 +369,18 @@ double orc_eval_link(int dim, const orc_link *lk, const orc_link_in *in) {
 /* ------------------------------------------------------------------------- */
 typedef struct {
     int dim, nx, ny, nz, has_h, has_g, nB;
+    int nC;                    /* concentration species (0, or 1..ORC_MAX_SPECIES with has_h) */
     long N;
     double tau_nu, tau_D, tau_eta;
+    double tau_Ds[ORC_MAX_SPECIES]; /* tau_D of each species (species 0: tau_D) */
+    double C0s[ORC_MAX_SPECIES];    /* initial C of species 1.. (species 0: orc_init's C0) */
+    orc_network net;           /* surface reactions of ORC_REACTION links */
     double accel[3];           /* body force per unit mass: F = rho * accel */
     uint8_t *solid;
-    double *f, *h, *g;         /* populations at t (after propagation, before relaxation) */
+    double *f, *h, *g;         /* populations at t (after propagation, before relaxation); h: [nC][qm][N] */
     double *fr, *hr, *gr;      /* relaxed populations at t */
     double *fn, *hn, *gn;      /* populations at t+1 */
-    double *rho, *u, *C, *B;   /* moments at t: rho[N], u[3N], C[N], B[3N] */
+    double *rho, *u, *C, *B;   /* moments at t: rho[N], u[3N], C[nC][N], B[3N] */
     int32_t *nbf, *nbm;        /* neighbour tables: node of x + e_a, [a * N + n] */
     orc_link *links;
     long nlinks;
@@ -362,6 +418,8 @@ orc_sim *orc_create(int dim, int nx, int ny, int nz, int has_h, int has_g,
     s->has_h = has_h; s->has_g = has_g; s->nB = dim;
     s->N = (long)nx * ny * nz;
     s->tau_nu = tau_nu; s->tau_D = tau_D; s->tau_eta = tau_eta;
+    s->nC = has_h ? 1 : 0;
+    s->tau_Ds[0] = tau_D;
     for (int k = 0; k < 3; ++k) s->accel[k] = accel ? accel[k] : 0.0;
     s->solid = (uint8_t *)malloc(s->N);
     memcpy(s->solid, solid, s->N);
@@ -405,6 +463,50 @@ void orc_destroy(orc_sim *s) {
 
 void orc_set_threads(orc_sim *s, int n) { s->nthreads = n > 0 ? n : 1; }
 
+/* Several concentration species (call after orc_create with has_h, before
+ * the links and the initial state): species k has relaxation time tau_D[k]
+ * and initial C0[k] (k >= 1; species 0's initial C is orc_init's C0).
+ * Returns 0, or -1 for a bad count or a context without C. */
+int orc_set_species(orc_sim *s, int nC, const double *tau_D, const double *C0) {
+    if (!s->has_h || nC < 1 || nC > ORC_MAX_SPECIES) return -1;
+    for (int k = 0; k < nC; ++k)
+        if (!(tau_D[k] > 0.5)) return -1;
+    int qm = scalar_lattice(s->dim).q;
+    free(s->h); free(s->hr); free(s->hn); free(s->C);
+    s->h = calloc((size_t)nC * qm * s->N, sizeof(double));
+    s->hr = calloc((size_t)nC * qm * s->N, sizeof(double));
+    s->hn = calloc((size_t)nC * qm * s->N, sizeof(double));
+    s->C = calloc((size_t)nC * s->N, sizeof(double));
+    s->nC = nC;
+    for (int k = 0; k < nC; ++k) {
+        s->tau_Ds[k] = tau_D[k];
+        s->C0s[k] = C0 ? C0[k] : 0.0;
+    }
+    s->tau_D = tau_D[0];
+    return 0;
+}
+
+/* The surface reaction network of ORC_REACTION links: n reactions (at most
+ * ORC_MAX_REACT), rate[j], order[j * 4 + m] in 0..2 and stoich[j * 4 + i].
+ * Returns 0 or -1. */
+int orc_set_network(orc_sim *s, int n, const double *rate, const int *order, const double *stoich) {
+    if (n < 0 || n > ORC_MAX_REACT) return -1;
+    memset(&s->net, 0, sizeof s->net);
+    s->net.n = n;
+    for (int j = 0; j < n; ++j) {
+        s->net.rate[j] = rate[j];
+        for (int m = 0; m < ORC_MAX_SPECIES; ++m) {
+            if (order[j * ORC_MAX_SPECIES + m] < 0 || order[j * ORC_MAX_SPECIES + m] > 2) return -1;
+            s->net.order[j][m] = order[j * ORC_MAX_SPECIES + m];
+            s->net.stoich[j][m] = stoich[j * ORC_MAX_SPECIES + m];
+        }
+    }
+    return 0;
+}
+
+/* h planes of species k: h[(k * qm + a) * N + n] */
+static double *hp(double *h, int qm, long N, int k) { return h + (long)k * qm * N; }
+
 /* g layout: g[(k * qm + a) * N + n] for component k */
 static double *gp(double *g, int qm, long N, int k, int a, long n) {
     return &g[((long)k * qm + a) * N + n];
@@ -420,7 +522,7 @@ int orc_set_links(orc_sim *s, const orc_link *links, long n) {
     (void)nfield;
     /* coverage table: per node, per field slot, per direction */
     int qmax = qf;
-    int nslots = 2 + 3;
+    int nslots = ORC_HS1 + ORC_MAX_SPECIES - 1;
     uint8_t *seen = calloc((size_t)s->N * nslots * qmax, 1);
     for (long i = 0; i < n; ++i) {
         const orc_link *lk = &links[i];
@@ -428,8 +530,10 @@ int orc_set_links(orc_sim *s, const orc_link *links, long n) {
         if (field == ORC_F) {
             if ((lk->kind != ORC_VELOCITY && lk->kind != ORC_VELOCITY_EQ15 && !(lk->kind == ORC_PRESSURE && !s->has_g && !s->has_h))
                 || lk->dir <= 0 || lk->dir >= qf) { free(seen); return -1; }
-        } else if (field == ORC_H) {
-            if (!s->has_h || (lk->kind != ORC_GIVEN && lk->kind != ORC_FLUX && lk->kind != ORC_NEUMANN_BFL && lk->kind != ORC_FLUX_SIMPLIFIED && lk->kind != ORC_FLUX_RATIONAL) || lk->dir <= 0 || lk->dir >= qm) { free(seen); return -1; }
+        } else if (species_of(field) >= 0) {
+            if (!s->has_h || species_of(field) >= s->nC ||
+                (lk->kind != ORC_GIVEN && lk->kind != ORC_FLUX && lk->kind != ORC_NEUMANN_BFL && lk->kind != ORC_FLUX_SIMPLIFIED &&
+                 lk->kind != ORC_FLUX_RATIONAL && lk->kind != ORC_REACTION) || lk->dir <= 0 || lk->dir >= qm) { free(seen); return -1; }
         } else if (field >= ORC_G0 && field < ORC_G0 + s->nB) {
             if (!s->has_g || (lk->kind != ORC_GIVEN && lk->kind != ORC_FLUX && lk->kind != ORC_NEUMANN_BFL && lk->kind != ORC_FLUX_SIMPLIFIED) || lk->dir <= 0 || lk->dir >= qm) { free(seen); return -1; }
         } else { free(seen); return -1; }
@@ -446,8 +550,9 @@ int orc_set_links(orc_sim *s, const orc_link *links, long n) {
     for (long x = 0; x < s->N; ++x) {
         if (s->solid[x]) continue;
         for (int field = 0; field < nslots; ++field) {
-            if (field == ORC_H && !s->has_h) continue;
-            if (field >= ORC_G0 && (!s->has_g || field >= ORC_G0 + s->nB)) continue;
+            int sp = species_of(field);
+            if (sp >= 0 && sp >= s->nC) continue;
+            if (field != ORC_F && sp < 0 && (!s->has_g || field >= ORC_G0 + s->nB)) continue;
             lattice L = field == ORC_F ? flow_lattice(s->dim) : scalar_lattice(s->dim);
             for (int a = 1; a < L.q; ++a) {
                 long Bn = neighbour(s, x, L.e[a], -1);
@@ -467,6 +572,7 @@ int orc_set_links(orc_sim *s, const orc_link *links, long n) {
  * Any of the arrays may be NULL: rho -> rho0, u -> 0, C -> C0, B -> B0[]. */
 void orc_init(orc_sim *s, const double *rho, const double *u, const double *C, const double *B,
               double rho0, double C0, const double B0[3]) {
+    s->C0s[0] = C0;
     int qf = flow_lattice(s->dim).q, qm = scalar_lattice(s->dim).q;
     for (long n = 0; n < s->N; ++n) {
         if (s->solid[n]) continue;
@@ -476,9 +582,9 @@ void orc_init(orc_sim *s, const double *rho, const double *u, const double *C, c
         if (s->has_g) for (int k = 0; k < 3; ++k) bb[k] = B ? B[3 * n + k] : B0[k];
         for (int a = 0; a < qf; ++a)
             s->f[(long)a * s->N + n] = orc_feq(s->dim, a, r, uu, s->has_g ? bb : NULL);
-        if (s->has_h) {
-            double c = C ? C[n] : C0;
-            for (int a = 0; a < qm; ++a) s->h[(long)a * s->N + n] = orc_heq(s->dim, a, c, uu);
+        for (int k = 0; k < s->nC; ++k) {
+            double c = (k == 0 && C) ? C[n] : (k == 0 ? C0 : s->C0s[k]);
+            for (int a = 0; a < qm; ++a) hp(s->h, qm, s->N, k)[(long)a * s->N + n] = orc_heq(s->dim, a, c, uu);
         }
         if (s->has_g)
             for (int k = 0; k < s->nB; ++k)
@@ -502,10 +608,10 @@ static void compute_moments(orc_sim *s) {
         }
         s->rho[n] = rho;
         for (int k = 0; k < 3; ++k) s->u[3 * n + k] = (j[k] + 0.5 * rho * s->accel[k]) / rho;
-        if (s->has_h) {
+        for (int k = 0; k < s->nC; ++k) {
             double C = 0;
-            for (int a = 0; a < M.q; ++a) C += s->h[(long)a * N + n];
-            s->C[n] = C;
+            for (int a = 0; a < M.q; ++a) C += hp(s->h, M.q, N, k)[(long)a * N + n];
+            s->C[(long)k * N + n] = C;
         }
         if (s->has_g) {
             for (int k = 0; k < 3; ++k) s->B[3 * n + k] = 0.0;
@@ -534,10 +640,12 @@ static void relax(orc_sim *s) {
             double feq = orc_feq(s->dim, a, rho, u, s->has_g ? B : NULL);
             s->fr[(long)a * N + n] = fa + (feq - fa) / s->tau_nu + orc_guo(s->dim, a, s->tau_nu, u, F);
         }
-        if (s->has_h) {
+        for (int k = 0; k < s->nC; ++k) {
+            const double *h = hp(s->h, M.q, N, k);
+            double *hr = hp(s->hr, M.q, N, k);
             for (int a = 0; a < M.q; ++a) {
-                double ha = s->h[(long)a * N + n];
-                s->hr[(long)a * N + n] = ha + (orc_heq(s->dim, a, s->C[n], u) - ha) / s->tau_D;
+                double ha = h[(long)a * N + n];
+                hr[(long)a * N + n] = ha + (orc_heq(s->dim, a, s->C[(long)k * N + n], u) - ha) / s->tau_Ds[k];
             }
         }
         if (s->has_g) {
@@ -575,20 +683,24 @@ static void link_inputs(const orc_sim *s, const orc_link *lk, orc_link *eff, orc
     long E = (lk->field == ORC_F ? s->nbf : s->nbm)[(long)a * N + A];   /* E = A + e_a */
     if (s->solid[E]) { E = A; eff->d = 0.5; }       /* E-solid reading */
     const double *pr;
+    int sp = species_of(lk->field);
     if (lk->field == ORC_F) pr = s->fr;
-    else if (lk->field == ORC_H) pr = s->hr;
+    else if (sp >= 0) pr = hp(s->hr, L.q, N, sp);
     else pr = s->gr + (long)(lk->field - ORC_G0) * L.q * N;
     in->p_a_A = pr[(long)a * N + A];
     in->p_ap_A = pr[(long)ap * N + A];
     in->p_ap_E = pr[(long)ap * N + E];
     if (lk->field == ORC_F) { in->phi_A = s->rho[A]; in->phi_E = s->rho[E]; }
-    else if (lk->field == ORC_H) { in->phi_A = s->C[A]; in->phi_E = s->C[E]; }
+    else if (sp >= 0) { in->phi_A = s->C[(long)sp * N + A]; in->phi_E = s->C[(long)sp * N + E]; }
     else {
         int k = lk->field - ORC_G0;
         in->phi_A = s->B[3 * A + k]; in->phi_E = s->B[3 * E + k];
     }
     for (int c = 0; c < 3; ++c) { in->B_A[c] = s->B[3 * A + c]; in->B_E[c] = s->B[3 * E + c]; }
     for (int c = 0; c < 3; ++c) { in->u_A[c] = s->u[3 * A + c]; in->u_E[c] = s->u[3 * E + c]; }
+    in->nspecies = s->nC;
+    in->net = &s->net;
+    for (int m = 0; m < s->nC; ++m) { in->C_A[m] = s->C[(long)m * N + A]; in->C_E[m] = s->C[(long)m * N + E]; }
     if (s->motion && lk->field == ORC_F && (lk->kind == ORC_VELOCITY || lk->kind == ORC_VELOCITY_EQ15)) {
         /* oscillating wall, Eq. 45: the wall velocity of the step t -> t+1 is
          * taken at t, the time of f^eq(X, t) in Eq. 41 and 43 */
@@ -607,8 +719,9 @@ static void apply_links(orc_sim *s) {
         link_inputs(s, &s->links[i], &eff, &in);
         double v = orc_eval_link(s->dim, &eff, &in);
         const orc_link *lk = &s->links[i];
+        int sp = species_of(lk->field);
         if (lk->field == ORC_F) s->fn[(long)lk->dir * N + lk->node] = v;
-        else if (lk->field == ORC_H) s->hn[(long)lk->dir * N + lk->node] = v;
+        else if (sp >= 0) hp(s->hn, qm, N, sp)[(long)lk->dir * N + lk->node] = v;
         else *gp(s->gn, qm, N, lk->field - ORC_G0, lk->dir, lk->node) = v;
     }
 }
@@ -619,7 +732,8 @@ void orc_step(orc_sim *s, int nsteps) {
         compute_moments(s);
         relax(s);
         propagate_field(s, L, s->nbf, s->fr, s->fn);
-        if (s->has_h) propagate_field(s, M, s->nbm, s->hr, s->hn);
+        for (int k = 0; k < s->nC; ++k)
+            propagate_field(s, M, s->nbm, hp(s->hr, M.q, s->N, k), hp(s->hn, M.q, s->N, k));
         if (s->has_g)
             for (int k = 0; k < s->nB; ++k)
                 propagate_field(s, M, s->nbm, s->gr + (long)k * M.q * s->N, s->gn + (long)k * M.q * s->N);
@@ -668,7 +782,8 @@ long orc_steps(const orc_sim *s) { return s->steps; }
 int orc_set_wall_motion(orc_sim *s, double omega, double phase) {
     for (long i = 0; i < s->nlinks; ++i) {
         const orc_link *lk = &s->links[i];
-        if (lk->field != ORC_F && (lk->kind == ORC_FLUX || lk->kind == ORC_FLUX_SIMPLIFIED || lk->kind == ORC_FLUX_RATIONAL) &&
+        if (lk->field != ORC_F && (lk->kind == ORC_FLUX || lk->kind == ORC_FLUX_SIMPLIFIED || lk->kind == ORC_FLUX_RATIONAL ||
+                                   lk->kind == ORC_REACTION) &&
             (lk->u_wall[0] != 0.0 || lk->u_wall[1] != 0.0 || lk->u_wall[2] != 0.0))
             return -1;
     }
@@ -692,10 +807,27 @@ void orc_sums(orc_sim *s, double out[6]) {
         if (s->has_h) out[1] += s->C[n];
         if (s->has_g) for (int k = 0; k < 3; ++k) out[2 + k] += s->B[3 * n + k];
         for (int a = 0; a < qf; ++a) if (!isfinite(s->f[(long)a * s->N + n])) out[5] += 1;
-        if (s->has_h) for (int a = 0; a < qm; ++a) if (!isfinite(s->h[(long)a * s->N + n])) out[5] += 1;
+        for (int k = 0; k < s->nC; ++k)
+            for (int a = 0; a < qm; ++a) if (!isfinite(hp(s->h, qm, s->N, k)[(long)a * s->N + n])) out[5] += 1;
         if (s->has_g) for (int k = 0; k < s->nB; ++k) for (int a = 0; a < qm; ++a)
             if (!isfinite(*gp(s->g, qm, s->N, k, a, n))) out[5] += 1;
     }
 }
 
 int orc_sizeof_link(void) { return (int)sizeof(orc_link); }
+
+/* Concentration of species k at the current time (C[N], solid nodes 0) and
+ * the FP64 sum over fluid nodes; returns the sum. */
+double orc_species(orc_sim *s, int k, double *C) {
+    compute_moments(s);
+    double sum = 0.0;
+    for (long n = 0; n < s->N; ++n) {
+        double v = (s->solid[n] || k < 0 || k >= s->nC) ? 0.0 : s->C[(long)k * s->N + n];
+        if (C) C[n] = v;
+        sum += v;
+    }
+    return sum;
+}
+
+/* The network production rate R_i at given concentrations (tests). */
+double orc_network_rate(const orc_sim *s, int i, const double *C) { return network_rate(&s->net, s->nC, i, C); }

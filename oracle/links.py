@@ -21,13 +21,14 @@ import math
 
 import numpy as np
 
-from . import LINK_DTYPE, F, H, G0, VELOCITY, GIVEN, FLUX, NEUMANN_BFL, VELOCITY_EQ15, FLUX_SIMPLIFIED, FLUX_RATIONAL, lattice
+from . import (LINK_DTYPE, F, H, G0, VELOCITY, GIVEN, FLUX, NEUMANN_BFL, VELOCITY_EQ15, FLUX_SIMPLIFIED,
+               FLUX_RATIONAL, REACTION, lattice, species_field)
 
 
-def _fields(dim, has_h, has_g):
+def _fields(dim, has_h, has_g, nspecies=1):
     out = [F]
     if has_h:
-        out.append(H)
+        out += [species_field(k) for k in range(nspecies)]
     if has_g:
         out += [G0 + k for k in range(dim)]
     return out
@@ -64,7 +65,7 @@ def _upstream_solid(solid3, e):
     return np.roll(solid3, shift=(e[2], e[1], e[0]), axis=(0, 1, 2))
 
 
-def box_links(dim, shape, walls, params, has_h=False, has_g=False):
+def box_links(dim, shape, walls, params, has_h=False, has_g=False, nspecies=1):
     """Links of a box with planar walls.
 
     walls:  axis -> (lo, hi) wall coordinates (see ``box_solid``).
@@ -79,7 +80,7 @@ def box_links(dim, shape, walls, params, has_h=False, has_g=False):
     z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
     coords = (x.ravel(), y.ravel(), z.ravel())
     out = []
-    for field in _fields(dim, has_h, has_g):
+    for field in _fields(dim, has_h, has_g, nspecies):
         e, _ = lattice(dim, scalar=(field != F))
         for a in range(1, len(e)):
             mask = (solid3 == 0) & (_upstream_solid(solid3, e[a]) == 1)
@@ -225,22 +226,28 @@ def pipe_links(shape, R, params, has_g=True, center=None):
 # ---------------------------------------------------------------------------
 # Random links for parity fuzzing
 # ---------------------------------------------------------------------------
-def random_links(dim, shape, solid, rng, has_h=False, has_g=False, kinds=None, phi_range=None, variants=False):
+def random_links(dim, shape, solid, rng, has_h=False, has_g=False, kinds=None, phi_range=None, variants=False,
+                 nspecies=1, reaction=False):
     """Every required link of a given solid mask, with kind, d and wall data
     drawn from ``rng`` (numpy Generator).  d in (0, 1]; both branches of every
     scheme occur.  phi_range maps a field to the (lo, hi) range of its given
     wall values (default (-0.5, 1.5)).  variants=True also draws the two
-    comparison schemes (Eq. 15/16 for every d, the simplified flux wall)."""
+    comparison schemes (Eq. 15/16 for every d, the simplified flux wall).
+    nspecies concentration fields; reaction=True also draws reaction links
+    (k1 in (0.5, 1], the area weight of the network's rate)."""
     nx, ny, nz = shape
     solid3 = np.asarray(solid, dtype=np.uint8).reshape(nz, ny, nx)
     out = []
-    for field in _fields(dim, has_h, has_g):
+    for field in _fields(dim, has_h, has_g, nspecies):
         e, _ = lattice(dim, scalar=(field != F))
+        is_c = field == H or field >= G0 + 3
         if field == F:
             allowed = np.array([VELOCITY, VELOCITY_EQ15] if variants else [VELOCITY])
         else:
             allowed = np.array(kinds or ([GIVEN, FLUX, NEUMANN_BFL, FLUX_SIMPLIFIED] if variants
                                          else [GIVEN, FLUX, NEUMANN_BFL]))
+            if reaction and is_c:
+                allowed = np.concatenate([allowed, [REACTION, REACTION]])
         for a in range(1, len(e)):
             nodes = np.flatnonzero(((solid3 == 0) & (_upstream_solid(solid3, e[a]) == 1)).ravel())
             m = nodes.size
@@ -258,6 +265,8 @@ def random_links(dim, shape, solid, rng, has_h=False, has_g=False, kinds=None, p
             r["phi_wall"] = rng.uniform(lo, hi, m)
             r["k0"] = rng.uniform(-0.01, 0.01, m)
             r["k1"] = rng.uniform(-0.05, 0.0, m)
+            react = r["kind"] == REACTION
+            r["k1"][react] = rng.uniform(0.5, 1.0, int(react.sum()))
             out.append(r)
     if not out:
         return np.zeros(0, LINK_DTYPE)
