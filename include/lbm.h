@@ -64,12 +64,15 @@ enum { LBM_FLOW = 1, LBM_CD = 2, LBM_MHD = 4 };
 /* One case (one domain).  tau_* > 1/2 (nu = (tau_nu - 1/2)/3, D = (tau_D - 1/2)/4,
  * eta = (tau_eta - 1/2)/4: Eq. 1, 3, 5).  rho0, C0, B0 are the default initial
  * state (rest at equilibrium; the paper initialises with u = 0, Sec. 5.2) and
- * the references of the 16-bit offset storage. */
+ * the references of the 16-bit offset storage.  With several concentration
+ * species (lbm_config.nspecies > 1), tau_D and C0 are species 0's and
+ * tau_Dk[k - 1], C0k[k - 1] those of species k = 1, 2, 3 (ignored otherwise). */
 typedef struct {
     int32_t nx, ny, nz;            /* nz = 1 for D2Q9; each >= 1 */
     double tau_nu, tau_D, tau_eta;
     double accel[3];               /* body force per unit mass */
     double rho0, C0, B0[3];
+    double tau_Dk[3], C0k[3];      /* concentration species 1..3 */
 } lbm_case;
 
 typedef struct {
@@ -80,9 +83,17 @@ typedef struct {
     const lbm_case *cases;         /* ncases entries, copied */
     void *stream;                  /* cudaStream_t; NULL = the context creates and owns a non-blocking stream */
     int32_t device;                /* CUDA device ordinal */
+    int32_t nspecies;              /* concentration species with LBM_CD: 0 or 1 = one; 2 or 3 = several
+                                      (Sec. 4.2.2, text after Eq. 23), then without LBM_MHD */
 } lbm_config;
 
-/* Wall-link kinds (Sec. 3-4).  Fields: 0 = f (flow), 1 = h (C), 2 + k = g_k (B_k). */
+/* Field code of concentration species k in lbm_link.field (k = 0 is the
+ * field 1 of a single concentration; the magnetic field keeps 2 + k). */
+#define LBM_FIELD_SPECIES(k) ((k) == 0 ? 1 : 4 + (k))
+#define LBM_MAX_SPECIES 3
+
+/* Wall-link kinds (Sec. 3-4).  Fields: 0 = f (flow), 1 = h (C, species 0),
+ * 2 + k = g_k (B_k), 4 + k = h of concentration species k = 1, 2. */
 typedef enum {
     LBM_W_VELOCITY = 0,    /* field f.  Given wall velocity u_wall: Eq. 15 with Eq. 16 for d < 1/2,
                               Eq. 43 for d >= 1/2 (static walls: Bouzidi, Eq. 11/12) */
@@ -102,10 +113,18 @@ typedef enum {
                                   at d = 1 (inaccurate at small c_w, Sec. 5.4), Eq. 28 at d = 1/2 */
     /* Open boundaries (Sec. 5.1): a given inlet velocity is LBM_W_VELOCITY with
      * u_wall normal to the boundary (Eq. 41, 43). */
-    LBM_W_PRESSURE = 6         /* field f, flow-only contexts.  Given density rho_w = phi_wall
+    LBM_W_PRESSURE = 6,        /* field f, flow-only contexts.  Given density rho_w = phi_wall
                                   (pressure rho_w c_s^2): f^eq_a(X) + f^eq_a'(X) - f_rel,a'(Y) with
                                   Y by Eq. 16 for d < 1/2, Eq. 44 for d >= 1/2 (Eq. 42 at d = 1/2);
                                   u(X) extrapolated by Eq. 13 from the fluid velocities at A and E */
+    /* (kind 7 is not used by this library) */
+    LBM_W_REACTION = 8         /* concentration species i, contexts with several species.  Surface
+                                  reaction flux of the case's network (lbm_set_reactions):
+                                  increment k0 + k1 R_i(C_1(X), C_2(X), ..) per link and step, with
+                                  every species' C(X) by Eq. 13 from its own C at A and E and no
+                                  coupled solve (Sec. 4.2.2, text after Eq. 23), imposed with the
+                                  moving-wall correction (Eq. 24) by the M scheme (Eq. 25-27); k1 is
+                                  the link's share of the wall area (1 for flat walls, Eq. 48) */
 } lbm_wall_kind;
 
 /* One wall link: the unknown population of direction dir (pointing from the
@@ -121,8 +140,20 @@ typedef struct {
     double d;
     double u_wall[3];              /* wall velocity (never extrapolated) */
     double phi_wall;               /* LBM_W_GIVEN: C or B_k on the wall; LBM_W_PRESSURE: density */
-    double k0, k1;                 /* LBM_W_FLUX: increment k0 + k1 * phi_X per step */
+    double k0, k1;                 /* LBM_W_FLUX: increment k0 + k1 * phi_X per step;
+                                      LBM_W_REACTION: k0 + k1 * R_i(C_X) */
 } lbm_link;
+
+/* One surface reaction of a case's network (several species): it runs at
+ * rate * prod_m C_m^order[m] per unit wall area and time (order 0, 1 or 2)
+ * and produces species i at stoich[i] times that rate (negative: consumed);
+ * R_i sums the reactions.  Mass-action kinetics: A + B -> P is order {1, 1, 0},
+ * stoich {-1, -1, 1}. */
+typedef struct {
+    double rate;
+    int32_t order[LBM_MAX_SPECIES];
+    double stoich[LBM_MAX_SPECIES];
+} lbm_reaction;
 
 /* Create a context: validates the configuration, allocates all device memory
  * for every case (two population buffers, node flags, tile list, reduction
@@ -191,10 +222,22 @@ lbm_status lbm_set_graph(lbm_ctx *ctx, int32_t steps_per_graph);
 lbm_status lbm_set_wall_motion(lbm_ctx *ctx, int32_t case_id, double omega, double phase);
 
 /* Macroscopic fields of one case at the current time, FP64, host arrays of N
- * (rho, C) or 3N (u, B) entries; NULL skips.  Solid nodes report 0.
- * Synchronises.  Errors: LBM_EINVAL, LBM_ECUDA. */
+ * (rho, C) or 3N (u, B) entries; NULL skips.  Solid nodes report 0.  C is
+ * concentration species 0.  Synchronises.  Errors: LBM_EINVAL, LBM_ECUDA. */
 lbm_status lbm_moments(lbm_ctx *ctx, int32_t case_id, double *rho, double *u,
                        double *C, double *B);
+
+/* Concentration of species k of one case at the current time: host array of
+ * N entries (solid nodes 0).  Synchronises.  Errors: LBM_EINVAL (k outside the
+ * context's species), LBM_ECUDA. */
+lbm_status lbm_species(lbm_ctx *ctx, int32_t case_id, int32_t k, double *C);
+
+/* The surface reaction network of one case (contexts with several species):
+ * n <= 4 reactions, copied; used by the case's LBM_W_REACTION links from the
+ * next step on (drops captured graphs).  n = 0 clears it (no reaction flux).
+ * Errors: LBM_EINVAL (one species, n, order outside 0..2, non-finite),
+ * LBM_ECUDA. */
+lbm_status lbm_set_reactions(lbm_ctx *ctx, int32_t case_id, int32_t n, const lbm_reaction *reactions);
 
 /* FP64 reductions over the fluid nodes of every case (invariants and the
  * steady-state test; the paper states no convergence criterion):
@@ -202,7 +245,9 @@ lbm_status lbm_moments(lbm_ctx *ctx, int32_t case_id, double *rho, double *u,
  *                     number of non-finite populations,
  *                     sum |phi - phi_prev|^2, sum |phi|^2 }
  * with phi = (u, C, B - B0) (the parts the physics mask enables) and phi_prev
- * the value at the previous call (the first call compares with zero).  The
+ * the value at the previous call (the first call compares with zero); with
+ * several concentration species, slots 2-4 hold sum C_1 .. sum C_3 and
+ * phi = (u, C_0, C_1, ..).  The
  * per-node terms are formed in the step's arithmetic precision (FP64 storage:
  * FP64, otherwise FP32, which also keeps phi_prev); every sum over nodes is
  * FP64.  The reduction is deterministic (fixed order).  out: host, 8*ncases

@@ -60,11 +60,18 @@ struct lbm_ctx {
     lbm_config cfg{};
     int dim = 2;
     bool hh = false, hg = false, dbl = false, offset = false;
+    int nc = 0;                        // concentration species (hh: nc >= 1)
     int QF = 9, QM = 5, NB = 2, H0 = 9, G0 = 9, P = 9;
     size_t elem = 4;
     Lat latf{}, latm{};
     std::vector<CaseHost> cases;
     int64_t pool_elems = 0, total_nodes = 0;
+    // the population buffers, each with `guard` elements before and after
+    // (pool[i] = pool_alloc[i] + guard elements): the paired-node step reads
+    // its pulls unwrapped first, up to a row and a slice plus a tile away
+    // from the case's planes
+    int64_t guard = 0;
+    void *pool_alloc[2] = {nullptr, nullptr};
     void *pool[2] = {nullptr, nullptr};
     int cur = 0;
     uint8_t *d_flags = nullptr;
@@ -83,8 +90,9 @@ struct lbm_ctx {
     std::vector<int2> h_tiles;         // host copies for the per-tile boundary ranges
     std::vector<BRec> h_brec;
     int32_t *d_tile_brec = nullptr;    // [ntiles + 1]
-    std::vector<uint8_t> h_flags;      // host copy of the node flags (tile classification)
-    uint8_t *d_tile_fluid = nullptr;   // [ntiles]: 1 when every node of the tile is bulk fluid
+    std::vector<uint8_t> h_flags;      // host copy of the node flags (span construction)
+    int4 *d_spans = nullptr;           // runs of bulk-fluid nodes, at most tile_nodes each
+    int32_t nspans = 0;
     void *d_links = nullptr;
     size_t cap_brec = 0, cap_links = 0;
     double *d_snap = nullptr, *d_part = nullptr, *d_red = nullptr, *h_red = nullptr;
@@ -110,6 +118,10 @@ struct lbm_ctx {
     long long *d_clock = nullptr;      // the context's step count, advanced by the clock kernel
     int2 *d_wall_links = nullptr;      // (link index, case) of every velocity link of an oscillating wall
     int32_t n_wall_links = 0;
+    // surface reaction networks (several species): one ReactDev per case
+    void *d_react = nullptr;
+    std::vector<lbm_reaction> h_react;   // MAX_REACT per case
+    std::vector<int32_t> h_nreact;
     int sm_count = 1;
     KernelSet ks{};
     std::string err;
@@ -146,13 +158,25 @@ bool finite3(const double *v) { return std::isfinite(v[0]) && std::isfinite(v[1]
 // A flux wall of h or g whose wall moves would need the same oscillation in
 // its moving-wall term; such links and wall motion exclude each other.
 bool moving_flux_link(const lbm_link &lk) {
-    return lk.field != 0 && (lk.kind == LBM_W_FLUX || lk.kind == LBM_W_FLUX_SIMPLIFIED) &&
+    return lk.field != 0 && (lk.kind == LBM_W_FLUX || lk.kind == LBM_W_FLUX_SIMPLIFIED || lk.kind == LBM_W_REACTION) &&
            (lk.u_wall[0] != 0.0 || lk.u_wall[1] != 0.0 || lk.u_wall[2] != 0.0);
 }
 
-// base plane of a field: 0 f, 1 h, 2 + k g_k
+// concentration species of a field code (1: species 0, 4 + k: species k >= 1), or -1
+int field_species(int field) { return field == 1 ? 0 : (field >= 5 && field < 4 + MAX_SPECIES ? field - 4 : -1); }
+
+// base plane of a field: 0 f, 1 / 4 + k concentration species, 2 + k g_k
 int field_base(const lbm_ctx *c, int field) {
-    return field == 0 ? 0 : (field == 1 ? c->H0 : c->G0 + (field - 2) * c->QM);
+    const int sp = field_species(field);
+    return field == 0 ? 0 : (sp >= 0 ? c->H0 + sp * c->QM : c->G0 + (field - 2) * c->QM);
+}
+
+// storage reference of a field of a case: rho0, C0 of the species, B0_k
+double field_ref(const CaseHost &cs, int field) {
+    const int sp = field_species(field);
+    if (field == 0) return cs.cfg.rho0;
+    if (sp >= 0) return sp == 0 ? cs.cfg.C0 : cs.cfg.C0k[sp - 1];
+    return cs.cfg.B0[field - 2];
 }
 
 int64_t wrap_node(const CaseHost &cs, int64_t n, const int e[3], int sign) {
@@ -188,6 +212,13 @@ CaseDev<T> case_dev(const lbm_ctx *c, const CaseHost &cs) {
     d.stride = cs.stride;
     d.node_off = cs.node_off;
     d.om_f = T(1.0 / cs.cfg.tau_nu);
+    d.index = (int32_t)(&cs - c->cases.data());
+    for (int k = 1; k < MAX_SPECIES; ++k) {
+        const bool on = k < c->nc;
+        d.sp_om[k - 1] = on ? T(1.0 / cs.cfg.tau_Dk[k - 1]) : T(0);
+        d.sp_omc[k - 1] = on ? T(1.0 - 1.0 / cs.cfg.tau_Dk[k - 1]) : T(1);
+        d.sp_ref[k - 1] = on ? T(cs.cfg.C0k[k - 1]) : T(0);
+    }
     d.om_h = c->hh ? T(1.0 / cs.cfg.tau_D) : T(0);
     d.om_g = c->hg ? T(1.0 / cs.cfg.tau_eta) : T(0);
     d.omc_f = T(1.0 - 1.0 / cs.cfg.tau_nu);
@@ -225,7 +256,7 @@ LinkDev<T> link_dev(const lbm_ctx *c, const CaseHost &cs, const lbm_link &lk) {
         E = A;
         d = 0.5;
     }
-    double c0 = 0, ca = 0, cap = 0, cape = 0, cphi = 0, cB[3] = {0, 0, 0};
+    double c0 = 0, ca = 0, cap = 0, cape = 0, cphi = 0, cB[3] = {0, 0, 0}, cR = 0;
     switch (lk.kind) {
     case LBM_W_VELOCITY: {
         // increment f^eq_a(X) - f^eq_a'(X) = 2 rho_X w (e.u_w)/c_s^2 (Sec. 4.1)
@@ -263,9 +294,10 @@ LinkDev<T> link_dev(const lbm_ctx *c, const CaseHost &cs, const lbm_link &lk) {
         else { ca = (2 * d - 1) / (2 * d); cap = 1 / (2 * d); }               // Eq. 22
         break;
     case LBM_W_FLUX:
-    case LBM_W_FLUX_SIMPLIFIED: {
+    case LBM_W_FLUX_SIMPLIFIED:
+    case LBM_W_REACTION: {
         double s;
-        if (lk.kind == LBM_W_FLUX) {
+        if (lk.kind == LBM_W_FLUX || lk.kind == LBM_W_REACTION) {
             // M scheme, Eq. 25-27: [ (d - 1/2) p_a(A) + (1/2 - d) p_a'(E) + (1/2 + d) p_a'(A)
             //                        + dflux + dmove ] / (d + 1/2)
             s = 1.0 / (d + 0.5);
@@ -285,7 +317,11 @@ LinkDev<T> link_dev(const lbm_ctx *c, const CaseHost &cs, const lbm_link &lk) {
             cap = s;
         }
         c0 = lk.k0 * s;
-        if (lk.field == 1) {
+        if (lk.kind == LBM_W_REACTION) {
+            // dflux = k0 + k1 R_i(C_X) (the kernel forms R_i, Sec. 4.2.2); dmove of Eq. 24 at C_X
+            cphi = 8.0 * w * eu * s;
+            cR = lk.k1 * s;
+        } else if (field_species(lk.field) >= 0) {
             // dmove = h^eq_a'(-u) - h^eq_a(-u) = 2 w C_X (e.u)/c_h^2 (Eq. 24)
             cphi = (lk.k1 + 8.0 * w * eu) * s;
         } else {
@@ -311,6 +347,10 @@ LinkDev<T> link_dev(const lbm_ctx *c, const CaseHost &cs, const lbm_link &lk) {
     else
         r.flags = (uint8_t)((cphi != 0.0 ? LINK_NEED_PHI : 0) |
                             ((cB[0] != 0.0 || cB[1] != 0.0 || cB[2] != 0.0) ? LINK_NEED_B : 0));
+    if (lk.kind == LBM_W_REACTION) {
+        r.flags |= LINK_NEED_REACT;
+        cB[0] = cR;                    // the reaction weight (h links use no B_X term)
+    }
     // the velocity term of a moving wall of an oscillating case (Eq. 45): the
     // clock kernel scales cphi from its steady value kept in cB[0] (unused by f links)
     const size_t ci = (size_t)(&cs - c->cases.data());
@@ -328,7 +368,7 @@ LinkDev<T> link_dev(const lbm_ctx *c, const CaseHost &cs, const lbm_link &lk) {
         if (!(r.flags & LINK_WALL_T)) r.cB[j] = T(cB[j]);
     // the planes store s = p - w phi_ref (w_a = w_a'): the formula on s gains
     // the constant (ca + cap + cape - 1) w phi_ref
-    const double ref = lk.field == 0 ? cs.cfg.rho0 : (lk.field == 1 ? cs.cfg.C0 : cs.cfg.B0[lk.field - 2]);
+    const double ref = field_ref(cs, lk.field);
     r.c0 = T(c0 + (ca + cap + cape - 1.0) * w * ref);
     r.ref_phi = T(ref);
     return r;
@@ -373,21 +413,28 @@ lbm_status build_tile_brec(lbm_ctx *ctx) {
     ctx->d_tile_brec = nullptr;
     CK(cudaMalloc(&ctx->d_tile_brec, r.size() * sizeof(int32_t)));
     CK(cudaMemcpy(ctx->d_tile_brec, r.data(), r.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    // tiles of bulk fluid only: the step kernel skips their per-node flag loads
-    std::vector<uint8_t> tf(ctx->h_tiles.size(), 0);
+    // spans: maximal runs of bulk-fluid nodes of each case, cut into pieces
+    // of at most tile_nodes nodes that start at even offsets (the paired-node
+    // step takes nodes two by two from an even node)
+    std::vector<int4> spans;
     if (!ctx->h_flags.empty())
-        for (size_t t = 0; t < ctx->h_tiles.size(); ++t) {
-            const int2 tl = ctx->h_tiles[t];
-            const CaseHost &cs = ctx->cases[tl.x];
-            const int64_t end = std::min<int64_t>(cs.N, (int64_t)tl.y + ctx->tile_nodes);
-            bool all = true;
-            for (int64_t n = tl.y; n < end && all; ++n) all = ctx->h_flags[cs.node_off + n] == NODE_FLUID;
-            tf[t] = all ? 1 : 0;
+        for (size_t c = 0; c < ctx->cases.size(); ++c) {
+            const CaseHost &cs = ctx->cases[c];
+            const uint8_t *f = ctx->h_flags.data() + cs.node_off;
+            for (int32_t n = 0; n < cs.N;) {
+                if (f[n] != NODE_FLUID) { ++n; continue; }
+                const int32_t a = n;
+                while (n < cs.N && f[n] == NODE_FLUID) ++n;
+                for (int64_t s0 = a & ~1; s0 < n; s0 += ctx->tile_nodes)
+                    spans.push_back(make_int4((int)c, (int)std::max<int64_t>(a, s0),
+                                              (int)std::min<int64_t>(n, s0 + ctx->tile_nodes), 0));
+            }
         }
-    if (ctx->d_tile_fluid) cudaFree(ctx->d_tile_fluid);
-    ctx->d_tile_fluid = nullptr;
-    CK(cudaMalloc(&ctx->d_tile_fluid, std::max<size_t>(1, tf.size())));
-    if (!tf.empty()) CK(cudaMemcpy(ctx->d_tile_fluid, tf.data(), tf.size(), cudaMemcpyHostToDevice));
+    if (ctx->d_spans) cudaFree(ctx->d_spans);
+    ctx->d_spans = nullptr;
+    ctx->nspans = (int32_t)spans.size();
+    CK(cudaMalloc(&ctx->d_spans, std::max<size_t>(1, spans.size()) * sizeof(int4)));
+    if (!spans.empty()) CK(cudaMemcpy(ctx->d_spans, spans.data(), spans.size() * sizeof(int4), cudaMemcpyHostToDevice));
     return LBM_OK;
 }
 
@@ -507,15 +554,17 @@ StepParams<T> step_params(const lbm_ctx *c) {
     p.brec = c->d_brec;
     p.nbrec = c->nbrec;
     p.tile_brec = c->d_tile_brec;
-    p.tile_fluid = c->d_tile_fluid;
+    p.spans = c->d_spans;
+    p.nspans = c->nspans;
     p.links = static_cast<const LinkDev<T> *>(c->d_links);
+    p.react = static_cast<const ReactDev<T> *>(c->d_react);
     return p;
 }
 
 int step_grid(const lbm_ctx *c) {
     if (c->launch.variant == 1 || c->launch.variant == 3) return std::max(1, std::min(c->ntiles, c->bulk_grid));
-    if (c->launch.blocks_per_sm <= 0) return c->ntiles;
-    return std::max(1, std::min(c->ntiles, c->launch.blocks_per_sm * c->sm_count));
+    if (c->launch.blocks_per_sm <= 0) return std::max(1, c->nspans);
+    return std::max(1, std::min(c->nspans, c->launch.blocks_per_sm * c->sm_count));
 }
 
 // Wall motion of the coming step (Eq. 45): every velocity link of an oscillating
@@ -568,8 +617,8 @@ cudaError_t launch_step_t(lbm_ctx *ctx) {
         bp.err = ctx->d_err;
         e = ctx->ks.ring(&p, bp, ctx->launch.stages, step_grid(ctx), ctx->bulk_smem, ctx->stream);
     } else if (ctx->launch.variant == 2) {
-        e = ctx->ks.pair[ctx->step_idx](&p, ctx->launch.nodes_per_thread, step_grid(ctx), ctx->launch.block,
-                                        ctx->stream);
+        e = ctx->ks.unw[ctx->step_idx](&p, ctx->launch.nodes_per_thread, step_grid(ctx), ctx->launch.block,
+                                       ctx->stream);
     } else {
         e = ctx->ks.step[ctx->step_idx](&p, ctx->launch.nodes_per_thread, step_grid(ctx), ctx->launch.block,
                                         ctx->stream);
@@ -601,11 +650,12 @@ lbm_status launch_init(lbm_ctx *ctx, int case_id, const FT *rho, const FT *u, co
     ip.B = B;
     ip.rho0 = T(cs.cfg.rho0);
     ip.C0 = T(cs.cfg.C0);
+    for (int k = 0; k < MAX_SPECIES; ++k) ip.C0s[k] = T(k == 0 ? cs.cfg.C0 : (k < ctx->nc ? cs.cfg.C0k[k - 1] : 0.0));
     for (int k = 0; k < 3; ++k) ip.B0[k] = T(cs.cfg.B0[k]);
     const int grid = (int)((cs.N + 255) / 256);
     CK(fn(&ip, grid, 256, ctx->stream));
     // residual history of the case starts again from zero
-    const size_t se = snap_elem(ctx) * snap_width(ctx->dim, ctx->hh, ctx->hg);
+    const size_t se = snap_elem(ctx) * snap_width(ctx->dim, ctx->nc, ctx->hg);
     CK(cudaMemsetAsync(reinterpret_cast<char *>(ctx->d_snap) + cs.node_off * se, 0, (size_t)cs.N * se, ctx->stream));
     return LBM_OK;
 }
@@ -642,10 +692,10 @@ lbm_status init_case_host(lbm_ctx *ctx, int case_id, const double *rho, const do
 void free_ctx(lbm_ctx *c) {
     if (!c) return;
     drop_graphs(c);
-    void *ptrs[] = {c->pool[0], c->pool[1], c->d_flags, c->d_cases, c->d_tiles, c->d_case_tile_lo, c->d_tile_brec,
-                    c->d_tile_fluid, c->d_rtiles,
+    void *ptrs[] = {c->pool_alloc[0], c->pool_alloc[1], c->d_flags, c->d_cases, c->d_tiles, c->d_case_tile_lo,
+                    c->d_tile_brec, c->d_spans, c->d_rtiles,
                     c->d_brec, c->d_links, c->d_snap, c->d_part, c->d_red, c->d_mom, c->d_err,
-                    c->d_motion, c->d_clock, c->d_wall_links};
+                    c->d_motion, c->d_clock, c->d_wall_links, c->d_react};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_red) cudaFreeHost(c->h_red);
@@ -656,6 +706,24 @@ void free_ctx(lbm_ctx *c) {
     if (c->side) cudaStreamDestroy(c->side);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
+}
+
+}  // namespace
+
+namespace {
+template <class T>
+ReactDev<T> react_dev(const lbm_reaction *r, int n) {
+    ReactDev<T> d{};
+    d.n = n;
+    for (int j = 0; j < n; ++j) {
+        d.rate[j] = T(r[j].rate);
+        d.ord[j] = 0;
+        for (int m = 0; m < LBM_MAX_SPECIES; ++m) {
+            d.ord[j] |= (uint32_t)r[j].order[m] << (8 * m);
+            d.st[j][m] = T(r[j].stoich[m]);
+        }
+    }
+    return d;
 }
 
 }  // namespace
@@ -710,6 +778,14 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
     ctx->cfg.cases = nullptr;
     ctx->dim = cfg->lattice == LBM_D2Q9 ? 2 : 3;
     ctx->hh = (cfg->physics & LBM_CD) != 0;
+    ctx->nc = ctx->hh ? std::max(1, (int)cfg->nspecies) : 0;
+    if (cfg->nspecies < 0 || ctx->nc > MAX_COMPILED_SPECIES || (cfg->nspecies > 1 && !ctx->hh) ||
+        (ctx->nc > 1 && (cfg->physics & LBM_MHD))) {
+        lbm_status s = fail(ctx, LBM_EINVAL, "nspecies %d: 0..%d with LBM_CD, and several species exclude LBM_MHD",
+                            cfg->nspecies, MAX_COMPILED_SPECIES);
+        delete ctx;
+        return s;
+    }
     ctx->hg = (cfg->physics & LBM_MHD) != 0;
     ctx->dbl = cfg->prec == LBM_FP64;
     ctx->offset = cfg->prec == LBM_FP16S || cfg->prec == LBM_BF16S;
@@ -720,7 +796,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
     ctx->QM = ctx->latm.q;
     ctx->NB = ctx->dim;
     ctx->H0 = ctx->QF;
-    ctx->G0 = ctx->QF + (ctx->hh ? ctx->QM : 0);
+    ctx->G0 = ctx->QF + ctx->nc * ctx->QM;
     ctx->P = ctx->G0 + (ctx->hg ? ctx->NB * ctx->QM : 0);
     int64_t pool = 0, nodes = 0;
     for (int c = 0; c < cfg->ncases; ++c) {
@@ -734,6 +810,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
         }
         const int64_t N = (int64_t)k.nx * k.ny * k.nz;
         bool bad_tau = !(k.tau_nu > 0.5) || (ctx->hh && !(k.tau_D > 0.5)) || (ctx->hg && !(k.tau_eta > 0.5));
+        for (int sp = 1; sp < ctx->nc; ++sp)
+            bad_tau = bad_tau || !(k.tau_Dk[sp - 1] > 0.5) || !std::isfinite(k.C0k[sp - 1]);
         if (N > (int64_t)1 << 30 || bad_tau || !finite3(k.accel) || !finite3(k.B0) || !std::isfinite(k.rho0) ||
             !(k.rho0 > 0) || !std::isfinite(k.C0)) {
             lbm_status s = fail(ctx, LBM_EINVAL, "case %d: bad parameters (tau must exceed 1/2)", c);
@@ -757,7 +835,22 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
     }
     ctx->pool_elems = pool;
     ctx->total_nodes = nodes;
-    switch ((ctx->dim == 3 ? 4 : 0) + (int)cfg->prec) {
+    int64_t reach = 0;                 // farthest unwrapped pull: a slice, a row and a node
+    for (const CaseHost &cs : ctx->cases)
+        reach = std::max<int64_t>(reach, (int64_t)cs.cfg.nx * cs.cfg.ny + cs.cfg.nx + 1);
+    ctx->guard = round_up(reach + 2 * 2048 + 64, 64);   // + the farthest pair beyond a span's end
+    if (ctx->nc > 1) {
+        switch ((ctx->dim == 3 ? 4 : 0) + (int)cfg->prec) {
+        case 0: ctx->ks = species_2d_f64(ctx->nc); break;
+        case 1: ctx->ks = species_2d_f32(ctx->nc); break;
+        case 2: ctx->ks = species_2d_f16(ctx->nc); break;
+        case 3: ctx->ks = species_2d_bf16(ctx->nc); break;
+        case 4: ctx->ks = species_3d_f64(ctx->nc); break;
+        case 5: ctx->ks = species_3d_f32(ctx->nc); break;
+        case 6: ctx->ks = species_3d_f16(ctx->nc); break;
+        default: ctx->ks = species_3d_bf16(ctx->nc); break;
+        }
+    } else switch ((ctx->dim == 3 ? 4 : 0) + (int)cfg->prec) {
     case 0: ctx->ks = kernels_2d_f64(ctx->hh, ctx->hg); break;
     case 1: ctx->ks = kernels_2d_f32(ctx->hh, ctx->hg); break;
     case 2: ctx->ks = kernels_2d_f16(ctx->hh, ctx->hg); break;
@@ -786,12 +879,14 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
     ck(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
     ck(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming), "cudaEventCreate");
     ck(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, cfg->device), "sm count");
-    const size_t pool_bytes = (size_t)pool * ctx->elem;
-    ck(cudaMalloc(&ctx->pool[0], pool_bytes), "population buffer 0");
-    ck(cudaMalloc(&ctx->pool[1], pool_bytes), "population buffer 1");
+    const size_t alloc_bytes = (size_t)(pool + 2 * ctx->guard) * ctx->elem;
+    ck(cudaMalloc(&ctx->pool_alloc[0], alloc_bytes), "population buffer 0");
+    ck(cudaMalloc(&ctx->pool_alloc[1], alloc_bytes), "population buffer 1");
     if (st == LBM_OK) {
-        ck(cudaMemset(ctx->pool[0], 0, pool_bytes), "memset");
-        ck(cudaMemset(ctx->pool[1], 0, pool_bytes), "memset");
+        ck(cudaMemset(ctx->pool_alloc[0], 0, alloc_bytes), "memset");
+        ck(cudaMemset(ctx->pool_alloc[1], 0, alloc_bytes), "memset");
+        for (int i = 0; i < 2; ++i)
+            ctx->pool[i] = static_cast<char *>(ctx->pool_alloc[i]) + (size_t)ctx->guard * ctx->elem;
     }
     ck(cudaMalloc(&ctx->d_flags, (size_t)nodes), "flags");
     ck(cudaMalloc(&ctx->d_cases, ctx->cases.size() * (ctx->dbl ? sizeof(CaseDev<double>) : sizeof(CaseDev<float>))),
@@ -804,6 +899,13 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
     ck(cudaEventCreateWithFlags(&ctx->ev_check, cudaEventDisableTiming), "cudaEventCreate");
     ck(cudaMalloc(&ctx->d_mom, (size_t)ctx->max_case_nodes * 8 * sizeof(double)), "moment scratch");
     ck(cudaMalloc(&ctx->d_err, sizeof(int32_t)), "error word");
+    ck(cudaMalloc(&ctx->d_react, ctx->cases.size() * std::max(sizeof(ReactDev<double>), sizeof(ReactDev<float>))),
+       "reaction networks");
+    if (st == LBM_OK)
+        ck(cudaMemset(ctx->d_react, 0, ctx->cases.size() * std::max(sizeof(ReactDev<double>), sizeof(ReactDev<float>))),
+           "memset");
+    ctx->h_react.assign(ctx->cases.size() * MAX_REACT, lbm_reaction{});
+    ctx->h_nreact.assign(ctx->cases.size(), 0);
     if (st == LBM_OK) ck(cudaMemset(ctx->d_err, 0, sizeof(int32_t)), "memset");
     if (st == LBM_OK) st = build_tiles(ctx);
     if (st == LBM_OK) st = upload_walls(ctx);
@@ -829,21 +931,22 @@ lbm_status lbm_set_walls(lbm_ctx *ctx, int32_t case_id, const uint8_t *solid, co
     const int64_t N = cs.N;
     std::vector<uint8_t> sol(solid, solid + N);
     for (auto &v : sol) v = v ? 1 : 0;
-    const int nfields = 1 + (ctx->hh ? 1 : 0) + (ctx->hg ? ctx->NB : 0);
-    (void)nfields;
+
     // coverage bitmap over (node, plane)
     std::vector<uint8_t> seen((size_t)N * ctx->P, 0);
     for (size_t i = 0; i < nlinks; ++i) {
         const lbm_link &lk = links[i];
         const int f = lk.field;
-        const bool ok_field = f == 0 || (f == 1 && ctx->hh) || (f >= 2 && f < 2 + ctx->NB && ctx->hg);
+        const int sp = field_species(f);
+        const bool ok_field = f == 0 || (sp >= 0 && sp < ctx->nc) || (sp < 0 && f >= 2 && f < 2 + ctx->NB && ctx->hg);
         if (!ok_field) return fail(ctx, LBM_EINVAL, "link %zu: field %d not enabled", i, f);
         const Lat &L = f == 0 ? ctx->latf : ctx->latm;
         if (lk.dir < 1 || lk.dir >= L.q) return fail(ctx, LBM_EINVAL, "link %zu: bad direction %d", i, lk.dir);
         const bool ok_kind = f == 0 ? (lk.kind == LBM_W_VELOCITY || lk.kind == LBM_W_VELOCITY_EQ15 ||
                                        (lk.kind == LBM_W_PRESSURE && !ctx->hg && !ctx->hh))
                                     : (lk.kind == LBM_W_GIVEN || lk.kind == LBM_W_FLUX || lk.kind == LBM_W_NEUMANN_BFL ||
-                                       lk.kind == LBM_W_FLUX_SIMPLIFIED);
+                                       lk.kind == LBM_W_FLUX_SIMPLIFIED ||
+                                       (lk.kind == LBM_W_REACTION && sp >= 0 && ctx->nc > 1));
         if (!ok_kind) return fail(ctx, LBM_EINVAL, "link %zu: kind %d not valid for field %d", i, lk.kind, f);
         if (ctx->motion && ctx->h_motion[MOTION_W * case_id + 2] != 0.0 && moving_flux_link(lk))
             return fail(ctx, LBM_EINVAL, "link %zu: a moving flux wall in a case with wall motion", i);
@@ -863,8 +966,9 @@ lbm_status lbm_set_walls(lbm_ctx *ctx, int32_t case_id, const uint8_t *solid, co
     tmp.cfg = cs.cfg;
     for (int64_t n = 0; n < N; ++n) {
         if (sol[n]) continue;
-        for (int f = 0; f < 2 + ctx->NB; ++f) {
-            if ((f == 1 && !ctx->hh) || (f >= 2 && !ctx->hg)) continue;
+        for (int f = 0; f < 4 + MAX_SPECIES; ++f) {
+            const int sp = field_species(f);
+            if (sp >= ctx->nc || (sp < 0 && f >= 2 && (!ctx->hg || f >= 2 + ctx->NB))) continue;
             const Lat &L = f == 0 ? ctx->latf : ctx->latm;
             for (int a = 1; a < L.q; ++a) {
                 if (sol[wrap_node(tmp, n, L.e[a], -1)] && !seen[(size_t)n * ctx->P + field_base(ctx, f) + a])
@@ -993,22 +1097,71 @@ lbm_status lbm_step(lbm_ctx *ctx, int32_t nsteps) {
     return LBM_OK;
 }
 
-lbm_status lbm_moments(lbm_ctx *ctx, int32_t case_id, double *rho, double *u, double *C, double *B) {
-    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
-    if (case_id < 0 || case_id >= (int)ctx->cases.size()) return fail(ctx, LBM_EINVAL, "bad case id %d", case_id);
-    const CaseHost &cs = ctx->cases[case_id];
-    const int64_t N = cs.N;
+// Moments of one case into the moment scratch (rho, u, C of `species`, B).
+static lbm_status moments_to_scratch(lbm_ctx *ctx, int32_t case_id, int32_t species) {
+    const int64_t N = ctx->cases[case_id].N;
     double *d = ctx->d_mom;
     const int grid = (int)((N + 255) / 256);
     if (ctx->dbl) {
         MomParams<double> mp{ctx->pool[ctx->cur], ctx->d_flags, static_cast<const CaseDev<double> *>(ctx->d_cases),
-                             case_id, d, d + N, d + 4 * N, d + 5 * N};
+                             case_id, d, d + N, d + 4 * N, d + 5 * N, species};
         CK(ctx->ks.moments(&mp, grid, 256, ctx->stream));
     } else {
         MomParams<float> mp{ctx->pool[ctx->cur], ctx->d_flags, static_cast<const CaseDev<float> *>(ctx->d_cases),
-                            case_id, d, d + N, d + 4 * N, d + 5 * N};
+                            case_id, d, d + N, d + 4 * N, d + 5 * N, species};
         CK(ctx->ks.moments(&mp, grid, 256, ctx->stream));
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_species(lbm_ctx *ctx, int32_t case_id, int32_t k, double *C) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (case_id < 0 || case_id >= (int)ctx->cases.size()) return fail(ctx, LBM_EINVAL, "bad case id %d", case_id);
+    if (k < 0 || k >= ctx->nc || !C) return fail(ctx, LBM_EINVAL, "species %d of %d (or C NULL)", k, ctx->nc);
+    const lbm_status st = moments_to_scratch(ctx, case_id, k);
+    if (st != LBM_OK) return st;
+    const int64_t N = ctx->cases[case_id].N;
+    CK(cudaMemcpyAsync(C, ctx->d_mom + 4 * N, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_reactions(lbm_ctx *ctx, int32_t case_id, int32_t n, const lbm_reaction *reactions) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (case_id < 0 || case_id >= (int)ctx->cases.size()) return fail(ctx, LBM_EINVAL, "bad case id %d", case_id);
+    if (ctx->nc < 2) return fail(ctx, LBM_EINVAL, "reaction networks need several concentration species");
+    if (n < 0 || n > MAX_REACT || (n > 0 && !reactions)) return fail(ctx, LBM_EINVAL, "0..%d reactions", MAX_REACT);
+    for (int j = 0; j < n; ++j) {
+        const lbm_reaction &r = reactions[j];
+        if (!std::isfinite(r.rate)) return fail(ctx, LBM_EINVAL, "reaction %d: non-finite rate", j);
+        for (int m = 0; m < LBM_MAX_SPECIES; ++m) {
+            if (r.order[m] < 0 || r.order[m] > 2) return fail(ctx, LBM_EINVAL, "reaction %d: order outside 0..2", j);
+            if (!std::isfinite(r.stoich[m])) return fail(ctx, LBM_EINVAL, "reaction %d: non-finite stoichiometry", j);
+            if (m >= ctx->nc && (r.order[m] != 0 || r.stoich[m] != 0.0))
+                return fail(ctx, LBM_EINVAL, "reaction %d: species %d is not in the context", j, m);
+        }
+        ctx->h_react[(size_t)case_id * MAX_REACT + j] = r;
+    }
+    ctx->h_nreact[case_id] = n;
+    const lbm_reaction *mine = ctx->h_react.data() + (size_t)case_id * MAX_REACT;
+    if (ctx->dbl) {
+        const ReactDev<double> d = react_dev<double>(mine, n);
+        CK(cudaMemcpy(static_cast<ReactDev<double> *>(ctx->d_react) + case_id, &d, sizeof d, cudaMemcpyHostToDevice));
+    } else {
+        const ReactDev<float> d = react_dev<float>(mine, n);
+        CK(cudaMemcpy(static_cast<ReactDev<float> *>(ctx->d_react) + case_id, &d, sizeof d, cudaMemcpyHostToDevice));
+    }
+    drop_graphs(ctx);
+    return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_ctx *ctx, int32_t case_id, double *rho, double *u, double *C, double *B) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (case_id < 0 || case_id >= (int)ctx->cases.size()) return fail(ctx, LBM_EINVAL, "bad case id %d", case_id);
+    const int64_t N = ctx->cases[case_id].N;
+    double *d = ctx->d_mom;
+    const lbm_status st = moments_to_scratch(ctx, case_id, 0);
+    if (st != LBM_OK) return st;
     if (rho) CK(cudaMemcpyAsync(rho, d, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     if (u) CK(cudaMemcpyAsync(u, d + N, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     if (C) CK(cudaMemcpyAsync(C, d + 4 * N, N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1164,7 +1317,7 @@ lbm_status lbm_convert_state(lbm_ctx *dst, lbm_ctx *src) {
         default: e = convert_from(static_cast<const __nv_bfloat16 *>(in), out, dst->cfg.prec, n, dst->stream); break;
     }
     CK(e);
-    const int64_t ns = src->total_nodes * snap_width(src->dim, src->hh, src->hg);
+    const int64_t ns = src->total_nodes * snap_width(src->dim, src->nc, src->hg);
     if (snap_elem(dst) == snap_elem(src)) {
         CK(cudaMemcpyAsync(dst->d_snap, src->d_snap, (size_t)ns * snap_elem(src), cudaMemcpyDeviceToDevice,
                            dst->stream));
@@ -1195,7 +1348,7 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
     int tile = L.block;
     int idx = 0;
     int sidx = 0;
-    if (L.variant == 0) {
+    if (L.variant == 0 || L.variant == 2) {
         if (L.blocks_per_sm < 0 || L.blocks_per_sm > 64) return fail(ctx, LBM_EINVAL, "blocks per SM must be 0..64");
         if (L.nodes_per_thread < 1 || L.nodes_per_thread > 8) return fail(ctx, LBM_EINVAL, "nodes per thread must be 1..8");
         sidx = -1;
@@ -1205,19 +1358,9 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
         if (sidx < 0)
             return fail(ctx, LBM_EINVAL, "min_blocks must be 1 or %d..%d", kstep_minb(ctx->dim, 0), kstep_minb(ctx->dim, 2));
         tile = L.block * L.nodes_per_thread;
-    } else if (L.variant == 2) {
-        if (ctx->elem != 2) return fail(ctx, LBM_EINVAL, "the paired-node variant serves 16-bit storage");
-        if (L.blocks_per_sm < 0 || L.blocks_per_sm > 64) return fail(ctx, LBM_EINVAL, "blocks per SM must be 0..64");
-        if (L.nodes_per_thread < 2 || L.nodes_per_thread > 8 || L.nodes_per_thread % 2)
-            return fail(ctx, LBM_EINVAL, "nodes per thread must be 2, 4, 6 or 8");
-        sidx = -1;
-        for (int k = 0; k < 3; ++k)
-            if (kpair_minb(ctx->dim, k) == L.min_blocks) sidx = k;
-        if (sidx < 0)
-            return fail(ctx, LBM_EINVAL, "min_blocks must be %d..%d", kpair_minb(ctx->dim, 0), kpair_minb(ctx->dim, 2));
-        tile = L.block * L.nodes_per_thread;
     } else if (L.variant == 3) {
-        if (ctx->dbl) return fail(ctx, LBM_EINVAL, "the ring variant serves FP32 and 16-bit storage");
+        if (ctx->dbl || !ctx->ks.ring)
+            return fail(ctx, LBM_EINVAL, "the ring variant serves FP32 and 16-bit storage of one concentration at most");
         if (L.stages < 2 || L.stages > RING_MAX_NS)
             return fail(ctx, LBM_EINVAL, "ring variant: stages must be 2..%d", RING_MAX_NS);
         if (L.blocks_per_sm < 0 || L.blocks_per_sm > 64) return fail(ctx, LBM_EINVAL, "blocks per SM must be 0..64");
@@ -1242,7 +1385,8 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
         if (idx < 0)
             return fail(ctx, LBM_EINVAL, "bulk-copy variant: (block = tile nodes, min_blocks) must be one of "
                                          "(128, 2), (256, 2), (256, 4), (512, 1), (512, 2)");
-        if (ctx->dbl) return fail(ctx, LBM_EINVAL, "the bulk-copy variant serves FP32 and 16-bit storage");
+        if (ctx->dbl || !ctx->ks.step_bulk[idx])
+            return fail(ctx, LBM_EINVAL, "the bulk-copy variant serves FP32 and 16-bit storage of one concentration at most");
         tile = L.block;
         const size_t smem = (size_t)bulk_layout_bytes(ctx->P, tile, (int)ctx->elem, BULK_NS[idx]);
         int maxsm = 0;
@@ -1350,11 +1494,10 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
                 for (int npt : {1, 2, 3, 4}) cands.push_back(lbm_launch{0, b, p, npt, 2, kstep_minb(ctx->dim, r)});
     if (!ctx->dbl)
         for (int k = 0; k < BULK_NCFG; ++k) cands.push_back(lbm_launch{1, BULK_TT[k], 0, 1, 2, BULK_MB[k]});
-    if (ctx->elem == 2)
-        for (int r = 0; r < 3; ++r)
-            for (int b : {128, 256})
-                for (int p : {0, 8})
-                    for (int npt : {2, 4}) cands.push_back(lbm_launch{2, b, p, npt, 2, kpair_minb(ctx->dim, r)});
+    for (int r = 0; r < 3; ++r)
+        for (int b : {64, 128, 256})
+            for (int p : {0, 8})
+                for (int npt : {1, 2, 3, 4}) cands.push_back(lbm_launch{2, b, p, npt, 2, kstep_minb(ctx->dim, r)});
     // (the shared-memory ring, variant 3, is not a candidate: it never won on
     // GB300 and one of its runs was once 400x slower for a reason not found;
     // lbm_set_launch still selects it)

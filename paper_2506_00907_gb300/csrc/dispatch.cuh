@@ -12,8 +12,6 @@ namespace lbm {
 
 // register budgets of k_step (resident 256-thread blocks per SM)
 constexpr int kstep_minb(int dim, int i) { return dim == 2 ? 4 + i : 2 + i; }
-// register budgets of k_step_pair (two nodes per thread need more registers)
-constexpr int kpair_minb(int dim, int i) { return dim == 2 ? 2 + i : 1 + i; }
 // nodes per consumer lane of k_step_ring: packed pairs in 2D, one node in 3D
 constexpr int kring_npl(int dim) { return dim == 2 ? 2 : 1; }
 constexpr int KRING_MINB = 2;
@@ -21,9 +19,8 @@ constexpr int KRING_MINB = 2;
 struct KernelSet {
     cudaError_t (*step[3])(const void *params, int npt, int grid, int block, cudaStream_t s);
     cudaError_t (*boundary)(const void *params, int grid, int block, cudaStream_t s);
-    // paired-node variants (16-bit storage only; null otherwise), budgets kpair_minb(dim, 0..2)
-    cudaError_t (*pair[3])(const void *params, int npt, int grid, int block, cudaStream_t s);
-    const void *pair_fn[3];
+    // unwrapped-pull variants (launch variant 2), budgets kstep_minb(dim, 0..2)
+    cudaError_t (*unw[3])(const void *params, int npt, int grid, int block, cudaStream_t s);
     cudaError_t (*init_d)(const void *params, int grid, int block, cudaStream_t s);   // FP64 host-side fields
     cudaError_t (*init_f)(const void *params, int grid, int block, cudaStream_t s);   // FP32 device fields
     cudaError_t (*moments)(const void *params, int grid, int block, cudaStream_t s);
@@ -38,56 +35,42 @@ struct KernelSet {
     const void *ring_fn;
 };
 
-template <int DIM, bool HH, bool HG, class S>
+template <int DIM, int NC, bool HG, class S>
 struct Launch {
     using T = typename Codec<S>::T;
     template <int MINB>
     static cudaError_t step(const void *p, int npt, int g, int b, cudaStream_t s) {
-        k_step<DIM, HH, HG, S, MINB><<<g, b, 0, s>>>(*static_cast<const StepParams<T> *>(p), npt);
+        k_step<DIM, NC, HG, S, MINB><<<g, b, 0, s>>>(*static_cast<const StepParams<T> *>(p), npt);
         return cudaGetLastError();
     }
-    template <int I>
-    static cudaError_t pair_launch(const void *p, int npt, int g, int b, cudaStream_t s) {
-        if constexpr (sizeof(S) == 2) {
-            k_step_pair<DIM, HH, HG, S, kpair_minb(DIM, I)><<<g, b, 0, s>>>(*static_cast<const StepParams<T> *>(p), npt);
-            return cudaGetLastError();
-        } else {
-            return cudaErrorInvalidValue;
-        }
-    }
-    template <int I>
-    static void set_pair(KernelSet &k) {
-        if constexpr (sizeof(S) == 2) {
-            k.pair[I] = &pair_launch<I>;
-            k.pair_fn[I] = reinterpret_cast<const void *>(&k_step_pair<DIM, HH, HG, S, kpair_minb(DIM, I)>);
-        } else {
-            k.pair[I] = nullptr;
-            k.pair_fn[I] = nullptr;
-        }
+    template <int MINB>
+    static cudaError_t unw(const void *p, int npt, int g, int b, cudaStream_t s) {
+        k_step_unwrapped<DIM, NC, HG, S, MINB><<<g, b, 0, s>>>(*static_cast<const StepParams<T> *>(p), npt);
+        return cudaGetLastError();
     }
     static cudaError_t boundary(const void *p, int g, int b, cudaStream_t s) {
-        k_boundary<DIM, HH, HG, S><<<g, b, 0, s>>>(*static_cast<const StepParams<T> *>(p));
+        k_boundary<DIM, NC, HG, S><<<g, b, 0, s>>>(*static_cast<const StepParams<T> *>(p));
         return cudaGetLastError();
     }
     static cudaError_t init_d(const void *p, int g, int b, cudaStream_t s) {
-        k_init<DIM, HH, HG, S, double><<<g, b, 0, s>>>(*static_cast<const InitParams<T, double> *>(p));
+        k_init<DIM, NC, HG, S, double><<<g, b, 0, s>>>(*static_cast<const InitParams<T, double> *>(p));
         return cudaGetLastError();
     }
     static cudaError_t init_f(const void *p, int g, int b, cudaStream_t s) {
-        k_init<DIM, HH, HG, S, float><<<g, b, 0, s>>>(*static_cast<const InitParams<T, float> *>(p));
+        k_init<DIM, NC, HG, S, float><<<g, b, 0, s>>>(*static_cast<const InitParams<T, float> *>(p));
         return cudaGetLastError();
     }
     static cudaError_t moments(const void *p, int g, int b, cudaStream_t s) {
-        k_moments<DIM, HH, HG, S><<<g, b, 0, s>>>(*static_cast<const MomParams<T> *>(p));
+        k_moments<DIM, NC, HG, S><<<g, b, 0, s>>>(*static_cast<const MomParams<T> *>(p));
         return cudaGetLastError();
     }
     static cudaError_t reduce(const void *p, int g, int b, cudaStream_t s) {
-        k_reduce<DIM, HH, HG, S><<<g, b, 0, s>>>(*static_cast<const RedParams<T> *>(p));
+        k_reduce<DIM, NC, HG, S><<<g, b, 0, s>>>(*static_cast<const RedParams<T> *>(p));
         return cudaGetLastError();
     }
     template <int I>
     static cudaError_t step_bulk(const void *p, const BulkParams &bp, int g, size_t smem, cudaStream_t s) {
-        k_step_bulk<DIM, HH, HG, S, BULK_MB[I], BULK_TT[I], BULK_NS[I]><<<g, BULK_THREADS, smem, s>>>(
+        k_step_bulk<DIM, NC, HG, S, BULK_MB[I], BULK_TT[I], BULK_NS[I]><<<g, BULK_THREADS, smem, s>>>(
             *static_cast<const StepParams<T> *>(p), bp);
         return cudaGetLastError();
     }
@@ -99,14 +82,14 @@ struct Launch {
         } else {
             k.step_bulk[I] = &step_bulk<I>;
             k.step_bulk_fn[I] = reinterpret_cast<const void *>(
-                &k_step_bulk<DIM, HH, HG, S, BULK_MB[I], BULK_TT[I], BULK_NS[I]>);
+                &k_step_bulk<DIM, NC, HG, S, BULK_MB[I], BULK_TT[I], BULK_NS[I]>);
         }
     }
     static cudaError_t ring(const void *p, const BulkParams &bp, int ns, int g, size_t smem, cudaStream_t s) {
         if constexpr (std::is_same<S, double>::value) {
             return cudaErrorInvalidValue;
         } else {
-            k_step_ring<DIM, HH, HG, S, kring_npl(DIM), KRING_MINB><<<g, RING_THREADS, smem, s>>>(
+            k_step_ring<DIM, NC, HG, S, kring_npl(DIM), KRING_MINB><<<g, RING_THREADS, smem, s>>>(
                 *static_cast<const StepParams<T> *>(p), bp, ns);
             return cudaGetLastError();
         }
@@ -117,32 +100,35 @@ struct Launch {
             k.ring_fn = nullptr;
         } else {
             k.ring = &ring;
-            k.ring_fn = reinterpret_cast<const void *>(&k_step_ring<DIM, HH, HG, S, kring_npl(DIM), KRING_MINB>);
+            k.ring_fn = reinterpret_cast<const void *>(&k_step_ring<DIM, NC, HG, S, kring_npl(DIM), KRING_MINB>);
         }
     }
     static KernelSet make() {
         KernelSet k{};
-        set_ring(k);
+        // the bulk-copy and ring variants serve one concentration species at most
+        if constexpr (NC <= 1) {
+            set_ring(k);
+            set_bulk<0>(k);
+            set_bulk<1>(k);
+            set_bulk<2>(k);
+            set_bulk<3>(k);
+            set_bulk<4>(k);
+            static_assert(BULK_NCFG == 5, "one set_bulk per configuration");
+        }
         k.step[0] = &step<kstep_minb(DIM, 0)>;
         k.step[1] = &step<kstep_minb(DIM, 1)>;
         k.step[2] = &step<kstep_minb(DIM, 2)>;
         k.boundary = &boundary;
-        set_pair<0>(k);
-        set_pair<1>(k);
-        set_pair<2>(k);
+        k.unw[0] = &unw<kstep_minb(DIM, 0)>;
+        k.unw[1] = &unw<kstep_minb(DIM, 1)>;
+        k.unw[2] = &unw<kstep_minb(DIM, 2)>;
         k.init_d = &init_d;
         k.init_f = &init_f;
         k.moments = &moments;
         k.reduce = &reduce;
-        set_bulk<0>(k);
-        set_bulk<1>(k);
-        set_bulk<2>(k);
-        set_bulk<3>(k);
-        set_bulk<4>(k);
-        static_assert(BULK_NCFG == 5, "one set_bulk per configuration");
-        k.step_fn[0] = reinterpret_cast<const void *>(&k_step<DIM, HH, HG, S, kstep_minb(DIM, 0)>);
-        k.step_fn[1] = reinterpret_cast<const void *>(&k_step<DIM, HH, HG, S, kstep_minb(DIM, 1)>);
-        k.step_fn[2] = reinterpret_cast<const void *>(&k_step<DIM, HH, HG, S, kstep_minb(DIM, 2)>);
+        k.step_fn[0] = reinterpret_cast<const void *>(&k_step<DIM, NC, HG, S, kstep_minb(DIM, 0)>);
+        k.step_fn[1] = reinterpret_cast<const void *>(&k_step<DIM, NC, HG, S, kstep_minb(DIM, 1)>);
+        k.step_fn[2] = reinterpret_cast<const void *>(&k_step<DIM, NC, HG, S, kstep_minb(DIM, 2)>);
         return k;
     }
 };
@@ -156,8 +142,26 @@ KernelSet kernels_3d_f64(bool hh, bool hg);
 KernelSet kernels_3d_f32(bool hh, bool hg);
 KernelSet kernels_3d_f16(bool hh, bool hg);
 KernelSet kernels_3d_bf16(bool hh, bool hg);
+// several concentration species (nc = 2 or 3; no magnetic field)
+constexpr int MAX_COMPILED_SPECIES = 3;
+KernelSet species_2d_f64(int nc);
+KernelSet species_2d_f32(int nc);
+KernelSet species_2d_f16(int nc);
+KernelSet species_2d_bf16(int nc);
+KernelSet species_3d_f64(int nc);
+KernelSet species_3d_f32(int nc);
+KernelSet species_3d_f16(int nc);
+KernelSet species_3d_bf16(int nc);
 
 }  // namespace lbm
+
+#define LBM_DEFINE_SPECIES_SET(NAME, DIM, S)                              \
+    namespace lbm {                                                       \
+    KernelSet NAME(int nc) {                                              \
+        if (nc == 3) return Launch<DIM, 3, false, S>::make();             \
+        return Launch<DIM, 2, false, S>::make();                          \
+    }                                                                     \
+    }
 
 #define LBM_DEFINE_KERNEL_SET(NAME, DIM, S)                               \
     namespace lbm {                                                       \

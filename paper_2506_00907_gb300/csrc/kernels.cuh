@@ -67,13 +67,15 @@ struct StepParams {
     void *dst;
     const uint8_t *flags;
     const CaseDev<T> *cases;
-    const int2 *tiles;        // (case, first node) per tile of blockDim.x nodes
+    const int2 *tiles;        // (case, first node) per tile of every node (bulk-copy and ring variants)
     int32_t ntiles;
+    const int4 *spans;        // (case, lo, hi, 0): nodes [lo, hi) are bulk fluid (k_step, k_step_pair)
+    int32_t nspans;
     const BRec *brec;         // boundary nodes of all cases
     int32_t nbrec;
     const LinkDev<T> *links;
     const int32_t *tile_brec; // boundary records of tile t: [tile_brec[t], tile_brec[t + 1])
-    const uint8_t *tile_fluid; // 1 when every node of tile t is bulk fluid
+    const ReactDev<T> *react; // surface reaction network per case (kernels with several species)
 };
 
 // ------------------------------------------------------------------ equilibria
@@ -208,7 +210,7 @@ LBM_HD constexpr int lead_sign(int a) { return L::ex(a) ? L::ex(a) : (L::ey(a) ?
 // The collision over accessors: getm(q) reads plane q for the moments,
 // getr(q) reads it again for its relaxation, put(q, v) takes the relaxed
 // value.  Every plane is read by getr once, before put writes it.
-template <class PL, bool HH, bool HG, class V, class T, class GetM, class GetR, class Put>
+template <class PL, int NC, bool HG, class V, class T, class GetM, class GetR, class Put>
 LBM_DEV void collide_g(GetM &&getm, GetR &&getr, Put &&put, const CaseDev<T> &c) {
     using F = typename PL::F;
     using M = typename PL::M;
@@ -302,13 +304,15 @@ LBM_DEV void collide_g(GetM &&getm, GetR &&getr, Put &&put, const CaseDev<T> &c)
         put(am, fma_v(getr(am), omc, we - wo));
     }
     const T w0 = T(M::w(0)), w1 = T(M::w(1));
-    if constexpr (HH) {
-        const V dC = plane_sum<V>(getm, PL::H0, QM);
-        const V C = dC + V(c.ref_C);
-        const T oh = c.om_h;
-        const V ohc = V(c.omc_h);
+#pragma unroll
+    for (int sp = 0; sp < NC; ++sp) {              // every concentration species, its own tau_D and C_ref
+        const int h0 = PL::H0 + sp * QM;
+        const V dC = plane_sum<V>(getm, h0, QM);
+        const V C = dC + V(species_ref(c, sp));
+        const T oh = species_om(c, sp);
+        const V ohc = V(species_omc(c, sp));
         const V ev = V(oh * w1) * dC, f4 = V(T(4) * oh * w1) * C;
-        put(PL::H0, fma_v(getr(PL::H0), ohc, V(oh * w0) * dC));
+        put(h0, fma_v(getr(h0), ohc, V(oh * w0) * dC));
 #pragma unroll
         for (int a = 1; a < QM; ++a) {
             const int b = M::opp(a);
@@ -316,8 +320,8 @@ LBM_DEV void collide_g(GetM &&getm, GetR &&getr, Put &&put, const CaseDev<T> &c)
             const int ap = lead_sign<M>(a) > 0 ? a : b, am = lead_sign<M>(a) > 0 ? b : a;
             const int i = M::ex(a) ? 0 : (M::ey(a) ? 1 : 2);
             const V od = f4 * u[i];
-            put(PL::H0 + ap, fma_v(getr(PL::H0 + ap), ohc, ev + od));
-            put(PL::H0 + am, fma_v(getr(PL::H0 + am), ohc, ev - od));
+            put(h0 + ap, fma_v(getr(h0 + ap), ohc, ev + od));
+            put(h0 + am, fma_v(getr(h0 + am), ohc, ev - od));
         }
     }
     if constexpr (HG) {
@@ -349,23 +353,23 @@ LBM_DEV void collide_g(GetM &&getm, GetR &&getr, Put &&put, const CaseDev<T> &c)
 }
 
 // in place on a register array
-template <class PL, bool HH, bool HG, class V, class T>
+template <class PL, int NC, bool HG, class V, class T>
 LBM_DEV void collide_v(V (&p)[PL::P], const CaseDev<T> &c) {
     auto get = [&](int q) -> V { return p[q]; };
     auto put = [&](int q, V v) { p[q] = v; };
-    collide_g<PL, HH, HG, V, T>(get, get, put, c);
+    collide_g<PL, NC, HG, V, T>(get, get, put, c);
 }
 
 // one node: FP64 as is, FP32 through F1
-template <class PL, bool HH, bool HG, class T>
+template <class PL, int NC, bool HG, class T>
 LBM_DEV void collide(T (&p)[PL::P], const CaseDev<T> &c) {
     if constexpr (sizeof(T) == 8) {
-        collide_v<PL, HH, HG, T, T>(p, c);
+        collide_v<PL, NC, HG, T, T>(p, c);
     } else {
         F1 v[PL::P];
 #pragma unroll
         for (int q = 0; q < PL::P; ++q) v[q] = F1(p[q]);
-        collide_v<PL, HH, HG, F1, float>(v, c);
+        collide_v<PL, NC, HG, F1, float>(v, c);
 #pragma unroll
         for (int q = 0; q < PL::P; ++q) p[q] = v[q].v;
     }
@@ -380,8 +384,39 @@ LBM_DEV T field_sum(const S *src, int stride, int q0, int node) {
     return s;
 }
 
+// The reaction increment of a link of species i (Sec. 4.2.2, text after
+// Eq. 23): every species' C_m(X) by Eq. 13 from its own C at A and E, the
+// network's production rate R_i at them, times the link's weight (cB[0],
+// folded with the M scheme's 1/(d + 1/2) on the host).
 template <class PL, class S, class T>
-LBM_DEV T eval_link(const LinkDev<T> &L, const S *src, const CaseDev<T> &c) {
+LBM_DEV T reaction_term(const LinkDev<T> &L, const S *src, int st, const CaseDev<T> &c, const ReactDev<T> &R) {
+    constexpr int NC = PL::NCS;
+    T CX[NC];
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+        const T CA = field_sum<PL::QM, S, T>(src, st, PL::H0 + m * PL::QM, L.nodeA) + species_ref(c, m);
+        const T CE = field_sum<PL::QM, S, T>(src, st, PL::H0 + m * PL::QM, L.nodeE) + species_ref(c, m);
+        CX[m] = (T(1) + L.d) * CA - L.d * CE;
+    }
+    const int i = ((int)L.phi_plane0 - PL::H0) / PL::QM;
+    T Ri = T(0);
+#pragma unroll
+    for (int j = 0; j < MAX_REACT; ++j) {
+        if (j >= R.n) break;
+        T r = R.rate[j];
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            const uint32_t o = (R.ord[j] >> (8 * m)) & 0xffu;
+            if (o >= 1) r = r * CX[m];
+            if (o >= 2) r = r * CX[m];
+        }
+        Ri = Ri + R.st[j][i] * r;
+    }
+    return L.cB[0] * Ri;
+}
+
+template <class PL, class S, class T>
+LBM_DEV T eval_link(const LinkDev<T> &L, const S *src, const CaseDev<T> &c, const ReactDev<T> *react) {
     const int st = (int)c.stride;
     const T paA = Codec<S>::ld(src + ((int)L.plane_a * st + L.nodeA));
     const T papA = Codec<S>::ld(src + ((int)L.plane_ap * st + L.nodeA));
@@ -427,6 +462,9 @@ LBM_DEV T eval_link(const LinkDev<T> &L, const S *src, const CaseDev<T> &c) {
         }
         v += L.cphi * (T(4.5) * eu * eu - T(1.5) * uu);
     }
+    if constexpr (PL::NCS >= 2) {
+        if (L.flags & LINK_NEED_REACT) v += reaction_term<PL, S, T>(L, src, st, c, *react);
+    }
     if constexpr (PL::G0 < PL::P) {
         if (L.flags & LINK_NEED_B) {
 #pragma unroll
@@ -454,7 +492,8 @@ LBM_DEV void apply_links(T (&p)[PL::P], const StepParams<T> &prm, const CaseDev<
         for (int j = 0; j < LCH; ++j)
             if (base + j < hi) L[j] = prm.links[base + j];
 #pragma unroll
-        for (int j = 0; j < LCH; ++j) v[j] = base + j < hi ? eval_link<PL, S, T>(L[j], src, c) : T(0);
+        for (int j = 0; j < LCH; ++j)
+            v[j] = base + j < hi ? eval_link<PL, S, T>(L[j], src, c, PL::NCS >= 2 ? prm.react + c.index : nullptr) : T(0);
 #pragma unroll
         for (int j = 0; j < LCH; ++j) {
             if (base + j >= hi) break;
@@ -499,10 +538,10 @@ template <> struct Pack16<__nv_bfloat16> {
 // ------------------------------------------------------------------ fused step
 // One node: pull, (boundary nodes: wall links [lo, hi)), collide, store
 // plane q to out[q * ostride] (out = 0: the node's entries of the target buffer).
-template <int DIM, bool HH, bool HG, class S, bool LINKS, int LCH = 4>
+template <int DIM, int NC, bool HG, class S, bool LINKS, int LCH = 4>
 LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDev<typename Codec<S>::T> &c, int n,
                        int lo, int hi, S *out = nullptr, int ostride = 0) {
-    using PL = Planes<DIM, HH, HG>;
+    using PL = Planes<DIM, NC, HG>;
     using T = typename Codec<S>::T;
     constexpr int P = PL::P;
     const S *src = static_cast<const S *>(prm.src) + c.pop_off;
@@ -549,7 +588,7 @@ LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDe
             return F1(Pack16<S>::get(w, q & 1));
         };
         auto put = [&](int q, F1 v) { Codec<S>::st(dp + q * os, v.v); };
-        collide_g<PL, HH, HG, F1, float>(getm, getr, put, c);
+        collide_g<PL, NC, HG, F1, float>(getm, getr, put, c);
         return;
     }
     T p[P];
@@ -557,128 +596,135 @@ LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDe
     for (int q = 0; q < P; ++q)
         p[q] = Codec<S>::ld(sp + (q * st32 + ox[1 - PL::ex(q)] + oy[1 - PL::ey(q)] + oz[1 - PL::ez(q)]));
     if constexpr (LINKS) apply_links<PL, S, T, LCH>(p, prm, c, src, lo, hi);
-    collide<PL, HH, HG, T>(p, c);
+    collide<PL, NC, HG, T>(p, c);
 #pragma unroll
     for (int q = 0; q < P; ++q) Codec<S>::st(dp + q * os, p[q]);
 }
 
-// Bulk nodes (fluid, no wall link).  Tiles of blockDim.x * npt nodes; each
-// thread takes nodes tid, tid + blockDim.x, ...  The next tile's record is
-// fetched one tile ahead.  Boundary nodes are left to k_boundary.
+// Bulk nodes (fluid, no wall link) over the span list: span t holds nodes
+// [lo, hi) of one case, all bulk fluid, at most blockDim.x * npt of them; each
+// thread takes nodes lo + tid, lo + tid + blockDim.x, ...  No node flag is
+// read: solid and wall-link nodes are in no span (k_boundary relaxes the
+// latter).
 // MINB: resident 256-thread blocks per SM the kernel is compiled for (its
 // register budget, 65536 / (256 MINB) registers per thread).
-template <int DIM, bool HH, bool HG, class S, int MINB>
+template <int DIM, int NC, bool HG, class S, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_step(const StepParams<typename Codec<S>::T> prm, const int npt) {
     using T = typename Codec<S>::T;
-    int t = blockIdx.x;
-    if (t >= prm.ntiles) return;
-    int2 tile = prm.tiles[t];
-    for (; t < prm.ntiles; t += gridDim.x) {
-        const int tn = t + gridDim.x;
-        const int2 next = tn < prm.ntiles ? prm.tiles[tn] : tile;
+    for (int t = blockIdx.x; t < prm.nspans; t += gridDim.x) {
+        const int4 sp = prm.spans[t];
         // the descriptor by value: the stores below cannot alias it, so it stays in registers
-        const CaseDev<T> c = prm.cases[tile.x];
-        // in a tile of bulk fluid only the pulls need not wait for a flag load;
-        // elsewhere the flags of all npt nodes are fetched together (byte k of fw)
-        const bool all_fluid = prm.tile_fluid[t] != 0;
-        uint64_t fw = 0;
-        if (!all_fluid)
-            for (int k = 0; k < npt; ++k) {
-                const int n = tile.y + (int)threadIdx.x + k * (int)blockDim.x;
-                if (n < c.N) fw |= (uint64_t)prm.flags[c.node_off + n] << (8 * k);
-            }
+        const CaseDev<T> c = prm.cases[sp.x];
         for (int k = 0; k < npt; ++k) {
-            const int n = tile.y + (int)threadIdx.x + k * (int)blockDim.x;
-            if (n >= c.N) break;
-            if (all_fluid || ((fw >> (8 * k)) & 0xffu) == NODE_FLUID) step_node<DIM, HH, HG, S, false>(prm, c, n, 0, 0);
+            const int n = sp.y + (int)threadIdx.x + k * (int)blockDim.x;
+            if (n >= sp.z) break;
+            step_node<DIM, NC, HG, S, false>(prm, c, n, 0, 0);
         }
-        tile = next;
     }
 }
 
-// ------------------------------------------------------------------ paired nodes (16-bit storage)
-// Two 16-bit populations of x-adjacent nodes n0 (even) and n0 + 1 share a
-// 32-bit word: planes whose pull offset is even are read as one word, the
-// others as two 16-bit loads, and every result plane is written as one word.
-template <class S> struct Pair16;
-template <> struct Pair16<__half> {
-    LBM_DEV static float2 ld(const __half *p) { return __half22float2(__ldg(reinterpret_cast<const __half2 *>(p))); }
-    LBM_DEV static void st(__half *p, float2 v) { *reinterpret_cast<__half2 *>(p) = __float22half2_rn(v); }
+// ------------------------------------------------------------------ unwrapped pulls (launch variant 2)
+// One bulk node n: every plane's pull is read unwrapped, at n - s_q with s_q
+// the flat offset of e_q, so that a plane's address is the node's own plus a
+// per-case constant (q * stride - s_q); the pool's guard bands keep these
+// reads inside the allocation.  A node on a periodic edge of its case then
+// reloads the planes whose source wraps (a short branch taken by those lanes
+// only).  16-bit populations stay packed two to a register until the
+// collision reads them (once for the moments, once for the relaxation).  Same
+// arithmetic as step_node: the bits are those of k_step.
+template <class S> struct Raw16 {
+    LBM_DEV static uint32_t ld(const S *p) { return __ldg(reinterpret_cast<const unsigned short *>(p)); }
+    LBM_DEV static float get(uint32_t w, int hi);
 };
-template <> struct Pair16<__nv_bfloat16> {
-    LBM_DEV static float2 ld(const __nv_bfloat16 *p) {
-        return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162 *>(p)));
-    }
-    LBM_DEV static void st(__nv_bfloat16 *p, float2 v) {
-        *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(v);
-    }
-};
+template <> LBM_DEV float Raw16<__half>::get(uint32_t w, int hi) {
+    __half2 h;
+    memcpy(&h, &w, 4);
+    return hi ? __high2float(h) : __low2float(h);
+}
+template <> LBM_DEV float Raw16<__nv_bfloat16>::get(uint32_t w, int hi) {
+    return __uint_as_float(hi ? (w & 0xffff0000u) : (w << 16));
+}
 
-// Nodes n0, n0 + 1 of one row, neither on a periodic edge (no wrap), both
-// bulk fluid.  PX = nx mod 2, PXY = nx ny mod 2 make the parity of each
-// plane's pull offset a compile-time fact.
-template <int DIM, bool HH, bool HG, class S, int PX, int PXY>
-LBM_DEV void pair_node(const CaseDev<float> &c, const S *src, S *dst, int n0) {
-    using PL = Planes<DIM, HH, HG>;
+template <int DIM, int NC, bool HG, class S>
+LBM_DEV void step_node_unwrapped(const StepParams<typename Codec<S>::T> &prm, const CaseDev<typename Codec<S>::T> &c,
+                                 const int n) {
+    using PL = Planes<DIM, NC, HG>;
+    using T = typename Codec<S>::T;
     constexpr int P = PL::P;
-    const int nx = c.nx, nxy = c.nx * c.ny;
-    const int st32 = (int)c.stride;
-    const S *__restrict__ sp = src + n0;
-    S *__restrict__ dp = dst + n0;
-    F2 v[P];
+    constexpr bool PACK = sizeof(S) == 2;
+    const S *__restrict__ src = static_cast<const S *>(prm.src) + c.pop_off;
+    S *__restrict__ dp = static_cast<S *>(prm.dst) + c.pop_off + n;
+    const int nx = c.nx, ny = c.ny, nxy = nx * ny;
+    const int st = (int)c.stride;
+    const S *__restrict__ sp = src + n;
+    // raw pulls: 16-bit values two to a 32-bit word (plane q in half q & 1 of
+    // word q >> 1), wider types as they are
+    uint32_t pk[PACK ? (P + 1) / 2 : 1];
+    T p[PACK ? 1 : P];
 #pragma unroll
     for (int q = 0; q < P; ++q) {
-        const int off = q * st32 - (PL::ex(q) + PL::ey(q) * nx + PL::ez(q) * nxy);
-        const int par = (PL::ex(q) + PL::ey(q) * PX + PL::ez(q) * PXY) & 1;
-        if (par == 0) {
-            const float2 w = Pair16<S>::ld(sp + off);
-            v[q] = F2(w.x, w.y);
+        const int o = q * st - (PL::ex(q) + PL::ey(q) * nx + PL::ez(q) * nxy);
+        if constexpr (PACK) {
+            const uint32_t w = Raw16<S>::ld(sp + o);
+            pk[q >> 1] = (q & 1) ? (pk[q >> 1] | (w << 16)) : w;
         } else {
-            v[q] = F2(Codec<S>::ld(sp + off), Codec<S>::ld(sp + off + 1));
+            p[q] = Codec<S>::ld(sp + o);
         }
     }
-    collide_v<PL, HH, HG, F2, float>(v, c);
+    int x, y, z, r;
+    coords<DIM, T>(c, n, x, y, z, r);
+    const int nz = c.nz;
+    if (x == 0 || x == nx - 1 || y == 0 || y == ny - 1 || (DIM == 3 && (z == 0 || z == nz - 1))) {
+        const int N = c.N;
 #pragma unroll
-    for (int q = 0; q < P; ++q) Pair16<S>::st(dp + q * st32, v[q].v);
-}
-
-// Bulk nodes in pairs (16-bit storage).  Tiles of blockDim.x * npt nodes (npt
-// even); each thread takes the pairs tid, tid + blockDim.x, ...  Pairs that
-// touch a periodic edge, a solid or a boundary node take the one-node path.
-template <int DIM, bool HH, bool HG, class S, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_step_pair(const StepParams<float> prm, const int npt) {
-    int t = blockIdx.x;
-    if (t >= prm.ntiles) return;
-    int2 tile = prm.tiles[t];
-    for (; t < prm.ntiles; t += gridDim.x) {
-        const int tn = t + gridDim.x;
-        const int2 next = tn < prm.ntiles ? prm.tiles[tn] : tile;
-        const CaseDev<float> c = prm.cases[tile.x];
-        const S *src = static_cast<const S *>(prm.src) + c.pop_off;
-        S *dst = static_cast<S *>(prm.dst) + c.pop_off;
-        const int px = c.nx & 1, pxy = (c.nx * c.ny) & 1;
-        for (int k = 0; k < npt / 2; ++k) {
-            const int n0 = tile.y + 2 * ((int)threadIdx.x + k * (int)blockDim.x);
-            if (n0 >= c.N) break;
-            const uint8_t f0 = prm.flags[c.node_off + n0];
-            const uint8_t f1 = n0 + 1 < c.N ? prm.flags[c.node_off + n0 + 1] : uint8_t(0);
-            int x, y, z, r;
-            coords<DIM, float>(c, n0, x, y, z, r);
-            const bool interior = x >= 1 && x + 2 <= c.nx - 1 && y >= 1 && y + 1 <= c.ny - 1 &&
-                                  (DIM == 2 || (z >= 1 && z + 1 <= c.nz - 1));
-            if (f0 == NODE_FLUID && f1 == NODE_FLUID && interior) {
-                if (!px)
-                    pair_node<DIM, HH, HG, S, 0, 0>(c, src, dst, n0);
-                else if (DIM == 2 || !pxy)
-                    pair_node<DIM, HH, HG, S, 1, 0>(c, src, dst, n0);
-                else
-                    pair_node<DIM, HH, HG, S, 1, 1>(c, src, dst, n0);
-            } else {
-                if (f0 == NODE_FLUID) step_node<DIM, HH, HG, S, false>(prm, c, n0, 0, 0);
-                if (f1 == NODE_FLUID) step_node<DIM, HH, HG, S, false>(prm, c, n0 + 1, 0, 0);
+        for (int q = 0; q < P; ++q) {
+            int corr = 0;
+            if (PL::ex(q) > 0 && x == 0) corr += nx;
+            if (PL::ex(q) < 0 && x == nx - 1) corr -= nx;
+            if (PL::ey(q) > 0 && y == 0) corr += nxy;
+            if (PL::ey(q) < 0 && y == ny - 1) corr -= nxy;
+            if (DIM == 3 && PL::ez(q) > 0 && z == 0) corr += N;
+            if (DIM == 3 && PL::ez(q) < 0 && z == nz - 1) corr -= N;
+            if (corr != 0) {
+                const int o = q * st - (PL::ex(q) + PL::ey(q) * nx + PL::ez(q) * nxy) + corr;
+                if constexpr (PACK) {
+                    const uint32_t w = Raw16<S>::ld(sp + o);
+                    pk[q >> 1] = (q & 1) ? ((pk[q >> 1] & 0x0000ffffu) | (w << 16)) : ((pk[q >> 1] & 0xffff0000u) | w);
+                } else {
+                    p[q] = Codec<S>::ld(sp + o);
+                }
             }
         }
-        tile = next;
+    }
+    if constexpr (PACK) {
+        auto getm = [&](int q) -> F1 { return F1(Raw16<S>::get(pk[q >> 1], q & 1)); };
+        auto getr = [&](int q) -> F1 {
+            uint32_t w = pk[q >> 1];
+            asm("" : "+r"(w));                 // convert again rather than keep the moments' copy alive
+            return F1(Raw16<S>::get(w, q & 1));
+        };
+        auto put = [&](int q, F1 v) { Codec<S>::st(dp + q * st, v.v); };
+        collide_g<PL, NC, HG, F1, float>(getm, getr, put, c);
+    } else {
+        collide<PL, NC, HG, T>(p, c);
+#pragma unroll
+        for (int q = 0; q < P; ++q) Codec<S>::st(dp + q * st, p[q]);
+    }
+}
+
+// Bulk nodes over the span list with unwrapped pulls (launch variant 2):
+// the same node order and tiling as k_step.
+template <int DIM, int NC, bool HG, class S, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_step_unwrapped(const StepParams<typename Codec<S>::T> prm, const int npt) {
+    using T = typename Codec<S>::T;
+    for (int t = blockIdx.x; t < prm.nspans; t += gridDim.x) {
+        const int4 spn = prm.spans[t];
+        const CaseDev<T> c = prm.cases[spn.x];
+        for (int k = 0; k < npt; ++k) {
+            const int n = spn.y + (int)threadIdx.x + k * (int)blockDim.x;
+            if (n >= spn.z) break;
+            step_node_unwrapped<DIM, NC, HG, S>(prm, c, n);
+        }
     }
 }
 
@@ -692,14 +738,14 @@ __global__ void __launch_bounds__(256, MINB) k_step_pair(const StepParams<float>
 // (Measured on GB300: Hartmann batch, MHD pipe FP32 and FP16.)
 template <class S, int DIM>
 LBM_HD constexpr bool boundary_lean() { return sizeof(S) == 2 || (DIM == 2 && sizeof(S) == 4); }
-template <int DIM, bool HH, bool HG, class S>
+template <int DIM, int NC, bool HG, class S>
 __global__ void __launch_bounds__(128, boundary_lean<S, DIM>() ? (DIM == 2 ? 8 : 6) : 1)
     k_boundary(const StepParams<typename Codec<S>::T> prm) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= prm.nbrec) return;
     const BRec b = prm.brec[i];
     const CaseDev<typename Codec<S>::T> c = prm.cases[b.cs];
-    step_node<DIM, HH, HG, S, true, boundary_lean<S, DIM>() ? 1 : 4>(prm, c, b.node, b.lo, b.hi);
+    step_node<DIM, NC, HG, S, true, boundary_lean<S, DIM>() ? 1 : 4>(prm, c, b.node, b.lo, b.hi);
 }
 
 // ------------------------------------------------------------------ initial state
@@ -714,11 +760,12 @@ struct InitParams {
     int32_t case_id;
     const FT *rho, *u, *C, *B;
     T rho0, C0, B0[3];
+    T C0s[MAX_SPECIES];       // initial C of every species (species 0: C0 unless the field C is given)
 };
 
-template <int DIM, bool HH, bool HG, class S, class FT>
+template <int DIM, int NC, bool HG, class S, class FT>
 __global__ void __launch_bounds__(256) k_init(const InitParams<typename Codec<S>::T, FT> ip) {
-    using PL = Planes<DIM, HH, HG>;
+    using PL = Planes<DIM, NC, HG>;
     using F = typename PL::F;
     using M = typename PL::M;
     using T = typename Codec<S>::T;
@@ -746,9 +793,11 @@ __global__ void __launch_bounds__(256) k_init(const InitParams<typename Codec<S>
     const T drho = rho - c.ref_rho;
 #pragma unroll
     for (int a = 0; a < PL::QF; ++a) p[a] = feq_dir<F, HG, T>(a, drho, rho, u, usq15, B, mag);
-    if constexpr (HH) {
 #pragma unroll
-        for (int a = 0; a < PL::QM; ++a) p[PL::H0 + a] = heq_dir<M, T>(a, C - c.ref_C, C, u);
+    for (int sp = 0; sp < NC; ++sp) {
+        const T Cs = sp == 0 ? C : ip.C0s[sp];
+#pragma unroll
+        for (int a = 0; a < PL::QM; ++a) p[PL::H0 + sp * PL::QM + a] = heq_dir<M, T>(a, Cs - species_ref(c, sp), Cs, u);
     }
     if constexpr (HG) {
 #pragma unroll
@@ -756,7 +805,7 @@ __global__ void __launch_bounds__(256) k_init(const InitParams<typename Codec<S>
 #pragma unroll
             for (int a = 0; a < PL::QM; ++a) p[PL::G0 + k * PL::QM + a] = geq_dir<M, T>(a, k, B[k] - c.ref_B[k], B, u);
     }
-    collide<PL, HH, HG, T>(p, c);
+    collide<PL, NC, HG, T>(p, c);
 #pragma unroll
     for (int q = 0; q < P; ++q) Codec<S>::st(dst + (q * st32 + n), p[q]);
 }

@@ -142,10 +142,10 @@ LBM_DEV void bulk_issue(const StepParams<T> &prm, int t, int st, unsigned char *
     }
 }
 
-template <int DIM, bool HH, bool HG, class S, int MINB, int TT, int NS>
+template <int DIM, int NC, bool HG, class S, int MINB, int TT, int NS>
 __global__ void __launch_bounds__(BULK_THREADS, MINB) k_step_bulk(const StepParams<typename Codec<S>::T> prm,
                                                                   const BulkParams bp) {
-    using PL = Planes<DIM, HH, HG>;
+    using PL = Planes<DIM, NC, HG>;
     using T = typename Codec<S>::T;
     constexpr int P = PL::P;
     using L = BulkLayout<P, TT, (int)sizeof(S), NS>;
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(BULK_THREADS, MINB) k_step_bulk(const StepPara
                                : Codec<S>::ld(src + (q * st32 + sn));
                 }
             }
-            collide<PL, HH, HG, T>(p, c);
+            collide<PL, NC, HG, T>(p, c);
 #pragma unroll
             for (int q = 0; q < P; ++q) Codec<S>::st(out + q * TT + i, p[q]);
         }
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(BULK_THREADS, MINB) k_step_bulk(const StepPara
         const int b_lo = prm.tile_brec[t], b_hi = prm.tile_brec[t + 1];
         for (int b = b_lo + tid; b < b_hi; b += BULK_THREADS) {
             const BRec rec = prm.brec[b];
-            step_node<DIM, HH, HG, S, true, 1>(prm, c, rec.node, rec.lo, rec.hi, out + (rec.node - tile.y), TT);
+            step_node<DIM, NC, HG, S, true, 1>(prm, c, rec.node, rec.lo, rec.hi, out + (rec.node - tile.y), TT);
         }
         // a ragged last tile stores up to the next 16 bytes: zeros there, inside the plane's padding
         const int lenA = ((len + A - 1) / A) * A;

@@ -48,8 +48,8 @@ constexpr int RING_ABORT = 16 * RING_MAX_NS;
 constexpr int RING_META = 256;
 constexpr int RM_TILE = 0;                         // int2
 constexpr int RM_CASE = 16;                        // CaseDev<float>
-constexpr int RM_SHIFT = 160;                      // int[RING_MAX_QF]: window index of the tile's first pull source
-constexpr int RM_FLAGS = 256;                      // uint8_t[tile nodes, rounded up to 16]
+constexpr int RM_SHIFT = 208;                      // int[RING_MAX_QF]: window index of the tile's first pull source
+constexpr int RM_FLAGS = 288;                      // uint8_t[tile nodes, rounded up to 16]
 __host__ __device__ constexpr int ring_meta_bytes(int npl) { return ((RM_FLAGS + ring_tile(npl) + 127) / 128) * 128; }
 __host__ __device__ constexpr int ring_win_off(int npl, int ns) { return RING_META + ns * ring_meta_bytes(npl); }
 __host__ __device__ constexpr int ring_smem_bytes(int P, int npl, int elem, int ns) {
@@ -210,10 +210,10 @@ LBM_DEV void ring_load_one(float (&p)[PL::P], const S *win, const int *shift, in
     for (int q = 0; q < PL::P; ++q) p[q] = Codec<S>::ld_shared(win + q * CAP + shift[flow_dir<PL>(q)] + local);
 }
 
-template <int DIM, bool HH, bool HG, class S, int NPL, int MINB>
+template <int DIM, int NC, bool HG, class S, int NPL, int MINB>
 __global__ void __launch_bounds__(RING_THREADS, MINB) k_step_ring(const StepParams<float> prm, const BulkParams bp,
                                                                   const int ns) {
-    using PL = Planes<DIM, HH, HG>;
+    using PL = Planes<DIM, NC, HG>;
     constexpr int P = PL::P;
     constexpr int CAP = ring_cap(NPL, (int)sizeof(S));
     static_assert(PL::QF <= RING_MAX_QF, "window shifts");
@@ -333,13 +333,13 @@ __global__ void __launch_bounds__(RING_THREADS, MINB) k_step_ring(const StepPara
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[st]);
             if (fast) {
-                collide_v<PL, HH, HG, F2, float>(v, c);
+                collide_v<PL, NC, HG, F2, float>(v, c);
                 S *__restrict__ dp = dst + n0;
 #pragma unroll
                 for (int q = 0; q < P; ++q) PairMem<S>::st(dp + q * st32, v[q].v);
             } else {
-                if (f0 == NODE_FLUID) step_node<DIM, HH, HG, S, false>(prm, c, n0, 0, 0);
-                if (f1 == NODE_FLUID) step_node<DIM, HH, HG, S, false>(prm, c, n0 + 1, 0, 0);
+                if (f0 == NODE_FLUID) step_node<DIM, NC, HG, S, false>(prm, c, n0, 0, 0);
+                if (f1 == NODE_FLUID) step_node<DIM, NC, HG, S, false>(prm, c, n0 + 1, 0, 0);
             }
         } else {
             float p[P];
@@ -347,12 +347,12 @@ __global__ void __launch_bounds__(RING_THREADS, MINB) k_step_ring(const StepPara
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[st]);
             if (fast) {
-                collide<PL, HH, HG, float>(p, c);
+                collide<PL, NC, HG, float>(p, c);
                 S *__restrict__ dp = dst + n0;
 #pragma unroll
                 for (int q = 0; q < P; ++q) Codec<S>::st(dp + q * st32, p[q]);
             } else if (f0 == NODE_FLUID) {
-                step_node<DIM, HH, HG, S, false>(prm, c, n0, 0, 0);
+                step_node<DIM, NC, HG, S, false>(prm, c, n0, 0, 0);
             }
         }
     }

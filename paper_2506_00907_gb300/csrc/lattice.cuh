@@ -69,23 +69,21 @@ struct D3Q7 {
     LBM_HD static constexpr int opp(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
 };
 
-// The concatenated population planes of one node: f (QF planes), then h (QM,
-// if CD), then g_0 .. g_{DIM-1} (QM each, if MHD).
-template <int DIM, bool HH, bool HG>
+// The concatenated population planes of one node: f (QF planes), then the
+// NC concentration species h_0 .. h_{NC-1} (QM each), then g_0 .. g_{DIM-1}
+// (QM each, if MHD).
+template <int DIM, int NC, bool HG>
 struct Planes {
     using F = typename std::conditional<DIM == 2, D2Q9, D3Q19>::type;
     using M = typename std::conditional<DIM == 2, D2Q5, D3Q7>::type;
     static constexpr int QF = F::Q;
     static constexpr int QM = M::Q;
     static constexpr int NB = DIM;
+    static constexpr int NCS = NC;       // concentration species
     static constexpr int H0 = QF;
-    static constexpr int G0 = QF + (HH ? QM : 0);
+    static constexpr int G0 = QF + NC * QM;
     static constexpr int P = G0 + (HG ? NB * QM : 0);
-    // field of plane q: 0 f, 1 h, 2 + k g_k
-    LBM_HD static constexpr int field(int q) {
-        return q < QF ? 0 : (q < G0 ? 1 : 2 + (q - G0) / QM);
-    }
-    LBM_HD static constexpr int dir(int q) { return q < QF ? q : (q < G0 ? q - H0 : (q - G0) % QM); }
+    LBM_HD static constexpr int dir(int q) { return q < QF ? q : (q < G0 ? (q - H0) % QM : (q - G0) % QM); }
     LBM_HD static constexpr int ex(int q) { return q < QF ? F::ex(q) : M::ex(dir(q)); }
     LBM_HD static constexpr int ey(int q) { return q < QF ? F::ey(q) : M::ey(dir(q)); }
     LBM_HD static constexpr int ez(int q) { return q < QF ? F::ez(q) : M::ez(dir(q)); }

@@ -8,17 +8,19 @@
 // Per node the reduction forms, in the arithmetic precision T of the step,
 // rho, C, B, a non-finite count and the residual terms
 //   r2 = |phi - phi_prev|^2,  p2 = |phi|^2,  phi = (u, C, B - B0)
-// (only the components the lattice and physics can make nonzero); sums over
-// nodes are FP64.  phi_prev is kept node by node in the snapshot buffer,
+// (only the components the lattice and physics can make nonzero; with
+// several concentration species, which exclude the magnetic field, phi =
+// (u, C_0, C_1, ..)); sums over nodes are FP64.  phi_prev is kept node by node in the snapshot buffer,
 // stored in T (FP64 storage: double, otherwise float), and is replaced by phi.
 #pragma once
 #include "kernels.cuh"
 
 namespace lbm {
 
+// C[k]: species k (k < PL::NCS; the rest 0)
 template <class PL, class S, class T>
 LBM_DEV void node_moments(const S *src, int64_t stride, int n, const CaseDev<T> &c,
-                          T &rho, T (&u)[3], T &C, T (&B)[3], int &nonfinite) {
+                          T &rho, T (&u)[3], T (&C)[MAX_SPECIES], T (&B)[3], int &nonfinite) {
     using F = typename PL::F;
     T drho = 0;
     T j[3] = {T(0), T(0), T(0)};
@@ -36,17 +38,19 @@ LBM_DEV void node_moments(const S *src, int64_t stride, int n, const CaseDev<T> 
     u[0] = (j[0] - T(0.5) * rho * c.ax) / rho;
     u[1] = (j[1] - T(0.5) * rho * c.ay) / rho;
     u[2] = F::DIM == 3 ? (j[2] - T(0.5) * rho * c.az) / rho : T(0);
-    C = 0;
     B[0] = B[1] = B[2] = T(0);
-    if constexpr (PL::G0 > PL::H0) {
+#pragma unroll
+    for (int k = 0; k < MAX_SPECIES; ++k) {
+        C[k] = T(0);
+        if (k >= PL::NCS) continue;
         T s = 0;
 #pragma unroll
         for (int a = 0; a < PL::QM; ++a) {
-            const T v = Codec<S>::ld(src + (int64_t)(PL::H0 + a) * stride + n);
+            const T v = Codec<S>::ld(src + (int64_t)(PL::H0 + k * PL::QM + a) * stride + n);
             nonfinite += !isfinite(v);
             s += v;
         }
-        C = s + c.ref_C;
+        C[k] = s + species_ref(c, k);
     }
     if constexpr (PL::P > PL::G0) {
 #pragma unroll
@@ -71,11 +75,12 @@ struct MomParams {
     const CaseDev<T> *cases;
     int32_t case_id;
     double *rho, *u, *C, *B;  // case-relative device outputs (u, B as [N][3])
+    int32_t species;          // the species C reports
 };
 
-template <int DIM, bool HH, bool HG, class S>
+template <int DIM, int NC, bool HG, class S>
 __global__ void __launch_bounds__(256) k_moments(const MomParams<typename Codec<S>::T> mp) {
-    using PL = Planes<DIM, HH, HG>;
+    using PL = Planes<DIM, NC, HG>;
     using T = typename Codec<S>::T;
     const CaseDev<T> &c = mp.cases[mp.case_id];
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -86,11 +91,11 @@ __global__ void __launch_bounds__(256) k_moments(const MomParams<typename Codec<
         for (int k = 0; k < 3; ++k) { mp.u[3 * n + k] = 0; mp.B[3 * n + k] = 0; }
         return;
     }
-    T rho, u[3], C, B[3];
+    T rho, u[3], C[MAX_SPECIES], B[3];
     int nf;
     node_moments<PL, S, T>(static_cast<const S *>(mp.src) + c.pop_off, c.stride, n, c, rho, u, C, B, nf);
     mp.rho[n] = (double)rho;
-    mp.C[n] = HH ? (double)C : 0.0;
+    mp.C[n] = mp.species < NC ? (double)C[mp.species & (MAX_SPECIES - 1)] : 0.0;
     for (int k = 0; k < 3; ++k) { mp.u[3 * n + k] = (double)u[k]; mp.B[3 * n + k] = HG ? (double)B[k] : 0.0; }
 }
 
@@ -100,19 +105,21 @@ __global__ void __launch_bounds__(256) k_moments(const MomParams<typename Codec<
 constexpr int RED_Q = 8;
 constexpr int SNAP_Q = 7;
 
-// Snapshot components that can be nonzero: u (DIM components), C, B - B0 (DIM).
+// Snapshot components that can be nonzero: u (DIM components), C_0, then
+// B - B0 (DIM) or the further species C_1 .. C_{NC-1}.
 template <class PL>
 LBM_HD constexpr bool snap_used(int k) {
     constexpr int D = PL::F::DIM;
-    constexpr bool hh = PL::G0 > PL::H0, hg = PL::P > PL::G0;
-    return k < 3 ? k < D : (k == 3 ? hh : (hg && k - 4 < D));
+    constexpr int nc = PL::NCS;
+    constexpr bool hg = PL::P > PL::G0;
+    return k < 3 ? k < D : (k == 3 ? nc >= 1 : (hg ? k - 4 < D : k - 4 < nc - 1));
 }
 
 // The context keeps phi_prev node by node: the used components packed into
 // snap_width entries (4 or 8, so that a node's entries are one or two
 // 16-byte vectors in FP32).
-LBM_HD constexpr int snap_width(int dim, bool hh, bool hg) {
-    return dim + (hh ? 1 : 0) + (hg ? dim : 0) <= 4 ? 4 : 8;
+LBM_HD constexpr int snap_width(int dim, int nc, bool hg) {
+    return dim + nc + (hg ? dim : 0) <= 4 ? 4 : 8;
 }
 template <class PL>
 LBM_HD constexpr int snap_slot(int k) {
@@ -123,17 +130,23 @@ LBM_HD constexpr int snap_slot(int k) {
 
 // Moments and phi = (u, C, B - B0) of node n.
 template <class PL, class S, class T>
-LBM_DEV void node_phi(const S *src, int64_t stride, int n, const CaseDev<T> &c, T &rho, T &C, T (&B)[3], int &nf,
-                      T (&phi)[SNAP_Q]) {
+LBM_DEV void node_phi(const S *src, int64_t stride, int n, const CaseDev<T> &c, T &rho, T (&C)[MAX_SPECIES],
+                      T (&B)[3], int &nf, T (&phi)[SNAP_Q]) {
     T u[3];
     node_moments<PL, S, T>(src, stride, n, c, rho, u, C, B, nf);
     phi[0] = u[0];
     phi[1] = u[1];
     phi[2] = u[2];
-    phi[3] = C;
-    phi[4] = B[0] - c.B0[0];
-    phi[5] = B[1] - c.B0[1];
-    phi[6] = B[2] - c.B0[2];
+    phi[3] = C[0];
+    if constexpr (PL::P > PL::G0) {
+        phi[4] = B[0] - c.B0[0];
+        phi[5] = B[1] - c.B0[1];
+        phi[6] = B[2] - c.B0[2];
+    } else {
+        phi[4] = C[1];
+        phi[5] = C[2];
+        phi[6] = C[3];
+    }
 }
 
 // Residual terms r2 = |phi - phi_prev|^2 and p2 = |phi|^2 over the used components.
@@ -154,7 +167,7 @@ LBM_DEV void resid_terms(const T (&phi)[SNAP_Q], const T (&old)[SNAP_Q], T &r2, 
 // accesses; p is aligned to the node's entries).
 template <class PL, class SnapT, class T>
 LBM_DEV void snap_exchange(SnapT *p, const T (&phi)[SNAP_Q], T (&old)[SNAP_Q]) {
-    constexpr int W = snap_width(PL::F::DIM, PL::G0 > PL::H0, PL::P > PL::G0);
+    constexpr int W = snap_width(PL::F::DIM, PL::NCS, PL::P > PL::G0);
     SnapT v[W];
     if constexpr (sizeof(SnapT) == 4) {
 #pragma unroll
@@ -237,15 +250,20 @@ struct RecAcc<float> {
 };
 
 // Adds the node terms to the record (non-finite count kept as an int).
+// Slots 2-4 hold sum B_k, or, with several species (no field), sum C_1..C_3.
 template <class PL, class T>
-LBM_DEV void add_terms(RecAcc<T> &acc, int &nfc, T rho, T C, const T (&B)[3], int nf, T r2, T p2) {
+LBM_DEV void add_terms(RecAcc<T> &acc, int &nfc, T rho, const T (&C)[MAX_SPECIES], const T (&B)[3], int nf, T r2,
+                       T p2) {
     constexpr int D = PL::F::DIM;
     acc.add(0, rho);
-    if constexpr (PL::G0 > PL::H0) acc.add(1, C);
+    if constexpr (PL::NCS >= 1) acc.add(1, C[0]);
     if constexpr (PL::P > PL::G0) {
         acc.add(2, B[0]);
         acc.add(3, B[1]);
         if constexpr (D == 3) acc.add(4, B[2]);
+    } else {
+#pragma unroll
+        for (int k = 1; k < PL::NCS; ++k) acc.add(1 + k, C[k]);
     }
     nfc += nf;
     acc.add(6, r2);
@@ -290,9 +308,9 @@ template <class T>
 using SnapOf = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
 
 // One block per tile: partial record of the tile's fluid nodes.
-template <int DIM, bool HH, bool HG, class S>
+template <int DIM, int NC, bool HG, class S>
 __global__ void __launch_bounds__(256) k_reduce(const RedParams<typename Codec<S>::T> rp) {
-    using PL = Planes<DIM, HH, HG>;
+    using PL = Planes<DIM, NC, HG>;
     using T = typename Codec<S>::T;
     using SnapT = SnapOf<T>;
     __shared__ double sh[RED_Q][32];
@@ -305,10 +323,10 @@ __global__ void __launch_bounds__(256) k_reduce(const RedParams<typename Codec<S
     for (int i = threadIdx.x; i < rp.tile_nodes; i += blockDim.x) {
         const int n = tile.y + i;
         if (n >= c.N || !(rp.flags[c.node_off + n] & NODE_FLUID)) continue;
-        T rho, C, B[3], r2, p2, phi[SNAP_Q], old[SNAP_Q];
+        T rho, C[MAX_SPECIES], B[3], r2, p2, phi[SNAP_Q], old[SNAP_Q];
         int nf;
         node_phi<PL, S, T>(static_cast<const S *>(rp.src) + c.pop_off, c.stride, n, c, rho, C, B, nf, phi);
-        constexpr int W = snap_width(DIM, HH, HG);
+        constexpr int W = snap_width(DIM, NC, HG);
         snap_exchange<PL, SnapT, T>(static_cast<SnapT *>(rp.snap) + (c.node_off + n) * W, phi, old);
         resid_terms<PL, T>(phi, old, r2, p2);
         add_terms<PL, T>(acc, nfc, rho, C, B, nf, r2, p2);

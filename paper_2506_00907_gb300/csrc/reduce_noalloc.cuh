@@ -13,11 +13,11 @@ constexpr int NOALLOC_MAX_BLOCKS = LBM_NOALLOC_MAX_NODES / NOALLOC_BLOCK;
 
 // Same per-node work as k_reduce, over a plain node range of one domain whose
 // descriptor arrives by value; partials go to scratch[block][RED_Q].
-template <int DIM, bool HH, bool HG, class S>
+template <int DIM, int NC, bool HG, class S>
 __global__ void __launch_bounds__(NOALLOC_BLOCK) k_reduce_noalloc(const CaseDev<typename Codec<S>::T> c,
                                                                  const void *pops, const uint8_t *flags,
                                                                  double *snap, double *scratch) {
-    using PL = Planes<DIM, HH, HG>;
+    using PL = Planes<DIM, NC, HG>;
     using T = typename Codec<S>::T;
     __shared__ double sh[RED_Q][32];
     const int n = blockIdx.x * NOALLOC_BLOCK + threadIdx.x;
@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(NOALLOC_BLOCK) k_reduce_noalloc(const CaseDev<
     acc.zero();
     int nfc = 0;
     if (n < c.N && (!flags || flags[n])) {
-        T rho, C, B[3], r2, p2, phi[SNAP_Q], old[SNAP_Q];
+        T rho, C[MAX_SPECIES], B[3], r2, p2, phi[SNAP_Q], old[SNAP_Q];
         int nf;
         node_phi<PL, S, T>(static_cast<const S *>(pops), c.stride, n, c, rho, C, B, nf, phi);
         // the caller's snapshot: SNAP_Q planes of N doubles
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(NOALLOC_BLOCK) k_reduce_noalloc(const CaseDev<
     block_record(acc, nfc, sh, scratch + (int64_t)blockIdx.x * RED_Q);
 }
 
-template <int DIM, bool HH, bool HG, class S>
+template <int DIM, int NC, bool HG, class S>
 cudaError_t launch_noalloc(const lbm_case &k, int64_t plane_stride, const void *pops, const uint8_t *flags,
                            double *snap, double *scratch, int nblocks, cudaStream_t s) {
     using T = typename Codec<S>::T;
@@ -54,12 +54,12 @@ cudaError_t launch_noalloc(const lbm_case &k, int64_t plane_stride, const void *
     c.ay = T(k.accel[1]);
     c.az = DIM == 3 ? T(k.accel[2]) : T(0);
     c.ref_rho = T(k.rho0);
-    c.ref_C = HH ? T(k.C0) : T(0);
+    c.ref_C = NC ? T(k.C0) : T(0);
     for (int j = 0; j < 3; ++j) {
         c.ref_B[j] = (HG && j < DIM) ? T(k.B0[j]) : T(0);
         c.B0[j] = j < DIM ? T(k.B0[j]) : T(0);
     }
-    k_reduce_noalloc<DIM, HH, HG, S><<<nblocks, NOALLOC_BLOCK, 0, s>>>(c, pops, flags, snap, scratch);
+    k_reduce_noalloc<DIM, NC, HG, S><<<nblocks, NOALLOC_BLOCK, 0, s>>>(c, pops, flags, snap, scratch);
     return cudaGetLastError();
 }
 

@@ -19,7 +19,14 @@ LBM_FLOW, LBM_CD, LBM_MHD = 1, 2, 4
 LBM_W_VELOCITY, LBM_W_GIVEN, LBM_W_FLUX, LBM_W_NEUMANN_BFL = 0, 1, 2, 3
 LBM_W_VELOCITY_EQ15, LBM_W_FLUX_SIMPLIFIED = 4, 5      # the paper's comparison schemes
 LBM_W_PRESSURE = 6                                      # open boundary of given density (Eq. 42, 44)
+LBM_W_REACTION = 8                                      # surface reaction network, several species (Sec. 4.2.2)
 FIELD_F, FIELD_H, FIELD_G = 0, 1, 2
+LBM_MAX_SPECIES, LBM_MAX_REACT = 3, 4
+
+
+def field_species(k):
+    """Field code of concentration species k (LBM_FIELD_SPECIES)."""
+    return 1 if k == 0 else 4 + k
 PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S, "bf16s": LBM_BF16S}
 
 LINK_DTYPE = np.dtype([
@@ -33,13 +40,17 @@ class lbm_case(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("tau_nu", ctypes.c_double), ("tau_D", ctypes.c_double), ("tau_eta", ctypes.c_double),
                 ("accel", ctypes.c_double * 3), ("rho0", ctypes.c_double), ("C0", ctypes.c_double),
-                ("B0", ctypes.c_double * 3)]
+                ("B0", ctypes.c_double * 3), ("tau_Dk", ctypes.c_double * 3), ("C0k", ctypes.c_double * 3)]
 
 
 class lbm_config(ctypes.Structure):
     _fields_ = [("lattice", ctypes.c_int), ("prec", ctypes.c_int), ("physics", ctypes.c_uint32),
                 ("ncases", ctypes.c_int32), ("cases", ctypes.POINTER(lbm_case)),
-                ("stream", ctypes.c_void_p), ("device", ctypes.c_int32)]
+                ("stream", ctypes.c_void_p), ("device", ctypes.c_int32), ("nspecies", ctypes.c_int32)]
+
+
+class lbm_reaction(ctypes.Structure):
+    _fields_ = [("rate", ctypes.c_double), ("order", ctypes.c_int32 * 3), ("stoich", ctypes.c_double * 3)]
 
 
 class lbm_launch(ctypes.Structure):
@@ -115,6 +126,8 @@ def lib():
                                                      ctypes.c_double, vp, vp])
         sig["lbm_reduce_noalloc"] = (ctypes.c_int, [i32, i32, ctypes.c_uint32, ctypes.POINTER(lbm_case), vp, i64,
                                                      vp, vp, dp, vp])
+        sig["lbm_species"] = (ctypes.c_int, [vp, i32, i32, dp])
+        sig["lbm_set_reactions"] = (ctypes.c_int, [vp, i32, i32, ctypes.POINTER(lbm_reaction)])
         for name, (res, args) in sig.items():
             f = getattr(L, name)
             f.restype = res
@@ -133,9 +146,9 @@ def _check(ctx, st):
 
 
 # ----------------------------------------------------------------- C-ABI mirrors
-def lbm_create(lattice, prec, physics, cases, stream=None, device=0):
+def lbm_create(lattice, prec, physics, cases, stream=None, device=0, nspecies=0):
     arr = (lbm_case * len(cases))(*cases)
-    cfg = lbm_config(lattice, prec, physics, len(cases), arr, stream, device)
+    cfg = lbm_config(lattice, prec, physics, len(cases), arr, stream, device, nspecies)
     h = ctypes.c_void_p()
     _check(None, lib().lbm_create(ctypes.byref(cfg), ctypes.byref(h)))
     return h
@@ -182,6 +195,25 @@ def lbm_moments(ctx, case_id, N):
     rho, u, C, B = np.zeros(N), np.zeros(3 * N), np.zeros(N), np.zeros(3 * N)
     _check(ctx, lib().lbm_moments(ctx, case_id, _dp(rho), _dp(u), _dp(C), _dp(B)))
     return {"rho": rho, "u": u.reshape(N, 3), "C": C, "B": B.reshape(N, 3)}
+
+
+def lbm_species(ctx, case_id, k, N):
+    C = np.zeros(N)
+    _check(ctx, lib().lbm_species(ctx, case_id, k, _dp(C)))
+    return C
+
+
+def lbm_set_reactions(ctx, case_id, reactions):
+    """reactions: list of dicts with rate, order (per species, 0..2) and stoich (per species)."""
+    n = len(reactions)
+    arr = (lbm_reaction * max(1, n))()
+    for j, r in enumerate(reactions):
+        arr[j].rate = r["rate"]
+        for m, o in enumerate(r.get("order", ())):
+            arr[j].order[m] = int(o)
+        for m, v in enumerate(r.get("stoich", ())):
+            arr[j].stoich[m] = float(v)
+    _check(ctx, lib().lbm_set_reactions(ctx, case_id, n, arr))
 
 
 def lbm_check(ctx, ncases, raise_unstable=True):
@@ -401,17 +433,20 @@ class Net:
 
 # ----------------------------------------------------------------- convenience
 def make_case(shape, tau_nu, tau_D=1.0, tau_eta=1.0, accel=(0.0, 0.0, 0.0), rho0=1.0, C0=0.0,
-              B0=(0.0, 0.0, 0.0)):
+              B0=(0.0, 0.0, 0.0), tau_Dk=(1.0, 1.0, 1.0), C0k=(0.0, 0.0, 0.0)):
+    """tau_Dk, C0k: relaxation times and initial C of concentration species 1..3."""
     nx, ny, nz = shape
+    td = list(tau_Dk) + [1.0] * (3 - len(tau_Dk))
+    c0 = list(C0k) + [0.0] * (3 - len(C0k))
     return lbm_case(nx, ny, nz, tau_nu, tau_D, tau_eta, (ctypes.c_double * 3)(*accel), rho0, C0,
-                    (ctypes.c_double * 3)(*B0))
+                    (ctypes.c_double * 3)(*B0), (ctypes.c_double * 3)(*td), (ctypes.c_double * 3)(*c0))
 
 
 class Solver:
     """One context: all cases share lattice, precision and physics and are
     advanced together, one fused launch per step."""
 
-    def __init__(self, lattice, prec, physics, cases, stream=None, device=0):
+    def __init__(self, lattice, prec, physics, cases, stream=None, device=0, nspecies=0):
         if isinstance(prec, str):
             prec = PRECISIONS[prec]
         if stream is None:
@@ -420,7 +455,7 @@ class Solver:
         self.cases = list(cases)
         self.N = [c.nx * c.ny * c.nz for c in self.cases]
         self.lattice, self.prec, self.physics = lattice, prec, physics
-        self.ctx = lbm_create(lattice, prec, physics, self.cases, stream, device)
+        self.ctx = lbm_create(lattice, prec, physics, self.cases, stream, device, nspecies)
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -453,6 +488,13 @@ class Solver:
 
     def moments(self, case_id=0):
         return lbm_moments(self.ctx, case_id, self.N[case_id])
+
+    def species(self, k, case_id=0):
+        """Concentration of species k (N entries)."""
+        return lbm_species(self.ctx, case_id, k, self.N[case_id])
+
+    def set_reactions(self, case_id, reactions):
+        lbm_set_reactions(self.ctx, case_id, reactions)
 
     def check(self, raise_unstable=True):
         return lbm_check(self.ctx, len(self.cases), raise_unstable)

@@ -79,7 +79,11 @@ def test_wall_kind_values_agree_with_the_header():
     assert header == {k: getattr(lbm, k) for k in header}
     oracle_names = {"LBM_W_VELOCITY": O.VELOCITY, "LBM_W_GIVEN": O.GIVEN, "LBM_W_FLUX": O.FLUX,
                     "LBM_W_NEUMANN_BFL": O.NEUMANN_BFL, "LBM_W_VELOCITY_EQ15": O.VELOCITY_EQ15,
-                    "LBM_W_FLUX_SIMPLIFIED": O.FLUX_SIMPLIFIED, "LBM_W_PRESSURE": O.PRESSURE}
+                    "LBM_W_FLUX_SIMPLIFIED": O.FLUX_SIMPLIFIED, "LBM_W_PRESSURE": O.PRESSURE,
+                    "LBM_W_REACTION": O.REACTION}
     assert set(oracle_names) == set(header)
     for k, v in oracle_names.items():
         assert header[k] == v, k
+    # concentration species fields: the header's macro, the binding and the oracle
+    for k in range(3):
+        assert lbm.field_species(k) == O.species_field(k) == (1 if k == 0 else 4 + k)

@@ -157,13 +157,14 @@ def test_fp64_open_boundaries(dim, d):
 @pytest.mark.parametrize("prec", [lbm.LBM_FP32, lbm.LBM_FP16S])
 def test_open_boundaries_every_launch_variant(prec):
     """The pressure links' velocity extrapolation runs in every launch variant
-    with the same arithmetic: variants 1 and 3 (FP32 and 16-bit storage) equal
-    variant 0 bit for bit on an open 2D channel."""
+    with the same arithmetic: variants 1, 2 and 3 (FP32 and 16-bit storage)
+    equal variant 0 bit for bit on an open 2D channel."""
     ref = _open_channel_pair(2, 0.7, prec=prec).gpu
     ref.set_launch(0, 128, 0)
     ref.step(30)
     want = ref.get_state()
-    for variant, kw in ((1, dict(min_blocks=2)), (3, dict(blocks_per_sm=1, stages=4, min_blocks=2))):
+    for variant, kw in ((1, dict(min_blocks=2)), (3, dict(blocks_per_sm=1, stages=4, min_blocks=2)),
+                        (2, dict(nodes_per_thread=2, min_blocks=5))):
         g = _open_channel_pair(2, 0.7, prec=prec).gpu
         g.set_launch(variant, 256, **kw)
         g.step(30)
@@ -674,19 +675,21 @@ def test_register_budgets_are_bitwise_identical(dim):
 
 
 @pytest.mark.parametrize("dim,prec,shape", [
-    (2, lbm.LBM_FP16S, (53, 41, 1)), (2, lbm.LBM_BF16S, (52, 41, 1)), (2, lbm.LBM_FP16S, (36, 30, 1)),
-    (3, lbm.LBM_FP16S, (21, 13, 11)), (3, lbm.LBM_BF16S, (20, 13, 11)), (3, lbm.LBM_FP16S, (22, 14, 9))])
-def test_paired_nodes_are_bitwise_identical(dim, prec, shape):
-    """Variant 2 (two x-adjacent nodes per thread, paired 32-bit loads and
-    stores of 16-bit populations) computes exactly what one thread per node
-    computes: odd and even nx and nx*ny (which decide the word alignment of
-    each pull plane), ragged tails, periodic edges and every link kind."""
+    (2, lbm.LBM_FP16S, (53, 41, 1)), (2, lbm.LBM_BF16S, (52, 41, 1)), (2, lbm.LBM_FP32, (36, 30, 1)),
+    (2, lbm.LBM_FP64, (31, 22, 1)), (3, lbm.LBM_FP16S, (21, 13, 11)), (3, lbm.LBM_BF16S, (20, 13, 11)),
+    (3, lbm.LBM_FP32, (22, 14, 9))])
+def test_unwrapped_pulls_are_bitwise_identical(dim, prec, shape):
+    """Variant 2 (pulls read unwrapped from the node's own address plus a
+    per-case constant, edge nodes reloading their wrapped planes, 16-bit
+    values kept packed) computes exactly what variant 0 computes: ragged
+    tails, periodic edges, solid blobs and every link kind, every register
+    budget."""
     ref = _random_pair(dim, True, True, seed=91, prec=prec, shape=shape).gpu
     ref.set_launch(0, 128, 0)
     ref.step(15)
     want = ref.get_state()
-    lo = 2 if dim == 2 else 1
-    for block, npt, mb in ((128, 2, lo), (256, 4, lo + 1), (128, 8, lo + 2)):
+    lo = 4 if dim == 2 else 2
+    for block, npt, mb in ((128, 2, lo), (256, 4, lo + 1), (64, 8, lo + 2)):
         g = _random_pair(dim, True, True, seed=91, prec=prec, shape=shape).gpu
         g.set_launch(2, block, 0, npt, 2, mb)
         g.set_graph(4)
@@ -695,7 +698,35 @@ def test_paired_nodes_are_bitwise_identical(dim, prec, shape):
         g.check()
 
 
-def test_paired_nodes_batched_cases_and_flow_only():
+@pytest.mark.parametrize("dim,prec,shape", [
+    (2, lbm.LBM_FP16S, (1, 37, 1)), (2, lbm.LBM_FP16S, (3, 29, 1)), (2, lbm.LBM_BF16S, (40, 27, 1)),
+    (2, lbm.LBM_FP16S, (65, 8, 1)), (3, lbm.LBM_FP16S, (1, 9, 11)), (3, lbm.LBM_FP16S, (7, 5, 6)),
+    (3, lbm.LBM_BF16S, (12, 9, 7))])
+def test_fully_periodic_boxes_every_variant_bitwise(dim, prec, shape):
+    """A box without walls, periodic along every axis, from random fields:
+    every bulk node wraps somewhere (x, y and z edges; odd and even nx; nx = 1,
+    where a node pair straddles two rows).  Every launch variant gives the
+    bits of the one-node step, which matches the FP64 oracle in FP64
+    (test_fully_periodic_domain_and_single_node_axes)."""
+    N = shape[0] * shape[1] * shape[2]
+    phys = lbm.LBM_FLOW | lbm.LBM_CD | lbm.LBM_MHD
+    lat = lbm.LBM_D2Q9 if dim == 2 else lbm.LBM_D3Q19
+    f = IN.random_fields(IN.rng(41 + dim), N, dim, B0=(0.0, 0.3, 0.0))
+
+    def run(launch):
+        g = lbm.Solver(lat, prec, phys, [lbm.make_case(shape, 0.8, 0.9, 0.7, (1e-5, -2e-5, 0), 1.0, 1.0,
+                                                       (0, 0.3, 0))])
+        g.init_equilibrium(0, rho=f["rho"], u=f["u"], C=f["C"], B=f["B"])
+        g.set_launch(*launch)
+        g.step(9)
+        return g.get_state()
+    want = run((0, 128, 0, 1, 2, 1))
+    lo = 4 if dim == 2 else 2
+    for launch in ((0, 64, 0, 3, 2, 1), (2, 128, 0, 2, 2, 1), (2, 64, 0, 8, 2, lo + 1), (1, 256, 0, 1, 2, 2)):
+        assert np.array_equal(run(launch), want), launch
+
+
+def test_unwrapped_pulls_batched_cases_and_flow_only():
     """Variant 2 over uneven batched cases (odd widths, empty-link cases) and
     for a flow-only D2Q9 lattice equals variant 0 bit for bit."""
     def make(phys):
@@ -715,17 +746,14 @@ def test_paired_nodes_batched_cases_and_flow_only():
         a.set_launch(0, 256, 4)
         a.step(30)
         b = make(phys)
-        b.set_launch(2, 128, 0, 2, 2, 4)
+        b.set_launch(2, 128, 0, 3, 2, 5)
         b.step(30)
         assert np.array_equal(a.get_state(), b.get_state()), phys
 
 
-def test_paired_nodes_reject_bad_shapes():
-    p = _random_pair(2, False, False, seed=5, prec=lbm.LBM_FP32)
-    with pytest.raises(lbm.LbmError):
-        p.gpu.set_launch(2, 128, 0, 2, 2, 3)       # 32-bit storage has no paired form
+def test_unwrapped_pulls_reject_bad_shapes():
     q = _random_pair(2, False, False, seed=5, prec=lbm.LBM_FP16S)
-    for bad in ((2, 128, 0, 3, 2, 3), (2, 128, 0, 2, 2, 9)):
+    for bad in ((2, 128, 0, 3, 2, 3), (2, 128, 0, 9, 2, 4), (2, 96 + 1, 0, 2, 2, 4), (2, 128, 65, 2, 2, 4)):
         with pytest.raises(lbm.LbmError):
             q.gpu.set_launch(*bad)
 
