@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--train-per-case", type=int, default=2048)
     ap.add_argument("--train-max-steps", type=int, default=200000)
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--storage", choices=["fp16s", "bf16s", "fp32", "fp64"], default=None,
+                    help="population storage (default: the workload's; bf16s rounds stochastically)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--launch", default=None,
                     help="variant,block,blocks_per_sm,nodes_per_thread,stages,min_blocks (skips the autotuner)")
@@ -513,6 +515,9 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B.build()
     spec = workload_spec(args.workload, rank, world)
+    if args.storage:
+        spec = dict(spec, prec=args.storage, storage={"fp16s": "fp16-offset", "bf16s": "bf16-offset-stochastic",
+                                                      "fp32": "fp32", "fp64": "fp64"}[args.storage])
     stream = torch.cuda.Stream()                 # the solver's stream; every event below is recorded on it
     torch.cuda.set_stream(stream)
     sol, geo, infos = make_solver(spec, stream, local)

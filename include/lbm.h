@@ -55,7 +55,12 @@ typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
 /* Storage precision of the populations.  Every precision stores the shifted
  * value p - w_a * phi_ref (phi_ref = rho0, C0 or B0_k of the case), which keeps
  * the small deviations that carry the solution resolvable; FP16S and BF16S
- * store it in 16 bits and compute in FP32, FP32 in FP32, FP64 in FP64. */
+ * store it in 16 bits and compute in FP32, FP32 in FP32, FP64 in FP64.
+ * FP16S rounds to nearest.  BF16S rounds stochastically (the random bits are a
+ * hash of the step count, the node and the plane, the same in every launch
+ * variant), so that its rounding error has zero mean: at a steady state,
+ * rounding to nearest repeats the same error every step and the flow
+ * integrates it over its diffusion time. */
 typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16S = 2, LBM_BF16S = 3 } lbm_prec;
 
 /* physics mask: LBM_FLOW is required */
@@ -291,13 +296,16 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes);
 int64_t lbm_steps_done(const lbm_ctx *ctx);
 
 /* Launch shape of the fused step.
- *   variant 0: one thread per node at a time; tiles of block *
- *              nodes_per_thread nodes (1..8); blocks_per_sm = resident
+ *   variant 0: one thread per node at a time over runs of bulk-fluid
+ *              nodes (wall-link nodes are stepped by a second kernel
+ *              beside it), in tiles of at most block * nodes_per_thread
+ *              nodes (1..8); blocks_per_sm = resident
  *              blocks per SM of a persistent tile loop (0 = one block per
  *              tile, up to 64); min_blocks selects the register budget the
  *              kernel was compiled for, as resident 256-thread blocks per SM:
  *              2D 4, 5 or 6, 3D 2, 3 or 4 (1 = the first).
- *   variant 1: bulk-copy loads and stores (FP32 and 16-bit storage):
+ *   variant 1: bulk-copy loads and stores (FP32 and FP16S storage, one
+ *              concentration species at most):
  *              persistent blocks of 256 threads copy each plane's source
  *              window of the next tile into shared memory with cp.async.bulk
  *              on mbarriers while computing the current tile, boundary nodes
@@ -306,13 +314,13 @@ int64_t lbm_steps_done(const lbm_ctx *ctx);
  *              is the tile size in nodes and `min_blocks` the register budget,
  *              one of (128, 2), (256, 2), (256, 4), (512, 1), (512, 2);
  *              blocks_per_sm, nodes_per_thread and stages are ignored.
- *   variant 2: as variant 0 for 16-bit storage, each thread taking pairs of
- *              x-adjacent nodes (nodes_per_thread 2, 4, 6 or 8): planes whose
- *              pull offset is even are read as one 32-bit word for both
- *              nodes and every result plane is written as one word; pairs on
- *              a periodic edge or next to a solid or boundary node take the
- *              one-node path.  min_blocks: 2D 2..4, 3D 1..3.
- *   variant 3: shared-memory ring (FP32 and 16-bit storage): persistent
+ *   variant 2: as variant 0 (same shapes and register budgets, every
+ *              precision), each node reading its pulls unwrapped, at its own
+ *              address plus a per-case offset per plane, and only nodes on a
+ *              periodic edge reloading the planes whose source wraps; 16-bit
+ *              values stay packed two to a register until the collision.
+ *   variant 3: shared-memory ring (FP32 and FP16S storage, one concentration
+ *              species at most): persistent
  *              blocks of one producer warp and 8 consumer warps.  The
  *              producer copies each plane's source window of the block's
  *              next tiles into a ring of `stages` (2..8) shared-memory stages

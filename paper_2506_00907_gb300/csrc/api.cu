@@ -80,6 +80,7 @@ struct lbm_ctx {
     int tile_nodes = 256, bulk_grid = 0, bulk_idx = 0, step_idx = 0;
     size_t bulk_smem = 0;
     int32_t *d_err = nullptr;
+    uint32_t *d_ctr = nullptr;         // [2]: the step count (stochastic rounding), slot cur = steps
     int2 *d_tiles = nullptr;
     int32_t ntiles = 0;
     int32_t *d_case_tile_lo = nullptr;  // [cases + 1]: each case's range of reduction tiles
@@ -558,6 +559,8 @@ StepParams<T> step_params(const lbm_ctx *c) {
     p.nspans = c->nspans;
     p.links = static_cast<const LinkDev<T> *>(c->d_links);
     p.react = static_cast<const ReactDev<T> *>(c->d_react);
+    p.ctr_rd = c->d_ctr + c->cur;
+    p.ctr_wr = c->d_ctr + (1 - c->cur);
     return p;
 }
 
@@ -695,7 +698,7 @@ void free_ctx(lbm_ctx *c) {
     void *ptrs[] = {c->pool_alloc[0], c->pool_alloc[1], c->d_flags, c->d_cases, c->d_tiles, c->d_case_tile_lo,
                     c->d_tile_brec, c->d_spans, c->d_rtiles,
                     c->d_brec, c->d_links, c->d_snap, c->d_part, c->d_red, c->d_mom, c->d_err,
-                    c->d_motion, c->d_clock, c->d_wall_links, c->d_react};
+                    c->d_motion, c->d_clock, c->d_wall_links, c->d_react, c->d_ctr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_red) cudaFreeHost(c->h_red);
@@ -899,6 +902,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
     ck(cudaEventCreateWithFlags(&ctx->ev_check, cudaEventDisableTiming), "cudaEventCreate");
     ck(cudaMalloc(&ctx->d_mom, (size_t)ctx->max_case_nodes * 8 * sizeof(double)), "moment scratch");
     ck(cudaMalloc(&ctx->d_err, sizeof(int32_t)), "error word");
+    ck(cudaMalloc(&ctx->d_ctr, 2 * sizeof(uint32_t)), "step count");
+    if (st == LBM_OK) ck(cudaMemset(ctx->d_ctr, 0, 2 * sizeof(uint32_t)), "memset");
     ck(cudaMalloc(&ctx->d_react, ctx->cases.size() * std::max(sizeof(ReactDev<double>), sizeof(ReactDev<float>))),
        "reaction networks");
     if (st == LBM_OK)
@@ -1022,11 +1027,15 @@ static lbm_status capture_graph(lbm_ctx *ctx) {
     return LBM_OK;
 }
 
-// The device clock of the wall motion follows the context's step count.
+// The device clock of the wall motion and the device step count of the
+// stochastic rounding follow the context's step count.
 static lbm_status set_clock(lbm_ctx *ctx) {
-    if (!ctx->d_clock) return LBM_OK;
-    const long long t = ctx->steps;
-    CK(cudaMemcpyAsync(ctx->d_clock, &t, sizeof t, cudaMemcpyHostToDevice, ctx->stream));
+    const uint32_t c32 = (uint32_t)ctx->steps;
+    CK(cudaMemcpyAsync(ctx->d_ctr + ctx->cur, &c32, sizeof c32, cudaMemcpyHostToDevice, ctx->stream));
+    if (ctx->d_clock) {
+        const long long t = ctx->steps;
+        CK(cudaMemcpyAsync(ctx->d_clock, &t, sizeof t, cudaMemcpyHostToDevice, ctx->stream));
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     return LBM_OK;
 }
@@ -1287,6 +1296,8 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes) {
     CK(cudaMemcpyAsync(ctx->pool[ctx->cur], h + 16, pool_bytes(ctx), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->steps = (int64_t)hdr[1];
+    const lbm_status st = set_clock(ctx);
+    if (st != LBM_OK) return st;
     return apply_motion(ctx, table.data());
 }
 
@@ -1333,6 +1344,8 @@ lbm_status lbm_convert_state(lbm_ctx *dst, lbm_ctx *src) {
     }
     CK(cudaStreamSynchronize(dst->stream));
     dst->steps = src->steps;
+    const lbm_status st_clk = set_clock(dst);
+    if (st_clk != LBM_OK) return st_clk;
     std::vector<double> table = src->h_motion;
     table.resize(MOTION_W * src->cases.size(), 0.0);
     return apply_motion(dst, table.data());

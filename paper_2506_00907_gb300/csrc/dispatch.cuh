@@ -105,8 +105,9 @@ struct Launch {
     }
     static KernelSet make() {
         KernelSet k{};
-        // the bulk-copy and ring variants serve one concentration species at most
-        if constexpr (NC <= 1) {
+        // the bulk-copy and ring variants serve one concentration species at most,
+        // and storage that rounds to nearest (not the stochastic BF16 rounding)
+        if constexpr (NC <= 1 && !Rounding<S>::SR) {
             set_ring(k);
             set_bulk<0>(k);
             set_bulk<1>(k);

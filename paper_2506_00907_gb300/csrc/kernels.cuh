@@ -58,6 +58,53 @@ template <> struct Codec<__nv_bfloat16> {
 
 LBM_DEV uint32_t fast_div(uint32_t n, FastDiv d) { return (__umulhi(n, d.m) + n) >> d.s; }
 
+// ------------------------------------------------------------------ stochastic rounding (BF16 storage)
+// BF16 storage rounds stochastically: a value is rounded up in magnitude with
+// the probability of its distance to the lower neighbour, so that the
+// rounding error has zero mean.  Round to nearest, at a steady state, makes
+// the same error every step, which the flow integrates over its diffusion
+// time; stochastic rounding (a published method: the random bits below the
+// kept mantissa are added before truncation) removes that bias.  The 16
+// random bits of (step, node, plane) come from a multiply-xorshift integer
+// hash of the step and the node (constants of Wellons' "lowbias32"), then one
+// multiplication per pair of planes, so every launch variant draws the same
+// bits for the same population.  The addition saturates in signed 32-bit
+// arithmetic, so a NaN (0x7fffffff on the GPU) stays a NaN.
+template <class S> struct Rounding { static constexpr bool SR = false; };
+template <> struct Rounding<__nv_bfloat16> { static constexpr bool SR = true; };
+
+LBM_DEV uint32_t sr_node_hash(uint32_t step, uint32_t node) {
+    uint32_t x = node * 0x9E3779B1u ^ step * 0x85EBCA77u;
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+// 16 random bits of plane q from the node's hash
+LBM_DEV uint32_t sr_plane_bits(uint32_t h, int q) {
+    const uint32_t r = h * (0x2545F491u + 0x9E3779B9u * (uint32_t)(q >> 1));
+    return (q & 1) ? (r >> 16) : (r & 0xffffu);
+}
+LBM_DEV uint32_t add_sat(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("add.sat.s32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+// stores population q of a node whose hash is h
+template <class S>
+LBM_DEV void store_pop(S *p, float v, uint32_t h, int q) {
+    if constexpr (Rounding<S>::SR) {
+        const uint32_t b = add_sat(__float_as_uint(v), sr_plane_bits(h, q));
+        *reinterpret_cast<unsigned short *>(p) = (unsigned short)(b >> 16);
+    } else {
+        Codec<S>::st(p, v);
+    }
+}
+template <class S>
+LBM_DEV void store_pop(S *p, double v, uint32_t, int) { Codec<S>::st(p, v); }
+
 LBM_DEV float fmaf_t(float a, float b, float c) { return fmaf(a, b, c); }
 LBM_DEV double fmaf_t(double a, double b, double c) { return a * b + c; }   // FP64 serves parity: no fused rounding
 
@@ -76,7 +123,15 @@ struct StepParams {
     const LinkDev<T> *links;
     const int32_t *tile_brec; // boundary records of tile t: [tile_brec[t], tile_brec[t + 1])
     const ReactDev<T> *react; // surface reaction network per case (kernels with several species)
+    const uint32_t *ctr_rd;   // the step count (stochastic rounding); the step's main kernel writes
+    uint32_t *ctr_wr;         // count + 1 into the other slot (slots swap every step, as src and dst)
 };
+
+// block 0 of a step's main kernel advances the device step count
+template <class T>
+LBM_DEV void advance_step_count(const StepParams<T> &prm) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *prm.ctr_wr = *prm.ctr_rd + 1u;
+}
 
 // ------------------------------------------------------------------ equilibria
 // Shifted equilibria e_a - w_a phi_ref, written with the deviations
@@ -587,7 +642,8 @@ LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDe
             asm("" : "+r"(w));
             return F1(Pack16<S>::get(w, q & 1));
         };
-        auto put = [&](int q, F1 v) { Codec<S>::st(dp + q * os, v.v); };
+        const uint32_t h = Rounding<S>::SR ? sr_node_hash(*prm.ctr_rd, (uint32_t)(c.node_off + n)) : 0u;
+        auto put = [&](int q, F1 v) { store_pop<S>(dp + q * os, v.v, h, q); };
         collide_g<PL, NC, HG, F1, float>(getm, getr, put, c);
         return;
     }
@@ -597,8 +653,9 @@ LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDe
         p[q] = Codec<S>::ld(sp + (q * st32 + ox[1 - PL::ex(q)] + oy[1 - PL::ey(q)] + oz[1 - PL::ez(q)]));
     if constexpr (LINKS) apply_links<PL, S, T, LCH>(p, prm, c, src, lo, hi);
     collide<PL, NC, HG, T>(p, c);
+    const uint32_t h = Rounding<S>::SR ? sr_node_hash(*prm.ctr_rd, (uint32_t)(c.node_off + n)) : 0u;
 #pragma unroll
-    for (int q = 0; q < P; ++q) Codec<S>::st(dp + q * os, p[q]);
+    for (int q = 0; q < P; ++q) store_pop<S>(dp + q * os, p[q], h, q);
 }
 
 // Bulk nodes (fluid, no wall link) over the span list: span t holds nodes
@@ -611,6 +668,7 @@ LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDe
 template <int DIM, int NC, bool HG, class S, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_step(const StepParams<typename Codec<S>::T> prm, const int npt) {
     using T = typename Codec<S>::T;
+    advance_step_count(prm);
     for (int t = blockIdx.x; t < prm.nspans; t += gridDim.x) {
         const int4 sp = prm.spans[t];
         // the descriptor by value: the stores below cannot alias it, so it stays in registers
@@ -703,7 +761,8 @@ LBM_DEV void step_node_unwrapped(const StepParams<typename Codec<S>::T> &prm, co
             asm("" : "+r"(w));                 // convert again rather than keep the moments' copy alive
             return F1(Raw16<S>::get(w, q & 1));
         };
-        auto put = [&](int q, F1 v) { Codec<S>::st(dp + q * st, v.v); };
+        const uint32_t h = Rounding<S>::SR ? sr_node_hash(*prm.ctr_rd, (uint32_t)(c.node_off + n)) : 0u;
+        auto put = [&](int q, F1 v) { store_pop<S>(dp + q * st, v.v, h, q); };
         collide_g<PL, NC, HG, F1, float>(getm, getr, put, c);
     } else {
         collide<PL, NC, HG, T>(p, c);
@@ -717,6 +776,7 @@ LBM_DEV void step_node_unwrapped(const StepParams<typename Codec<S>::T> &prm, co
 template <int DIM, int NC, bool HG, class S, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_step_unwrapped(const StepParams<typename Codec<S>::T> prm, const int npt) {
     using T = typename Codec<S>::T;
+    advance_step_count(prm);
     for (int t = blockIdx.x; t < prm.nspans; t += gridDim.x) {
         const int4 spn = prm.spans[t];
         const CaseDev<T> c = prm.cases[spn.x];

@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(BULK_THREADS, MINB) k_step_bulk(const StepPara
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L::BAR);
     const int tid = threadIdx.x;
+    advance_step_count(prm);
     const bool w0 = tid < 32;
     if (tid == 0) {
         for (int k = 0; k < NS; ++k) mbar_init(&bar[k], 1);

@@ -222,6 +222,7 @@ __global__ void __launch_bounds__(RING_THREADS, MINB) k_step_ring(const StepPara
     uint64_t *empty = reinterpret_cast<uint64_t *>(smem + RING_EMPTY);
     volatile int *abort_word = reinterpret_cast<volatile int *>(smem + RING_ABORT);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    advance_step_count(prm);
     if (threadIdx.x == 0) {
         for (int k = 0; k < ns; ++k) {
             mbar_init(&full[k], 1);

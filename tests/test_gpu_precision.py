@@ -15,9 +15,12 @@ of either side shows up; the measured values are listed in the design notes.
 FP64 meets the 1e-12 parity target per step (``test_gpu_parity.py``); over
 thousands of steps the two sides' different rounding orders accumulate over
 the flow's relaxation time, to about 4e-12 after 2000 steps and 8e-12 at
-steady state.  The 16-bit storages round to nearest, and at a steady state
-the same rounding recurs every step: it acts as a fixed spurious source that
-the flow integrates over its diffusion time, which sets their errors.
+steady state.  FP16 storage rounds to nearest: at a steady state the same
+rounding recurs every step and acts as a fixed spurious source that the flow
+integrates over its diffusion time (errors of 10-26 % at steady state).  BF16
+storage rounds stochastically: the error has zero mean, so the steady state
+is within about 1 % although BF16 keeps three mantissa bits fewer; early in
+a transient, small signals are within its noise.
 """
 import concurrent.futures as cf
 import os
@@ -117,7 +120,7 @@ BATCH_MEASURED = {
     "fp64": {"u": 4.02e-12, "b": 2.39e-12, "rho": 1.47e-13},
     "fp32": {"u": 5.39e-4, "b": 7.12e-5, "rho": 4.12e-7},
     "fp16s": {"u": 0.226, "b": 0.990, "rho": 2.26e-4},
-    "bf16s": {"u": 7.66, "b": 0.723, "rho": 2.52e-3},
+    "bf16s": {"u": 0.912, "b": 37.2, "rho": 3.54e-2},
 }
 
 
@@ -150,7 +153,7 @@ STEADY_MEASURED = {
     "fp64": {"u": 6.26e-12, "b": 8.22e-12},
     "fp32": {"u": 8.0e-5, "b": 1.14e-4},
     "fp16s": {"u": 0.191, "b": 0.247},
-    "bf16s": {"u": 0.603, "b": 0.889},
+    "bf16s": {"u": 1.12e-2, "b": 1.14e-2},
 }
 
 
@@ -205,6 +208,7 @@ CD_MEASURED = {
     "fp64": {"u": 1.43e-13, "C": 1.66e-14, "rho": 1.13e-13},
     "fp32": {"u": 4.67e-6, "C": 1.11e-5, "rho": 1.13e-13},
     "fp16s": {"u": 1.35e-2, "C": 8.82e-3, "rho": 5.81e-5},
+    "bf16s": {"u": 9.25e-3, "C": 3.56e-3, "rho": 5.46e-4},
 }
 
 
@@ -214,7 +218,7 @@ def cd_batch():
     return spec, _oracle_rows(spec, CD_STEPS, ("C",))
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s", "bf16s"])
 def test_reactive_channels_against_oracle(cd_batch, prec):
     """The 12 flow + concentration channels of 512 x 256 (q in {0, 1/4, 1/2,
     3/4}, k in {1e-3, 1e-2, 1e-1}, top wall U = 0.05), 2000 steps from rest."""
@@ -226,10 +230,11 @@ def test_reactive_channels_against_oracle(cd_batch, prec):
 
 
 CD_STEADY_STEPS = 100000
-CD_STEADY_MEASURED = {"fp32": {"u": 2.19e-4, "C": 1.40e-4}, "fp16s": {"u": 0.189, "C": 0.260}}
+CD_STEADY_MEASURED = {"fp32": {"u": 2.19e-4, "C": 1.40e-4}, "fp16s": {"u": 0.189, "C": 0.260},
+                      "bf16s": {"u": 9.3e-3, "C": 4.56e-3}}
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp16s"])
+@pytest.mark.parametrize("prec", ["fp32", "fp16s", "bf16s"])
 def test_reactive_channels_steady_state_against_closed_form(prec):
     """The same 12 (q, k) channels at height 66 (2H = 63 + 2d), run to steady
     state (100 000 steps, ten diffusion times): the storage against the
@@ -263,10 +268,11 @@ def test_reactive_channels_steady_state_against_closed_form(prec):
 # ----------------------------------------------------------------------------- the MHD pipe, 32 x 128 x 128
 PIPE_STEPS = 1000
 PIPE_MEASURED = {"fp32": {"u": 2.24e-5, "b": 2.60e-5, "rho": 6.57e-8},
-                 "fp16s": {"u": 7.46e-3, "b": 6.49e-3, "rho": 6.49e-6}}
+                 "fp16s": {"u": 7.46e-3, "b": 6.49e-3, "rho": 6.49e-6},
+                 "bf16s": {"u": 4.59e-3, "b": 6.88e-3, "rho": 4.69e-5}}
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp16s"])
+@pytest.mark.parametrize("prec", ["fp32", "fp16s", "bf16s"])
 def test_pipe_against_oracle(prec):
     """The 3D pipe (R = 62, curved Shercliff wall, every q in (0, 1) on the
     circle), 1000 steps from rest, every fluid node against the oracle."""
@@ -278,7 +284,8 @@ def test_pipe_against_oracle(prec):
     _assert_within(errs, {k: MARGIN * v for k, v in PIPE_MEASURED[prec].items()})
 
 
-PIPE_STEADY_MEASURED = {"fp32": {"u": 1.11e-2, "b": 1.66e-2}, "fp16s": {"u": 0.108, "b": 1.99e-2}}
+PIPE_STEADY_MEASURED = {"fp32": {"u": 1.11e-2, "b": 1.66e-2}, "fp16s": {"u": 0.108, "b": 1.99e-2},
+                        "bf16s": {"u": 1.19e-2, "b": 2.01e-2}}
 
 
 def test_pipe_steady_state_against_finite_volume_solution():
@@ -292,7 +299,7 @@ def test_pipe_steady_state_against_finite_volume_solution():
     r, th, uf, bf = FD.solve(P["R"], P["B0"], P["nu"], P["eta"], P["accel"], wall=P["wall"], nr=96, nt=192)
     out = {}
     steps = None
-    for prec in ("fp32", "fp16s"):
+    for prec in ("fp32", "fp16s", "bf16s"):
         sol, geo, _ = bench.make_solver(dict(spec, prec=prec), stream, 0)
         sol.set_graph(100)
         if steps is None:
@@ -311,6 +318,6 @@ def test_pipe_steady_state_against_finite_volume_solution():
                      "b": float(np.abs(m["B"][fl, 0] - ba).max() / np.abs(ba).max())}
         sol.close()
         _report("pipe steady %s vs finite volume (%d steps)" % (prec, steps), out[prec])
-    for k in ("u", "b"):
-        assert out["fp32"][k] <= MARGIN * PIPE_STEADY_MEASURED["fp32"][k], (k, out["fp32"][k])
-        assert out["fp16s"][k] <= MARGIN * PIPE_STEADY_MEASURED["fp16s"][k], (k, out["fp16s"][k])
+    for prec in out:
+        for k in ("u", "b"):
+            assert out[prec][k] <= MARGIN * PIPE_STEADY_MEASURED[prec][k], (prec, k, out[prec][k])
