@@ -193,9 +193,21 @@ def measured_traffic(workload):
 def peaks():
     try:
         pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        return dict(hbm=float(pk["hbm_gbs"]), kind="measured")
+        return dict(hbm=float(pk["hbm_gbs"]), kind="measured", sm_mhz=float(pk.get("sm_max_mhz", 2070.0)))
     except Exception:
-        return dict(hbm=6800.0, kind="fallback")
+        return dict(hbm=6800.0, kind="fallback", sm_mhz=2070.0)
+
+
+def fp64_ops(workload):
+    """FP64 operations per bulk node of the FP64 step from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "fp64_ops.json"))).get(workload)
+    except Exception:
+        return None
+    if not rec or rec.get("kernel_hash") != kernel_hash():
+        return None
+    return rec
 
 
 class Clocks:
@@ -656,10 +668,22 @@ def fp64_record(spec, stream, local, pk):
     ms = min(a.elapsed_time(b) for a, b in ev) / GRAPH
     sol.close()
     alg = 2.0 * spec["planes"] * 8 * spec["fluid"]
-    return {"mlups": spec["fluid"] / (ms * 1e-3) / 1e6, "ms_per_time_step": ms, "bytes_per_time_step": alg,
-            "hbm": {"achieved": alg / (ms * 1e-3) / 1e9, "peak": pk["hbm"], "unit": "GB/s",
-                    "frac": alg / (ms * 1e-3) / 1e9 / pk["hbm"]},
-            "timing": "best of 3 replays of the %d-step graph, step launches only" % GRAPH}
+    out = {"mlups": spec["fluid"] / (ms * 1e-3) / 1e6, "ms_per_time_step": ms, "bytes_per_time_step": alg,
+           "hbm": {"achieved": alg / (ms * 1e-3) / 1e9, "peak": pk["hbm"], "unit": "GB/s",
+                   "frac": alg / (ms * 1e-3) / 1e9 / pk["hbm"]},
+           "timing": "best of 3 replays of the %d-step graph, step launches only" % GRAPH}
+    ops = fp64_ops("hartmann_batch")
+    if ops:
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        peak = 2.0 * sms * pk["sm_mhz"] * 1e6 / 1e9          # FP64 operations per clock per SM: 2
+        achieved = ops["fp64_ops_per_bulk_node"] * ops["bulk_nodes"] / (ms * 1e-3) / 1e9
+        out["alu"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G FP64 op/s",
+                      "frac": achieved / peak, "ops_per_bulk_node": ops["fp64_ops_per_bulk_node"],
+                      "peak_kind": "derived: 2 FP64 operations per clock per SM x %d SMs x %.0f MHz" % (
+                          sms, pk["sm_mhz"]),
+                      "source": ops["source"]}
+        out["bound"] = "alu" if out["alu"]["frac"] > out["hbm"]["frac"] else "hbm"
+    return out
 
 
 # ----------------------------------------------------------------------------- time to steady state
