@@ -279,6 +279,33 @@ lbm_status lbm_check_wait(lbm_ctx *ctx, double *out);
 lbm_status lbm_run_to_steady(lbm_ctx *ctx, int64_t max_steps, int32_t interval, double tol,
                              int64_t *steps_done, double *residual);
 
+/* Freezes (active = 0) or resumes (active != 0) one case.  A frozen case is
+ * left out of the step: none of its nodes is read or written, its state is
+ * kept identical in both population buffers, and lbm_check reports a zero
+ * residual for it while its sums stay those of the frozen state.  The other
+ * cases step as they would alone (their arithmetic never reads another
+ * case's nodes).  Freezing copies the case's populations once on the device
+ * and synchronises the stream; every change rebuilds the step's node and
+ * wall-link lists and drops the captured graphs.  A state written into the
+ * current buffer from outside the step (initialisation, lbm_set_state,
+ * lbm_convert_state, a write through lbm_device_state) is copied to the other
+ * buffer of each frozen case before the next step.  Launch variants 1 and 3
+ * step every case: freezing is refused while one of them is set, and
+ * lbm_set_launch and lbm_autotune refuse them while a case is frozen.
+ * Errors: LBM_EINVAL (bad case id, variant 1 or 3 set), LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_set_active(lbm_ctx *ctx, int32_t case_id, int32_t active);
+
+/* lbm_run_to_steady case by case: every `interval` steps each active case
+ * whose own relative residual is below tol is frozen (lbm_set_active), so
+ * that the remaining steps serve only the cases still moving; stops when all
+ * are frozen or max_steps are done, then resumes the cases it froze (cases
+ * frozen by the caller before the call stay frozen).  *steps_done counts
+ * time steps of the whole batch; *residual is the largest of the cases' last
+ * measured residuals (INFINITY for a case never measured).  Synchronises.
+ * Errors: those of lbm_step, lbm_check and lbm_set_active. */
+lbm_status lbm_run_each_to_steady(lbm_ctx *ctx, int64_t max_steps, int32_t interval, double tol,
+                                  int64_t *steps_done, double *residual);
+
 /* Checkpoint: size in bytes of the state blob, and copy it out / in (host
  * memory, synchronises).  The blob holds every population of every case, the
  * step count and the wall-motion table of lbm_set_wall_motion (per case

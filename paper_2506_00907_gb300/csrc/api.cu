@@ -88,6 +88,12 @@ struct lbm_ctx {
     int32_t nrtiles = 0;
     BRec *d_brec = nullptr;
     int32_t nbrec = 0;
+    // cases being stepped (lbm_set_active): the spans and the boundary records
+    // of the boundary kernel hold active cases only
+    std::vector<uint8_t> active;
+    BRec *d_brec_step = nullptr;
+    int32_t nbrec_step = 0;
+    bool frozen_dirty = false;                 // the current buffer was written from outside the step
     std::vector<int2> h_tiles;         // host copies for the per-tile boundary ranges
     std::vector<BRec> h_brec;
     int32_t *d_tile_brec = nullptr;    // [ntiles + 1]
@@ -420,6 +426,7 @@ lbm_status build_tile_brec(lbm_ctx *ctx) {
     std::vector<int4> spans;
     if (!ctx->h_flags.empty())
         for (size_t c = 0; c < ctx->cases.size(); ++c) {
+            if (!ctx->active.empty() && !ctx->active[c]) continue;
             const CaseHost &cs = ctx->cases[c];
             const uint8_t *f = ctx->h_flags.data() + cs.node_off;
             for (int32_t n = 0; n < cs.N;) {
@@ -436,6 +443,15 @@ lbm_status build_tile_brec(lbm_ctx *ctx) {
     ctx->nspans = (int32_t)spans.size();
     CK(cudaMalloc(&ctx->d_spans, std::max<size_t>(1, spans.size()) * sizeof(int4)));
     if (!spans.empty()) CK(cudaMemcpy(ctx->d_spans, spans.data(), spans.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    // the boundary kernel's records: those of active cases
+    std::vector<BRec> bs;
+    for (const BRec &b : ctx->h_brec)
+        if (b.node >= 0 && (ctx->active.empty() || ctx->active[b.cs])) bs.push_back(b);
+    if (ctx->d_brec_step) cudaFree(ctx->d_brec_step);
+    ctx->d_brec_step = nullptr;
+    ctx->nbrec_step = (int32_t)bs.size();
+    CK(cudaMalloc(&ctx->d_brec_step, std::max<size_t>(1, bs.size()) * sizeof(BRec)));
+    if (!bs.empty()) CK(cudaMemcpy(ctx->d_brec_step, bs.data(), bs.size() * sizeof(BRec), cudaMemcpyHostToDevice));
     return LBM_OK;
 }
 
@@ -607,10 +623,13 @@ cudaError_t launch_step_t(lbm_ctx *ctx) {
     }
     // boundary nodes (disjoint from the bulk nodes; same source and target
     // buffers) on the side stream, concurrently with the bulk launch
-    if (ctx->nbrec > 0) {
+    if (ctx->nbrec_step > 0) {
+        StepParams<T> pb = p;
+        pb.brec = ctx->d_brec_step;
+        pb.nbrec = ctx->nbrec_step;
         cudaError_t e = cudaEventRecord(ctx->ev_fork, ctx->stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
-        if (e == cudaSuccess) e = ctx->ks.boundary(&p, (ctx->nbrec + 127) / 128, 128, ctx->side);
+        if (e == cudaSuccess) e = ctx->ks.boundary(&pb, (ctx->nbrec_step + 127) / 128, 128, ctx->side);
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
         if (e != cudaSuccess) return e;
     }
@@ -627,7 +646,7 @@ cudaError_t launch_step_t(lbm_ctx *ctx) {
                                         ctx->stream);
     }
     if (e != cudaSuccess) return e;
-    if (ctx->nbrec > 0) return cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
+    if (ctx->nbrec_step > 0) return cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
     return cudaSuccess;
 }
 
@@ -644,6 +663,7 @@ lbm_status launch_init(lbm_ctx *ctx, int case_id, const FT *rho, const FT *u, co
     const CaseHost &cs = ctx->cases[case_id];
     InitParams<T, FT> ip{};
     ip.dst = ctx->pool[ctx->cur];
+    ctx->frozen_dirty = true;
     ip.flags = ctx->d_flags;
     ip.cases = static_cast<const CaseDev<T> *>(ctx->d_cases);
     ip.case_id = case_id;
@@ -697,7 +717,7 @@ void free_ctx(lbm_ctx *c) {
     drop_graphs(c);
     void *ptrs[] = {c->pool_alloc[0], c->pool_alloc[1], c->d_flags, c->d_cases, c->d_tiles, c->d_case_tile_lo,
                     c->d_tile_brec, c->d_spans, c->d_rtiles,
-                    c->d_brec, c->d_links, c->d_snap, c->d_part, c->d_red, c->d_mom, c->d_err,
+                    c->d_brec, c->d_brec_step, c->d_links, c->d_snap, c->d_part, c->d_red, c->d_mom, c->d_err,
                     c->d_motion, c->d_clock, c->d_wall_links, c->d_react, c->d_ctr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -838,6 +858,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
     }
     ctx->pool_elems = pool;
     ctx->total_nodes = nodes;
+    ctx->active.assign(ctx->cases.size(), 1);
     int64_t reach = 0;                 // farthest unwrapped pull: a slice, a row and a node
     for (const CaseHost &cs : ctx->cases)
         reach = std::max<int64_t>(reach, (int64_t)cs.cfg.nx * cs.cfg.ny + cs.cfg.nx + 1);
@@ -1083,9 +1104,15 @@ lbm_status lbm_set_wall_motion(lbm_ctx *ctx, int32_t case_id, double omega, doub
     return apply_motion(ctx, t.data());
 }
 
+static lbm_status mirror_frozen(lbm_ctx *ctx);
+
 lbm_status lbm_step(lbm_ctx *ctx, int32_t nsteps) {
     if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (nsteps < 0) return fail(ctx, LBM_EINVAL, "nsteps < 0");
+    if (nsteps > 0) {
+        const lbm_status st = mirror_frozen(ctx);
+        if (st != LBM_OK) return st;
+    }
     int32_t left = nsteps;
     while (left > 0) {
         if (ctx->graph_steps > 0 && left >= ctx->graph_steps) {
@@ -1266,6 +1293,86 @@ static constexpr uint64_t STATE_MAGIC = 0x32544154534d424cull;   // "LBMSTAT2"
 
 static size_t pool_bytes(const lbm_ctx *ctx) { return (size_t)ctx->pool_elems * ctx->elem; }
 
+// A frozen case keeps the same state in both buffers; after the current
+// buffer was written from outside the step (initialisation, a state blob, a
+// conversion, the device pointer) the frozen cases are copied over again.
+static lbm_status mirror_case(lbm_ctx *ctx, int32_t c) {
+    const CaseHost &cs = ctx->cases[c];
+    const size_t off = (size_t)cs.pop_off * ctx->elem, bytes = (size_t)cs.stride * ctx->P * ctx->elem;
+    CK(cudaMemcpyAsync(static_cast<char *>(ctx->pool[1 - ctx->cur]) + off,
+                       static_cast<char *>(ctx->pool[ctx->cur]) + off, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    return LBM_OK;
+}
+
+static lbm_status mirror_frozen(lbm_ctx *ctx) {
+    if (!ctx->frozen_dirty) return LBM_OK;
+    for (size_t c = 0; c < ctx->cases.size(); ++c)
+        if (!ctx->active[c]) {
+            const lbm_status st = mirror_case(ctx, (int32_t)c);
+            if (st != LBM_OK) return st;
+        }
+    ctx->frozen_dirty = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_active(lbm_ctx *ctx, int32_t case_id, int32_t active) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (case_id < 0 || case_id >= (int)ctx->cases.size()) return fail(ctx, LBM_EINVAL, "bad case id %d", case_id);
+    const uint8_t a = active ? 1 : 0;
+    if (ctx->active[case_id] == a) return LBM_OK;
+    if (!a && (ctx->launch.variant == 1 || ctx->launch.variant == 3))
+        return fail(ctx, LBM_EINVAL, "launch variants 1 and 3 step every case");
+    if (!a) {
+        // the frozen state in both buffers, so that it stays as it is
+        const lbm_status st = mirror_case(ctx, case_id);
+        if (st != LBM_OK) return st;
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    ctx->active[case_id] = a;
+    drop_graphs(ctx);
+    return build_tile_brec(ctx);
+}
+
+lbm_status lbm_run_each_to_steady(lbm_ctx *ctx, int64_t max_steps, int32_t interval, double tol, int64_t *steps_done,
+                                  double *residual) {
+    if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (interval < 1 || max_steps < 0) return fail(ctx, LBM_EINVAL, "bad interval / max_steps");
+    const size_t n = ctx->cases.size();
+    std::vector<double> out(n * RED_Q), last(n, INFINITY);
+    lbm_status st = lbm_check(ctx, out.data());   // baseline snapshot
+    if (st != LBM_OK) return st;
+    int64_t done = 0;
+    size_t left = 0;
+    for (size_t c = 0; c < n; ++c) left += ctx->active[c] ? 1 : 0;
+    std::vector<uint8_t> mine(n, 0);             // frozen here, reactivated at the end
+    while (done < max_steps && left > 0) {
+        const int32_t k = (int32_t)std::min<int64_t>(interval, max_steps - done);
+        if ((st = lbm_step(ctx, k)) != LBM_OK) break;
+        done += k;
+        if ((st = lbm_check(ctx, out.data())) != LBM_OK) break;
+        for (size_t c = 0; c < n && st == LBM_OK; ++c) {
+            if (!ctx->active[c]) continue;
+            const double den = out[c * RED_Q + 7];
+            last[c] = den > 0 ? std::sqrt(out[c * RED_Q + 6] / den) : 0.0;
+            if (last[c] < tol) {
+                st = lbm_set_active(ctx, (int32_t)c, 0);
+                mine[c] = 1;
+                --left;
+            }
+        }
+    }
+    for (size_t c = 0; c < n; ++c)
+        if (mine[c]) {
+            const lbm_status s2 = lbm_set_active(ctx, (int32_t)c, 1);
+            if (st == LBM_OK) st = s2;
+        }
+    double worst = 0.0;
+    for (size_t c = 0; c < n; ++c) worst = std::max(worst, last[c]);
+    if (steps_done) *steps_done = done;
+    if (residual) *residual = worst;
+    return st;
+}
+
 size_t lbm_state_bytes(const lbm_ctx *ctx) {
     return ctx ? 16 + pool_bytes(ctx) + MOTION_W * ctx->cases.size() * sizeof(double) : 0;
 }
@@ -1293,6 +1400,7 @@ lbm_status lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes) {
     if (hdr[0] != STATE_MAGIC) return fail(ctx, LBM_EINVAL, "not a state blob");
     std::vector<double> table(MOTION_W * ctx->cases.size());
     std::memcpy(table.data(), h + 16 + pool_bytes(ctx), table.size() * sizeof(double));
+    ctx->frozen_dirty = true;
     CK(cudaMemcpyAsync(ctx->pool[ctx->cur], h + 16, pool_bytes(ctx), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->steps = (int64_t)hdr[1];
@@ -1321,6 +1429,7 @@ lbm_status lbm_convert_state(lbm_ctx *dst, lbm_ctx *src) {
     const int64_t n = src->pool_elems;
     void *out = dst->pool[dst->cur];
     const void *in = src->pool[src->cur];
+    dst->frozen_dirty = true;
     switch (src->cfg.prec) {
         case LBM_FP64: e = convert_from(static_cast<const double *>(in), out, dst->cfg.prec, n, dst->stream); break;
         case LBM_FP32: e = convert_from(static_cast<const float *>(in), out, dst->cfg.prec, n, dst->stream); break;
@@ -1356,6 +1465,8 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
     if (!lp) return fail(ctx, LBM_EINVAL, "launch is NULL");
     const lbm_launch L = *lp;
     if (L.variant < 0 || L.variant > 3) return fail(ctx, LBM_EINVAL, "variant must be 0, 1, 2 or 3");
+    if ((L.variant == 1 || L.variant == 3) && std::count(ctx->active.begin(), ctx->active.end(), 0) > 0)
+        return fail(ctx, LBM_EINVAL, "variants 1 and 3 step every case: reactivate the frozen cases first");
     if ((L.variant == 0 || L.variant == 2) && (L.block < 64 || L.block > 256 || L.block % 32))
         return fail(ctx, LBM_EINVAL, "block must be 64..256 in steps of 32");
     int tile = L.block;
@@ -1431,7 +1542,7 @@ lbm_status lbm_get_launch(const lbm_ctx *ctx, lbm_launch *lp) {
 
 int32_t lbm_launches_per_step(const lbm_ctx *ctx) {
     if (!ctx) return 0;
-    return ctx->launch.variant == 1 ? 1 : 1 + (ctx->nbrec > 0 ? 1 : 0);
+    return ctx->launch.variant == 1 ? 1 : 1 + (ctx->nbrec_step > 0 ? 1 : 0);
 }
 
 lbm_status lbm_device_state(lbm_ctx *ctx, int32_t case_id, void **base, int32_t *elem_bytes, int64_t *plane_stride,
@@ -1439,6 +1550,7 @@ lbm_status lbm_device_state(lbm_ctx *ctx, int32_t case_id, void **base, int32_t 
     if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
     if (case_id < 0 || case_id >= (int)ctx->cases.size()) return fail(ctx, LBM_EINVAL, "bad case id %d", case_id);
     if (base) *base = ctx->pool[ctx->cur];
+    ctx->frozen_dirty = true;
     if (elem_bytes) *elem_bytes = (int32_t)ctx->elem;
     if (plane_stride) *plane_stride = ctx->cases[case_id].stride;
     if (case_offset) *case_offset = ctx->cases[case_id].pop_off;
@@ -1449,6 +1561,8 @@ lbm_status lbm_device_state(lbm_ctx *ctx, int32_t case_id, void **base, int32_t 
 // ----------------------------------------------------------------------------- autotuner
 lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm_launch *best_out, double *best_ms) {
     if (!ctx) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+    if (std::count(ctx->active.begin(), ctx->active.end(), 0) > 0)
+        return fail(ctx, LBM_ESTATE, "autotune times every case: reactivate the frozen cases first");
     if (iters < 1) iters = 20;
     cudaDeviceProp prop{};
     CK(cudaGetDeviceProperties(&prop, ctx->cfg.device));
@@ -1543,6 +1657,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm
     ctx->graph_steps = saved_graph;
     const lbm_status st_set = lbm_set_launch(ctx, st == LBM_OK ? &best : &before);
     if (save) {
+        ctx->frozen_dirty = true;
         cudaMemcpyAsync(ctx->pool[ctx->cur], save, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
         cudaStreamSynchronize(ctx->stream);
         cudaFree(save);

@@ -96,6 +96,9 @@ def lib():
             "lbm_check_wait": (ctypes.c_int, [vp, dp]),
             "lbm_run_to_steady": (ctypes.c_int, [vp, i64, i32, ctypes.c_double,
                                                  ctypes.POINTER(i64), dp]),
+            "lbm_set_active": (ctypes.c_int, [vp, i32, i32]),
+            "lbm_run_each_to_steady": (ctypes.c_int, [vp, i64, i32, ctypes.c_double,
+                                                      ctypes.POINTER(i64), dp]),
             "lbm_state_bytes": (ctypes.c_size_t, [vp]),
             "lbm_get_state": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
             "lbm_set_state": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
@@ -241,6 +244,18 @@ def lbm_run_to_steady(ctx, max_steps, interval, tol):
     res = ctypes.c_double()
     _check(ctx, lib().lbm_run_to_steady(ctx, int(max_steps), int(interval), float(tol),
                                         ctypes.byref(done), ctypes.byref(res)))
+    return done.value, res.value
+
+
+def lbm_set_active(ctx, case_id, active):
+    _check(ctx, lib().lbm_set_active(ctx, int(case_id), 1 if active else 0))
+
+
+def lbm_run_each_to_steady(ctx, max_steps, interval, tol):
+    done = ctypes.c_int64()
+    res = ctypes.c_double()
+    _check(ctx, lib().lbm_run_each_to_steady(ctx, int(max_steps), int(interval), float(tol),
+                                             ctypes.byref(done), ctypes.byref(res)))
     return done.value, res.value
 
 
@@ -507,6 +522,15 @@ class Solver:
 
     def run_to_steady(self, max_steps, interval=100, tol=1e-8):
         return lbm_run_to_steady(self.ctx, max_steps, interval, tol)
+
+    def set_active(self, case_id, active):
+        """Freeze (False) or resume (True) one case; see lbm_set_active."""
+        lbm_set_active(self.ctx, case_id, active)
+
+    def run_each_to_steady(self, max_steps, interval=500, tol=1e-9):
+        """Freeze each case once its own residual is below tol; returns
+        (time steps of the batch, largest last residual)."""
+        return lbm_run_each_to_steady(self.ctx, max_steps, interval, tol)
 
     def get_state(self):
         return lbm_get_state(self.ctx)
