@@ -9,6 +9,7 @@ import pytest
 from oracle import mlp as M
 from paper_2506_00907_gb300 import inputs as IN
 from paper_2506_00907_gb300 import lbm
+from paper_2506_00907_gb300 import steady as SD
 from paper_2506_00907_gb300 import surrogate as SG
 
 torch = pytest.importorskip("torch")
@@ -168,8 +169,8 @@ def test_out_of_range_case_starts_cold(trained):
 
 
 def test_combined_form_reaches_the_plain_accuracy(trained):
-    """Warm start + FP16 storage + one launch for all cases, then FP32 from
-    the FP16 residual level on, against the plain form (FP32, one case at a
+    """Warm start + one launch for all cases + BF16 storage (stochastic
+    rounding) until each case's residual levels off, then FP32, against the plain form (FP32, one case at a
     time, cold): both against the independent finite-volume solution of the
     pipe (the oracle), the combined error within 5 % of the plain one."""
     from oracle import pipe_fd as FD
@@ -177,18 +178,16 @@ def test_combined_form_reaches_the_plain_accuracy(trained):
     held = IN.pipe_draws(3, seed=2508, Ha=HA, cw=CW)
     group = SG.pipe_cases(held, N_PIPE, R_PIPE)
     _, plain = _cold(group)
-    s16 = lbm.Solver(lbm.LBM_D3Q19, lbm.LBM_FP16S, PHYS, [g[0] for g in group])
+    slo = lbm.Solver(lbm.LBM_D3Q19, lbm.LBM_BF16S, PHYS, [g[0] for g in group])
     s32 = lbm.Solver(lbm.LBM_D3Q19, lbm.LBM_FP32, PHYS, [g[0] for g in group])
     for i, g in enumerate(group):
-        s16.set_walls(i, g[1], g[2])
+        slo.set_walls(i, g[1], g[2])
         s32.set_walls(i, g[1], g[2])
-        assert SG.warm_start(s16, i, sur, g[3], (1, N_PIPE, N_PIPE), R_PIPE, held[i]["Ha"], held[i]["cw"])
-    s16.set_graph(100)
+        assert SG.warm_start(slo, i, sur, g[3], (1, N_PIPE, N_PIPE), R_PIPE, held[i]["Ha"], held[i]["cw"])
+    slo.set_graph(100)
     s32.set_graph(100)
-    s16.run_to_steady(20000, 100, 1e-4)
-    s32.convert_from(s16)
-    k, res = s32.run_to_steady(100000, 100, 1e-5)
-    assert res < 1e-5
+    rec = SD.two_precision_steady(slo, s32, 1e-5, 100000, 100)
+    assert rec["lo_steps"] > 0 and rec["hi_residual"] < 1e-5
     c = (N_PIPE - 1) / 2.0
     zz, yy = np.meshgrid(np.arange(N_PIPE) - c, np.arange(N_PIPE) - c, indexing="ij")
     for i, ((case, solid, links, info), h) in enumerate(zip(group, held)):
