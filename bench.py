@@ -43,6 +43,11 @@ GRAPH = 100                  # time steps per bench step (one graph replay + one
 CASES_PER_RANK = 64
 
 
+# 16-bit storage names: offsets from w_a phi_ref, FP16 scaled by 2^12, both
+# rounded stochastically by the step
+FP16_STORAGE = "fp16-offset-x4096-stochastic"
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -66,7 +71,7 @@ def parse():
     ap.add_argument("--train-max-steps", type=int, default=200000)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--storage", choices=["fp16s", "bf16s", "fp32", "fp64"], default=None,
-                    help="population storage (default: the workload's; bf16s rounds stochastically)")
+                    help="population storage (default: the workload's; 16-bit storages round stochastically)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--launch", default=None,
                     help="variant,block,blocks_per_sm,nodes_per_thread,stages,min_blocks (skips the autotuner)")
@@ -109,7 +114,7 @@ def workload_spec(name, rank=0, world=1):
         mine = partition(sizes, world)[rank]
         params = [allp[i] for i in mine]
         fluid = sum(p["W"] * p["W"] for p in params)
-        return dict(kind="hartmann", params=params, dim=2, planes=19, storage="fp16-offset", prec="fp16s",
+        return dict(kind="hartmann", params=params, dim=2, planes=19, storage=FP16_STORAGE, prec="fp16s",
                     fluid=fluid, cw_clamped=sum(1 for p in params if p["cw_clamped"]),
                     desc="%d batched 2D Hartmann channels%s, W~U{64..512} (W x (W+2) nodes), Ha~U[1,30], "
                          "q~U[0,1), c_w~logU[1e-3,1], seed 2506%s; D2Q9 + D2Q5 x 2 (B1, B2)" % (
@@ -123,7 +128,7 @@ def workload_spec(name, rank=0, world=1):
         fluid = 32 * int(np.sum(yy ** 2 + zz ** 2 < 62.0 ** 2))
         fp32 = name == "pipe_fp32"
         return dict(kind="pipe", params=[P], shape=shape, dim=3, planes=40, fluid=fluid,
-                    storage="fp32" if fp32 else "fp16-offset", prec="fp32" if fp32 else "fp16s", cw_clamped=0,
+                    storage="fp32" if fp32 else FP16_STORAGE, prec="fp32" if fp32 else "fp16s", cw_clamped=0,
                     desc="3D MHD pipe 32x128x128 (periodic axial), R = 62, Ha=%.2f, Shercliff c_w=%.3g; "
                          "D3Q19 + D3Q7 x 3" % (dr["Ha"], dr["cw"]))
     params = IN.reactive_grid(512, 256)
@@ -526,7 +531,7 @@ def run_ours(args):
     B.build()
     spec = workload_spec(args.workload, rank, world)
     if args.storage:
-        spec = dict(spec, prec=args.storage, storage={"fp16s": "fp16-offset", "bf16s": "bf16-offset-stochastic",
+        spec = dict(spec, prec=args.storage, storage={"fp16s": FP16_STORAGE, "bf16s": "bf16-offset-stochastic",
                                                       "fp32": "fp32", "fp64": "fp64"}[args.storage])
     stream = torch.cuda.Stream()                 # the solver's stream; every event below is recorded on it
     torch.cuda.set_stream(stream)
@@ -697,14 +702,14 @@ def steady_pipes(shape, R, n, seed):
 def steady_compare(stream, shape, R, n_cases, train_cases, train_epochs, tol, max_steps, args):
     """Wall time to the steady-state residual: the plain form (FP32 storage,
     one case per context, cold start) against the combined form (network warm
-    start, all cases in one launch per step, BF16 storage with stochastic
+    start, all cases in one launch per step, FP16 storage with stochastic
     rounding until each case's residual stops falling, then FP32 storage to the
     residual, each case leaving the launch when done).  The network is trained
     in the same run on steady fields the batched solver produces for
     `train_cases` draws at radius train-R (one axial node); generation and
     training times are reported beside, not inside, the combined time.  Every
     context is created, given its walls and autotuned before its timed region.
-    The warm-started FP32 batch without the BF16 phase is timed too, to show
+    The warm-started FP32 batch without the FP16 phase is timed too, to show
     what each part gains."""
     import torch
     from paper_2506_00907_gb300 import inputs as IN
@@ -765,7 +770,7 @@ def steady_compare(stream, shape, R, n_cases, train_cases, train_epochs, tol, ma
     warm32_s = time.perf_counter() - t
     s32.close()
     # the combined form
-    slo, launch_lo = context(lbm.LBM_BF16S, group)
+    slo, launch_lo = context(lbm.LBM_FP16S, group)
     s32, launch_hi = context(lbm.LBM_FP32, group)
     torch.cuda.synchronize()
     t = time.perf_counter()
@@ -784,7 +789,7 @@ def steady_compare(stream, shape, R, n_cases, train_cases, train_epochs, tol, ma
             "residual": tol, "max_steps": max_steps,
             "plain_s": plain_s, "combined_s": comb_s, "speedup": plain_s / comb_s,
             "plain": [{"steps": p["steps"], "residual": p["residual"], "s": p["s"]} for p in plain],
-            "combined": dict(phases, warm_started=warmed, bf16_launch=launch_lo, fp32_launch=launch_hi),
+            "combined": dict(phases, warm_started=warmed, fp16_launch=launch_lo, fp32_launch=launch_hi),
             "warm_fp32_batched": {"s": warm32_s, "steps": int(k_w), "residual": float(r_w),
                                   "speedup": plain_s / warm32_s},
             "plain_node_updates": int(sum(f * p["steps"] for f, p in zip(fluid, plain))),
@@ -793,7 +798,7 @@ def steady_compare(stream, shape, R, n_cases, train_cases, train_epochs, tol, ma
                           "loss_first": float(hist[0]), "loss_last": float(hist[-1]), "generate": gstats},
             "plain_form": "FP32 storage, one case per context, cold start, autotuned launch, CUDA graphs of %d "
                           "steps, residual every %d steps" % (GRAPH, GRAPH),
-            "combined_form": "network warm start, all cases in one launch per step, BF16 storage with stochastic "
+            "combined_form": "network warm start, all cases in one launch per step, FP16 storage with stochastic "
                              "rounding until each case's residual levels off (its minimum over 1000 steps falls by "
                              "less than 10 % against the 1000 steps before), then FP32 storage (state converted on "
                              "the GPU) to the residual; each case leaves the launch when done",
@@ -833,7 +838,7 @@ def run_steady(args):
             "ms_per_step": 1e3 * st["combined_s"], "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": desc, "residual": st["residual"],
-                       "switch": "BF16 phase ends per case when its residual levels off (minimum over 1000 "
+                       "switch": "FP16 phase ends per case when its residual levels off (minimum over 1000 "
                                  "steps > 0.9 x the minimum over the 1000 before)",
                        "l2": "state > 129 MB L2, no flush"},
             "steady": {k: v for k, v in st.items() if k != "cases"},

@@ -56,11 +56,15 @@ typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
  * value p - w_a * phi_ref (phi_ref = rho0, C0 or B0_k of the case), which keeps
  * the small deviations that carry the solution resolvable; FP16S and BF16S
  * store it in 16 bits and compute in FP32, FP32 in FP32, FP64 in FP64.
- * FP16S rounds to nearest.  BF16S rounds stochastically (the random bits are a
- * hash of the step count, the node and the plane, the same in every launch
- * variant), so that its rounding error has zero mean: at a steady state,
- * rounding to nearest repeats the same error every step and the flow
- * integrates it over its diffusion time. */
+ * FP16S stores the shifted value times 2^12, so that offsets down to 1.5e-8
+ * keep FP16's 11-bit significand (|p - w_a phi_ref| must stay below 16).
+ * FP16S and BF16S round the step's results stochastically (the hardware's
+ * conversion with random bits; the bits are a hash of the step count, the
+ * node and the pair of planes, the same in every launch variant), so that the
+ * rounding error has zero mean: rounding to nearest repeats the same error
+ * every step at a steady state, which the flow integrates over its diffusion
+ * time, and loses every change smaller than half a spacing, which stalls slow
+ * transients.  Initialisation and lbm_convert_state round to nearest. */
 typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16S = 2, LBM_BF16S = 3 } lbm_prec;
 
 /* physics mask: LBM_FLOW is required */
@@ -331,7 +335,7 @@ int64_t lbm_steps_done(const lbm_ctx *ctx);
  *              tile, up to 64); min_blocks selects the register budget the
  *              kernel was compiled for, as resident 256-thread blocks per SM:
  *              2D 4, 5 or 6, 3D 2, 3 or 4 (1 = the first).
- *   variant 1: bulk-copy loads and stores (FP32 and FP16S storage, one
+ *   variant 1: bulk-copy loads and stores (FP32 storage, one
  *              concentration species at most):
  *              persistent blocks of 256 threads copy each plane's source
  *              window of the next tile into shared memory with cp.async.bulk
@@ -346,7 +350,7 @@ int64_t lbm_steps_done(const lbm_ctx *ctx);
  *              address plus a per-case offset per plane, and only nodes on a
  *              periodic edge reloading the planes whose source wraps; 16-bit
  *              values stay packed two to a register until the collision.
- *   variant 3: shared-memory ring (FP32 and FP16S storage, one concentration
+ *   variant 3: shared-memory ring (FP32 storage, one concentration
  *              species at most): persistent
  *              blocks of one producer warp and 8 consumer warps.  The
  *              producer copies each plane's source window of the block's
@@ -399,7 +403,7 @@ int32_t lbm_launches_per_step(const lbm_ctx *ctx);
 /* Device storage of the current populations (for zero-copy inspection):
  * base pointer, bytes per population, plane stride in elements and element
  * offset of case_id's first plane.  Planes hold the relaxed populations
- * shifted by w_a * phi_ref.  Errors: LBM_EINVAL. */
+ * shifted by w_a * phi_ref (FP16S: times 2^12).  Errors: LBM_EINVAL. */
 lbm_status lbm_device_state(lbm_ctx *ctx, int32_t case_id, void **base, int32_t *elem_bytes,
                             int64_t *plane_stride, int64_t *case_offset, int32_t *planes);
 

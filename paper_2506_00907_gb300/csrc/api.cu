@@ -756,11 +756,13 @@ ReactDev<T> react_dev(const lbm_reaction *r, int n) {
 namespace {
 __device__ __forceinline__ double cv_load(const double *p, int64_t i) { return p[i]; }
 __device__ __forceinline__ double cv_load(const float *p, int64_t i) { return (double)p[i]; }
-__device__ __forceinline__ double cv_load(const __half *p, int64_t i) { return (double)__half2float(p[i]); }
+__device__ __forceinline__ double cv_load(const __half *p, int64_t i) {
+    return (double)__half2float(p[i]) * (double)H_UNSCALE;
+}
 __device__ __forceinline__ double cv_load(const __nv_bfloat16 *p, int64_t i) { return (double)__bfloat162float(p[i]); }
 __device__ __forceinline__ void cv_store(double *p, int64_t i, double v) { p[i] = v; }
 __device__ __forceinline__ void cv_store(float *p, int64_t i, double v) { p[i] = (float)v; }
-__device__ __forceinline__ void cv_store(__half *p, int64_t i, double v) { p[i] = __double2half(v); }
+__device__ __forceinline__ void cv_store(__half *p, int64_t i, double v) { p[i] = __double2half(v * (double)H_SCALE); }
 __device__ __forceinline__ void cv_store(__nv_bfloat16 *p, int64_t i, double v) { p[i] = __double2bfloat16(v); }
 
 // Both pools hold p - w*phi_ref with the same references (same cases), so a
@@ -1484,7 +1486,7 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
         tile = L.block * L.nodes_per_thread;
     } else if (L.variant == 3) {
         if (ctx->dbl || !ctx->ks.ring)
-            return fail(ctx, LBM_EINVAL, "the ring variant serves FP32 and 16-bit storage of one concentration at most");
+            return fail(ctx, LBM_EINVAL, "the ring variant serves FP32 storage of one concentration at most");
         if (L.stages < 2 || L.stages > RING_MAX_NS)
             return fail(ctx, LBM_EINVAL, "ring variant: stages must be 2..%d", RING_MAX_NS);
         if (L.blocks_per_sm < 0 || L.blocks_per_sm > 64) return fail(ctx, LBM_EINVAL, "blocks per SM must be 0..64");
@@ -1510,7 +1512,7 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, const lbm_launch *lp) {
             return fail(ctx, LBM_EINVAL, "bulk-copy variant: (block = tile nodes, min_blocks) must be one of "
                                          "(128, 2), (256, 2), (256, 4), (512, 1), (512, 2)");
         if (ctx->dbl || !ctx->ks.step_bulk[idx])
-            return fail(ctx, LBM_EINVAL, "the bulk-copy variant serves FP32 and 16-bit storage of one concentration at most");
+            return fail(ctx, LBM_EINVAL, "the bulk-copy variant serves FP32 storage of one concentration at most");
         tile = L.block;
         const size_t smem = (size_t)bulk_layout_bytes(ctx->P, tile, (int)ctx->elem, BULK_NS[idx]);
         int maxsm = 0;

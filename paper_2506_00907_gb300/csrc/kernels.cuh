@@ -43,11 +43,17 @@ template <> struct Codec<float> {
     LBM_DEV static float ld_shared(const float *p) { return *p; }
     LBM_DEV static void st(float *p, float v) { *p = v; }
 };
+// FP16 storage holds the offsets times 2^12 (exact: a power of two), so that
+// offsets down to 1.5e-8 keep FP16's full 11-bit significand instead of
+// falling into its subnormal range below 6.1e-5 (the induced magnetic field
+// and the second-order parts of f^eq are that small); |offset| < 16 fits.
+constexpr float H_SCALE = 4096.0f;
+constexpr float H_UNSCALE = 1.0f / 4096.0f;
 template <> struct Codec<__half> {
     using T = float;
-    LBM_DEV static float ld(const __half *p) { return __half2float(__ldg(p)); }
-    LBM_DEV static float ld_shared(const __half *p) { return __half2float(*p); }
-    LBM_DEV static void st(__half *p, float v) { *p = __float2half_rn(v); }
+    LBM_DEV static float ld(const __half *p) { return __half2float(__ldg(p)) * H_UNSCALE; }
+    LBM_DEV static float ld_shared(const __half *p) { return __half2float(*p) * H_UNSCALE; }
+    LBM_DEV static void st(__half *p, float v) { *p = __float2half_rn(v * H_SCALE); }
 };
 template <> struct Codec<__nv_bfloat16> {
     using T = float;
@@ -58,20 +64,25 @@ template <> struct Codec<__nv_bfloat16> {
 
 LBM_DEV uint32_t fast_div(uint32_t n, FastDiv d) { return (__umulhi(n, d.m) + n) >> d.s; }
 
-// ------------------------------------------------------------------ stochastic rounding (BF16 storage)
-// BF16 storage rounds stochastically: a value is rounded up in magnitude with
-// the probability of its distance to the lower neighbour, so that the
-// rounding error has zero mean.  Round to nearest, at a steady state, makes
-// the same error every step, which the flow integrates over its diffusion
-// time; stochastic rounding (a published method: the random bits below the
-// kept mantissa are added before truncation) removes that bias.  The 16
-// random bits of (step, node, plane) come from a multiply-xorshift integer
-// hash of the step and the node (constants of Wellons' "lowbias32"), then one
-// multiplication per pair of planes, so every launch variant draws the same
-// bits for the same population.  The addition saturates in signed 32-bit
-// arithmetic, so a NaN (0x7fffffff on the GPU) stays a NaN.
+// ------------------------------------------------------------------ stochastic rounding (16-bit storage)
+// 16-bit storage rounds stochastically: a value is rounded up in magnitude
+// with the probability of its distance to the lower neighbour (in units of
+// their spacing), so that the rounding error has zero mean.  Round to nearest,
+// at a steady state, makes the same error every step, which the flow
+// integrates over its diffusion time; and a change smaller than half a
+// spacing per step is lost every step, so slow transients stall.  The
+// conversion instruction that takes random bits (cvt.rs, sm_100a and later)
+// rounds two FP32 values to an FP16 or BF16 pair, each lane from its own half
+// of a 32-bit random word.  Planes are rounded in pairs: a direction and its
+// opposite (the member whose leading component is +1 in the low lane), rest
+// planes alone in the low lane.  The random word of (step, node, pair) comes
+// from a multiply-xorshift integer hash of the step and the node (constants
+// of Wellons' "lowbias32"), then one multiplication by a constant of the
+// pair's low plane, so every launch variant draws the same bits for the same
+// population in the same lane.
 template <class S> struct Rounding { static constexpr bool SR = false; };
 template <> struct Rounding<__nv_bfloat16> { static constexpr bool SR = true; };
+template <> struct Rounding<__half> { static constexpr bool SR = true; };
 
 LBM_DEV uint32_t sr_node_hash(uint32_t step, uint32_t node) {
     uint32_t x = node * 0x9E3779B1u ^ step * 0x85EBCA77u;
@@ -82,24 +93,41 @@ LBM_DEV uint32_t sr_node_hash(uint32_t step, uint32_t node) {
     x ^= x >> 16;
     return x;
 }
-// 16 random bits of plane q from the node's hash
-LBM_DEV uint32_t sr_plane_bits(uint32_t h, int q) {
-    const uint32_t r = h * (0x2545F491u + 0x9E3779B9u * (uint32_t)(q >> 1));
-    return (q & 1) ? (r >> 16) : (r & 0xffffu);
-}
-LBM_DEV uint32_t add_sat(uint32_t a, uint32_t b) {
+// the random word of the pair whose low plane is q, at the node whose hash is h
+LBM_DEV uint32_t sr_word(uint32_t h, int q) { return h * (0x2545F491u + 0x9E3779B9u * (uint32_t)q); }
+
+// (lo, hi) rounded stochastically to one 32-bit word of two 16-bit values
+template <class S> LBM_DEV uint32_t sr_pack(float lo, float hi, uint32_t r);
+template <> LBM_DEV uint32_t sr_pack<__half>(float lo, float hi, uint32_t r) {
     uint32_t d;
-    asm("add.sat.s32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi * H_SCALE), "f"(lo * H_SCALE), "r"(r));
     return d;
 }
-// stores population q of a node whose hash is h
+template <> LBM_DEV uint32_t sr_pack<__nv_bfloat16>(float lo, float hi, uint32_t r) {
+    uint32_t d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+    return d;
+}
+template <class S> LBM_DEV void store_bits(S *p, uint32_t w) { *reinterpret_cast<unsigned short *>(p) = (unsigned short)w; }
+
+// stores rest plane q of a node whose hash is h
 template <class S>
 LBM_DEV void store_pop(S *p, float v, uint32_t h, int q) {
-    if constexpr (Rounding<S>::SR) {
-        const uint32_t b = add_sat(__float_as_uint(v), sr_plane_bits(h, q));
-        *reinterpret_cast<unsigned short *>(p) = (unsigned short)(b >> 16);
-    } else {
+    if constexpr (Rounding<S>::SR)
+        store_bits(p, sr_pack<S>(v, 0.0f, sr_word(h, q)));
+    else
         Codec<S>::st(p, v);
+}
+// stores the pair of planes qp (low lane) and its opposite (high lane)
+template <class S, class V>
+LBM_DEV void store_pop_pair(S *pp, S *pm, V vp, V vm, uint32_t h, int qp) {
+    if constexpr (Rounding<S>::SR) {
+        const uint32_t d = sr_pack<S>(vp, vm, sr_word(h, qp));
+        store_bits(pp, d);
+        store_bits(pm, d >> 16);
+    } else {
+        Codec<S>::st(pp, vp);
+        Codec<S>::st(pm, vm);
     }
 }
 template <class S>
@@ -264,9 +292,11 @@ LBM_HD constexpr int lead_sign(int a) { return L::ex(a) ? L::ex(a) : (L::ey(a) ?
 
 // The collision over accessors: getm(q) reads plane q for the moments,
 // getr(q) reads it again for its relaxation, put(q, v) takes the relaxed
-// value.  Every plane is read by getr once, before put writes it.
-template <class PL, int NC, bool HG, class V, class T, class GetM, class GetR, class Put>
-LBM_DEV void collide_g(GetM &&getm, GetR &&getr, Put &&put, const CaseDev<T> &c) {
+// value of a rest plane and put2(qp, qm, vp, vm) those of a direction qp
+// (leading component +1) and its opposite qm.  Every plane is read by getr
+// once, before it is written.
+template <class PL, int NC, bool HG, class V, class T, class GetM, class GetR, class Put, class Put2>
+LBM_DEV void collide_g(GetM &&getm, GetR &&getr, Put &&put, Put2 &&put2, const CaseDev<T> &c) {
     using F = typename PL::F;
     using M = typename PL::M;
     constexpr int QF = PL::QF, QM = PL::QM, NB = PL::NB, DIM = F::DIM;
@@ -355,8 +385,8 @@ LBM_DEV void collide_g(GetM &&getm, GetR &&getr, Put &&put, const CaseDev<T> &c)
         }
         const V w = V(T(F::w(ap)));
         const V we = even * w, wo = odd * w;
-        put(ap, fma_v(getr(ap), omc, we + wo));
-        put(am, fma_v(getr(am), omc, we - wo));
+        const V vp = fma_v(getr(ap), omc, we + wo);
+        put2(ap, am, vp, fma_v(getr(am), omc, we - wo));
     }
     const T w0 = T(M::w(0)), w1 = T(M::w(1));
 #pragma unroll
@@ -375,8 +405,8 @@ LBM_DEV void collide_g(GetM &&getm, GetR &&getr, Put &&put, const CaseDev<T> &c)
             const int ap = lead_sign<M>(a) > 0 ? a : b, am = lead_sign<M>(a) > 0 ? b : a;
             const int i = M::ex(a) ? 0 : (M::ey(a) ? 1 : 2);
             const V od = f4 * u[i];
-            put(h0 + ap, fma_v(getr(h0 + ap), ohc, ev + od));
-            put(h0 + am, fma_v(getr(h0 + am), ohc, ev - od));
+            const V vp = fma_v(getr(h0 + ap), ohc, ev + od);
+            put2(h0 + ap, h0 + am, vp, fma_v(getr(h0 + am), ohc, ev - od));
         }
     }
     if constexpr (HG) {
@@ -395,12 +425,12 @@ LBM_DEV void collide_g(GetM &&getm, GetR &&getr, Put &&put, const CaseDev<T> &c)
                 const int ap = lead_sign<M>(a) > 0 ? a : b, am = lead_sign<M>(a) > 0 ? b : a;
                 const int i = M::ex(a) ? 0 : (M::ey(a) ? 1 : 2);
                 if (i == k) {                                        // u_k B_k - B_k u_k = 0
-                    put(q0 + ap, fma_v(getr(q0 + ap), ogc, ev));
-                    put(q0 + am, fma_v(getr(q0 + am), ogc, ev));
+                    const V vp = fma_v(getr(q0 + ap), ogc, ev);
+                    put2(q0 + ap, q0 + am, vp, fma_v(getr(q0 + am), ogc, ev));
                 } else {
                     const V od = og4 * fma_v(u[i], B[k], nB[i] * u[k]);
-                    put(q0 + ap, fma_v(getr(q0 + ap), ogc, ev + od));
-                    put(q0 + am, fma_v(getr(q0 + am), ogc, ev - od));
+                    const V vp = fma_v(getr(q0 + ap), ogc, ev + od);
+                    put2(q0 + ap, q0 + am, vp, fma_v(getr(q0 + am), ogc, ev - od));
                 }
             }
         }
@@ -412,7 +442,11 @@ template <class PL, int NC, bool HG, class V, class T>
 LBM_DEV void collide_v(V (&p)[PL::P], const CaseDev<T> &c) {
     auto get = [&](int q) -> V { return p[q]; };
     auto put = [&](int q, V v) { p[q] = v; };
-    collide_g<PL, NC, HG, V, T>(get, get, put, c);
+    auto put2 = [&](int qp, int qm, V vp, V vm) {
+        p[qp] = vp;
+        p[qm] = vm;
+    };
+    collide_g<PL, NC, HG, V, T>(get, get, put, put2, c);
 }
 
 // one node: FP64 as is, FP32 through F1
@@ -580,7 +614,7 @@ template <> struct Pack16<__half> {
     LBM_DEV static uint32_t raw(const __half *p) { return __ldg(reinterpret_cast<const unsigned short *>(p)); }
     LBM_DEV static float get(uint32_t w, int hi) {
         const __half2 h = *reinterpret_cast<const __half2 *>(&w);
-        return hi ? __high2float(h) : __low2float(h);
+        return (hi ? __high2float(h) : __low2float(h)) * H_UNSCALE;
     }
 };
 template <> struct Pack16<__nv_bfloat16> {
@@ -589,6 +623,41 @@ template <> struct Pack16<__nv_bfloat16> {
     }
     LBM_DEV static float get(uint32_t w, int hi) { return __uint_as_float(hi ? (w & 0xffff0000u) : (w << 16)); }
 };
+
+// Stores every plane of a node in the pairs of collide_g: rest planes alone,
+// a direction with its opposite (the same lanes and random words as the
+// collision's own put and put2).
+template <class PL, int NC, bool HG, class S, class V>
+LBM_DEV void store_node(S *dp, int os, const V (&p)[PL::P], uint32_t h) {
+    using F = typename PL::F;
+    using M = typename PL::M;
+    auto pairs = [&](auto L, int q0, int nq) {
+        using LL = decltype(L);
+#pragma unroll
+        for (int a = 1; a < nq; ++a) {
+            const int b = LL::opp(a);
+            if (b < a) continue;
+            const int ap = lead_sign<LL>(a) > 0 ? a : b, am = lead_sign<LL>(a) > 0 ? b : a;
+            store_pop_pair<S>(dp + (q0 + ap) * os, dp + (q0 + am) * os, p[q0 + ap], p[q0 + am], h, q0 + ap);
+        }
+    };
+    store_pop<S>(dp, p[0], h, 0);
+    pairs(F{}, 0, PL::QF);
+#pragma unroll
+    for (int sp = 0; sp < NC; ++sp) {
+        const int h0 = PL::H0 + sp * PL::QM;
+        store_pop<S>(dp + h0 * os, p[h0], h, h0);
+        pairs(M{}, h0, PL::QM);
+    }
+    if constexpr (HG) {
+#pragma unroll
+        for (int k = 0; k < PL::NB; ++k) {
+            const int q0 = PL::G0 + k * PL::QM;
+            store_pop<S>(dp + q0 * os, p[q0], h, q0);
+            pairs(M{}, q0, PL::QM);
+        }
+    }
+}
 
 // ------------------------------------------------------------------ fused step
 // One node: pull, (boundary nodes: wall links [lo, hi)), collide, store
@@ -644,7 +713,8 @@ LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDe
         };
         const uint32_t h = Rounding<S>::SR ? sr_node_hash(*prm.ctr_rd, (uint32_t)(c.node_off + n)) : 0u;
         auto put = [&](int q, F1 v) { store_pop<S>(dp + q * os, v.v, h, q); };
-        collide_g<PL, NC, HG, F1, float>(getm, getr, put, c);
+        auto put2 = [&](int qp, int qm, F1 vp, F1 vm) { store_pop_pair<S>(dp + qp * os, dp + qm * os, vp.v, vm.v, h, qp); };
+        collide_g<PL, NC, HG, F1, float>(getm, getr, put, put2, c);
         return;
     }
     T p[P];
@@ -654,8 +724,7 @@ LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDe
     if constexpr (LINKS) apply_links<PL, S, T, LCH>(p, prm, c, src, lo, hi);
     collide<PL, NC, HG, T>(p, c);
     const uint32_t h = Rounding<S>::SR ? sr_node_hash(*prm.ctr_rd, (uint32_t)(c.node_off + n)) : 0u;
-#pragma unroll
-    for (int q = 0; q < P; ++q) store_pop<S>(dp + q * os, p[q], h, q);
+    store_node<PL, NC, HG, S>(dp, os, p, h);
 }
 
 // Bulk nodes (fluid, no wall link) over the span list: span t holds nodes
@@ -697,7 +766,7 @@ template <class S> struct Raw16 {
 template <> LBM_DEV float Raw16<__half>::get(uint32_t w, int hi) {
     __half2 h;
     memcpy(&h, &w, 4);
-    return hi ? __high2float(h) : __low2float(h);
+    return (hi ? __high2float(h) : __low2float(h)) * H_UNSCALE;
 }
 template <> LBM_DEV float Raw16<__nv_bfloat16>::get(uint32_t w, int hi) {
     return __uint_as_float(hi ? (w & 0xffff0000u) : (w << 16));
@@ -763,7 +832,8 @@ LBM_DEV void step_node_unwrapped(const StepParams<typename Codec<S>::T> &prm, co
         };
         const uint32_t h = Rounding<S>::SR ? sr_node_hash(*prm.ctr_rd, (uint32_t)(c.node_off + n)) : 0u;
         auto put = [&](int q, F1 v) { store_pop<S>(dp + q * st, v.v, h, q); };
-        collide_g<PL, NC, HG, F1, float>(getm, getr, put, c);
+        auto put2 = [&](int qp, int qm, F1 vp, F1 vm) { store_pop_pair<S>(dp + qp * st, dp + qm * st, vp.v, vm.v, h, qp); };
+        collide_g<PL, NC, HG, F1, float>(getm, getr, put, put2, c);
     } else {
         collide<PL, NC, HG, T>(p, c);
 #pragma unroll

@@ -89,8 +89,13 @@ template <> struct PairMem<float> {
     LBM_DEV static void st(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
 };
 template <> struct PairMem<__half> {
-    LBM_DEV static float2 lds(const __half *p) { return __half22float2(*reinterpret_cast<const __half2 *>(p)); }
-    LBM_DEV static void st(__half *p, float2 v) { *reinterpret_cast<__half2 *>(p) = __float22half2_rn(v); }
+    LBM_DEV static float2 lds(const __half *p) {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2 *>(p));
+        return make_float2(v.x * H_UNSCALE, v.y * H_UNSCALE);
+    }
+    LBM_DEV static void st(__half *p, float2 v) {
+        *reinterpret_cast<__half2 *>(p) = __float22half2_rn(make_float2(v.x * H_SCALE, v.y * H_SCALE));
+    }
 };
 template <> struct PairMem<__nv_bfloat16> {
     LBM_DEV static float2 lds(const __nv_bfloat16 *p) {

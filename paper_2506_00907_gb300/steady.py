@@ -1,8 +1,8 @@
 """Steady runs in two storage precisions (not part of the paper's method: it
 changes how long the method runs, not its arithmetic).
 
-A batch of cases first steps with 16-bit storage (BF16S: stochastic rounding,
-so the mean field follows the exact dynamics while each value carries zero-mean
+A batch of cases first steps with 16-bit storage (stochastic rounding, so the
+mean field follows the exact dynamics while each value carries zero-mean
 rounding noise), each case until its residual stops falling, which is where the
 noise takes over; the state is then converted on the GPU to FP32 storage and
 every case runs on to the residual `tol`.  Cases leave the launch
@@ -26,8 +26,9 @@ def run_to_plateau(sol, max_steps, interval=100, window=10, ratio=0.9, tol=0.0):
     levels off, or is below `tol`, or max_steps are done: levelled off means
     that the smallest residual of the last `window` checks is above `ratio`
     times the smallest of the `window` checks before them (minima, because the
-    residual of a warm start oscillates with its acoustic transient); each case is frozen when it
-    stops, and all cases the call froze are resumed before it returns.
+    residual of a warm start oscillates with its acoustic transient); each
+    case is frozen when it stops, and all cases the call froze are resumed
+    before it returns.
     Every case of `sol` is taken to be active on entry.  Returns (time
     steps of the batch, last residual of each case)."""
     n = sol.check().shape[0]

@@ -1,7 +1,8 @@
 """Changing the storage precision of a running state (lbm_convert_state):
 FP64 -> FP32 keeps the FP32 parity bar against the FP64 oracle afterwards,
 FP32 -> FP16 -> FP32 is exactly the element-wise rounding of the stored
-values, and mismatched contexts are rejected."""
+values (FP16 storage holds them times 2^12, rounded to nearest on
+conversion), and mismatched contexts are rejected."""
 import numpy as np
 import pytest
 
@@ -60,7 +61,8 @@ def test_fp32_fp16_fp32_round_trip_is_elementwise_rounding():
     for q in range(planes):
         a = s0[off + q * stride: off + q * stride + N]
         b = s1[off + q * stride: off + q * stride + N]
-        assert np.array_equal(a.astype(np.float16).astype(np.float32), b), q
+        want = (a * np.float32(4096)).astype(np.float16).astype(np.float32) / np.float32(4096)
+        assert np.array_equal(want, b), q
     assert back.steps == f32.steps
 
 

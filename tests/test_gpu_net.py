@@ -169,7 +169,7 @@ def test_out_of_range_case_starts_cold(trained):
 
 
 def test_combined_form_reaches_the_plain_accuracy(trained):
-    """Warm start + one launch for all cases + BF16 storage (stochastic
+    """Warm start + one launch for all cases + FP16 storage (stochastic
     rounding) until each case's residual levels off, then FP32, against the plain form (FP32, one case at a
     time, cold): both against the independent finite-volume solution of the
     pipe (the oracle), the combined error within 5 % of the plain one."""
@@ -178,7 +178,7 @@ def test_combined_form_reaches_the_plain_accuracy(trained):
     held = IN.pipe_draws(3, seed=2508, Ha=HA, cw=CW)
     group = SG.pipe_cases(held, N_PIPE, R_PIPE)
     _, plain = _cold(group)
-    slo = lbm.Solver(lbm.LBM_D3Q19, lbm.LBM_BF16S, PHYS, [g[0] for g in group])
+    slo = lbm.Solver(lbm.LBM_D3Q19, lbm.LBM_FP16S, PHYS, [g[0] for g in group])
     s32 = lbm.Solver(lbm.LBM_D3Q19, lbm.LBM_FP32, PHYS, [g[0] for g in group])
     for i, g in enumerate(group):
         slo.set_walls(i, g[1], g[2])
