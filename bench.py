@@ -799,8 +799,8 @@ def steady_compare(stream, shape, R, n_cases, train_cases, train_epochs, tol, ma
             "plain_form": "FP32 storage, one case per context, cold start, autotuned launch, CUDA graphs of %d "
                           "steps, residual every %d steps" % (GRAPH, GRAPH),
             "combined_form": "network warm start, all cases in one launch per step, FP16 storage with stochastic "
-                             "rounding until each case's residual levels off (its minimum over 1000 steps falls by "
-                             "less than 10 % against the 1000 steps before), then FP32 storage (state converted on "
+                             "rounding until each case's residual levels off (its mean over 2000 steps falls by "
+                             "less than 10 % against the 2000 steps before), then FP32 storage (state converted on "
                              "the GPU) to the residual; each case leaves the launch when done",
             "cases": cases}
 
@@ -838,8 +838,8 @@ def run_steady(args):
             "ms_per_step": 1e3 * st["combined_s"], "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": desc, "residual": st["residual"],
-                       "switch": "FP16 phase ends per case when its residual levels off (minimum over 1000 "
-                                 "steps > 0.9 x the minimum over the 1000 before)",
+                       "switch": "FP16 phase ends per case when its residual levels off (mean over 2000 "
+                                 "steps > 0.9 x the mean over the 2000 before)",
                        "l2": "state > 129 MB L2, no flush"},
             "steady": {k: v for k, v in st.items() if k != "cases"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm"], "unit": "GB/s",
