@@ -168,7 +168,7 @@ STEP_SOURCES = ("lattice.cuh", "types.cuh", "kernels.cuh", "kernels_bulk.cuh", "
 STEP_KERNEL = {
     0: "k_step (bulk nodes) + k_boundary (wall-link nodes)",
     1: "k_step_bulk (bulk-copy loads and stores, boundary nodes included)",
-    2: "k_step_pair (x-adjacent node pairs, packed FP32) + k_boundary (wall-link nodes)",
+    2: "k_step_unwrapped (pulls unwrapped, edge nodes reload wrapped planes) + k_boundary (wall-link nodes)",
     3: "k_step_ring (producer warp, bulk-copy ring of stages, consumer warps) + k_boundary (wall-link nodes)"}
 
 

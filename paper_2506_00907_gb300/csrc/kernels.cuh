@@ -34,12 +34,14 @@ template <class S> struct Codec;
 template <> struct Codec<double> {
     using T = double;
     LBM_DEV static double ld(const double *p) { return __ldg(p); }
+    LBM_DEV static double ld_raw(const double *p) { return __ldg(p); }
     LBM_DEV static double ld_shared(const double *p) { return *p; }
     LBM_DEV static void st(double *p, double v) { *p = v; }
 };
 template <> struct Codec<float> {
     using T = float;
     LBM_DEV static float ld(const float *p) { return __ldg(p); }
+    LBM_DEV static float ld_raw(const float *p) { return __ldg(p); }
     LBM_DEV static float ld_shared(const float *p) { return *p; }
     LBM_DEV static void st(float *p, float v) { *p = v; }
 };
@@ -49,15 +51,23 @@ template <> struct Codec<float> {
 // and the second-order parts of f^eq are that small); |offset| < 16 fits.
 constexpr float H_SCALE = 4096.0f;
 constexpr float H_UNSCALE = 1.0f / 4096.0f;
+// log2 of the factor between stored and true offsets.  The bulk-node paths
+// relax the stored values as they are, with the factor folded into the
+// collision's constants (a power of two: the results are exactly those of
+// the unscaled arithmetic, scaled).
+template <class S> struct StoreScale { static constexpr int L2 = 0; };
+template <> struct StoreScale<__half> { static constexpr int L2 = 12; };
 template <> struct Codec<__half> {
     using T = float;
     LBM_DEV static float ld(const __half *p) { return __half2float(__ldg(p)) * H_UNSCALE; }
+    LBM_DEV static float ld_raw(const __half *p) { return __half2float(__ldg(p)); }       // as stored
     LBM_DEV static float ld_shared(const __half *p) { return __half2float(*p) * H_UNSCALE; }
     LBM_DEV static void st(__half *p, float v) { *p = __float2half_rn(v * H_SCALE); }
 };
 template <> struct Codec<__nv_bfloat16> {
     using T = float;
     LBM_DEV static float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    LBM_DEV static float ld_raw(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
     LBM_DEV static float ld_shared(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     LBM_DEV static void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
@@ -97,10 +107,11 @@ LBM_DEV uint32_t sr_node_hash(uint32_t step, uint32_t node) {
 LBM_DEV uint32_t sr_word(uint32_t h, int q) { return h * (0x2545F491u + 0x9E3779B9u * (uint32_t)q); }
 
 // (lo, hi) rounded stochastically to one 32-bit word of two 16-bit values
+// (values as stored: FP16 ones already scaled)
 template <class S> LBM_DEV uint32_t sr_pack(float lo, float hi, uint32_t r);
 template <> LBM_DEV uint32_t sr_pack<__half>(float lo, float hi, uint32_t r) {
     uint32_t d;
-    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi * H_SCALE), "f"(lo * H_SCALE), "r"(r));
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
     return d;
 }
 template <> LBM_DEV uint32_t sr_pack<__nv_bfloat16>(float lo, float hi, uint32_t r) {
@@ -110,19 +121,25 @@ template <> LBM_DEV uint32_t sr_pack<__nv_bfloat16>(float lo, float hi, uint32_t
 }
 template <class S> LBM_DEV void store_bits(S *p, uint32_t w) { *reinterpret_cast<unsigned short *>(p) = (unsigned short)w; }
 
-// stores rest plane q of a node whose hash is h
-template <class S>
+// the value as stored (SCALED: it already is)
+template <class S, bool SCALED>
+LBM_DEV float to_stored(float v) {
+    if constexpr (StoreScale<S>::L2 != 0 && !SCALED) return v * float(1 << StoreScale<S>::L2);
+    else return v;
+}
+// stores rest plane q of a node whose hash is h (SCALED: v is a stored value)
+template <class S, bool SCALED = false>
 LBM_DEV void store_pop(S *p, float v, uint32_t h, int q) {
     if constexpr (Rounding<S>::SR)
-        store_bits(p, sr_pack<S>(v, 0.0f, sr_word(h, q)));
+        store_bits(p, sr_pack<S>(to_stored<S, SCALED>(v), 0.0f, sr_word(h, q)));
     else
         Codec<S>::st(p, v);
 }
 // stores the pair of planes qp (low lane) and its opposite (high lane)
-template <class S, class V>
+template <class S, bool SCALED = false, class V>
 LBM_DEV void store_pop_pair(S *pp, S *pm, V vp, V vm, uint32_t h, int qp) {
     if constexpr (Rounding<S>::SR) {
-        const uint32_t d = sr_pack<S>(vp, vm, sr_word(h, qp));
+        const uint32_t d = sr_pack<S>(to_stored<S, SCALED>(vp), to_stored<S, SCALED>(vm), sr_word(h, qp));
         store_bits(pp, d);
         store_bits(pm, d >> 16);
     } else {
@@ -130,7 +147,7 @@ LBM_DEV void store_pop_pair(S *pp, S *pm, V vp, V vm, uint32_t h, int qp) {
         Codec<S>::st(pm, vm);
     }
 }
-template <class S>
+template <class S, bool SCALED = false>
 LBM_DEV void store_pop(S *p, double v, uint32_t, int) { Codec<S>::st(p, v); }
 
 LBM_DEV float fmaf_t(float a, float b, float c) { return fmaf(a, b, c); }
@@ -295,15 +312,23 @@ LBM_HD constexpr int lead_sign(int a) { return L::ex(a) ? L::ex(a) : (L::ey(a) ?
 // value of a rest plane and put2(qp, qm, vp, vm) those of a direction qp
 // (leading component +1) and its opposite qm.  Every plane is read by getr
 // once, before it is written.
-template <class PL, int NC, bool HG, class V, class T, class GetM, class GetR, class Put, class Put2>
+// With SL2 > 0 the planes hold the offsets times 2^SL2: the moments are
+// scaled back once, and the relaxed values come out scaled through the
+// weights (exact: powers of two).
+template <class PL, int NC, bool HG, class V, class T, int SL2 = 0, class GetM, class GetR, class Put, class Put2>
 LBM_DEV void collide_g(GetM &&getm, GetR &&getr, Put &&put, Put2 &&put2, const CaseDev<T> &c) {
     using F = typename PL::F;
     using M = typename PL::M;
     constexpr int QF = PL::QF, QM = PL::QM, NB = PL::NB, DIM = F::DIM;
-    const V drho = plane_sum<V>(getm, 0, QF);
+    constexpr double SC = double(1 << SL2);
+    auto unscale = [](V v) -> V {
+        if constexpr (SL2 != 0) return v * V(T(1.0 / SC));
+        else return v;
+    };
+    const V drho = unscale(plane_sum<V>(getm, 0, QF));
     V j[3];
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) j[i] = axis_sum<F, QF, V>(getm, 0, i);
+    for (int i = 0; i < DIM; ++i) j[i] = unscale(axis_sum<F, QF, V>(getm, 0, i));
     const V rho = drho + V(c.ref_rho);
     const V inv = recip_v(rho);
     const T acc[3] = {c.ax, c.ay, c.az};
@@ -318,7 +343,7 @@ LBM_DEV void collide_g(GetM &&getm, GetR &&getr, Put &&put, Put2 &&put2, const C
     if constexpr (HG) {
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
-            dB[k] = plane_sum<V>(getm, PL::G0 + k * QM, QM);
+            dB[k] = unscale(plane_sum<V>(getm, PL::G0 + k * QM, QM));
             B[k] = dB[k] + V(c.ref_B[k]);
             nB[k] = neg_v(B[k]);
         }
@@ -358,7 +383,7 @@ LBM_DEV void collide_g(GetM &&getm, GetR &&getr, Put &&put, Put2 &&put2, const C
         Tc[pr] = fma_v(t, V(om), V(g) * fma_v(u[i], Fo[k], Fo[i] * u[k])) * V(T(9));
     }
     const V omc = V(c.omc_f);
-    put(0, fma_v(getr(0), omc, A * V(T(F::w(0)))));                      // rest: even part A only
+    put(0, fma_v(getr(0), omc, A * V(T(F::w(0) * SC))));                 // rest: even part A only
 #pragma unroll
     for (int a = 1; a < QF; ++a) {
         const int b = F::opp(a);
@@ -383,16 +408,16 @@ LBM_DEV void collide_g(GetM &&getm, GetR &&getr, Put &&put, Put2 &&put2, const C
             const int s2 = e[i] * e[k];
             if (s2) even = s2 > 0 ? even + Tc[pr] : even - Tc[pr];
         }
-        const V w = V(T(F::w(ap)));
+        const V w = V(T(F::w(ap) * SC));
         const V we = even * w, wo = odd * w;
         const V vp = fma_v(getr(ap), omc, we + wo);
         put2(ap, am, vp, fma_v(getr(am), omc, we - wo));
     }
-    const T w0 = T(M::w(0)), w1 = T(M::w(1));
+    const T w0 = T(M::w(0) * SC), w1 = T(M::w(1) * SC);
 #pragma unroll
     for (int sp = 0; sp < NC; ++sp) {              // every concentration species, its own tau_D and C_ref
         const int h0 = PL::H0 + sp * QM;
-        const V dC = plane_sum<V>(getm, h0, QM);
+        const V dC = unscale(plane_sum<V>(getm, h0, QM));
         const V C = dC + V(species_ref(c, sp));
         const T oh = species_om(c, sp);
         const V ohc = V(species_omc(c, sp));
@@ -438,7 +463,7 @@ LBM_DEV void collide_g(GetM &&getm, GetR &&getr, Put &&put, Put2 &&put2, const C
 }
 
 // in place on a register array
-template <class PL, int NC, bool HG, class V, class T>
+template <class PL, int NC, bool HG, class V, class T, int SL2 = 0>
 LBM_DEV void collide_v(V (&p)[PL::P], const CaseDev<T> &c) {
     auto get = [&](int q) -> V { return p[q]; };
     auto put = [&](int q, V v) { p[q] = v; };
@@ -446,19 +471,19 @@ LBM_DEV void collide_v(V (&p)[PL::P], const CaseDev<T> &c) {
         p[qp] = vp;
         p[qm] = vm;
     };
-    collide_g<PL, NC, HG, V, T>(get, get, put, put2, c);
+    collide_g<PL, NC, HG, V, T, SL2>(get, get, put, put2, c);
 }
 
-// one node: FP64 as is, FP32 through F1
-template <class PL, int NC, bool HG, class T>
+// one node: FP64 as is, FP32 through F1 (SL2: values scaled by 2^SL2)
+template <class PL, int NC, bool HG, class T, int SL2 = 0>
 LBM_DEV void collide(T (&p)[PL::P], const CaseDev<T> &c) {
     if constexpr (sizeof(T) == 8) {
-        collide_v<PL, NC, HG, T, T>(p, c);
+        collide_v<PL, NC, HG, T, T, SL2>(p, c);
     } else {
         F1 v[PL::P];
 #pragma unroll
         for (int q = 0; q < PL::P; ++q) v[q] = F1(p[q]);
-        collide_v<PL, NC, HG, F1, float>(v, c);
+        collide_v<PL, NC, HG, F1, float, SL2>(v, c);
 #pragma unroll
         for (int q = 0; q < PL::P; ++q) p[q] = v[q].v;
     }
@@ -609,12 +634,13 @@ LBM_DEV void coords(const CaseDev<T> &c, int n, int &x, int &y, int &z, int &r) 
 }
 
 // 16-bit populations two to a 32-bit register: plane q in half (q & 1) of word q >> 1
+// (values as stored)
 template <class S> struct Pack16;
 template <> struct Pack16<__half> {
     LBM_DEV static uint32_t raw(const __half *p) { return __ldg(reinterpret_cast<const unsigned short *>(p)); }
     LBM_DEV static float get(uint32_t w, int hi) {
         const __half2 h = *reinterpret_cast<const __half2 *>(&w);
-        return (hi ? __high2float(h) : __low2float(h)) * H_UNSCALE;
+        return hi ? __high2float(h) : __low2float(h);
     }
 };
 template <> struct Pack16<__nv_bfloat16> {
@@ -627,7 +653,7 @@ template <> struct Pack16<__nv_bfloat16> {
 // Stores every plane of a node in the pairs of collide_g: rest planes alone,
 // a direction with its opposite (the same lanes and random words as the
 // collision's own put and put2).
-template <class PL, int NC, bool HG, class S, class V>
+template <class PL, int NC, bool HG, class S, bool SCALED, class V>
 LBM_DEV void store_node(S *dp, int os, const V (&p)[PL::P], uint32_t h) {
     using F = typename PL::F;
     using M = typename PL::M;
@@ -638,22 +664,22 @@ LBM_DEV void store_node(S *dp, int os, const V (&p)[PL::P], uint32_t h) {
             const int b = LL::opp(a);
             if (b < a) continue;
             const int ap = lead_sign<LL>(a) > 0 ? a : b, am = lead_sign<LL>(a) > 0 ? b : a;
-            store_pop_pair<S>(dp + (q0 + ap) * os, dp + (q0 + am) * os, p[q0 + ap], p[q0 + am], h, q0 + ap);
+            store_pop_pair<S, SCALED>(dp + (q0 + ap) * os, dp + (q0 + am) * os, p[q0 + ap], p[q0 + am], h, q0 + ap);
         }
     };
-    store_pop<S>(dp, p[0], h, 0);
+    store_pop<S, SCALED>(dp, p[0], h, 0);
     pairs(F{}, 0, PL::QF);
 #pragma unroll
     for (int sp = 0; sp < NC; ++sp) {
         const int h0 = PL::H0 + sp * PL::QM;
-        store_pop<S>(dp + h0 * os, p[h0], h, h0);
+        store_pop<S, SCALED>(dp + h0 * os, p[h0], h, h0);
         pairs(M{}, h0, PL::QM);
     }
     if constexpr (HG) {
 #pragma unroll
         for (int k = 0; k < PL::NB; ++k) {
             const int q0 = PL::G0 + k * PL::QM;
-            store_pop<S>(dp + q0 * os, p[q0], h, q0);
+            store_pop<S, SCALED>(dp + q0 * os, p[q0], h, q0);
             pairs(M{}, q0, PL::QM);
         }
     }
@@ -712,19 +738,26 @@ LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDe
             return F1(Pack16<S>::get(w, q & 1));
         };
         const uint32_t h = Rounding<S>::SR ? sr_node_hash(*prm.ctr_rd, (uint32_t)(c.node_off + n)) : 0u;
-        auto put = [&](int q, F1 v) { store_pop<S>(dp + q * os, v.v, h, q); };
-        auto put2 = [&](int qp, int qm, F1 vp, F1 vm) { store_pop_pair<S>(dp + qp * os, dp + qm * os, vp.v, vm.v, h, qp); };
-        collide_g<PL, NC, HG, F1, float>(getm, getr, put, put2, c);
+        auto put = [&](int q, F1 v) { store_pop<S, true>(dp + q * os, v.v, h, q); };
+        auto put2 = [&](int qp, int qm, F1 vp, F1 vm) {
+            store_pop_pair<S, true>(dp + qp * os, dp + qm * os, vp.v, vm.v, h, qp);
+        };
+        collide_g<PL, NC, HG, F1, float, StoreScale<S>::L2>(getm, getr, put, put2, c);
         return;
     }
+    // bulk nodes relax the values as stored; wall-link nodes the true offsets
+    // (the link formulas take them)
+    constexpr int SL2 = LINKS ? 0 : StoreScale<S>::L2;
     T p[P];
 #pragma unroll
-    for (int q = 0; q < P; ++q)
-        p[q] = Codec<S>::ld(sp + (q * st32 + ox[1 - PL::ex(q)] + oy[1 - PL::ey(q)] + oz[1 - PL::ez(q)]));
+    for (int q = 0; q < P; ++q) {
+        const S *a = sp + (q * st32 + ox[1 - PL::ex(q)] + oy[1 - PL::ey(q)] + oz[1 - PL::ez(q)]);
+        p[q] = SL2 ? Codec<S>::ld_raw(a) : Codec<S>::ld(a);
+    }
     if constexpr (LINKS) apply_links<PL, S, T, LCH>(p, prm, c, src, lo, hi);
-    collide<PL, NC, HG, T>(p, c);
+    collide<PL, NC, HG, T, SL2>(p, c);
     const uint32_t h = Rounding<S>::SR ? sr_node_hash(*prm.ctr_rd, (uint32_t)(c.node_off + n)) : 0u;
-    store_node<PL, NC, HG, S>(dp, os, p, h);
+    store_node<PL, NC, HG, S, SL2 != 0>(dp, os, p, h);
 }
 
 // Bulk nodes (fluid, no wall link) over the span list: span t holds nodes
@@ -766,7 +799,7 @@ template <class S> struct Raw16 {
 template <> LBM_DEV float Raw16<__half>::get(uint32_t w, int hi) {
     __half2 h;
     memcpy(&h, &w, 4);
-    return (hi ? __high2float(h) : __low2float(h)) * H_UNSCALE;
+    return hi ? __high2float(h) : __low2float(h);
 }
 template <> LBM_DEV float Raw16<__nv_bfloat16>::get(uint32_t w, int hi) {
     return __uint_as_float(hi ? (w & 0xffff0000u) : (w << 16));
@@ -831,9 +864,11 @@ LBM_DEV void step_node_unwrapped(const StepParams<typename Codec<S>::T> &prm, co
             return F1(Raw16<S>::get(w, q & 1));
         };
         const uint32_t h = Rounding<S>::SR ? sr_node_hash(*prm.ctr_rd, (uint32_t)(c.node_off + n)) : 0u;
-        auto put = [&](int q, F1 v) { store_pop<S>(dp + q * st, v.v, h, q); };
-        auto put2 = [&](int qp, int qm, F1 vp, F1 vm) { store_pop_pair<S>(dp + qp * st, dp + qm * st, vp.v, vm.v, h, qp); };
-        collide_g<PL, NC, HG, F1, float>(getm, getr, put, put2, c);
+        auto put = [&](int q, F1 v) { store_pop<S, true>(dp + q * st, v.v, h, q); };
+        auto put2 = [&](int qp, int qm, F1 vp, F1 vm) {
+            store_pop_pair<S, true>(dp + qp * st, dp + qm * st, vp.v, vm.v, h, qp);
+        };
+        collide_g<PL, NC, HG, F1, float, StoreScale<S>::L2>(getm, getr, put, put2, c);
     } else {
         collide<PL, NC, HG, T>(p, c);
 #pragma unroll
