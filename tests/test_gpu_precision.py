@@ -16,14 +16,15 @@ FP64 meets the 1e-12 parity target per step (``test_gpu_parity.py``); over
 thousands of steps the two sides' different rounding orders accumulate over
 the flow's relaxation time, to about 4e-12 after 2000 steps and 8e-12 at
 steady state.  Both 16-bit storages round stochastically: the error has zero
-mean, so the steady states are within 0.15 % (FP16, whose offsets are scaled
-by 2^12 to stay out of its subnormal range) and 1.2 % (BF16, three significand
-bits fewer).  Early in a transient from rest, small signals are within that
-noise: the induced field b of the wide Hartmann channels after 2000 steps is
-orders of magnitude below its steady value, and its relative error is above
-one.  (Rounding to nearest, measured on the same runs before, left errors of
-10-26 % at steady state: the same rounding recurs every step and acts as a
-fixed spurious source that the flow integrates over its diffusion time.)
+mean, so the steady states are within 0.2 % (FP16, whose offsets are scaled
+by 2^12 to stay out of its subnormal range) and 1.7 % (BF16, three significand
+bits fewer) of the oracle's.  (Rounding to nearest, measured on the same runs
+before, left errors of 10-26 % at steady state: the same rounding recurs every
+step and acts as a fixed spurious source that the flow integrates over its
+diffusion time.)  Rounding noise also excites every mode the geometry allows,
+including modes that vary along a wall, which a start uniform along the wall
+never excites in exact-order arithmetic: the Shercliff-flux limits the case
+builders use are measured from perturbed starts for that reason.
 """
 import concurrent.futures as cf
 import os
@@ -120,10 +121,10 @@ def _assert_within(errs, bound):
 BATCH_STEPS = 2000
 # errors measured on GB300 after 2000 steps from rest (all 64 cases, every fluid node)
 BATCH_MEASURED = {
-    "fp64": {"u": 4.02e-12, "b": 2.39e-12, "rho": 1.47e-13},
-    "fp32": {"u": 5.39e-4, "b": 7.12e-5, "rho": 4.12e-7},
-    "fp16s": {"u": 0.192, "b": 8.29, "rho": 1.78e-3},
-    "bf16s": {"u": 1.34, "b": 48.8, "rho": 6.06e-2},
+    "fp64": {"u": 4.53e-12, "b": 2.59e-12, "rho": 1.46e-13},
+    "fp32": {"u": 5.39e-4, "b": 5.60e-5, "rho": 3.88e-7},
+    "fp16s": {"u": 3.67e-3, "b": 1.93e-3, "rho": 3.97e-5},
+    "bf16s": {"u": 2.60e-2, "b": 1.70e-2, "rho": 3.40e-4},
 }
 
 
@@ -153,10 +154,10 @@ def test_hartmann_batch_against_oracle(batch, prec):
 STEADY_DRAWS = (22, 57, 10)          # W = 100, 77, 150 of the batch draws
 STEADY_STEPS = 140000
 STEADY_MEASURED = {
-    "fp64": {"u": 6.26e-12, "b": 8.22e-12},
-    "fp32": {"u": 8.0e-5, "b": 1.14e-4},
-    "fp16s": {"u": 1.51e-3, "b": 1.39e-3},
-    "bf16s": {"u": 1.22e-2, "b": 1.22e-2},
+    "fp64": {"u": 6.26e-12, "b": 8.39e-12},
+    "fp32": {"u": 9.57e-5, "b": 1.14e-4},
+    "fp16s": {"u": 1.51e-3, "b": 1.83e-3},
+    "bf16s": {"u": 1.22e-2, "b": 1.74e-2},
 }
 
 
@@ -188,7 +189,8 @@ def _closed_form_errors(spec, rows, exact, widen):
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16s", "bf16s"])
 def test_hartmann_steady_state_against_closed_form(hartmann_steady, prec):
     """Three channels of the batch (W = 100, 77, 150; Ha 17, 21, 15; c_w
-    0.0028, 0.0011, 0.041) run to steady state (140 000 steps): each storage
+    0.0028, 0.0011 (raised from 0.00107 to the flux stability limit), 0.041)
+    run to steady state (140 000 steps): each storage
     against the oracle's steady state node by node, and its error against the
     Hartmann closed form (Sec. 5.4) against the oracle's own."""
     spec, ref, exact = hartmann_steady
@@ -287,8 +289,8 @@ def test_pipe_against_oracle(prec):
     _assert_within(errs, {k: MARGIN * v for k, v in PIPE_MEASURED[prec].items()})
 
 
-PIPE_STEADY_MEASURED = {"fp32": {"u": 1.11e-2, "b": 1.66e-2}, "fp16s": {"u": 0.108, "b": 1.99e-2},
-                        "bf16s": {"u": 1.19e-2, "b": 2.01e-2}}
+PIPE_STEADY_MEASURED = {"fp32": {"u": 1.11e-2, "b": 1.66e-2}, "fp16s": {"u": 1.13e-2, "b": 1.70e-2},
+                        "bf16s": {"u": 1.18e-2, "b": 1.95e-2}}
 
 
 def test_pipe_steady_state_against_finite_volume_solution():
