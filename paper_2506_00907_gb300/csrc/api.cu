@@ -67,9 +67,11 @@ struct lbm_ctx {
     std::vector<CaseHost> cases;
     int64_t pool_elems = 0, total_nodes = 0;
     // the population buffers, each with `guard` elements before and after
-    // (pool[i] = pool_alloc[i] + guard elements): the paired-node step reads
-    // its pulls unwrapped first, up to a row and a slice plus a tile away
-    // from the case's planes
+    // (pool[i] = pool_alloc[i] + guard elements): the unwrapped-pull step
+    // (launch variant 2) reads every pull at the node's own address plus a
+    // per-plane offset first, up to a slice, a row and a node away from the
+    // case's planes; the guard adds a margin of 2 x 2048 + 64 elements to that
+    // reach
     int64_t guard = 0;
     void *pool_alloc[2] = {nullptr, nullptr};
     void *pool[2] = {nullptr, nullptr};
@@ -420,9 +422,8 @@ lbm_status build_tile_brec(lbm_ctx *ctx) {
     ctx->d_tile_brec = nullptr;
     CK(cudaMalloc(&ctx->d_tile_brec, r.size() * sizeof(int32_t)));
     CK(cudaMemcpy(ctx->d_tile_brec, r.data(), r.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    // spans: maximal runs of bulk-fluid nodes of each case, cut into pieces
-    // of at most tile_nodes nodes that start at even offsets (the paired-node
-    // step takes nodes two by two from an even node)
+    // spans: maximal runs of bulk-fluid nodes of each active case, cut into
+    // pieces of at most tile_nodes nodes that start at even offsets
     std::vector<int4> spans;
     if (!ctx->h_flags.empty())
         for (size_t c = 0; c < ctx->cases.size(); ++c) {
@@ -864,7 +865,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out) {
     int64_t reach = 0;                 // farthest unwrapped pull: a slice, a row and a node
     for (const CaseHost &cs : ctx->cases)
         reach = std::max<int64_t>(reach, (int64_t)cs.cfg.nx * cs.cfg.ny + cs.cfg.nx + 1);
-    ctx->guard = round_up(reach + 2 * 2048 + 64, 64);   // + the farthest pair beyond a span's end
+    ctx->guard = round_up(reach + 2 * 2048 + 64, 64);
     if (ctx->nc > 1) {
         switch ((ctx->dim == 3 ? 4 : 0) + (int)cfg->prec) {
         case 0: ctx->ks = species_2d_f64(ctx->nc); break;
