@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--train-per-case", type=int, default=2048)
     ap.add_argument("--train-max-steps", type=int, default=200000)
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the record of the other configurations")
     ap.add_argument("--storage", choices=["fp16s", "bf16s", "fp32", "fp64"], default=None,
                     help="population storage (default: the workload's; 16-bit storages round stochastically)")
     ap.add_argument("--no-autotune", action="store_true")
@@ -542,7 +543,7 @@ def run_ours(args):
         tune = sol.get_launch()
     elif not args.no_autotune:
         cache = os.path.join(ROOT, "paper_2506_00907_gb300", "_build", "autotune.txt")
-        sol.autotune(cache, iters=20)
+        sol.autotune(cache, iters=GRAPH)
         tune = sol.get_launch()
     sol.set_graph(GRAPH)
     K, W = args.steps, max(3, args.warmup)
@@ -606,6 +607,12 @@ def run_ours(args):
         sol.close()
         sol = None
         fp64 = fp64_record(spec, stream, local, pk)
+    configs = None
+    if rank == 0 and world == 1 and not args.no_configs and args.workload == "hartmann_batch":
+        if sol is not None:
+            sol.close()
+            sol = None
+        configs = configs_record(stream, local, pk)
     steady = None
     if rank == 0 and world == 1 and not args.no_steady and args.workload == "hartmann_batch":
         if sol is not None:
@@ -630,6 +637,8 @@ def run_ours(args):
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         if fp64:
             line["fp64"] = fp64
+        if configs:
+            line["configs"] = configs
         if steady:
             line["steady"] = {k: v for k, v in steady.items() if k != "cases"}
         if do_oracle:
@@ -686,6 +695,41 @@ def fp64_record(spec, stream, local, pk):
                           sms, pk["sm_mhz"]),
                       "source": ops["source"]}
         out["bound"] = "alu" if out["alu"]["frac"] > out["hbm"]["frac"] else "hbm"
+    return out
+
+
+def configs_record(stream, local, pk):
+    """The other configurations of the metric, each timed like the main line
+    (autotuned launch, 3 untimed and 10 timed bench steps, CUDA events around
+    the graph replays): MLUPS and the fraction of the HBM copy bandwidth."""
+    import torch
+    out = {}
+    cache = os.path.join(ROOT, "paper_2506_00907_gb300", "_build", "autotune.txt")
+    for name in ("pipe", "pipe_fp32", "cd"):
+        spec = workload_spec(name)
+        sol, geo, _ = make_solver(spec, stream, local)
+        sol.autotune(cache, iters=GRAPH)
+        tune = sol.get_launch()
+        sol.set_graph(GRAPH)
+        run, kernel_ev = bench_runner(sol, stream, 3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if run(10, True):
+            sol.check_wait(raise_unstable=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ms_kernel = sum(a.elapsed_time(b) for a, b in kernel_ev) / (GRAPH * len(kernel_ev))
+        elem = 4 if spec["prec"] == "fp32" else 2
+        alg = 2.0 * spec["planes"] * elem * spec["fluid"]
+        state = 2.0 * spec["planes"] * elem * sum(int(np.prod(g[0].shape)) for g in geo)
+        stable = bool(np.all(sol.check(raise_unstable=False)[:, 5] == 0))
+        sol.close()
+        out[name] = {"workload": spec["desc"], "storage": spec["storage"], "fluid_nodes": spec["fluid"],
+                     "mlups": spec["fluid"] * 10 * GRAPH / (ms * 1e-3) / 1e6, "ms_per_time_step_kernels": ms_kernel,
+                     "roofline_frac": alg / (ms_kernel * 1e-3) / 1e9 / pk["hbm"], "bytes_per_time_step": alg,
+                     "state_bytes": state, "l2": "state below the 129 MB L2" if state < 129e6 else "state above L2",
+                     "launch": tune, "stable": stable}
     return out
 
 

@@ -106,7 +106,7 @@ struct Launch {
     static KernelSet make() {
         KernelSet k{};
         // the bulk-copy and ring variants serve one concentration species at most,
-        // and storage that rounds to nearest (not the stochastic BF16 rounding)
+        // and storage that rounds to nearest (not the stochastic 16-bit rounding)
         if constexpr (NC <= 1 && !Rounding<S>::SR) {
             set_ring(k);
             set_bulk<0>(k);
