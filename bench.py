@@ -167,10 +167,10 @@ def product_cases(spec):
 STEP_SOURCES = ("lattice.cuh", "types.cuh", "kernels.cuh", "kernels_bulk.cuh", "kernels_ring.cuh")   # the step kernels
 
 STEP_KERNEL = {
-    0: "k_step (bulk nodes) + k_boundary (wall-link nodes)",
+    0: "k_step (bulk nodes) + k_links (wall links) + k_boundary (wall-link nodes)",
     1: "k_step_bulk (bulk-copy loads and stores, boundary nodes included)",
-    2: "k_step_unwrapped (pulls unwrapped, edge nodes reload wrapped planes) + k_boundary (wall-link nodes)",
-    3: "k_step_ring (producer warp, bulk-copy ring of stages, consumer warps) + k_boundary (wall-link nodes)"}
+    2: "k_step_unwrapped (pulls unwrapped, edge nodes reload wrapped planes) + k_links + k_boundary",
+    3: "k_step_ring (producer warp, bulk-copy ring of stages, consumer warps) + k_links + k_boundary"}
 
 
 def kernel_hash():
@@ -888,7 +888,7 @@ def run_steady(args):
             "steady": {k: v for k, v in st.items() if k != "cases"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm"], "unit": "GB/s",
                          "frac": achieved / pk["hbm"], "traffic": None, "peak_kind": pk["kind"],
-                         "kernel": "plain form, k_step + k_boundary FP32 with the residual check every %d steps"
+                         "kernel": "plain form, k_step + k_links + k_boundary FP32 with the residual check every %d steps"
                                    % GRAPH},
             "e2e": {"value": st["combined_s"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                     "step": "the combined run (contexts and walls set up before it)"},

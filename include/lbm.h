@@ -396,8 +396,9 @@ lbm_status lbm_get_launch(const lbm_ctx *ctx, lbm_launch *launch);
 lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t iters, lbm_launch *best, double *best_ms);
 
 /* Kernel launches issued per time step (for launch accounting): the bulk
- * step over the node tiles, plus the boundary-node step when any case has
- * wall links. */
+ * step over the spans of bulk nodes, plus, when an active case has wall
+ * links, the wall-link kernel (one thread per link) and the boundary-node
+ * step that uses its values (launch variant 1: one launch in all). */
 int32_t lbm_launches_per_step(const lbm_ctx *ctx);
 
 /* Device storage of the current populations (for zero-copy inspection):

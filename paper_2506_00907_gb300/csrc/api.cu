@@ -90,6 +90,9 @@ struct lbm_ctx {
     int32_t nrtiles = 0;
     BRec *d_brec = nullptr;
     int32_t nbrec = 0;
+    void *d_linkout = nullptr;                 // LinkOut<T> per link
+    size_t cap_linkout = 0;
+    int32_t nlinks = 0;
     // cases being stepped (lbm_set_active): the spans and the boundary records
     // of the boundary kernel hold active cases only
     std::vector<uint8_t> active;
@@ -511,7 +514,9 @@ lbm_status upload_walls_t(lbm_ctx *ctx) {
             b.cs = (int32_t)ci;
             b.lo = (int32_t)links.size();
             while (i < order.size() && cs.links[order[i]].node == node) {
-                links.push_back(link_dev<T>(ctx, cs, cs.links[order[i]]));
+                LinkDev<T> l = link_dev<T>(ctx, cs, cs.links[order[i]]);
+                l.cs = (int32_t)ci;
+                links.push_back(l);
                 ++i;
             }
             b.hi = (int32_t)links.size();
@@ -520,6 +525,7 @@ lbm_status upload_walls_t(lbm_ctx *ctx) {
         }
     }
     ctx->nbrec = (int32_t)brec.size();
+    ctx->nlinks = (int32_t)links.size();
     ctx->h_brec = brec;
     // velocity links of oscillating walls, for the clock kernel
     std::vector<int2> wl;
@@ -546,6 +552,7 @@ lbm_status upload_walls_t(lbm_ctx *ctx) {
     lbm_status st;
     if ((st = grow((void **)&ctx->d_brec, ctx->cap_brec, brec.size() * sizeof(BRec))) != LBM_OK) return st;
     if ((st = grow(&ctx->d_links, ctx->cap_links, links.size() * sizeof(LinkDev<T>))) != LBM_OK) return st;
+    if ((st = grow(&ctx->d_linkout, ctx->cap_linkout, links.size() * sizeof(LinkOut<T>))) != LBM_OK) return st;
     CK(cudaMemcpy(ctx->d_brec, brec.data(), brec.size() * sizeof(BRec), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_links, links.data(), links.size() * sizeof(LinkDev<T>), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_flags, flags.data(), flags.size(), cudaMemcpyHostToDevice));
@@ -575,6 +582,8 @@ StepParams<T> step_params(const lbm_ctx *c) {
     p.spans = c->d_spans;
     p.nspans = c->nspans;
     p.links = static_cast<const LinkDev<T> *>(c->d_links);
+    p.linkout = static_cast<LinkOut<T> *>(c->d_linkout);
+    p.nlinks = c->nlinks;
     p.react = static_cast<const ReactDev<T> *>(c->d_react);
     p.ctr_rd = c->d_ctr + c->cur;
     p.ctr_wr = c->d_ctr + (1 - c->cur);
@@ -622,14 +631,16 @@ cudaError_t launch_step_t(lbm_ctx *ctx) {
         bp.err = ctx->d_err;
         return ctx->ks.step_bulk[ctx->bulk_idx](&p, bp, step_grid(ctx), ctx->bulk_smem, ctx->stream);
     }
-    // boundary nodes (disjoint from the bulk nodes; same source and target
-    // buffers) on the side stream, concurrently with the bulk launch
+    // wall links (3D) and then the boundary nodes (disjoint from the bulk
+    // nodes; same source and target buffers) on the side stream, concurrently
+    // with the bulk launch
     if (ctx->nbrec_step > 0) {
         StepParams<T> pb = p;
         pb.brec = ctx->d_brec_step;
         pb.nbrec = ctx->nbrec_step;
         cudaError_t e = cudaEventRecord(ctx->ev_fork, ctx->stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+        if (e == cudaSuccess && ctx->ks.links) e = ctx->ks.links(&pb, (ctx->nlinks + 255) / 256, 256, ctx->side);
         if (e == cudaSuccess) e = ctx->ks.boundary(&pb, (ctx->nbrec_step + 127) / 128, 128, ctx->side);
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
         if (e != cudaSuccess) return e;
@@ -718,7 +729,7 @@ void free_ctx(lbm_ctx *c) {
     drop_graphs(c);
     void *ptrs[] = {c->pool_alloc[0], c->pool_alloc[1], c->d_flags, c->d_cases, c->d_tiles, c->d_case_tile_lo,
                     c->d_tile_brec, c->d_spans, c->d_rtiles,
-                    c->d_brec, c->d_brec_step, c->d_links, c->d_snap, c->d_part, c->d_red, c->d_mom, c->d_err,
+                    c->d_brec, c->d_brec_step, c->d_links, c->d_linkout, c->d_snap, c->d_part, c->d_red, c->d_mom, c->d_err,
                     c->d_motion, c->d_clock, c->d_wall_links, c->d_react, c->d_ctr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -1545,7 +1556,7 @@ lbm_status lbm_get_launch(const lbm_ctx *ctx, lbm_launch *lp) {
 
 int32_t lbm_launches_per_step(const lbm_ctx *ctx) {
     if (!ctx) return 0;
-    return ctx->launch.variant == 1 ? 1 : 1 + (ctx->nbrec_step > 0 ? 1 : 0);
+    return ctx->launch.variant == 1 ? 1 : 1 + (ctx->nbrec_step > 0 ? (ctx->ks.links ? 2 : 1) : 0);
 }
 
 lbm_status lbm_device_state(lbm_ctx *ctx, int32_t case_id, void **base, int32_t *elem_bytes, int64_t *plane_stride,

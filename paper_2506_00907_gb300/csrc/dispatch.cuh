@@ -19,6 +19,7 @@ constexpr int KRING_MINB = 2;
 struct KernelSet {
     cudaError_t (*step[3])(const void *params, int npt, int grid, int block, cudaStream_t s);
     cudaError_t (*boundary)(const void *params, int grid, int block, cudaStream_t s);
+    cudaError_t (*links)(const void *params, int grid, int block, cudaStream_t s);   // null: links inline
     // unwrapped-pull variants (launch variant 2), budgets kstep_minb(dim, 0..2)
     cudaError_t (*unw[3])(const void *params, int npt, int grid, int block, cudaStream_t s);
     cudaError_t (*init_d)(const void *params, int grid, int block, cudaStream_t s);   // FP64 host-side fields
@@ -50,6 +51,11 @@ struct Launch {
     }
     static cudaError_t boundary(const void *p, int g, int b, cudaStream_t s) {
         k_boundary<DIM, NC, HG, S><<<g, b, 0, s>>>(*static_cast<const StepParams<T> *>(p));
+        return cudaGetLastError();
+    }
+    static cudaError_t links(const void *p, int g, int b, cudaStream_t s) {
+        if constexpr (links_apart<DIM>())
+            k_links<DIM, NC, HG, S><<<g, b, 0, s>>>(*static_cast<const StepParams<T> *>(p));
         return cudaGetLastError();
     }
     static cudaError_t init_d(const void *p, int g, int b, cudaStream_t s) {
@@ -120,6 +126,7 @@ struct Launch {
         k.step[1] = &step<kstep_minb(DIM, 1)>;
         k.step[2] = &step<kstep_minb(DIM, 2)>;
         k.boundary = &boundary;
+        k.links = links_apart<DIM>() ? &links : nullptr;
         k.unw[0] = &unw<kstep_minb(DIM, 0)>;
         k.unw[1] = &unw<kstep_minb(DIM, 1)>;
         k.unw[2] = &unw<kstep_minb(DIM, 2)>;

@@ -166,6 +166,8 @@ struct StepParams {
     const BRec *brec;         // boundary nodes of all cases
     int32_t nbrec;
     const LinkDev<T> *links;
+    LinkOut<T> *linkout;      // per link: its value for the coming step (k_links writes, k_boundary reads)
+    int32_t nlinks;
     const int32_t *tile_brec; // boundary records of tile t: [tile_brec[t], tile_brec[t + 1])
     const ReactDev<T> *react; // surface reaction network per case (kernels with several species)
     const uint32_t *ctr_rd;   // the step count (stochastic rounding); the step's main kernel writes
@@ -619,6 +621,16 @@ LBM_DEV void apply_links(T (&p)[PL::P], const StepParams<T> &prm, const CaseDev<
     }
 }
 
+// The same with the values already computed by k_links.
+template <class PL, class T>
+LBM_DEV void apply_links_pre(T (&p)[PL::P], const StepParams<T> &prm, int lo, int hi) {
+    for (int j = lo; j < hi; ++j) {
+        const LinkOut<T> o = prm.linkout[j];
+#pragma unroll
+        for (int q = 0; q < PL::P; ++q) p[q] = (q == o.plane) ? o.v : p[q];
+    }
+}
+
 // node coordinates of case-relative index n; r = y + ny*z is the row
 template <int DIM, class T>
 LBM_DEV void coords(const CaseDev<T> &c, int n, int &x, int &y, int &z, int &r) {
@@ -688,7 +700,9 @@ LBM_DEV void store_node(S *dp, int os, const V (&p)[PL::P], uint32_t h) {
 // ------------------------------------------------------------------ fused step
 // One node: pull, (boundary nodes: wall links [lo, hi)), collide, store
 // plane q to out[q * ostride] (out = 0: the node's entries of the target buffer).
-template <int DIM, int NC, bool HG, class S, bool LINKS, int LCH = 4>
+// LINKS: 0 a bulk node; 1 a wall-link node whose links are evaluated here
+// (LCH at a time); 2 a wall-link node whose link values k_links computed.
+template <int DIM, int NC, bool HG, class S, int LINKS, int LCH = 4>
 LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDev<typename Codec<S>::T> &c, int n,
                        int lo, int hi, S *out = nullptr, int ostride = 0) {
     using PL = Planes<DIM, NC, HG>;
@@ -754,7 +768,8 @@ LBM_DEV void step_node(const StepParams<typename Codec<S>::T> &prm, const CaseDe
         const S *a = sp + (q * st32 + ox[1 - PL::ex(q)] + oy[1 - PL::ey(q)] + oz[1 - PL::ez(q)]);
         p[q] = SL2 ? Codec<S>::ld_raw(a) : Codec<S>::ld(a);
     }
-    if constexpr (LINKS) apply_links<PL, S, T, LCH>(p, prm, c, src, lo, hi);
+    if constexpr (LINKS == 1) apply_links<PL, S, T, LCH>(p, prm, c, src, lo, hi);
+    if constexpr (LINKS == 2) apply_links_pre<PL, T>(p, prm, lo, hi);
     collide<PL, NC, HG, T, SL2>(p, c);
     const uint32_t h = Rounding<S>::SR ? sr_node_hash(*prm.ctr_rd, (uint32_t)(c.node_off + n)) : 0u;
     store_node<PL, NC, HG, S, SL2 != 0>(dp, os, p, h);
@@ -778,7 +793,7 @@ __global__ void __launch_bounds__(256, MINB) k_step(const StepParams<typename Co
         for (int k = 0; k < npt; ++k) {
             const int n = sp.y + (int)threadIdx.x + k * (int)blockDim.x;
             if (n >= sp.z) break;
-            step_node<DIM, NC, HG, S, false>(prm, c, n, 0, 0);
+            step_node<DIM, NC, HG, S, 0>(prm, c, n, 0, 0);
         }
     }
 }
@@ -893,24 +908,57 @@ __global__ void __launch_bounds__(256, MINB) k_step_unwrapped(const StepParams<t
     }
 }
 
-// Boundary nodes: one thread per record of the compact boundary list (the
-// nodes of a wall row are consecutive records, so a warp works along a wall).
-// It runs beside the bulk step on a side stream.  In 2D and for 16-bit 3D
-// storage it is built lean (links one at a time, a small register budget), so
-// that its blocks take few of the registers the bulk step's blocks would use;
-// 3D FP32 walls (many links per node, on curved walls) run faster with four
-// links evaluated together and the full budget, and FP64 needs that budget.
-// (Measured on GB300: Hartmann batch, MHD pipe FP32 and FP16.)
+// 3D walls (curved walls give a node many links) evaluate their links in a
+// kernel of their own ahead of k_boundary, so that the links of a node run in
+// parallel instead of one after another; 2D walls (a few links per node, the
+// wall-link kernel far off the critical path) evaluate them inside
+// k_boundary and save the launch.  (Measured on GB300: MHD pipe FP16 and FP32
+// against the Hartmann batch.)
+template <int DIM>
+LBM_HD constexpr bool links_apart() { return DIM == 3; }
+// In 2D and for 16-bit 3D storage the inline link evaluation is built lean
+// (links one at a time, a small register budget), so that its blocks take few
+// of the registers the bulk step's blocks would use; FP64 needs the full budget.
 template <class S, int DIM>
 LBM_HD constexpr bool boundary_lean() { return sizeof(S) == 2 || (DIM == 2 && sizeof(S) == 4); }
+template <class S, int DIM>
+LBM_HD constexpr int boundary_minb() {
+    return links_apart<DIM>() ? (sizeof(S) == 8 ? 2 : 6) : (boundary_lean<S, DIM>() ? 8 : 1);
+}
+
+// Wall links, one thread per link: the value each link gives its unknown
+// population in the coming step (from the relaxed populations at t, which the
+// step only reads), with the plane it replaces.  It runs on the side stream
+// ahead of k_boundary.  Links of frozen cases are evaluated too (their values
+// are not used).
 template <int DIM, int NC, bool HG, class S>
-__global__ void __launch_bounds__(128, boundary_lean<S, DIM>() ? (DIM == 2 ? 8 : 6) : 1)
-    k_boundary(const StepParams<typename Codec<S>::T> prm) {
+__global__ void __launch_bounds__(256) k_links(const StepParams<typename Codec<S>::T> prm) {
+    using PL = Planes<DIM, NC, HG>;
+    using T = typename Codec<S>::T;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= prm.nlinks) return;
+    const LinkDev<T> L = prm.links[i];
+    const CaseDev<T> &c = prm.cases[L.cs];
+    const S *src = static_cast<const S *>(prm.src) + c.pop_off;
+    LinkOut<T> o;
+    o.v = eval_link<PL, S, T>(L, src, c, PL::NCS >= 2 ? prm.react + c.index : nullptr);
+    o.plane = L.plane_a;
+    prm.linkout[i] = o;
+}
+
+// Boundary nodes: one thread per record of the compact boundary list (the
+// nodes of a wall row are consecutive records, so a warp works along a wall).
+// It runs beside the bulk step on a side stream.
+template <int DIM, int NC, bool HG, class S>
+__global__ void __launch_bounds__(128, boundary_minb<S, DIM>()) k_boundary(const StepParams<typename Codec<S>::T> prm) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= prm.nbrec) return;
     const BRec b = prm.brec[i];
     const CaseDev<typename Codec<S>::T> c = prm.cases[b.cs];
-    step_node<DIM, NC, HG, S, true, boundary_lean<S, DIM>() ? 1 : 4>(prm, c, b.node, b.lo, b.hi);
+    if constexpr (links_apart<DIM>())
+        step_node<DIM, NC, HG, S, 2>(prm, c, b.node, b.lo, b.hi);
+    else
+        step_node<DIM, NC, HG, S, 1, boundary_lean<S, DIM>() ? 1 : 4>(prm, c, b.node, b.lo, b.hi);
 }
 
 // ------------------------------------------------------------------ initial state

@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(BULK_THREADS, MINB) k_step_bulk(const StepPara
         const int b_lo = prm.tile_brec[t], b_hi = prm.tile_brec[t + 1];
         for (int b = b_lo + tid; b < b_hi; b += BULK_THREADS) {
             const BRec rec = prm.brec[b];
-            step_node<DIM, NC, HG, S, true, 1>(prm, c, rec.node, rec.lo, rec.hi, out + (rec.node - tile.y), TT);
+            step_node<DIM, NC, HG, S, 1, 1>(prm, c, rec.node, rec.lo, rec.hi, out + (rec.node - tile.y), TT);
         }
         // a ragged last tile stores up to the next 16 bytes: zeros there, inside the plane's padding
         const int lenA = ((len + A - 1) / A) * A;

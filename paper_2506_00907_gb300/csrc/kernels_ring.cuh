@@ -344,8 +344,8 @@ __global__ void __launch_bounds__(RING_THREADS, MINB) k_step_ring(const StepPara
 #pragma unroll
                 for (int q = 0; q < P; ++q) PairMem<S>::st(dp + q * st32, v[q].v);
             } else {
-                if (f0 == NODE_FLUID) step_node<DIM, NC, HG, S, false>(prm, c, n0, 0, 0);
-                if (f1 == NODE_FLUID) step_node<DIM, NC, HG, S, false>(prm, c, n0 + 1, 0, 0);
+                if (f0 == NODE_FLUID) step_node<DIM, NC, HG, S, 0>(prm, c, n0, 0, 0);
+                if (f1 == NODE_FLUID) step_node<DIM, NC, HG, S, 0>(prm, c, n0 + 1, 0, 0);
             }
         } else {
             float p[P];
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(RING_THREADS, MINB) k_step_ring(const StepPara
 #pragma unroll
                 for (int q = 0; q < P; ++q) Codec<S>::st(dp + q * st32, p[q]);
             } else if (f0 == NODE_FLUID) {
-                step_node<DIM, NC, HG, S, false>(prm, c, n0, 0, 0);
+                step_node<DIM, NC, HG, S, 0>(prm, c, n0, 0, 0);
             }
         }
     }

@@ -78,9 +78,18 @@ struct alignas(16) LinkDev {
     uint8_t plane_ap;     // plane of the opposite direction a'
     uint8_t phi_plane0;   // first plane of the link's field
     uint8_t flags;        // LINK_NEED_PHI | LINK_NEED_B | LINK_NEED_U | LINK_WALL_T
+    int32_t cs;           // case index
     T d, c0, ca, cap, cape, cphi;
     T cB[3];
     T ref_phi;            // storage reference of the link's field (phi = sum of stored + ref_phi)
+};
+
+// The value a link gives its unknown population in the coming step, and the
+// plane it replaces (written by the link kernel, read by the boundary kernel).
+template <class T>
+struct LinkOut {
+    T v;
+    int32_t plane;
 };
 
 // Boundary record of a fluid node that owns links.
