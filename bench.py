@@ -167,10 +167,10 @@ def product_cases(spec):
 STEP_SOURCES = ("lattice.cuh", "types.cuh", "kernels.cuh", "kernels_bulk.cuh", "kernels_ring.cuh")   # the step kernels
 
 STEP_KERNEL = {
-    0: "k_step (bulk nodes) + k_links (wall links) + k_boundary (wall-link nodes)",
+    0: "k_step (bulk nodes) + k_boundary (wall-link nodes)",
     1: "k_step_bulk (bulk-copy loads and stores, boundary nodes included)",
-    2: "k_step_unwrapped (pulls unwrapped, edge nodes reload wrapped planes) + k_links + k_boundary",
-    3: "k_step_ring (producer warp, bulk-copy ring of stages, consumer warps) + k_links + k_boundary"}
+    2: "k_step_unwrapped (pulls unwrapped, edge nodes reload wrapped planes) + k_boundary (wall-link nodes)",
+    3: "k_step_ring (producer warp, bulk-copy ring of stages, consumer warps) + k_boundary (wall-link nodes)"}
 
 
 def kernel_hash():
@@ -633,6 +633,7 @@ def run_ours(args):
                              "timing": "CUDA events on the solver stream around each replay of the %d-step "
                                        "graph inside the timed region (step launches only)" % GRAPH,
                              "kernel": STEP_KERNEL[tune["variant"] if tune else 0]
+                                       + (" + k_links (3D wall links)" if per_step == 3 else "")
                                        + ": one time step, %d launches" % per_step},
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk}
         if fp64:
