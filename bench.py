@@ -16,7 +16,9 @@ Besides the headline figures the default line carries:
   * ``steady``     -- time to steady state at fixed error, plain form against
                       the warm-started, 16-bit, batched form (bounded size);
   * ``fp64``       -- the same workload with FP64 storage, with its HBM and
-                      FP64-arithmetic bounds.
+                      FP64-arithmetic bounds;
+  * ``configs``    -- the MHD pipe (FP16, FP32) and the flow + concentration
+                      channels, each autotuned and timed like the main line.
 The oracle (``oracle/``) runs only in the CPU-baseline leg (``oracle_leg``),
 which times it and checks the GPU results, and in ``--impl reference``.
 
@@ -28,6 +30,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -174,10 +177,16 @@ STEP_KERNEL = {
 
 
 def kernel_hash():
+    """Hash of the step kernels' code: the sources that define them with
+    comments and whitespace taken out, so that a changed comment keeps the
+    committed ncu records while any change of code retires them."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2506_00907_gb300", "csrc")
     for f in STEP_SOURCES:
-        h.update(open(os.path.join(d, f), "rb").read())
+        text = open(os.path.join(d, f)).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

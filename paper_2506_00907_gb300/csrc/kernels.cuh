@@ -161,7 +161,7 @@ struct StepParams {
     const CaseDev<T> *cases;
     const int2 *tiles;        // (case, first node) per tile of every node (bulk-copy and ring variants)
     int32_t ntiles;
-    const int4 *spans;        // (case, lo, hi, 0): nodes [lo, hi) are bulk fluid (k_step, k_step_pair)
+    const int4 *spans;        // (case, lo, hi, 0): nodes [lo, hi) are bulk fluid (k_step, k_step_unwrapped)
     int32_t nspans;
     const BRec *brec;         // boundary nodes of all cases
     int32_t nbrec;
