@@ -156,3 +156,33 @@ def test_run_each_to_steady_matches_run_to_steady():
     assert np.array_equal(_case_bytes(c, c.get_state(), 3), _case_bytes(c, keep, 3))
     with pytest.raises(lbm.LbmError):
         c.set_launch(1, 256, 0, 1, 2, 2)
+
+
+@pytest.mark.parametrize("prec", [lbm.LBM_FP32, lbm.LBM_FP16S])
+def test_frozen_pipe_with_link_kernel(prec):
+    """3D cases evaluate their wall links in a kernel of their own (one thread
+    per link, the links of frozen cases included): freezing one of three
+    curved-wall pipes keeps its bits and leaves the others as they step
+    alone."""
+    from paper_2506_00907_gb300 import cases as CS
+    geo = [CS.pipe((4, 36, 36), 16.0, 10.0, "insulating"), CS.pipe((6, 36, 36), 16.0, 15.0, ("shercliff", 0.5)),
+           CS.pipe((3, 36, 36), 16.0, 5.0, "conducting")]
+
+    def solver():
+        g = lbm.Solver(lbm.LBM_D3Q19, prec, lbm.LBM_FLOW | lbm.LBM_MHD, [c for c, _, _, _ in geo])
+        for i, (_, solid, links, _) in enumerate(geo):
+            g.set_walls(i, solid, links)
+        g.set_graph(10)
+        return g
+    a = solver()
+    assert lbm.lib().lbm_launches_per_step(a.ctx) == 3          # bulk, links, boundary nodes
+    a.step(30)
+    at30 = a.get_state()
+    a.set_active(1, False)
+    a.step(41)
+    b = solver()
+    b.step(71)
+    sa, sb = a.get_state(), b.get_state()
+    assert np.array_equal(_case_bytes(a, sa, 1), _case_bytes(a, at30, 1))
+    for i in (0, 2):
+        assert np.array_equal(_case_bytes(a, sa, i), _case_bytes(b, sb, i)), i
