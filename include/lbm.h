@@ -165,8 +165,10 @@ typedef struct {
 } lbm_reaction;
 
 /* Create a context: validates the configuration, allocates all device memory
- * for every case (two population buffers, node flags, tile list, reduction
- * scratch) and initialises every case at rest (equilibrium of rho0, C0, B0).
+ * for every case (two population buffers with guard bands, node flags, the
+ * span and tile lists, reduction scratch) and initialises every case at rest
+ * (equilibrium of rho0, C0, B0).  Wall-link records and their per-link output
+ * are allocated by lbm_set_walls.
  * Errors: LBM_EINVAL (bad config), LBM_ENOMEM, LBM_ECUDA.  *out is NULL on error. */
 lbm_status lbm_create(const lbm_config *cfg, lbm_ctx **out);
 
