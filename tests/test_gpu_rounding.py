@@ -8,8 +8,8 @@ is chosen so small that after ~2000 steps each step's change of a population
 is below half the FP16 spacing of its (scaled) offset: storage that rounds to
 nearest would stop following the solution there, while rounding stochastically
 keeps the mean over the nodes on it, up to the random walk of the rounding
-noise: a spacing of 2^-10 of the offsets, about 8e-9 of u per population and
-step, summed over 5000 steps and averaged over 4096 nodes, is about 3e-4 of u
+noise: about 0.3 of a spacing (2^-10 of an offset) per population and step,
+as a random walk over 5000 steps averaged over 4096 nodes, is about 3e-4 of u
 in FP16 and 8 times more in BF16 (the tolerances below).  Measured on GB300:
 -1.2e-5 (FP16), -9.2e-4 (BF16); FP32, which rounds to nearest, -6.2e-5 (its
 bias is the larger); FP64 -2.7e-13."""
